@@ -1,0 +1,268 @@
+"""Benchmark of the full D0/D1/D2 pipeline on one GPU (or N independent
+replicas under torchrun), printing one JSON line.
+
+Workload: 256^3 float32 white noise (seed 2) -- the paper's "random" stress
+case (largest diagrams, densest critical cells), one field per step.  A step
+is one pass of the whole pipeline (gradient, critical simplices, D0, D2, D1,
+output) over that field.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the standard reduction of Alg. 1) on
+bounded sub-volumes of the same field, on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthfields as sf  # noqa: E402
+
+WORKLOAD = "noise256_f32"
+METRIC = "full-diagram Mvertices/s"
+UNIT = "Mvertices/s"
+L2_BYTES = 129 * 2**20
+ORACLE_SAMPLE = 40          # edge of the cube cropped for the oracle
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.t:
+                self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_sample(field, edge):
+    """Times the oracle on an edge^3 crop of the field (CPU, single thread)."""
+    import oracle
+    oracle.build()
+    crop = np.ascontiguousarray(field[:edge, :edge, :edge])
+    t0 = time.perf_counter()
+    rows = oracle.pairsimplices(crop)
+    dt = time.perf_counter() - t0
+    return crop.size, dt, len(rows)
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    field = sf.config_field(WORKLOAD)
+    for _ in range(args.warmup):
+        _oracle_sample(field, 16)
+    tot_v, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        nv, dt, _ = _oracle_sample(field, ORACLE_SAMPLE)
+        tot_v += nv
+        tot_t += dt
+    value = tot_v / tot_t / 1e6
+    sample = f"{ORACLE_SAMPLE}^3 crop of the 256^3 white-noise field per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": "256^3 float32 white noise U[0,1), seed 2",
+                                        "oracle_sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    import paper_2206_13932_gb300 as dms
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dms.build()
+    shape, dtype, recipe = sf.CONFIGS[WORKLOAD]
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    field = sf.config_field(WORKLOAD)
+    dev = torch.from_numpy(field).cuda()
+    host = torch.from_numpy(field).pin_memory()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    g = dms.Grid(shape, dtype)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+        g.compute(dev)
+    # ---- device-resident timing (inputs in HBM, L2 flushed before each step)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kern = {k: 0.0 for k in g.KERNELS}
+    launches = 0
+    barrier()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            g.compute(dev)
+            ends[k].record(stream)
+            for name, ms in g.kernel_ms().items():
+                kern[name] += ms
+            launches += g.stats()["launches"]
+        barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n / (ms * 1e-3) / 1e6
+    stats = g.stats()
+    counts = g.counts()
+    # ---- end to end through the C ABI: host field in, host pairs out
+    e2e_ms = []
+    d2h = 0
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.compute(host)
+        pairs = [g.fetch(d) for d in range(3)]
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        d2h = sum(p.nbytes for p in pairs)
+    e2e_val = ws * n / (statistics.mean(e2e_ms) * 1e-3) / 1e6
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel family
+    kavg = {k: v / args.steps for k, v in kern.items()}
+    dom = max(kavg, key=kavg.get)
+    s_in = np.dtype(dtype).itemsize
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    cls_bytes = n * s_in + n + 4 * (n // 2048 + 1)      # values in, flag bytes out, tile counts
+    cls_gbs = cls_bytes / (kavg["classify"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "classify", "achieved": cls_gbs, "peak": hbm,
+                "unit": "GB/s", "frac": cls_gbs / hbm, "traffic": None,
+                "algorithmic_bytes_per_launch": cls_bytes,
+                "peak_source": "measured" if peaks else "fallback"}
+    # oracle on a bounded crop of the same field
+    nv, dt, _ = _oracle_sample(field, ORACLE_SAMPLE)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "256^3 float32 white noise U[0,1), seed 2 (one field per step)",
+                   "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": n * s_in,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "dominant_kernel": {"name": dom, "ms": kavg[dom]},
+        "kernel_ms": kavg,
+        "stage_ms": g.stage_ms(),
+        "stats": stats,
+        "pairs": {"d0": counts[0][0], "d1": counts[0][1], "d2": counts[0][2],
+                  "essential": list(counts[1])},
+        "cpu_baseline": {"value": nv / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{ORACLE_SAMPLE}^3 crop of the same field, standard reduction",
+                         "seconds": dt},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    g.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,141 @@
+/*
+ * dms.h -- C ABI of libdms: persistence diagrams D0, D1, D2 of a piecewise
+ * linear scalar field on a 3D regular grid by the Discrete Morse Sandwich
+ * (Guillou, Vidal, Tierny, arXiv 2206.13932), computed on one NVIDIA GPU.
+ *
+ * The paper's definitions this library follows:
+ *   Sec. 2.1  input: a PL field on the vertices of a 3D grid triangulated by
+ *             Freudenthal (6 tetrahedra per cube, 14 neighbours per vertex),
+ *             made injective by symbolic perturbation: vertices are ordered
+ *             by (value, vertex id).
+ *   Sec. 2.2  the lexicographic filtration of all simplices.
+ *   Sec. 2.4  persistence pairs (birth p-simplex, death (p+1)-simplex);
+ *             the value of a simplex is the value of its maximum vertex.
+ *   Sec. 4    Alg. 2 (zero-persistence skip through the discrete gradient of
+ *             Robins et al.'s ProcessLowerStars) and Alg. 3
+ *             (PairCriticalSimplices).
+ *   Sec. 5    D0 from the unstable sets of 1-saddles, D2 from the stable sets
+ *             of 2-saddles with a virtual maximum on the outer boundary.
+ *   Sec. 6    infinite-persistence classes, reported at (f(sigma), f*),
+ *             f* = the maximum value.
+ *
+ * The result equals, simplex id for simplex id, the pairs of the standard
+ * reduction of the lexicographic filtration whose two simplices have
+ * different maximum vertices, plus the infinite-persistence classes.
+ *
+ * Threading: one handle per stream; calls on one handle are not reentrant.
+ * Errors: every entry point returns a dms_status; no exception crosses the
+ * ABI.  After a failed dms_compute_diagram the handle holds no result
+ * (dms_get_counts and dms_fetch_pairs return DMS_ERR_STATE) until the next
+ * successful compute.
+ */
+#ifndef DMS_H
+#define DMS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DMS_OK = 0,
+    DMS_ERR_INVALID_ARG = 1,   /* bad size, dtype, pointer or dimension      */
+    DMS_ERR_NAN = 2,           /* the field holds a NaN                      */
+    DMS_ERR_OOM = 3,           /* device or host allocation failed           */
+    DMS_ERR_CUDA = 4,          /* a CUDA runtime call failed                 */
+    DMS_ERR_ITER_LIMIT = 5,    /* a bounded device loop hit its limit        */
+    DMS_ERR_STATE = 6,         /* no result available / inconsistent result  */
+    DMS_ERR_CAPACITY = 7       /* a per-item scratch limit was exceeded      */
+} dms_status;
+
+typedef enum { DMS_U16 = 0, DMS_F32 = 1, DMS_F64 = 2 } dms_dtype;
+
+typedef struct {
+    int virtual_max;      /* 1 (the only supported value): Sec. 5.2 virtual
+                             maximum on the outer boundary                   */
+    int64_t max_iters;    /* cap on device round loops; 0 = default          */
+} dms_options;
+
+/* One persistence pair (or infinite class) of the result.
+ * Simplex ids (a convention of this library; the paper fixes none).  With
+ * v = x + nx*(y + ny*z) and offsets o (bit0 +x, bit1 +y, bit2 +z), each
+ * simplex is a chain of offsets anchored at its componentwise-min corner v:
+ *   vertex   v                                  id = v
+ *   edge     (v, v+o), o in 1..7                id = 7v + (o-1)
+ *   triangle (v, v+a, v+b), a subset of b       id = 12v + k, k indexing (b,a)
+ *            (3,1)(3,2)(5,1)(5,4)(6,2)(6,4)(7,1)(7,2)(7,3)(7,4)(7,5)(7,6)
+ *   tet      (v, v+a, v+b, v+7)                 id = 6v + k, k indexing (a,b)
+ *            (1,3)(1,5)(2,3)(2,6)(4,5)(4,6)
+ * birth_vertex / death_vertex are the maximum vertices of the two simplices;
+ * birth_bits / death_bits are the raw bits of their values (zero-extended
+ * uint16, float or double bits).  An infinite class has death_simplex = -1,
+ * death_vertex = -1 and death_bits = the bits of the maximum value f*.  */
+typedef struct {
+    int64_t birth_simplex, death_simplex;
+    int64_t birth_vertex, death_vertex;
+    uint64_t birth_bits, death_bits;
+    uint8_t dim, essential, pad[6];
+} dms_pair;
+
+typedef struct dms_grid_s *dms_grid;
+
+/* Creates a handle for an nx*ny*nz grid (each >= 1, product < 2^31) of the
+ * given dtype.  opts may be NULL (defaults).  Allocates the grid-sized device
+ * buffers on the current device.  *out is set only on success. */
+dms_status dms_grid_create(int64_t nx, int64_t ny, int64_t nz, dms_dtype dtype,
+                           const dms_options *opts, dms_grid *out);
+
+/* Computes D0, D1, D2 and the infinite classes of the field `values`
+ * (nx*ny*nz elements, x fastest).  values_on_host = 0: a device pointer that
+ * must stay valid until `stream` (a cudaStream_t, NULL = legacy default)
+ * reaches the end of the call; = 1: a host pointer, copied in on `stream`.
+ * The call returns after the result is resident on the device (it
+ * synchronises `stream`).  NaN in the field -> DMS_ERR_NAN. */
+dms_status dms_compute_diagram(dms_grid grid, const void *values, int values_on_host,
+                               void *stream);
+
+/* Number of finite pairs per dimension and of infinite classes per dimension
+ * of the last successful compute. */
+dms_status dms_get_counts(dms_grid grid, int64_t pairs[3], int64_t essential[4]);
+
+/* Copies the pairs of dimension dim (0..2) -- the finite pairs in increasing
+ * lexicographic order of the critical simplex that indexes them (the death
+ * edge for D0, the death triangle for D1, the birth triangle for D2), then the
+ * infinite classes of that dimension -- into out[0..cap).  *written = number copied; if cap is smaller
+ * than the count, DMS_ERR_CAPACITY is returned and nothing is copied.
+ * out_is_device = 1: out is a device pointer (copy on the compute stream). */
+dms_status dms_fetch_pairs(dms_grid grid, int dim, dms_pair *out, int64_t cap,
+                           int64_t *written, int out_is_device);
+
+/* Per-stage device milliseconds of the last compute (CUDA events):
+ * [0] gradient (classification + ProcessLowerStars + compaction),
+ * [1] sorting critical simplices, [2] D0, [3] D2, [4] D1, [5] output,
+ * [6] total, [7] host-to-device copy (values_on_host = 1 only). */
+dms_status dms_get_stage_ms(dms_grid grid, float ms[8]);
+
+/* Statistics of the last compute: [0] critical vertices, [1..4] critical
+ * simplices of dimension 0..3, [5] kernel launches, [6] D0 rounds,
+ * [7] D2 rounds, [8] D1 reduction rounds, [9] D1 columns. */
+dms_status dms_get_stats(dms_grid grid, int64_t stats[10]);
+
+/* Device milliseconds of the last compute per kernel family, from CUDA event
+ * pairs recorded on the compute stream around the launches (host round trips
+ * between launches of one family are included): [0] classify (the per-vertex
+ * stencil), [1] compaction, [2] radix sort, [3] ProcessLowerStars, [4] emit
+ * of the critical simplices, [5] D0 arcs, [6] D0 union-find rounds, [7] D2
+ * arcs, [8] D2 union-find rounds, [9] D1 boundary tracing, [10] D1
+ * reduction, [11] output. */
+dms_status dms_get_kernel_ms(dms_grid grid, float ms[12]);
+
+/* Frees every device and host resource of the handle. */
+dms_status dms_grid_destroy(dms_grid grid);
+
+/* Static description of a status code. */
+const char *dms_status_string(dms_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMS_H */

@@ -1,0 +1,204 @@
+"""GB300-native Discrete Morse Sandwich: persistence diagrams D0, D1, D2 of a
+PL scalar field on a 3D grid (Freudenthal triangulation), computed on one GPU.
+
+This module is a thin binding of the C ABI in ``include/dms.h`` (library
+``_build/libdms.so``): argument marshalling only, every step of the method runs
+in the CUDA kernels of ``csrc/``.  PyTorch is used for device memory and
+streams.  There is no CPU fallback: if the library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from ._build_lib import LIB as _LIB_PATH
+from ._build_lib import build
+
+__all__ = ["build", "load", "Grid", "diagram", "PAIR_DTYPE", "DmsError", "STATUS"]
+
+PAIR_DTYPE = np.dtype([("birth_simplex", "<i8"), ("death_simplex", "<i8"),
+                       ("birth_vertex", "<i8"), ("death_vertex", "<i8"),
+                       ("birth_bits", "<u8"), ("death_bits", "<u8"),
+                       ("dim", "u1"), ("essential", "u1"), ("pad", "V6")])
+assert PAIR_DTYPE.itemsize == 56
+
+STATUS = {0: "DMS_OK", 1: "DMS_ERR_INVALID_ARG", 2: "DMS_ERR_NAN", 3: "DMS_ERR_OOM",
+          4: "DMS_ERR_CUDA", 5: "DMS_ERR_ITER_LIMIT", 6: "DMS_ERR_STATE",
+          7: "DMS_ERR_CAPACITY"}
+_DTYPE_CODE = {np.dtype(np.uint16): 0, np.dtype(np.float32): 1, np.dtype(np.float64): 2}
+
+
+class DmsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("virtual_max", ctypes.c_int), ("max_iters", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build_if_missing: bool = False):
+    """The loaded libdms (ctypes).  Raises if it is not built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                if not build_if_missing:
+                    raise RuntimeError(f"libdms is not built ({_LIB_PATH}); run build()")
+                build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            i64, vp, p64 = ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+            lib.dms_grid_create.argtypes = [i64, i64, i64, ctypes.c_int,
+                                            ctypes.POINTER(_Options), ctypes.POINTER(vp)]
+            lib.dms_compute_diagram.argtypes = [vp, vp, ctypes.c_int, vp]
+            lib.dms_get_counts.argtypes = [vp, p64, p64]
+            lib.dms_fetch_pairs.argtypes = [vp, ctypes.c_int, vp, i64, p64, ctypes.c_int]
+            lib.dms_get_stage_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+            lib.dms_get_stats.argtypes = [vp, p64]
+            lib.dms_get_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+            lib.dms_grid_destroy.argtypes = [vp]
+            lib.dms_status_string.argtypes = [ctypes.c_int]
+            lib.dms_status_string.restype = ctypes.c_char_p
+            for f in ("dms_grid_create", "dms_compute_diagram", "dms_get_counts",
+                      "dms_fetch_pairs", "dms_get_stage_ms", "dms_get_stats", "dms_get_kernel_ms",
+                      "dms_grid_destroy"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise DmsError(st, where)
+
+
+class Grid:
+    """A handle of ``dms_grid``: one grid shape and dtype, reusable across fields."""
+
+    def __init__(self, shape_xyz, dtype, max_iters: int = 0):
+        self._lib = load()
+        self.shape_xyz = tuple(int(s) for s in shape_xyz)
+        self.dtype = np.dtype(dtype)
+        if self.dtype not in _DTYPE_CODE:
+            raise TypeError(f"unsupported dtype {self.dtype}")
+        opts = _Options(1, int(max_iters))
+        h = ctypes.c_void_p()
+        nx, ny, nz = self.shape_xyz
+        _check(self._lib.dms_grid_create(nx, ny, nz, _DTYPE_CODE[self.dtype],
+                                         ctypes.byref(opts), ctypes.byref(h)),
+               "dms_grid_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dms_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _field_ptr(self, values):
+        """(pointer, on_host, keepalive) for a torch tensor or numpy array."""
+        nx, ny, nz = self.shape_xyz
+        try:
+            import torch
+        except ImportError:  # pragma: no cover
+            torch = None
+        if torch is not None and isinstance(values, torch.Tensor):
+            if values.numel() != nx * ny * nz or not values.is_contiguous():
+                raise ValueError("field must be contiguous with nx*ny*nz elements")
+            if np.dtype(str(values.dtype).replace("torch.", "")) != self.dtype:
+                raise TypeError("dtype mismatch")
+            return values.data_ptr(), (0 if values.is_cuda else 1), values
+        arr = np.ascontiguousarray(values)
+        if arr.size != nx * ny * nz or arr.dtype != self.dtype:
+            raise ValueError("field size or dtype mismatch")
+        return arr.ctypes.data, 1, arr
+
+    def compute(self, values, stream=None):
+        """Runs the pipeline on ``values`` (torch CUDA tensor: device pointer;
+        numpy array or CPU tensor: host pointer copied in on the stream)."""
+        ptr, on_host, keep = self._field_ptr(values)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:  # pragma: no cover
+                stream = 0
+        _check(self._lib.dms_compute_diagram(self._h, ctypes.c_void_p(ptr), on_host,
+                                             ctypes.c_void_p(int(stream))),
+               "dms_compute_diagram")
+        del keep
+        return self
+
+    def counts(self):
+        p = (ctypes.c_int64 * 3)()
+        e = (ctypes.c_int64 * 4)()
+        _check(self._lib.dms_get_counts(self._h, p, e), "dms_get_counts")
+        return tuple(p), tuple(e)
+
+    def fetch(self, dim: int) -> np.ndarray:
+        """Pairs of dimension ``dim`` as a structured array of PAIR_DTYPE."""
+        p, e = self.counts()
+        n = p[dim] + e[dim]
+        out = np.zeros(n, PAIR_DTYPE)
+        w = ctypes.c_int64(0)
+        _check(self._lib.dms_fetch_pairs(self._h, dim, out.ctypes.data if n else None, n,
+                                         ctypes.byref(w), 0), "dms_fetch_pairs")
+        return out[: w.value]
+
+    def fetch_device(self, dim: int, out_ptr: int, cap: int) -> int:
+        w = ctypes.c_int64(0)
+        _check(self._lib.dms_fetch_pairs(self._h, dim, ctypes.c_void_p(out_ptr), cap,
+                                         ctypes.byref(w), 1), "dms_fetch_pairs")
+        return w.value
+
+    def stage_ms(self):
+        ms = (ctypes.c_float * 8)()
+        _check(self._lib.dms_get_stage_ms(self._h, ms), "dms_get_stage_ms")
+        names = ("gradient", "sort", "d0", "d2", "d1", "output", "total", "h2d")
+        return dict(zip(names, [float(x) for x in ms]))
+
+    KERNELS = ("classify", "compact", "sort", "process_lower_stars", "emit", "d0_arcs",
+               "d0_rounds", "d2_arcs", "d2_rounds", "d1_trace", "d1_reduce", "output")
+
+    def kernel_ms(self):
+        ms = (ctypes.c_float * 12)()
+        _check(self._lib.dms_get_kernel_ms(self._h, ms), "dms_get_kernel_ms")
+        return dict(zip(self.KERNELS, [float(x) for x in ms]))
+
+    def stats(self):
+        s = (ctypes.c_int64 * 10)()
+        _check(self._lib.dms_get_stats(self._h, s), "dms_get_stats")
+        names = ("critical_vertices", "c0", "c1", "c2", "c3", "launches", "rounds_d0",
+                 "rounds_d2", "rounds_d1", "d1_columns")
+        return dict(zip(names, [int(x) for x in s]))
+
+
+def diagram(values, shape_xyz=None, stream=None) -> dict:
+    """D0, D1, D2 of a field (indexed [z, y, x]) as ``{dim: PAIR_DTYPE array}``."""
+    if shape_xyz is None:
+        nz, ny, nx = values.shape
+        shape_xyz = (nx, ny, nz)
+    dt = np.dtype(str(values.dtype).replace("torch.", "")) if not isinstance(values, np.ndarray) \
+        else values.dtype
+    with Grid(shape_xyz, dt) as g:
+        g.compute(values, stream)
+        return {d: g.fetch(d) for d in range(3)}

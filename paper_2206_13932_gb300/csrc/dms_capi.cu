@@ -1,0 +1,98 @@
+// dms_capi.cu -- the extern "C" entry points of libdms (declared in
+// include/dms.h).  Argument checking and handle management only; the work is
+// in dms_pipeline.cu.
+#include <new>
+
+#include "dms_pipeline.h"
+
+struct dms_grid_s {
+    dms::Pipeline p;
+};
+
+extern "C" {
+
+dms_status dms_grid_create(int64_t nx, int64_t ny, int64_t nz, dms_dtype dtype,
+                           const dms_options *opts, dms_grid *out) {
+    if (!out) return DMS_ERR_INVALID_ARG;
+    dms_grid g = new (std::nothrow) dms_grid_s;
+    if (!g) return DMS_ERR_OOM;
+    dms_status s = g->p.init(nx, ny, nz, dtype, opts);
+    if (s != DMS_OK) {
+        g->p.destroy();
+        delete g;
+        return s;
+    }
+    *out = g;
+    return DMS_OK;
+}
+
+dms_status dms_compute_diagram(dms_grid grid, const void *values, int values_on_host,
+                               void *stream) {
+    if (!grid) return DMS_ERR_INVALID_ARG;
+    return grid->p.compute(values, values_on_host, stream);
+}
+
+dms_status dms_get_counts(dms_grid grid, int64_t pairs[3], int64_t essential[4]) {
+    if (!grid || !pairs || !essential) return DMS_ERR_INVALID_ARG;
+    if (!grid->p.has_result) return DMS_ERR_STATE;
+    for (int d = 0; d < 3; d++) pairs[d] = grid->p.n_pairs[d];
+    for (int d = 0; d < 4; d++) essential[d] = grid->p.n_ess[d];
+    return DMS_OK;
+}
+
+dms_status dms_fetch_pairs(dms_grid grid, int dim, dms_pair *out, int64_t cap, int64_t *written,
+                           int out_is_device) {
+    if (!grid) return DMS_ERR_INVALID_ARG;
+    return grid->p.fetch(dim, out, cap, written, out_is_device);
+}
+
+dms_status dms_get_stage_ms(dms_grid grid, float ms[8]) {
+    if (!grid || !ms) return DMS_ERR_INVALID_ARG;
+    if (!grid->p.has_result) return DMS_ERR_STATE;
+    for (int k = 0; k < 8; k++) ms[k] = grid->p.stage_ms[k];
+    return DMS_OK;
+}
+
+dms_status dms_get_stats(dms_grid grid, int64_t stats[10]) {
+    if (!grid || !stats) return DMS_ERR_INVALID_ARG;
+    if (!grid->p.has_result) return DMS_ERR_STATE;
+    const dms::Pipeline &p = grid->p;
+    stats[0] = p.n_crit;
+    for (int d = 0; d < 4; d++) stats[1 + d] = p.n_c[d];
+    stats[5] = p.launches;
+    stats[6] = p.rounds_d0;
+    stats[7] = p.rounds_d2;
+    stats[8] = p.rounds_d1;
+    stats[9] = p.d1_cols;
+    return DMS_OK;
+}
+
+dms_status dms_get_kernel_ms(dms_grid grid, float ms[12]) {
+    if (!grid || !ms) return DMS_ERR_INVALID_ARG;
+    if (!grid->p.has_result) return DMS_ERR_STATE;
+    for (int k = 0; k < 12; k++) ms[k] = grid->p.kernel_ms[k];
+    return DMS_OK;
+}
+
+dms_status dms_grid_destroy(dms_grid grid) {
+    if (!grid) return DMS_ERR_INVALID_ARG;
+    grid->p.destroy();
+    delete grid;
+    return DMS_OK;
+}
+
+const char *dms_status_string(dms_status status) {
+    switch (status) {
+        case DMS_OK: return "ok";
+        case DMS_ERR_INVALID_ARG: return "invalid argument";
+        case DMS_ERR_NAN: return "the field holds a NaN";
+        case DMS_ERR_OOM: return "out of memory";
+        case DMS_ERR_CUDA: return "CUDA runtime error";
+        case DMS_ERR_ITER_LIMIT: return "a bounded device loop reached its limit";
+        case DMS_ERR_STATE: return "no result available or inconsistent state";
+        case DMS_ERR_CAPACITY: return "capacity exceeded";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

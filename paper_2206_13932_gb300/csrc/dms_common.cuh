@@ -1,0 +1,332 @@
+// dms_common.cuh -- shared device definitions of libdms: the star of a vertex
+// in the Freudenthal triangulation, the vertex order and ProcessLowerStars.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dms {
+
+// ---------------------------------------------------------------------------
+// The star of a vertex x (Sec. 2.1: Freudenthal, 14-vertex neighbourhood).
+//
+// Link vertex n in [0,14): n < 7 is x + o, n >= 7 is x - o, with offset
+// bitmask o = (n % 7) + 1 (bit0 x, bit1 y, bit2 z).  A set of grid points is
+// a Freudenthal simplex iff it is a chain of the componentwise order whose
+// extent fits in one unit cube; the star holds 14 edges (one per link
+// vertex), 36 triangles (link edges) and 24 tetrahedra (link triangles).
+// ---------------------------------------------------------------------------
+constexpr int kLinks = 14, kTris = 36, kTets = 24;
+constexpr uint16_t kAllLinks = 0x3FFF;
+constexpr uint64_t kAllTris = (1ull << kTris) - 1;
+constexpr uint32_t kAllTets = (1u << kTets) - 1;
+constexpr uint8_t kNoDescent = 0xF;   // flags low nibble of a minimum
+constexpr uint8_t kFlagCritical = 0x10;
+
+struct StarTables {
+    int8_t dx[kLinks], dy[kLinks], dz[kLinks];
+    uint8_t tri_v[kTris][2];          // the two link vertices of a star triangle
+    uint8_t tet_v[kTets][3];          // the three link vertices of a star tet
+    uint8_t tet_f[kTets][3];          // its three star triangles (faces in the star)
+    uint16_t tri_mask[kTris];         // link-vertex mask of a star triangle
+    uint16_t tet_mask[kTets];         // link-vertex mask of a star tet
+    uint64_t tris_of_link[kLinks];    // star triangles containing link vertex n
+    uint32_t tets_of_link[kLinks];    // star tets containing link vertex n
+    uint32_t tets_of_tri[kTris];      // star tets containing star triangle s
+    int8_t tri_of_pair[kLinks][kLinks];
+    int8_t link_of_dc[27];            // (dx+1)+3(dy+1)+9(dz+1) -> link or -1
+    int8_t edge_anchor[kLinks], edge_type[kLinks];   // anchor: -1 = x itself
+    int8_t tri_anchor[kTris], tri_type[kTris];
+    int8_t tet_anchor[kTets], tet_type[kTets];
+    uint16_t neg[3], pos[3];          // links with d = -1 / +1 along each axis
+};
+
+// Grid constants passed by value to kernels.
+struct GridParams {
+    int32_t nx, ny, nz;
+    int64_t n;                        // nx*ny*nz (< 2^31)
+    int32_t dlin[kLinks];             // linear id offset of each link vertex
+};
+
+// ---------------------------------------------------------------------------
+// Vertex order (Sec. 2.1): values mapped to unsigned keys that order like the
+// numbers (-0.0 = +0.0), ties broken by vertex id.
+// ---------------------------------------------------------------------------
+template <typename T> struct Key;
+template <> struct Key<uint16_t> {
+    using K = uint32_t;
+    __device__ __forceinline__ static K of(uint16_t v) { return v; }
+    __device__ __forceinline__ static bool nan(uint16_t) { return false; }
+    __device__ __forceinline__ static uint64_t bits(uint16_t v) { return v; }
+};
+template <> struct Key<float> {
+    using K = uint32_t;
+    __device__ __forceinline__ static K of(float f) {
+        uint32_t u = __float_as_uint(f);
+        if (u == 0x80000000u) u = 0;
+        return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    }
+    __device__ __forceinline__ static bool nan(float f) {
+        return (__float_as_uint(f) & 0x7fffffffu) > 0x7f800000u;
+    }
+    __device__ __forceinline__ static uint64_t bits(float f) { return __float_as_uint(f); }
+};
+template <> struct Key<double> {
+    using K = uint64_t;
+    __device__ __forceinline__ static K of(double d) {
+        uint64_t u = (uint64_t)__double_as_longlong(d);
+        if (u == 0x8000000000000000ull) u = 0;
+        return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+    }
+    __device__ __forceinline__ static bool nan(double d) {
+        return ((uint64_t)__double_as_longlong(d) & 0x7fffffffffffffffull) >
+               0x7ff0000000000000ull;
+    }
+    __device__ __forceinline__ static uint64_t bits(double d) {
+        return (uint64_t)__double_as_longlong(d);
+    }
+};
+
+// Present link vertices of vertex (cx, cy, cz) (those inside the grid).
+__device__ __forceinline__ uint16_t present_links(const StarTables &S, const GridParams &g,
+                                                  int cx, int cy, int cz) {
+    uint16_t m = kAllLinks;
+    if (cx == 0) m &= ~S.neg[0];
+    if (cx == g.nx - 1) m &= ~S.pos[0];
+    if (cy == 0) m &= ~S.neg[1];
+    if (cy == g.ny - 1) m &= ~S.pos[1];
+    if (cz == 0) m &= ~S.neg[2];
+    if (cz == g.nz - 1) m &= ~S.pos[2];
+    return m;
+}
+
+__device__ __forceinline__ void coords(const GridParams &g, int64_t v, int &cx, int &cy,
+                                       int &cz) {
+    int32_t vi = (int32_t)v;
+    int32_t row = vi / g.nx;
+    cx = vi - row * g.nx;
+    cz = row / g.ny;
+    cy = row - cz * g.ny;
+}
+
+// The star of vertex v with the vertex order: lower mask (the link vertices
+// below v) and the rank of each lower link vertex among them (0 = lowest).
+struct StarView {
+    uint16_t present, lower;
+    uint8_t rank[kLinks];   // valid for lower links
+    uint8_t descent;        // lowest lower link or kNoDescent
+};
+
+template <typename T>
+__device__ __forceinline__ void load_star(const StarTables &S, const GridParams &g,
+                                          const T *__restrict__ values, int64_t v,
+                                          StarView &sv) {
+    using K = typename Key<T>::K;
+    int cx, cy, cz;
+    coords(g, v, cx, cy, cz);
+    sv.present = present_links(S, g, cx, cy, cz);
+    const K kv = Key<T>::of(values[v]);
+    K kn[kLinks];
+    uint16_t lower = 0;
+#pragma unroll
+    for (int n = 0; n < kLinks; n++) {
+        kn[n] = 0;
+        if (sv.present >> n & 1) {
+            kn[n] = Key<T>::of(values[v + g.dlin[n]]);
+            // a neighbour is lower if its value is smaller, or equal with a
+            // smaller id (a negative offset)
+            bool lo = kn[n] < kv || (kn[n] == kv && n >= 7);
+            lower |= (uint16_t)lo << n;
+        }
+    }
+    sv.lower = lower;
+    sv.descent = kNoDescent;
+#pragma unroll
+    for (int n = 0; n < kLinks; n++) {
+        uint8_t r = 0;
+        if (lower >> n & 1) {
+#pragma unroll
+            for (int m = 0; m < kLinks; m++)
+                if ((lower >> m & 1) && m != n &&
+                    (kn[m] < kn[n] || (kn[m] == kn[n] && g.dlin[m] < g.dlin[n])))
+                    r++;
+            if (r == 0) sv.descent = (uint8_t)n;
+        }
+        sv.rank[n] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ProcessLowerStars (the expansion gradient of Robins et al., which Alg. 2
+// applies; the paper cites it without pseudo-code).  Inside the lower star
+// of a vertex x every cell is keyed by G = the ranks of its other vertices in
+// decreasing order (the lexicographic key restricted to one lower star); a
+// face precedes its cofaces.
+//   - no lower edge: x is a minimum;
+//   - else x is paired with its lowest edge; the other edges wait in PQzero;
+//     cofaces with exactly one unclassified face in the lower star go to
+//     PQone;
+//   - PQone is drained by smallest G: a cell with no unclassified face moves
+//     to PQzero, otherwise it is paired with its unique unclassified face;
+//     then the smallest cell of PQzero becomes critical.
+// Faces outside the lower star never count as unclassified; a cell popped
+// after it was classified is skipped.
+// ---------------------------------------------------------------------------
+struct PLSResult {
+    uint16_t crit_e;       // critical star edges
+    uint32_t crit_h;       // critical star tets
+    uint64_t crit_t;       // critical star triangles
+    bool is_min;
+    int8_t q_pair;         // query answer (see pls())
+    int8_t q_order;        // query: classification order of the queried edge
+};
+
+enum { kQueryNone = 0, kQueryTet = 1, kQueryEdge = 2 };
+
+__device__ __forceinline__ uint16_t code_edge(const uint8_t *r, int n) {
+    return (uint16_t)((r[n] + 1) << 8);
+}
+__device__ __forceinline__ uint16_t code_tri(const StarTables &S, const uint8_t *r, int s) {
+    int a = r[S.tri_v[s][0]], b = r[S.tri_v[s][1]];
+    int hi = a > b ? a : b, lo = a > b ? b : a;
+    return (uint16_t)(((hi + 1) << 8) | ((lo + 1) << 4));
+}
+__device__ __forceinline__ uint16_t code_tet(const StarTables &S, const uint8_t *r, int h) {
+    int a = r[S.tet_v[h][0]], b = r[S.tet_v[h][1]], c = r[S.tet_v[h][2]];
+    int t;
+    if (a < b) { t = a; a = b; b = t; }
+    if (b < c) { t = b; b = c; c = t; }
+    if (a < b) { t = a; a = b; b = t; }
+    return (uint16_t)(((a + 1) << 8) | ((b + 1) << 4) | (c + 1));
+}
+
+// Query kQueryTet (cell = star tet h): q_pair = the star triangle paired with
+// h, or -1 if h is critical.  kQueryEdge (cell = link n): q_pair = the star
+// triangle paired with edge n, -2 if n is paired with the vertex, -1 if
+// critical; q_order = the order in which the edges of the lower star were
+// classified (0 = first).
+__device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank, int qkind,
+                           int qcell, PLSResult &R) {
+    R.crit_e = 0; R.crit_h = 0; R.crit_t = 0; R.is_min = false;
+    R.q_pair = -1; R.q_order = -1;
+    if (L == 0) { R.is_min = true; return; }
+
+    // lower star cells
+    uint64_t LT = kAllTris;
+    uint32_t LH = kAllTets;
+    for (uint16_t out = (uint16_t)(~L & kAllLinks); out; out &= out - 1) {
+        int n = __ffs(out) - 1;
+        LT &= ~S.tris_of_link[n];
+        LH &= ~S.tets_of_link[n];
+    }
+    uint16_t codeT[kTris];
+    uint16_t codeH[kTets];
+    for (uint64_t m = LT; m; m &= m - 1) { int s = __ffsll(m) - 1; codeT[s] = code_tri(S, rank, s); }
+    for (uint32_t m = LH; m; m &= m - 1) { int h = __ffs(m) - 1; codeH[h] = code_tet(S, rank, h); }
+
+    uint16_t cE = 0;  uint64_t cT = 0;  uint32_t cH = 0;   // classified
+    uint64_t pT = 0;  uint32_t pH = 0;                     // PQone
+    uint16_t zE = 0;  uint64_t zT = 0;  uint32_t zH = 0;   // PQzero
+    int eorder = 0;
+
+    auto unpaired_tri = [&](int s) -> uint16_t {   // unclassified edges of s
+        return (uint16_t)(((1u << S.tri_v[s][0]) | (1u << S.tri_v[s][1])) & ~cE);
+    };
+    auto unpaired_tet = [&](int h) -> uint64_t {   // unclassified faces of h
+        return ((1ull << S.tet_f[h][0]) | (1ull << S.tet_f[h][1]) | (1ull << S.tet_f[h][2])) & ~cT;
+    };
+    auto push_cof_edge = [&](int n) {
+        for (uint64_t m = S.tris_of_link[n] & LT & ~cT; m; m &= m - 1) {
+            int s = __ffsll(m) - 1;
+            if (__popc(unpaired_tri(s)) == 1) pT |= 1ull << s;
+        }
+    };
+    auto push_cof_tri = [&](int s) {
+        for (uint32_t m = S.tets_of_tri[s] & LH & ~cH; m; m &= m - 1) {
+            int h = __ffs(m) - 1;
+            if (__popcll(unpaired_tet(h)) == 1) pH |= 1u << h;
+        }
+    };
+
+    // the vertex is paired with its lowest edge
+    int n0 = -1;
+    for (uint16_t m = L; m; m &= m - 1) { int n = __ffs(m) - 1; if (rank[n] == 0) n0 = n; }
+    cE = (uint16_t)(1u << n0);
+    if (qkind == kQueryEdge && qcell == n0) { R.q_pair = -2; R.q_order = (int8_t)eorder; }
+    eorder++;
+    zE = (uint16_t)(L & ~cE);
+    push_cof_edge(n0);
+
+    for (int guard = 0; guard < 4 * (kLinks + kTris + kTets); guard++) {
+        while (pT | pH) {
+            // pop the smallest G among PQone
+            uint16_t best = 0xFFFF; int bi = -1; bool btet = false;
+            for (uint64_t m = pT; m; m &= m - 1) {
+                int s = __ffsll(m) - 1;
+                if (codeT[s] < best) { best = codeT[s]; bi = s; btet = false; }
+            }
+            for (uint32_t m = pH; m; m &= m - 1) {
+                int h = __ffs(m) - 1;
+                if (codeH[h] < best) { best = codeH[h]; bi = h; btet = true; }
+            }
+            if (!btet) {
+                int s = bi;
+                pT &= ~(1ull << s);
+                if (cT >> s & 1) continue;
+                uint16_t u = unpaired_tri(s);
+                if (u == 0) { zT |= 1ull << s; continue; }
+                int n = __ffs(u) - 1;                  // the unique unclassified edge
+                cE |= (uint16_t)(1u << n); cT |= 1ull << s; zE &= (uint16_t)~(1u << n);
+                if (qkind == kQueryEdge && qcell == n) { R.q_pair = (int8_t)s; R.q_order = (int8_t)eorder; }
+                eorder++;
+                push_cof_tri(s);
+                push_cof_edge(n);
+            } else {
+                int h = bi;
+                pH &= ~(1u << h);
+                if (cH >> h & 1) continue;
+                uint64_t u = unpaired_tet(h);
+                if (u == 0) { zH |= 1u << h; continue; }
+                int s = __ffsll(u) - 1;                // the unique unclassified face
+                cT |= 1ull << s; cH |= 1u << h; zT &= ~(1ull << s);
+                if (qkind == kQueryTet && qcell == h) R.q_pair = (int8_t)s;
+                push_cof_tri(s);
+            }
+        }
+        if (!(zE | zT | zH)) break;
+        // the smallest G among PQzero is critical
+        uint16_t best = 0xFFFF; int bi = -1, bd = -1;
+        for (uint16_t m = zE; m; m &= m - 1) {
+            int n = __ffs(m) - 1;
+            uint16_t c = code_edge(rank, n);
+            if (c < best) { best = c; bi = n; bd = 1; }
+        }
+        for (uint64_t m = zT; m; m &= m - 1) {
+            int s = __ffsll(m) - 1;
+            if (codeT[s] < best) { best = codeT[s]; bi = s; bd = 2; }
+        }
+        for (uint32_t m = zH; m; m &= m - 1) {
+            int h = __ffs(m) - 1;
+            if (codeH[h] < best) { best = codeH[h]; bi = h; bd = 3; }
+        }
+        if (bd == 1) {
+            zE &= (uint16_t)~(1u << bi); cE |= (uint16_t)(1u << bi); R.crit_e |= (uint16_t)(1u << bi);
+            if (qkind == kQueryEdge && qcell == bi) { R.q_pair = -1; R.q_order = (int8_t)eorder; }
+            eorder++;
+            push_cof_edge(bi);
+        } else if (bd == 2) {
+            zT &= ~(1ull << bi); cT |= 1ull << bi; R.crit_t |= 1ull << bi;
+            push_cof_tri(bi);
+        } else {
+            zH &= ~(1u << bi); cH |= 1u << bi; R.crit_h |= 1u << bi;
+        }
+    }
+}
+
+// Code of a critical cell of a lower star from packed 4-bit ranks.
+__device__ __forceinline__ void unpack_ranks(uint64_t packed, uint8_t *r) {
+#pragma unroll
+    for (int n = 0; n < kLinks; n++) r[n] = (uint8_t)((packed >> (4 * n)) & 0xF);
+}
+
+}  // namespace dms

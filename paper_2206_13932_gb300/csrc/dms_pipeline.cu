@@ -1,0 +1,1764 @@
+// dms_pipeline.cu -- the device pipeline of libdms.
+//
+// Stages (the paper's order, Sec. 7.1):
+//   gradient   classify every vertex by its lower link (HBM-bound stencil),
+//              compact the PL-critical vertices in id order, sort them by
+//              value, run ProcessLowerStars on each (Alg. 2: the critical
+//              simplices C0..C3, already in lexicographic order);
+//   D0         descend from both ends of each critical edge along the
+//              vertex->edge vectors to two minima (Sec. 5.1 (a)-(b)) and pair
+//              the arcs of that graph by the elder rule (Sec. 5.1 (c)-(d));
+//   D2         ascend from each critical triangle through tet->triangle
+//              vectors to critical tets or the virtual maximum (Sec. 5.2) and
+//              pair in decreasing order;
+//   D1         trace the Morse boundary of each 2-saddle not paired in D2 over
+//              the 1-saddles not paired in D0 and reduce those columns
+//              (Alg. 3 restricted, Sec. 4.2 (b), Sec. 6);
+//   output     pairs and infinite classes (Sec. 6).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "dms_common.cuh"
+#include "dms_pipeline.h"
+
+namespace dms {
+
+__device__ StarTables g_star;
+__device__ uint32_t g_regular[(1 << kLinks) / 32];   // bit m: lower mask m is PL-regular
+
+enum : uint32_t { kErrNan = 1, kErrIter = 2, kErrCap = 4, kErrState = 8 };
+constexpr int32_t kNoOwner = 0x7F7F7F7F;   // memset(0x7F) fill of the pivot owners
+
+struct DevStatus {
+    uint32_t err;
+    uint32_t pad;
+    unsigned long long maxkey;     // largest vertex key
+    long long total[4];            // scan totals
+    long long parts[8];            // output part sizes
+    int changed;                   // D1: columns changed this round
+    unsigned long long pool_top;   // D1 column pool bump pointer
+    long long misc[4];
+};
+
+// Record of a critical vertex after ProcessLowerStars.
+struct CritRec {
+    uint64_t crit_t;      // critical star triangles
+    uint64_t ranks;       // 4-bit rank of each lower link vertex (0xF: not lower)
+    uint32_t crit_h;      // critical star tets
+    uint16_t crit_e;      // critical star edges
+    uint8_t is_min, pad;
+};
+
+struct HeapEnt { unsigned long long hi, lo; };
+struct HashEnt {
+    unsigned long long key;
+    int32_t gen, row;
+    uint8_t parity, kind, pair, pad[5];
+};
+enum { kKindRow = 1, kKindReg = 2 };
+
+// ------------------------------------------------------------ host tables
+
+static bool build_star_tables(StarTables &S) {
+    memset(&S, 0, sizeof S);
+    int d[kLinks][3];
+    for (int n = 0; n < kLinks; n++) {
+        int o = n % 7 + 1, sg = n < 7 ? 1 : -1;
+        d[n][0] = sg * (o & 1); d[n][1] = sg * ((o >> 1) & 1); d[n][2] = sg * ((o >> 2) & 1);
+        S.dx[n] = (int8_t)d[n][0]; S.dy[n] = (int8_t)d[n][1]; S.dz[n] = (int8_t)d[n][2];
+        S.edge_anchor[n] = (int8_t)(n < 7 ? -1 : n);
+        S.edge_type[n] = (int8_t)(o - 1);
+        for (int a = 0; a < 3; a++) {
+            if (d[n][a] < 0) S.neg[a] |= (uint16_t)(1u << n);
+            if (d[n][a] > 0) S.pos[a] |= (uint16_t)(1u << n);
+        }
+    }
+    for (int i = 0; i < 27; i++) S.link_of_dc[i] = -1;
+    for (int n = 0; n < kLinks; n++)
+        S.link_of_dc[(d[n][0] + 1) + 3 * (d[n][1] + 1) + 9 * (d[n][2] + 1)] = (int8_t)n;
+    for (int a = 0; a < kLinks; a++)
+        for (int b = 0; b < kLinks; b++) S.tri_of_pair[a][b] = -1;
+
+    static const int TRI_B[12] = {3, 3, 5, 5, 6, 6, 7, 7, 7, 7, 7, 7};
+    static const int TRI_A[12] = {1, 2, 1, 4, 2, 4, 1, 2, 3, 4, 5, 6};
+    static const int TET_A[6] = {1, 1, 2, 2, 4, 4};
+    static const int TET_B[6] = {3, 5, 3, 6, 5, 6};
+
+    // points: index -1 = the centre (0,0,0), otherwise a link vertex
+    auto pt = [&](int l, int k) { return l < 0 ? 0 : d[l][k]; };
+    // is {centre} + links a chain of the componentwise order within one cube?
+    // returns the anchor (min point) and the offset masks of the others.
+    auto chain = [&](const int *ls, int cnt, int *anchor, int *offs) -> bool {
+        int pts[4] = {-1, ls[0], cnt > 1 ? ls[1] : -1, cnt > 2 ? ls[2] : -1};
+        int m = cnt + 1;
+        // sort by coordinate sum
+        for (int i = 1; i < m; i++)
+            for (int j = i; j > 0; j--) {
+                int sa = pt(pts[j - 1], 0) + pt(pts[j - 1], 1) + pt(pts[j - 1], 2);
+                int sb = pt(pts[j], 0) + pt(pts[j], 1) + pt(pts[j], 2);
+                if (sa > sb) std::swap(pts[j - 1], pts[j]);
+            }
+        for (int i = 0; i + 1 < m; i++)
+            for (int k = 0; k < 3; k++)
+                if (pt(pts[i], k) > pt(pts[i + 1], k)) return false;
+        for (int k = 0; k < 3; k++) {
+            int e = pt(pts[m - 1], k) - pt(pts[0], k);
+            if (e < 0 || e > 1) return false;
+        }
+        *anchor = pts[0];
+        for (int i = 1; i < m; i++) {
+            int o = 0;
+            for (int k = 0; k < 3; k++) o |= (pt(pts[i], k) - pt(pts[0], k)) << k;
+            offs[i - 1] = o;
+        }
+        return true;
+    };
+    int nt = 0, nh = 0;
+    for (int a = 0; a < kLinks; a++)
+        for (int b = a + 1; b < kLinks; b++) {
+            int ls[2] = {a, b}, anc, offs[2];
+            if (!chain(ls, 2, &anc, offs)) continue;
+            if (nt >= kTris) return false;
+            S.tri_v[nt][0] = (uint8_t)a; S.tri_v[nt][1] = (uint8_t)b;
+            S.tri_mask[nt] = (uint16_t)((1u << a) | (1u << b));
+            S.tri_of_pair[a][b] = S.tri_of_pair[b][a] = (int8_t)nt;
+            S.tri_anchor[nt] = (int8_t)anc;
+            int lo = offs[0], hi = offs[1];
+            if (__builtin_popcount(lo) > __builtin_popcount(hi)) std::swap(lo, hi);
+            S.tri_type[nt] = -1;
+            for (int k = 0; k < 12; k++)
+                if (TRI_A[k] == lo && TRI_B[k] == hi) S.tri_type[nt] = (int8_t)k;
+            if (S.tri_type[nt] < 0) return false;
+            S.tris_of_link[a] |= 1ull << nt;
+            S.tris_of_link[b] |= 1ull << nt;
+            nt++;
+        }
+    for (int a = 0; a < kLinks; a++)
+        for (int b = a + 1; b < kLinks; b++)
+            for (int c = b + 1; c < kLinks; c++) {
+                int ls[3] = {a, b, c}, anc, offs[3];
+                if (!chain(ls, 3, &anc, offs)) continue;
+                if (nh >= kTets) return false;
+                S.tet_v[nh][0] = (uint8_t)a; S.tet_v[nh][1] = (uint8_t)b; S.tet_v[nh][2] = (uint8_t)c;
+                S.tet_mask[nh] = (uint16_t)((1u << a) | (1u << b) | (1u << c));
+                S.tet_f[nh][0] = (uint8_t)S.tri_of_pair[a][b];
+                S.tet_f[nh][1] = (uint8_t)S.tri_of_pair[a][c];
+                S.tet_f[nh][2] = (uint8_t)S.tri_of_pair[b][c];
+                S.tet_anchor[nh] = (int8_t)anc;
+                int one = 0, two = 0;
+                for (int i = 0; i < 3; i++) {
+                    if (__builtin_popcount(offs[i]) == 1) one = offs[i];
+                    if (__builtin_popcount(offs[i]) == 2) two = offs[i];
+                }
+                S.tet_type[nh] = -1;
+                for (int k = 0; k < 6; k++)
+                    if (TET_A[k] == one && TET_B[k] == two) S.tet_type[nh] = (int8_t)k;
+                if (S.tet_type[nh] < 0) return false;
+                for (int i = 0; i < 3; i++) {
+                    S.tets_of_link[S.tet_v[nh][i]] |= 1u << nh;
+                    S.tets_of_tri[S.tet_f[nh][i]] |= 1u << nh;
+                }
+                nh++;
+            }
+    return nt == kTris && nh == kTets;
+}
+
+// Lower mask m is PL-regular iff the subcomplex of the link induced by m is
+// non-empty and acyclic (reduced Betti numbers all zero).  Robins et al.'s
+// gradient puts critical cells exactly where the lower link has homology.
+static void build_regular_lut(const StarTables &S, std::vector<uint32_t> &lut) {
+    lut.assign((1 << kLinks) / 32, 0);
+    for (int m = 0; m < (1 << kLinks); m++) {
+        int parent[kLinks];
+        for (int i = 0; i < kLinks; i++) parent[i] = i;
+        auto find = [&](int a) { while (parent[a] != a) a = parent[a] = parent[parent[a]]; return a; };
+        int V = __builtin_popcount(m), E = 0, F = 0;
+        for (int s = 0; s < kTris; s++)
+            if ((S.tri_mask[s] & m) == S.tri_mask[s]) {
+                E++;
+                int a = find(S.tri_v[s][0]), b = find(S.tri_v[s][1]);
+                if (a != b) parent[a] = b;
+            }
+        for (int h = 0; h < kTets; h++)
+            if ((S.tet_mask[h] & m) == S.tet_mask[h]) F++;
+        int b0 = 0;
+        for (int i = 0; i < kLinks; i++)
+            if ((m >> i & 1) && find(i) == i) b0++;
+        int b2 = m == kAllLinks ? 1 : 0;
+        int chi = V - E + F;
+        int b1 = b0 - chi + b2;
+        bool regular = V > 0 && b0 == 1 && b1 == 0 && b2 == 0;
+        if (regular) lut[m >> 5] |= 1u << (m & 31);
+    }
+}
+
+// ------------------------------------------------------------- utilities
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Local index of critical cell `loc` of dimension `dim` among the critical
+// cells of that dimension of the same vertex, in lexicographic (G) order.
+__device__ __forceinline__ int local_index(const StarTables &S, const CritRec &rec, int dim,
+                                           int loc) {
+    uint8_t r[kLinks];
+    unpack_ranks(rec.ranks, r);
+    int k = 0;
+    if (dim == 1) {
+        uint16_t c = code_edge(r, loc);
+        for (uint16_t m = rec.crit_e; m; m &= m - 1) k += code_edge(r, __ffs(m) - 1) < c;
+    } else if (dim == 2) {
+        uint16_t c = code_tri(S, r, loc);
+        for (uint64_t m = rec.crit_t; m; m &= m - 1) k += code_tri(S, r, __ffsll(m) - 1) < c;
+    } else {
+        uint16_t c = code_tet(S, r, loc);
+        for (uint32_t m = rec.crit_h; m; m &= m - 1) k += code_tet(S, r, __ffs(m) - 1) < c;
+    }
+    return k;
+}
+
+__device__ __forceinline__ int64_t edge_id(const StarTables &S, const GridParams &g, int64_t x,
+                                           int n) {
+    int64_t anchor = S.edge_anchor[n] < 0 ? x : x + g.dlin[S.edge_anchor[n]];
+    return 7 * anchor + S.edge_type[n];
+}
+__device__ __forceinline__ int64_t tri_id(const StarTables &S, const GridParams &g, int64_t x,
+                                          int s) {
+    int64_t anchor = S.tri_anchor[s] < 0 ? x : x + g.dlin[S.tri_anchor[s]];
+    return 12 * anchor + S.tri_type[s];
+}
+__device__ __forceinline__ int64_t tet_id(const StarTables &S, const GridParams &g, int64_t x,
+                                          int h) {
+    int64_t anchor = S.tet_anchor[h] < 0 ? x : x + g.dlin[S.tet_anchor[h]];
+    return 6 * anchor + S.tet_type[h];
+}
+
+// ------------------------------------------------------------------ scan
+
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *total) {
+    __shared__ int ws[kScanThreads / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    int pre = 0, tot = 0;
+    for (int i = 0; i < kScanThreads / 32; i++) {
+        if (i < w) pre += ws[i];
+        tot += ws[i];
+    }
+    __syncthreads();
+    *total = tot;
+    return pre + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partial(const int32_t *__restrict__ in,
+                                                               int64_t n, int32_t *partial) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + k * kScanThreads + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    int tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t *__restrict__ in,
+                                                             int32_t *out, int64_t n,
+                                                             const int32_t *__restrict__ off,
+                                                             long long *total) {
+    __shared__ int tile[kScanTile];
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + k * kScanThreads + threadIdx.x;
+        tile[k * kScanThreads + threadIdx.x] = i < n ? in[i] : 0;
+    }
+    __syncthreads();
+    int loc[kScanItems], s = 0;
+    for (int k = 0; k < kScanItems; k++) { loc[k] = tile[threadIdx.x * kScanItems + k]; s += loc[k]; }
+    int tot;
+    int pre = block_exclusive_scan(s, &tot) + (off ? off[blockIdx.x] : 0);
+    for (int k = 0; k < kScanItems; k++) { tile[threadIdx.x * kScanItems + k] = pre; pre += loc[k]; }
+    __syncthreads();
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + k * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = tile[k * kScanThreads + threadIdx.x];
+    }
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1)
+        *total = (long long)pre;
+}
+
+// --------------------------------------------------- stage 1: classification
+
+constexpr int kClsThreads = 256, kClsItems = 8, kClsTile = kClsThreads * kClsItems;
+
+template <typename T>
+__global__ void __launch_bounds__(kClsThreads)
+    k_classify(const T *__restrict__ values, GridParams g, uint8_t *__restrict__ flags,
+               int32_t *__restrict__ tile_cnt, DevStatus *st) {
+    using K = typename Key<T>::K;
+    __shared__ uint32_t lut[(1 << kLinks) / 32];
+    __shared__ int scnt[kClsThreads / 32];
+    __shared__ unsigned long long smax[kClsThreads / 32];
+    for (int i = threadIdx.x; i < (1 << kLinks) / 32; i += kClsThreads) lut[i] = g_regular[i];
+    __syncthreads();
+    const StarTables &S = g_star;
+    int64_t base = (int64_t)blockIdx.x * kClsTile;
+    int cnt = 0;
+    K kmax = 0;
+    bool bad = false;
+    for (int k = 0; k < kClsItems; k++) {
+        int64_t v = base + k * kClsThreads + threadIdx.x;
+        if (v >= g.n) break;
+        int cx, cy, cz;
+        coords(g, v, cx, cy, cz);
+        uint16_t pres = present_links(S, g, cx, cy, cz);
+        T xv = values[v];
+        bad |= Key<T>::nan(xv);
+        K kv = Key<T>::of(xv);
+        uint16_t lower = 0;
+        K best = 0;
+        int bn = -1;
+#pragma unroll
+        for (int n = 0; n < kLinks; n++) {
+            if (pres >> n & 1) {
+                K kn = Key<T>::of(values[v + g.dlin[n]]);
+                bool lo = kn < kv || (kn == kv && n >= 7);
+                if (lo) {
+                    lower |= (uint16_t)(1u << n);
+                    if (bn < 0 || kn < best || (kn == best && g.dlin[n] < g.dlin[bn])) {
+                        best = kn;
+                        bn = n;
+                    }
+                }
+            }
+        }
+        bool crit = !((lut[lower >> 5] >> (lower & 31)) & 1);
+        flags[v] = (uint8_t)((bn < 0 ? kNoDescent : bn) | (crit ? kFlagCritical : 0));
+        cnt += crit;
+        kmax = kv > kmax ? kv : kmax;
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long km = kmax;
+    for (int o = 16; o; o >>= 1) {
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        unsigned long long y = __shfl_down_sync(0xffffffffu, km, o);
+        km = y > km ? y : km;
+    }
+    if (lane == 0) { scnt[w] = cnt; smax[w] = km; }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->err, kErrNan);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        unsigned long long m = 0;
+        for (int i = 0; i < kClsThreads / 32; i++) { c += scnt[i]; m = smax[i] > m ? smax[i] : m; }
+        tile_cnt[blockIdx.x] = c;
+        atomicMax(&st->maxkey, m);
+    }
+}
+
+// Critical vertex ids in increasing id order.
+__global__ void __launch_bounds__(kClsThreads)
+    k_compact(const uint8_t *__restrict__ flags, int64_t n, const int32_t *__restrict__ tile_off,
+              int32_t *__restrict__ vc) {
+    __shared__ int ws[kClsThreads / 32];
+    int64_t base = (int64_t)blockIdx.x * kClsTile;
+    int off = tile_off[blockIdx.x];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = 0; k < kClsItems; k++) {
+        int64_t v = base + k * kClsThreads + threadIdx.x;
+        bool c = v < n && (flags[v] & kFlagCritical);
+        unsigned b = __ballot_sync(0xffffffffu, c);
+        if (lane == 0) ws[w] = __popc(b);
+        __syncthreads();
+        int pre = 0, tot = 0;
+        for (int i = 0; i < kClsThreads / 32; i++) { if (i < w) pre += ws[i]; tot += ws[i]; }
+        if (c) vc[off + pre + __popc(b & lanemask_lt())] = (int32_t)v;
+        off += tot;
+        __syncthreads();
+    }
+}
+
+// ----------------------------------- stage 2: stable LSD radix sort by key
+
+constexpr int kRsThreads = 256, kRsWarps = kRsThreads / 32, kRsPerWarp = 512,
+              kRsTile = kRsWarps * kRsPerWarp;
+
+template <typename T>
+__global__ void k_gather_keys(const T *__restrict__ values, const int32_t *__restrict__ vc,
+                              int64_t nc, typename Key<T>::K *keys) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc) keys[i] = Key<T>::of(values[vc[i]]);
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kRsThreads)
+    k_rs_hist(const K *__restrict__ keys, int64_t n, int shift, int32_t *hist, int ntiles) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int k = threadIdx.x; k < kRsTile; k += kRsThreads) {
+        int64_t i = base + k;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kRsThreads)
+    k_rs_scatter(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *kout,
+                 int32_t *vout, int64_t n, int shift, const int32_t *__restrict__ hoff,
+                 int ntiles) {
+    __shared__ int wc[kRsWarps][256];
+    __shared__ int wb[kRsWarps][256];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&wc[0][0])[i] = 0;
+    __syncthreads();
+    int64_t wbase = (int64_t)blockIdx.x * kRsTile + (int64_t)w * kRsPerWarp;
+    for (int it = 0; it < kRsPerWarp / 32; it++) {
+        int64_t i = wbase + it * 32 + lane;
+        bool ok = i < n;
+        int d = ok ? (int)((kin[i] >> shift) & 255) : 256 + lane;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (ok && lane == __ffs(peers) - 1) wc[w][d] += __popc(peers);
+    }
+    __syncthreads();
+    {
+        int d = threadIdx.x;
+        int run = hoff[(int64_t)d * ntiles + blockIdx.x];
+        for (int q = 0; q < kRsWarps; q++) { wb[q][d] = run; run += wc[q][d]; }
+    }
+    __syncthreads();
+    for (int it = 0; it < kRsPerWarp / 32; it++) {
+        int64_t i = wbase + it * 32 + lane;
+        bool ok = i < n;
+        K kv = ok ? kin[i] : 0;
+        int d = ok ? (int)((kv >> shift) & 255) : 256 + lane;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (ok) {
+            int pos = wb[w][d] + __popc(peers & lanemask_lt());
+            kout[pos] = kv;
+            vout[pos] = vin[i];
+        }
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) wb[w][d] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+// -------------------------------- stage 3: ProcessLowerStars on critical ones
+
+template <typename T>
+__global__ void k_pls(const T *__restrict__ values, GridParams g,
+                      const int32_t *__restrict__ vc, int64_t nc, CritRec *recs,
+                      int32_t *cnt0, int32_t *cnt1, int32_t *cnt2, int32_t *cnt3,
+                      int32_t *vrank) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const StarTables &S = g_star;
+    int64_t x = vc[i];
+    StarView sv;
+    load_star(S, g, values, x, sv);
+    PLSResult R;
+    pls(S, sv.lower, sv.rank, kQueryNone, 0, R);
+    uint64_t packed = 0;
+    for (int n = 0; n < kLinks; n++)
+        packed |= (uint64_t)((sv.lower >> n & 1) ? sv.rank[n] : 0xF) << (4 * n);
+    CritRec rec;
+    rec.crit_t = R.crit_t; rec.ranks = packed; rec.crit_h = R.crit_h; rec.crit_e = R.crit_e;
+    rec.is_min = R.is_min; rec.pad = 0;
+    recs[i] = rec;
+    cnt0[i] = R.is_min;
+    cnt1[i] = __popc(R.crit_e);
+    cnt2[i] = __popcll(R.crit_t);
+    cnt3[i] = __popc(R.crit_h);
+    vrank[x] = (int32_t)i;
+}
+
+// Critical simplices of each dimension in lexicographic order: by vertex (the
+// critical vertices are sorted) then by G inside the lower star.
+__global__ void k_emit(const int32_t *__restrict__ vc, int64_t nc, const CritRec *__restrict__ recs,
+                       const int32_t *b0, const int32_t *b1, const int32_t *b2, const int32_t *b3,
+                       int32_t *v0, int32_t *v1, uint8_t *l1, int32_t *v2, uint8_t *l2,
+                       int32_t *v3, uint8_t *l3) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const StarTables &S = g_star;
+    CritRec rec = recs[i];
+    int32_t x = vc[i];
+    uint8_t r[kLinks];
+    unpack_ranks(rec.ranks, r);
+    if (rec.is_min) v0[b0[i]] = x;
+    int k = b1[i];
+    for (uint16_t m = rec.crit_e; m;) {
+        int bi = -1; uint16_t bc = 0xFFFF;
+        for (uint16_t q = m; q; q &= q - 1) {
+            int n = __ffs(q) - 1; uint16_t c = code_edge(r, n);
+            if (c < bc) { bc = c; bi = n; }
+        }
+        v1[k] = x; l1[k] = (uint8_t)bi; k++;
+        m &= (uint16_t)~(1u << bi);
+    }
+    k = b2[i];
+    for (uint64_t m = rec.crit_t; m;) {
+        int bi = -1; uint16_t bc = 0xFFFF;
+        for (uint64_t q = m; q; q &= q - 1) {
+            int s = __ffsll(q) - 1; uint16_t c = code_tri(S, r, s);
+            if (c < bc) { bc = c; bi = s; }
+        }
+        v2[k] = x; l2[k] = (uint8_t)bi; k++;
+        m &= ~(1ull << bi);
+    }
+    k = b3[i];
+    for (uint32_t m = rec.crit_h; m;) {
+        int bi = -1; uint16_t bc = 0xFFFF;
+        for (uint32_t q = m; q; q &= q - 1) {
+            int h = __ffs(q) - 1; uint16_t c = code_tet(S, r, h);
+            if (c < bc) { bc = c; bi = h; }
+        }
+        v3[k] = x; l3[k] = (uint8_t)bi; k++;
+        m &= ~(1u << bi);
+    }
+}
+
+// ------------------------------------------------------ stage 4: D0 arcs
+
+// The minimum reached by following descent links from w, or -1 (and the
+// iteration-limit error) if max_steps is exceeded.
+__device__ __forceinline__ int64_t descend(const GridParams &g, const uint8_t *__restrict__ flags,
+                                           int64_t w, int64_t max_steps, DevStatus *st) {
+    for (int64_t s = 0; s < max_steps; s++) {
+        int d = flags[w] & 0xF;
+        if (d == kNoDescent) return w;
+        w += g.dlin[d];
+    }
+    atomicOr(&st->err, kErrIter);
+    return -1;
+}
+
+// Each critical edge links the two minima that its two descending v-paths
+// (vertex -> edge vectors: each regular vertex is paired with the edge to its
+// lowest neighbour) reach (Sec. 5.1 (a)-(b)).
+__global__ void k_d0_arcs(GridParams g, const uint8_t *__restrict__ flags,
+                          const int32_t *__restrict__ vrank, const int32_t *__restrict__ v1,
+                          const uint8_t *__restrict__ l1, int64_t n1, int32_t *A, int32_t *B,
+                          int32_t *young, int64_t max_steps, DevStatus *st) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n1) return;
+    int64_t x = v1[j];
+    int64_t u = x + g.dlin[l1[j]];
+    int64_t ma = descend(g, flags, x, max_steps, st), mb = descend(g, flags, u, max_steps, st);
+    // on failure both ends go to node 0: a self-loop, harmless until the
+    // host reports the error
+    A[j] = ma < 0 || mb < 0 ? 0 : vrank[ma];
+    B[j] = ma < 0 || mb < 0 ? 0 : vrank[mb];
+    young[j] = -1;
+}
+
+// ------------------------------------- elder rule by divide and conquer
+//
+// The elder rule (Sec. 5.1 (c)-(d)) processes arcs in (in/de)creasing order
+// with a union-find: an arc joining two components kills the younger
+// component's extremum; an arc inside one component closes a cycle and stays
+// unpaired.  Its outcome depends only on the two components at the arc's
+// turn.  Those are computed for every arc at once by halving the arc order:
+// for a segment of arcs whose endpoint labels name the components at the
+// segment's start (each component is named by its oldest node), the light
+// half keeps those labels and the heavy half is relabelled by the connected
+// components of the light half (named by their oldest label).  After
+// ceil(log2 E) levels every arc's labels name the components at its own turn.
+// Each level runs a lock-free union-find keyed by (segment, label) in a hash
+// table, since one label may name different components in different
+// segments.
+
+__device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
+    k ^= k >> 31; k *= 0x7fb5d329728ea185ull; k ^= k >> 27; k *= 0x81dadef4bc2dd44dull;
+    k ^= k >> 33;
+    return (uint32_t)k;
+}
+
+__device__ __forceinline__ int64_t dc_time(int64_t j, int64_t narcs, int descending) {
+    return descending ? narcs - 1 - j : j;
+}
+
+// slot of key (inserting it if absent); -1 if the table is full
+__device__ __forceinline__ int32_t dc_insert(unsigned long long *keys, uint32_t mask,
+                                             unsigned long long key, bool *fresh) {
+    uint32_t h = hash_key(key) & mask;
+    for (uint32_t p = 0; p <= mask; p++) {
+        uint32_t s = (h + p) & mask;
+        unsigned long long k = keys[s];
+        if (k == key) { *fresh = false; return (int32_t)s; }
+        if (k == ~0ull) {
+            unsigned long long old = atomicCAS(&keys[s], ~0ull, key);
+            if (old == ~0ull) { *fresh = true; return (int32_t)s; }
+            if (old == key) { *fresh = false; return (int32_t)s; }
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int32_t dc_lookup(const unsigned long long *keys, uint32_t mask,
+                                             unsigned long long key) {
+    uint32_t h = hash_key(key) & mask;
+    for (uint32_t p = 0; p <= mask; p++) {
+        uint32_t s = (h + p) & mask;
+        unsigned long long k = keys[s];
+        if (k == key) return (int32_t)s;
+        if (k == ~0ull) return -1;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int32_t dc_find(int32_t *par, int32_t a) {
+    while (true) {
+        int32_t p = par[a];
+        if (p == a) return a;
+        int32_t gp = par[p];
+        if (gp != p) par[a] = gp;
+        a = gp;
+    }
+}
+
+// light arcs of each segment: register both endpoint labels
+__global__ void k_dc_insert(int64_t narcs, int shift, int descending, const int32_t *A,
+                            const int32_t *B, unsigned long long *keys, int32_t *par,
+                            int32_t *lab, uint32_t mask, DevStatus *st) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= narcs) return;
+    int64_t t = dc_time(j, narcs, descending);
+    int64_t seg = t >> shift;
+    if ((t >> (shift - 1)) & 1) return;                  // heavy half
+    int32_t ab[2] = {A[j], B[j]};
+    for (int e = 0; e < 2; e++) {
+        unsigned long long key = ((unsigned long long)seg << 32) | (uint32_t)ab[e];
+        bool fresh;
+        int32_t s = dc_insert(keys, mask, key, &fresh);
+        if (s < 0) { atomicOr(&st->err, kErrCap); return; }
+        if (fresh) { par[s] = s; lab[s] = ab[e]; }
+    }
+}
+
+// light arcs: union their endpoints; a root is hooked under the root holding
+// the older label (smaller for D0, larger for D2)
+__global__ void k_dc_union(int64_t narcs, int shift, int descending, int older_is_larger,
+                           const int32_t *A, const int32_t *B, const unsigned long long *keys,
+                           int32_t *par, const int32_t *lab, uint32_t mask, DevStatus *st) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= narcs) return;
+    int64_t t = dc_time(j, narcs, descending);
+    int64_t seg = t >> shift;
+    if ((t >> (shift - 1)) & 1) return;
+    int32_t a = A[j], b = B[j];
+    if (a == b) return;
+    int32_t sa = dc_lookup(keys, mask, ((unsigned long long)seg << 32) | (uint32_t)a);
+    int32_t sb = dc_lookup(keys, mask, ((unsigned long long)seg << 32) | (uint32_t)b);
+    if (sa < 0 || sb < 0) { atomicOr(&st->err, kErrState); return; }
+    for (int it = 0; it < (1 << 20); it++) {
+        int32_t ra = dc_find(par, sa), rb = dc_find(par, sb);
+        if (ra == rb) return;
+        bool a_older = older_is_larger ? lab[ra] > lab[rb] : lab[ra] < lab[rb];
+        int32_t young = a_older ? rb : ra, old = a_older ? ra : rb;
+        if (atomicCAS(&par[young], young, old) == young) return;
+    }
+    atomicOr(&st->err, kErrIter);
+}
+
+// heavy arcs: relabel endpoints by the light half's components
+__global__ void k_dc_relabel(int64_t narcs, int shift, int descending, int32_t *A, int32_t *B,
+                             const unsigned long long *keys, int32_t *par, const int32_t *lab,
+                             uint32_t mask) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= narcs) return;
+    int64_t t = dc_time(j, narcs, descending);
+    int64_t seg = t >> shift;
+    if (!((t >> (shift - 1)) & 1)) return;               // light half
+    int32_t *ends[2] = {&A[j], &B[j]};
+    for (int e = 0; e < 2; e++) {
+        int32_t s = dc_lookup(keys, mask, ((unsigned long long)seg << 32) | (uint32_t)*ends[e]);
+        if (s >= 0) *ends[e] = lab[dc_find(par, s)];
+    }
+}
+
+// every arc now sees the components at its turn: the elder rule
+__global__ void k_dc_decide(int64_t narcs, int older_is_larger, const int32_t *A,
+                            const int32_t *B, int32_t *young, uint8_t *died) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= narcs) return;
+    int32_t a = A[j], b = B[j];
+    if (a == b) { young[j] = -1; return; }
+    int32_t y = older_is_larger ? (a < b ? a : b) : (a > b ? a : b);
+    young[j] = y;
+    died[y] = 1;
+}
+
+// ------------------------------------------------------ stage 5: D2 arcs
+
+// The critical tet (node index) or the virtual maximum reached from tet h of
+// the star of y by the ascending walk of the dual gradient (Sec. 5.2): a
+// regular tet is the head of a triangle->tet vector; cross that triangle to
+// its other tet; the outer boundary is the virtual maximum.
+template <typename T>
+__device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__restrict__ values,
+                          const uint8_t *__restrict__ flags, const int32_t *__restrict__ vrank,
+                          const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
+                          int64_t y, int h, int32_t vmax, int64_t max_steps, DevStatus *st) {
+    using K = typename Key<T>::K;
+    for (int64_t step = 0; step < max_steps; step++) {
+        // the maximum vertex of the tet
+        K kb = Key<T>::of(values[y]);
+        int64_t best = y;
+        int bl = -1;
+        for (int k = 0; k < 3; k++) {
+            int l = S.tet_v[h][k];
+            int64_t v = y + g.dlin[l];
+            K kv = Key<T>::of(values[v]);
+            if (kv > kb || (kv == kb && v > best)) { kb = kv; best = v; bl = l; }
+        }
+        if (bl >= 0) {   // re-express the tet in the star of its maximum vertex
+            uint16_t mask = 0;
+            int ox = -S.dx[bl], oy = -S.dy[bl], oz = -S.dz[bl];
+            int ly = S.link_of_dc[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
+            if (ly < 0) { atomicOr(&st->err, kErrState); return vmax; }
+            mask |= (uint16_t)(1u << ly);
+            for (int k = 0; k < 3; k++) {
+                int l = S.tet_v[h][k];
+                if (l == bl) continue;
+                int ex = S.dx[l] + ox, ey = S.dy[l] + oy, ez = S.dz[l] + oz;
+                if (ex < -1 || ex > 1 || ey < -1 || ey > 1 || ez < -1 || ez > 1) {
+                    atomicOr(&st->err, kErrState);
+                    return vmax;
+                }
+                int lk = S.link_of_dc[(ex + 1) + 3 * (ey + 1) + 9 * (ez + 1)];
+                if (lk < 0) { atomicOr(&st->err, kErrState); return vmax; }
+                mask |= (uint16_t)(1u << lk);
+            }
+            int hn = -1;
+            for (int q = 0; q < kTets; q++) if (S.tet_mask[q] == mask) hn = q;
+            if (hn < 0) { atomicOr(&st->err, kErrState); return vmax; }
+            y = best;
+            h = hn;
+        }
+        if (flags[y] & kFlagCritical) {
+            int32_t i = vrank[y];
+            CritRec rec = recs[i];
+            if (rec.crit_h >> h & 1) return base3[i] + local_index(S, rec, 3, h);
+        }
+        StarView sv;
+        load_star(S, g, values, y, sv);
+        PLSResult R;
+        pls(S, sv.lower, sv.rank, kQueryTet, h, R);
+        int s2 = R.q_pair;
+        if (s2 < 0) { atomicOr(&st->err, kErrState); return vmax; }
+        uint32_t other = S.tets_of_tri[s2] & ~(1u << h);
+        if (!other) { atomicOr(&st->err, kErrState); return vmax; }
+        int h2 = __ffs(other) - 1;
+        int w = __ffs(S.tet_mask[h2] & ~S.tri_mask[s2]) - 1;
+        if (!(sv.present >> w & 1)) return vmax;   // the outer boundary
+        h = h2;
+    }
+    atomicOr(&st->err, kErrIter);
+    return vmax;
+}
+
+template <typename T>
+__global__ void k_d2_arcs(const T *__restrict__ values, GridParams g,
+                          const uint8_t *__restrict__ flags, const int32_t *__restrict__ vrank,
+                          const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
+                          const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
+                          int64_t n2, int32_t vmax, int32_t *A, int32_t *B,
+                          int32_t *young, int64_t max_steps, DevStatus *st) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n2) return;
+    const StarTables &S = g_star;
+    int64_t x = v2[j];
+    int s = l2[j];
+    int cx, cy, cz;
+    coords(g, x, cx, cy, cz);
+    uint16_t pres = present_links(S, g, cx, cy, cz);
+    int32_t ends[2];
+    uint32_t m = S.tets_of_tri[s];
+    for (int e = 0; e < 2; e++) {
+        int h = __ffs(m) - 1;
+        m &= m - 1;
+        int w = __ffs(S.tet_mask[h] & ~S.tri_mask[s]) - 1;
+        ends[e] = (pres >> w & 1) ? ascend(S, g, values, flags, vrank, recs, base3, x, h, vmax,
+                                           max_steps, st)
+                                  : vmax;
+    }
+    A[j] = ends[0];
+    B[j] = ends[1];
+    young[j] = -1;
+}
+
+// ------------------------------------------ stage 6: D1 boundary tracing
+
+struct TraceCtx {
+    HeapEnt *heap;
+    HashEnt *hash;
+    int32_t *rows;
+    int hcap, hashmask, rcap;
+    int hn, rn, used;
+    int32_t gen;
+    bool overflow;
+};
+
+__device__ __forceinline__ uint32_t hash64(unsigned long long k) {
+    k ^= k >> 33; k *= 0xff51afd7ed558ccdull; k ^= k >> 33; k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return (uint32_t)k;
+}
+
+__device__ __forceinline__ bool heap_less(const HeapEnt &a, const HeapEnt &b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+__device__ void heap_push(TraceCtx &c, HeapEnt e) {
+    if (c.hn >= c.hcap) { c.overflow = true; return; }
+    int i = c.hn++;
+    while (i > 0) {
+        int p = (i - 1) >> 1;
+        if (!heap_less(c.heap[p], e)) break;
+        c.heap[i] = c.heap[p];
+        i = p;
+    }
+    c.heap[i] = e;
+}
+
+__device__ HeapEnt heap_pop(TraceCtx &c) {
+    HeapEnt top = c.heap[0];
+    HeapEnt last = c.heap[--c.hn];
+    int i = 0;
+    while (true) {
+        int l = 2 * i + 1;
+        if (l >= c.hn) break;
+        int r = l + 1;
+        int m = (r < c.hn && heap_less(c.heap[l], c.heap[r])) ? r : l;
+        if (!heap_less(last, c.heap[m])) break;
+        c.heap[i] = c.heap[m];
+        i = m;
+    }
+    if (c.hn > 0) c.heap[i] = last;
+    return top;
+}
+
+// Toggles (mod 2) edge (y, link m) of the expanding boundary.  Edges that are
+// heads of vertex->edge vectors and critical edges already paired in D0 are
+// dropped (they never carry the pivot; compression of Sec. 1.1 / 5).  A
+// regular edge is pushed on the max-heap keyed by (vertex order of its
+// maximum vertex y, classification order inside the lower star of y), which is
+// a topological order of the gradient paths, so that every regular edge is
+// expanded at most once.
+template <typename T>
+__device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams &g,
+                             const T *__restrict__ values, const uint8_t *__restrict__ flags,
+                             const int32_t *__restrict__ vrank, const CritRec *__restrict__ recs,
+                             const int32_t *__restrict__ base1, const uint8_t *__restrict__ is_row,
+                             int64_t y, int m, DevStatus *st) {
+    if (m < 0 || m >= kLinks) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
+    uint8_t fy = flags[y];
+    if ((fy & 0xF) == m) return;
+    unsigned long long key = (((unsigned long long)y << 4) | (unsigned)m) + 1;
+    uint32_t hpos = hash64(key) & c.hashmask;
+    HashEnt *slot = nullptr;
+    for (int p = 0; p <= c.hashmask; p++) {
+        HashEnt *e = &c.hash[(hpos + p) & c.hashmask];
+        if (e->gen != c.gen) { slot = e; break; }
+        if (e->key == key) { e->parity ^= 1; return; }
+    }
+    if (!slot || c.used * 4 >= (c.hashmask + 1) * 3) { c.overflow = true; return; }
+    int32_t row = -1;
+    uint8_t kind, pair = 0;
+    if (fy & kFlagCritical) {
+        int32_t i = vrank[y];
+        CritRec rec = recs[i];
+        if (rec.crit_e >> m & 1) {
+            int32_t j1 = base1[i] + local_index(S, rec, 1, m);
+            if (!is_row[j1]) return;            // paired in D0: dropped
+            if (c.rn >= c.rcap) { c.overflow = true; return; }
+            row = j1;
+            kind = kKindRow;
+            c.rows[c.rn++] = (int32_t)(slot - c.hash);
+            goto insert;
+        }
+    }
+    {
+        StarView sv;
+        load_star(S, g, values, y, sv);
+        PLSResult R;
+        pls(S, sv.lower, sv.rank, kQueryEdge, m, R);
+        if (R.q_pair < 0) { atomicOr(&st->err, kErrState); return; }
+        pair = (uint8_t)R.q_pair;
+        kind = kKindReg;
+        HeapEnt he;
+        he.hi = (unsigned long long)Key<T>::of(values[y]);
+        he.lo = ((unsigned long long)y << 12) | ((unsigned long long)R.q_order << 4) | (unsigned)m;
+        heap_push(c, he);
+        if (c.overflow) return;
+    }
+insert:
+    slot->key = key;
+    slot->gen = c.gen;
+    slot->row = row;
+    slot->parity = 1;
+    slot->kind = kind;
+    slot->pair = pair;
+    c.used++;
+}
+
+template <typename T>
+__device__ HashEnt *trace_find(TraceCtx &c, int64_t y, int m) {
+    unsigned long long key = (((unsigned long long)y << 4) | (unsigned)m) + 1;
+    uint32_t hpos = hash64(key) & c.hashmask;
+    for (int p = 0; p <= c.hashmask; p++) {
+        HashEnt *e = &c.hash[(hpos + p) & c.hashmask];
+        if (e->gen != c.gen) return nullptr;
+        if (e->key == key) return e;
+    }
+    return nullptr;
+}
+
+// One thread per column: the Morse boundary of a critical triangle restricted
+// to the rows (1-saddles not paired in D0), as a descending list of C1
+// indices appended to the column pool.
+template <typename T>
+__global__ void k_d1_trace(const T *__restrict__ values, GridParams g,
+                           const uint8_t *__restrict__ flags, const int32_t *__restrict__ vrank,
+                           const CritRec *__restrict__ recs, const int32_t *__restrict__ base1,
+                           const uint8_t *__restrict__ is_row, const int32_t *__restrict__ v2,
+                           const uint8_t *__restrict__ l2, const int32_t *__restrict__ colmap,
+                           const int32_t *__restrict__ todo, int64_t ntodo, HeapEnt *heap_all,
+                           HashEnt *hash_all, int32_t *rows_all, int hcap, int hashcap, int rcap,
+                           int32_t gen_base, int32_t *pool, int64_t pool_cap, int64_t *col_start,
+                           int32_t *col_len, uint8_t *overflow, DevStatus *st) {
+    const StarTables &S = g_star;
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    TraceCtx c;
+    c.heap = heap_all + tid * hcap;
+    c.hash = hash_all + tid * hashcap;
+    c.rows = rows_all + tid * rcap;
+    c.hcap = hcap; c.hashmask = hashcap - 1; c.rcap = rcap;
+    for (int64_t q = tid; q < ntodo; q += nth) {
+        int32_t cj = todo ? todo[q] : (int32_t)q;
+        int32_t j2 = colmap[cj];
+        int64_t x = v2[j2];
+        int s = l2[j2];
+        c.hn = 0; c.rn = 0; c.used = 0; c.overflow = false;
+        c.gen = gen_base + cj;
+        int a = S.tri_v[s][0], b = S.tri_v[s][1];
+        // boundary: (x,a), (x,b) and the edge between x+a and x+b
+        trace_toggle<T>(c, S, g, values, flags, vrank, recs, base1, is_row, x, a, st);
+        trace_toggle<T>(c, S, g, values, flags, vrank, recs, base1, is_row, x, b, st);
+        {
+            int64_t va = x + g.dlin[a], vb = x + g.dlin[b];
+            auto ka = Key<T>::of(values[va]), kb = Key<T>::of(values[vb]);
+            bool aup = ka > kb || (ka == kb && va > vb);
+            int hi = aup ? a : b, lo = aup ? b : a;
+            int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
+                                 9 * (S.dz[lo] - S.dz[hi] + 1)];
+            trace_toggle<T>(c, S, g, values, flags, vrank, recs, base1, is_row,
+                            x + g.dlin[hi], l, st);
+        }
+        while (c.hn > 0 && !c.overflow) {
+            HeapEnt top = heap_pop(c);
+            int64_t y = (int64_t)(top.lo >> 12);
+            int m = (int)(top.lo & 0xF);
+            HashEnt *e = trace_find<T>(c, y, m);
+            if (!e || !e->parity) continue;
+            e->parity = 0;
+            int sp = e->pair;
+            int ta = S.tri_v[sp][0], tb = S.tri_v[sp][1];
+            int other = ta == m ? tb : ta;
+            trace_toggle<T>(c, S, g, values, flags, vrank, recs, base1, is_row, y, other, st);
+            int64_t va = y + g.dlin[ta], vb = y + g.dlin[tb];
+            auto ka = Key<T>::of(values[va]), kb = Key<T>::of(values[vb]);
+            bool aup = ka > kb || (ka == kb && va > vb);
+            int hi = aup ? ta : tb, lo = aup ? tb : ta;
+            int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
+                                 9 * (S.dz[lo] - S.dz[hi] + 1)];
+            trace_toggle<T>(c, S, g, values, flags, vrank, recs, base1, is_row,
+                            y + g.dlin[hi], l, st);
+        }
+        if (c.overflow) {
+            overflow[cj] = 1;
+            col_len[cj] = 0;
+            continue;
+        }
+        // collect the rows with odd multiplicity, sorted decreasingly
+        int len = 0;
+        for (int k = 0; k < c.rn; k++) {
+            HashEnt *e = &c.hash[c.rows[k]];
+            if (e->parity) c.rows[len++] = e->row;
+        }
+        for (int k = 1; k < len; k++) {
+            int32_t v = c.rows[k];
+            int p = k;
+            while (p > 0 && c.rows[p - 1] < v) { c.rows[p] = c.rows[p - 1]; p--; }
+            c.rows[p] = v;
+        }
+        overflow[cj] = 0;
+        if (len == 0) { col_len[cj] = 0; col_start[cj] = 0; continue; }
+        unsigned long long pos = atomicAdd(&st->pool_top, (unsigned long long)len);
+        if ((int64_t)(pos + len) > pool_cap) {
+            atomicOr(&st->err, kErrCap);
+            col_len[cj] = 0;
+            continue;
+        }
+        for (int k = 0; k < len; k++) pool[pos + k] = c.rows[k];
+        col_start[cj] = (int64_t)pos;
+        col_len[cj] = len;
+    }
+}
+
+// --------------------------------------------- stage 7: D1 column reduction
+//
+// Standard reduction of the columns (increasing lexicographic order) with the
+// pivot = the largest row (Alg. 3 = reduction restricted to critical columns,
+// Sec. 4.2 (b)), run in rounds: every non-zero column claims its pivot with
+// an atomic minimum over column indices; a column that lost its pivot to an
+// earlier column adds that column's current boundary (mod 2).  The owner of a
+// pivot never changes in a round, so the boundary it adds is stable; the
+// owner of a row is always a column whose pivot is that row (the CAS
+// "temporary pairs" of Sec. 7.2, made round-synchronous).
+
+__global__ void k_red_claim(int64_t ncols, const int64_t *__restrict__ start,
+                            const int32_t *__restrict__ len, const int32_t *__restrict__ pool,
+                            int32_t *owner) {
+    int64_t cj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cj >= ncols || len[cj] == 0) return;
+    atomicMin(&owner[pool[start[cj]]], (int32_t)cj);
+}
+
+__global__ void k_red_add(int64_t ncols, int64_t *start, int32_t *len, int32_t *pool,
+                          const int32_t *__restrict__ owner, int64_t pool_cap, DevStatus *st) {
+    int64_t cj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cj >= ncols) return;
+    int la = len[cj];
+    if (la == 0) return;
+    int64_t sa = start[cj];
+    int32_t k = owner[pool[sa]];
+    if (k == cj) return;
+    int64_t sb = start[k];
+    int lb = len[k];
+    unsigned long long pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
+    if ((int64_t)(pos + la + lb) > pool_cap) { atomicOr(&st->err, kErrCap); return; }
+    int i = 0, q = 0, o = 0;
+    while (i < la || q < lb) {
+        int32_t x = i < la ? pool[sa + i] : -1, y = q < lb ? pool[sb + q] : -1;
+        if (x > y) { pool[pos + o++] = x; i++; }
+        else if (y > x) { pool[pos + o++] = y; q++; }
+        else { i++; q++; }                      // 1 + 1 = 0 (mod 2)
+    }
+    start[cj] = (int64_t)pos;
+    len[cj] = o;
+    atomicAdd(&st->changed, 1);
+}
+
+// ------------------------------------------------------ stage 8: output
+
+__device__ __forceinline__ uint64_t key_to_bits32(uint32_t k) {   // f32 keys
+    return (k & 0x80000000u) ? (uint64_t)(k ^ 0x80000000u) : (uint64_t)(~k);
+}
+
+template <typename T> __device__ __forceinline__ uint64_t fmax_bits(unsigned long long key);
+template <> __device__ __forceinline__ uint64_t fmax_bits<uint16_t>(unsigned long long key) {
+    return key;
+}
+template <> __device__ __forceinline__ uint64_t fmax_bits<float>(unsigned long long key) {
+    return key_to_bits32((uint32_t)key) & 0xffffffffull;
+}
+template <> __device__ __forceinline__ uint64_t fmax_bits<double>(unsigned long long key) {
+    return (key & 0x8000000000000000ull) ? (key ^ 0x8000000000000000ull) : ~key;
+}
+
+struct OutArgs {
+    const int32_t *vc;
+    const int32_t *v0;
+    const int32_t *v1; const uint8_t *l1;
+    const int32_t *v2; const uint8_t *l2;
+    const int32_t *v3; const uint8_t *l3;
+    const int32_t *young0, *young2;
+    const uint8_t *died0, *died3;
+    const int32_t *colmap;
+    const int64_t *col_start; const int32_t *col_len;
+    const int32_t *pool, *owner1;
+    const uint8_t *is_row, *is_col;
+};
+
+// flag kernels for the ordered output: one per (dimension, kind)
+__global__ void k_flag(int kind, OutArgs a, int64_t n, int32_t *flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int f = 0;
+    switch (kind) {
+        case 0: f = a.young0[i] >= 0; break;                          // D0 finite (C1)
+        case 2: f = a.col_len[i] > 0; break;                          // D1 finite (cols)
+        case 3: f = a.is_row[i] && a.owner1[i] == kNoOwner; break;    // D1 infinite (C1)
+        case 4: f = a.young2[i] >= 0; break;                          // D2 finite (C2)
+        case 5: f = a.col_len[i] == 0; break;                         // D2 infinite (cols)
+        case 6: f = !a.died3[i]; break;                               // D3 infinite (C3)
+    }
+    flag[i] = f;
+}
+
+// D0 infinite: minima never killed.  node ids of minima are their critical ranks.
+__global__ void k_flag_min(const int32_t *v0, int64_t n0, const int32_t *vrank,
+                           const uint8_t *died0, int32_t *flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n0) flag[i] = !died0[vrank[v0[i]]];
+}
+
+template <typename T>
+__global__ void k_write(int kind, OutArgs a, const T *__restrict__ values, GridParams g,
+                        int64_t n, const int32_t *__restrict__ flag,
+                        const int32_t *__restrict__ pos, int64_t offset, const int32_t *vrank,
+                        unsigned long long fmax_key, dms_pair *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flag[i]) return;
+    const StarTables &S = g_star;
+    dms_pair p;
+    memset(&p, 0, sizeof p);
+    int64_t bs = -1, ds = -1, bv = -1, dv = -1;
+    int dim = 0, ess = 0;
+    switch (kind) {
+        case 0: {   // D0: (minimum, critical edge)
+            bv = a.vc[a.young0[i]]; bs = bv;
+            dv = a.v1[i]; ds = edge_id(S, g, dv, a.l1[i]);
+            dim = 0; break;
+        }
+        case 1: {   // D0 infinite
+            bv = a.v0[i]; bs = bv; dim = 0; ess = 1; break;
+        }
+        case 2: {   // D1: (critical edge = pivot row, critical triangle)
+            int32_t row = a.pool[a.col_start[i]];
+            bv = a.v1[row]; bs = edge_id(S, g, bv, a.l1[row]);
+            int32_t j2 = a.colmap[i];
+            dv = a.v2[j2]; ds = tri_id(S, g, dv, a.l2[j2]);
+            dim = 1; break;
+        }
+        case 3: {
+            bv = a.v1[i]; bs = edge_id(S, g, bv, a.l1[i]); dim = 1; ess = 1; break;
+        }
+        case 4: {   // D2: (critical triangle, critical tet)
+            bv = a.v2[i]; bs = tri_id(S, g, bv, a.l2[i]);
+            int32_t t = a.young2[i];
+            dv = a.v3[t]; ds = tet_id(S, g, dv, a.l3[t]);
+            dim = 2; break;
+        }
+        case 5: {
+            int32_t j2 = a.colmap[i];
+            bv = a.v2[j2]; bs = tri_id(S, g, bv, a.l2[j2]); dim = 2; ess = 1; break;
+        }
+        case 6: {
+            bv = a.v3[i]; bs = tet_id(S, g, bv, a.l3[i]); dim = 3; ess = 1; break;
+        }
+    }
+    p.birth_simplex = bs; p.death_simplex = ds; p.birth_vertex = bv; p.death_vertex = dv;
+    p.birth_bits = Key<T>::bits(values[bv]);
+    p.death_bits = dv >= 0 ? Key<T>::bits(values[dv]) : fmax_bits<T>(fmax_key);
+    p.dim = (uint8_t)dim; p.essential = (uint8_t)ess;
+    out[offset + pos[i]] = p;
+}
+
+// ------------------------------------------------------ small helper kernels
+
+__global__ void k_unpaired(const int32_t *young, int64_t n, uint8_t *flag, int32_t *flag32) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { uint8_t f = young[i] < 0; flag[i] = f; if (flag32) flag32[i] = f; }
+}
+__global__ void k_compact_idx(const uint8_t *flag, const int32_t *pos, int64_t n, int32_t *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[pos[i]] = (int32_t)i;
+}
+
+// ------------------------------------------------------------- host side
+
+bool DevBuf::ensure(size_t need) {
+    if (need <= bytes && p) return true;
+    if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+    size_t b = need < 256 ? 256 : need;
+    if (cudaMalloc(&p, b) != cudaSuccess) { p = nullptr; cudaGetLastError(); return false; }
+    bytes = b;
+    return true;
+}
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+namespace {
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+struct Ctx {
+    Pipeline &P;
+    cudaStream_t s;
+    GridParams g;
+    DevStatus *st;
+    DevStatus *hst;
+    cudaEvent_t *ev;    // stage boundaries
+    cudaEvent_t *kev;   // kernel family start/end pairs
+    int64_t launches = 0;
+};
+#define KEV(i) cudaEventRecord(c.kev[i], c.s)
+
+uint32_t g_tables_ready = 0;   // one bit per device id (< 32)
+
+#define DMS_CUDA(call)                                                                 \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            fprintf(stderr, "libdms: %s failed: %s\n", #call, cudaGetErrorString(e_)); \
+            return DMS_ERR_CUDA;                                                       \
+        }                                                                              \
+    } while (0)
+#define DMS_TRY(x)                      \
+    do {                                \
+        dms_status s_ = (x);            \
+        if (s_ != DMS_OK) return s_;    \
+    } while (0)
+#define DMS_ALLOC(buf, nbytes)                               \
+    do {                                                     \
+        if (!(buf).ensure((size_t)(nbytes))) return DMS_ERR_OOM; \
+    } while (0)
+// launches a kernel over `count` items unless there are none
+#define DMS_LAUNCH(count, threads, kernel, ...)                                          \
+    do {                                                                                 \
+        if ((count) > 0) {                                                               \
+            kernel<<<blocks_for((count), (threads)), (threads), 0, c.s>>>(__VA_ARGS__);  \
+            c.launches++;                                                                \
+            cudaError_t e_ = cudaGetLastError();                                         \
+            if (e_ != cudaSuccess) {                                                     \
+                fprintf(stderr, "libdms: launch of %s failed: %s\n", #kernel,            \
+                        cudaGetErrorString(e_));                                         \
+                return DMS_ERR_CUDA;                                                     \
+            }                                                                            \
+        }                                                                                \
+    } while (0)
+
+dms_status ensure_tables(int device) {
+    if (device < 32 && (g_tables_ready >> device & 1)) return DMS_OK;
+    StarTables S;
+    if (!build_star_tables(S)) return DMS_ERR_STATE;
+    std::vector<uint32_t> lut;
+    build_regular_lut(S, lut);
+    DMS_CUDA(cudaMemcpyToSymbol(g_star, &S, sizeof S));
+    DMS_CUDA(cudaMemcpyToSymbol(g_regular, lut.data(), lut.size() * sizeof(uint32_t)));
+    if (device < 32) g_tables_ready |= 1u << device;
+    return DMS_OK;
+}
+
+// Exclusive scan of n int32 values into out; the total goes to *total.
+dms_status scan(Ctx &c, const int32_t *in, int32_t *out, int64_t n, long long *total) {
+    if (n == 0) {
+        DMS_CUDA(cudaMemsetAsync(total, 0, sizeof(long long), c.s));
+        return DMS_OK;
+    }
+    int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles == 1) {
+        k_scan_apply<<<1, kScanThreads, 0, c.s>>>(in, out, n, nullptr, total);
+        c.launches++;
+        return cudaGetLastError() == cudaSuccess ? DMS_OK : DMS_ERR_CUDA;
+    }
+    std::vector<int64_t> sizes;   // partial counts per level, all > 1
+    for (int64_t m = ntiles; m > 1; m = (m + kScanTile - 1) / kScanTile) sizes.push_back(m);
+    size_t need = 0;
+    for (int64_t m : sizes) need += 2 * (size_t)m;
+    if (!c.P.scan_tmp.ensure(4 * need + 1024)) return DMS_ERR_OOM;
+    int32_t *base = c.P.scan_tmp.as<int32_t>();
+    std::vector<const int32_t *> lin;
+    std::vector<int32_t *> loff;
+    const int32_t *cur = in;
+    int64_t curn = n;
+    size_t at = 0;
+    for (int64_t m : sizes) {
+        int32_t *part = base + at; at += m;
+        int32_t *off = base + at; at += m;
+        k_scan_partial<<<(unsigned)m, kScanThreads, 0, c.s>>>(cur, curn, part);
+        c.launches++;
+        lin.push_back(cur);
+        loff.push_back(off);
+        cur = part;
+        curn = m;
+    }
+    k_scan_apply<<<1, kScanThreads, 0, c.s>>>(cur, loff.back(), curn, nullptr, nullptr);
+    c.launches++;
+    for (int lv = (int)sizes.size() - 1; lv >= 0; lv--) {
+        int64_t lvn = lv == 0 ? n : sizes[lv - 1];
+        int32_t *lvout = lv == 0 ? out : loff[lv - 1];
+        k_scan_apply<<<(unsigned)sizes[lv], kScanThreads, 0, c.s>>>(lin[lv], lvout, lvn, loff[lv],
+                                                                    lv == 0 ? total : nullptr);
+        c.launches++;
+    }
+    return cudaGetLastError() == cudaSuccess ? DMS_OK : DMS_ERR_CUDA;
+}
+
+dms_status sync_status(Ctx &c) {
+    DMS_CUDA(cudaMemcpyAsync(c.hst, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.s));
+    DMS_CUDA(cudaStreamSynchronize(c.s));
+    if (c.hst->err & kErrNan) return DMS_ERR_NAN;
+    if (c.hst->err & kErrIter) return DMS_ERR_ITER_LIMIT;
+    if (c.hst->err & kErrCap) return DMS_ERR_CAPACITY;
+    if (c.hst->err & kErrState) return DMS_ERR_STATE;
+    return DMS_OK;
+}
+
+// Elder-rule pairing of one arc graph (D0: increasing order, older = smaller
+// node id; D2: decreasing order, older = larger node id).  Returns the number
+// of halving levels.
+dms_status elder_rule(Ctx &c, int64_t narcs, int descending, int older_is_larger, int32_t *young,
+                      uint8_t *died, int64_t *levels_out) {
+    Pipeline &P = c.P;
+    int32_t *A = P.arc_a.as<int32_t>(), *B = P.arc_b.as<int32_t>();
+    *levels_out = 0;
+    if (narcs == 0) return DMS_OK;
+    int L = 0;
+    while (((int64_t)1 << L) < narcs) L++;
+    uint32_t cap = 1024;
+    while ((int64_t)cap < 2 * narcs + 2) cap <<= 1;
+    DMS_ALLOC(P.dc_keys, 8 * (size_t)cap);
+    DMS_ALLOC(P.dc_par, 4 * (size_t)cap);
+    DMS_ALLOC(P.dc_lab, 4 * (size_t)cap);
+    auto *keys = P.dc_keys.as<unsigned long long>();
+    int32_t *par = P.dc_par.as<int32_t>(), *lab = P.dc_lab.as<int32_t>();
+    for (int shift = L; shift >= 1; shift--) {
+        DMS_CUDA(cudaMemsetAsync(keys, 0xFF, 8 * (size_t)cap, c.s));
+        DMS_LAUNCH(narcs, 256, k_dc_insert, narcs, shift, descending, A, B, keys, par, lab,
+                   cap - 1, c.st);
+        DMS_LAUNCH(narcs, 256, k_dc_union, narcs, shift, descending, older_is_larger, A, B, keys,
+                   par, lab, cap - 1, c.st);
+        DMS_LAUNCH(narcs, 256, k_dc_relabel, narcs, shift, descending, A, B, keys, par, lab,
+                   cap - 1);
+    }
+    DMS_LAUNCH(narcs, 256, k_dc_decide, narcs, older_is_larger, A, B, young, died);
+    *levels_out = L;
+    return DMS_OK;
+}
+
+template <typename T> dms_status run(Ctx &c, const T *values) {
+    using K = typename Key<T>::K;
+    Pipeline &P = c.P;
+    cudaEvent_t *ev = c.ev;
+    const int64_t n = P.n;
+    const int64_t max_steps = P.max_iters > 0 ? P.max_iters : n + 1;
+    DMS_CUDA(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s));
+
+    // ---- gradient: classification, compaction, sort, ProcessLowerStars
+    const int64_t ntiles = (n + kClsTile - 1) / kClsTile;
+    for (int i = 0; i < 24; i++) KEV(i);   // families that do not run read 0 ms
+    KEV(0);
+    k_classify<T><<<(unsigned)ntiles, kClsThreads, 0, c.s>>>(values, c.g, P.flags.as<uint8_t>(),
+                                                            P.tile_cnt.as<int32_t>(), c.st);
+    c.launches++;
+    DMS_CUDA(cudaGetLastError());
+    KEV(1);
+    DMS_TRY(scan(c, P.tile_cnt.as<int32_t>(), P.tile_off.as<int32_t>(), ntiles, &c.st->total[0]));
+    DMS_TRY(sync_status(c));
+    const int64_t nc = c.hst->total[0];
+    P.n_crit = nc;
+    DMS_ALLOC(P.vc, 4 * nc + 4);
+    DMS_ALLOC(P.vc_tmp, 4 * nc + 4);
+    DMS_ALLOC(P.keys, sizeof(K) * nc + 8);
+    DMS_ALLOC(P.keys_tmp, sizeof(K) * nc + 8);
+    DMS_ALLOC(P.recs, sizeof(CritRec) * nc + 8);
+    for (int d = 0; d < 4; d++) {
+        DMS_ALLOC(P.cnt[d], 4 * nc + 4);
+        DMS_ALLOC(P.base[d], 4 * nc + 4);
+    }
+    KEV(2);
+    k_compact<<<(unsigned)ntiles, kClsThreads, 0, c.s>>>(P.flags.as<uint8_t>(), n,
+                                                        P.tile_off.as<int32_t>(),
+                                                        P.vc.as<int32_t>());
+    c.launches++;
+    DMS_CUDA(cudaGetLastError());
+    KEV(3);
+    if (nc > 0) {
+        // stable LSD radix sort of the critical vertices (in id order) by value
+        KEV(4);
+        DMS_LAUNCH(nc, 256, k_gather_keys<T>, values, P.vc.as<int32_t>(), nc, P.keys.as<K>());
+        const int rtiles = (int)((nc + kRsTile - 1) / kRsTile);
+        DMS_ALLOC(P.flag_a, 4 * (size_t)256 * rtiles);
+        DMS_ALLOC(P.flag_b, 4 * (size_t)256 * rtiles);
+        K *kin = P.keys.as<K>(), *kout = P.keys_tmp.as<K>();
+        int32_t *vin = P.vc.as<int32_t>(), *vout = P.vc_tmp.as<int32_t>();
+        for (int shift = 0; shift < (int)(8 * sizeof(T)); shift += 8) {
+            k_rs_hist<K><<<rtiles, kRsThreads, 0, c.s>>>(kin, nc, shift, P.flag_a.as<int32_t>(),
+                                                        rtiles);
+            c.launches++;
+            DMS_TRY(scan(c, P.flag_a.as<int32_t>(), P.flag_b.as<int32_t>(), (int64_t)256 * rtiles,
+                         &c.st->total[1]));
+            k_rs_scatter<K><<<rtiles, kRsThreads, 0, c.s>>>(kin, vin, kout, vout, nc, shift,
+                                                           P.flag_b.as<int32_t>(), rtiles);
+            c.launches++;
+            DMS_CUDA(cudaGetLastError());
+            std::swap(kin, kout);
+            std::swap(vin, vout);
+        }
+        if (vin != P.vc.as<int32_t>()) {
+            std::swap(P.vc, P.vc_tmp);
+            std::swap(P.keys, P.keys_tmp);
+        }
+        KEV(5);
+        KEV(6);
+        DMS_LAUNCH(nc, 128, k_pls<T>, values, c.g, P.vc.as<int32_t>(), nc, P.recs.as<CritRec>(),
+                   P.cnt[0].as<int32_t>(), P.cnt[1].as<int32_t>(), P.cnt[2].as<int32_t>(),
+                   P.cnt[3].as<int32_t>(), P.vrank.as<int32_t>());
+        KEV(7);
+    }
+    cudaEventRecord(ev[2], c.s);
+
+    // ---- critical simplices C0..C3 in lexicographic order
+    for (int d = 0; d < 4; d++)
+        DMS_TRY(scan(c, P.cnt[d].as<int32_t>(), P.base[d].as<int32_t>(), nc, &c.st->total[d]));
+    DMS_TRY(sync_status(c));
+    for (int d = 0; d < 4; d++) P.n_c[d] = c.hst->total[d];
+    const int64_t n0 = P.n_c[0], n1 = P.n_c[1], n2 = P.n_c[2], n3 = P.n_c[3];
+    for (int d = 0; d < 4; d++) {
+        DMS_ALLOC(P.c_vert[d], 4 * P.n_c[d] + 4);
+        DMS_ALLOC(P.c_loc[d], P.n_c[d] + 4);
+    }
+    KEV(8);
+    DMS_LAUNCH(nc, 128, k_emit, P.vc.as<int32_t>(), nc, P.recs.as<CritRec>(),
+               P.base[0].as<int32_t>(), P.base[1].as<int32_t>(), P.base[2].as<int32_t>(),
+               P.base[3].as<int32_t>(), P.c_vert[0].as<int32_t>(), P.c_vert[1].as<int32_t>(),
+               P.c_loc[1].as<uint8_t>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
+               P.c_vert[3].as<int32_t>(), P.c_loc[3].as<uint8_t>());
+    KEV(9);
+    cudaEventRecord(ev[3], c.s);
+
+    // union-find state shared by D0 and D2; results kept for the output
+    const int64_t narc_max = std::max(n1, n2);
+    DMS_ALLOC(P.arc_a, 4 * narc_max + 4);
+    DMS_ALLOC(P.arc_b, 4 * narc_max + 4);
+    DMS_ALLOC(P.young, 4 * (n1 + n2) + 8);
+    DMS_ALLOC(P.died, nc + n3 + 16);
+    int32_t *young0 = P.young.as<int32_t>(), *young2 = young0 + n1;
+    uint8_t *died0 = P.died.as<uint8_t>(), *died3 = died0 + nc;
+    DMS_CUDA(cudaMemsetAsync(died0, 0, nc + n3 + 1, c.s));
+
+    // ---- D0: arcs between minima, elder rule in increasing order
+    KEV(10);
+    DMS_LAUNCH(n1, 256, k_d0_arcs, c.g, P.flags.as<uint8_t>(), P.vrank.as<int32_t>(),
+               P.c_vert[1].as<int32_t>(), P.c_loc[1].as<uint8_t>(), n1, P.arc_a.as<int32_t>(),
+               P.arc_b.as<int32_t>(), young0, max_steps, c.st);
+    KEV(11);
+    KEV(12);
+    DMS_TRY(elder_rule(c, n1, 0, 0, young0, died0, &P.rounds_d0));
+    KEV(13);
+    cudaEventRecord(ev[4], c.s);
+
+    // ---- D2: arcs between maxima (node n3 = the virtual maximum), decreasing
+    const int32_t vmax = (int32_t)n3;
+    KEV(14);
+    DMS_LAUNCH(n2, 128, k_d2_arcs<T>, values, c.g, P.flags.as<uint8_t>(), P.vrank.as<int32_t>(),
+               P.recs.as<CritRec>(), P.base[3].as<int32_t>(), P.c_vert[2].as<int32_t>(),
+               P.c_loc[2].as<uint8_t>(), n2, vmax, P.arc_a.as<int32_t>(), P.arc_b.as<int32_t>(),
+               young2, max_steps, c.st);
+    KEV(15);
+    KEV(16);
+    DMS_TRY(elder_rule(c, n2, 1, 1, young2, died3, &P.rounds_d2));
+    KEV(17);
+    DMS_TRY(sync_status(c));
+    cudaEventRecord(ev[5], c.s);
+
+    // ---- D1: rows = C1 not paired in D0, columns = C2 not paired in D2
+    DMS_ALLOC(P.rowcol, n1 + n2 + 16);
+    uint8_t *is_row = P.rowcol.as<uint8_t>(), *is_col = is_row + n1;
+    DMS_ALLOC(P.flag_a, 4 * (n2 + 4));
+    DMS_ALLOC(P.flag_b, 4 * (n2 + 4));
+    DMS_LAUNCH(n1, 256, k_unpaired, young0, n1, is_row, (int32_t *)nullptr);
+    DMS_LAUNCH(n2, 256, k_unpaired, young2, n2, is_col, P.flag_a.as<int32_t>());
+    DMS_TRY(scan(c, P.flag_a.as<int32_t>(), P.flag_b.as<int32_t>(), n2, &c.st->total[2]));
+    DMS_TRY(sync_status(c));
+    const int64_t ncols = c.hst->total[2];
+    P.d1_cols = ncols;
+    DMS_ALLOC(P.d1_colmap, 4 * ncols + 4);
+    DMS_ALLOC(P.d1_start, 8 * ncols + 8);
+    DMS_ALLOC(P.d1_len, 4 * ncols + 4);
+    DMS_ALLOC(P.d1_owner, 4 * n1 + 4);
+    DMS_ALLOC(P.d1_ovf, ncols + 4);
+    DMS_LAUNCH(n2, 256, k_compact_idx, is_col, P.flag_b.as<int32_t>(), n2, P.d1_colmap.as<int32_t>());
+    DMS_CUDA(cudaMemsetAsync(P.d1_owner.p, 0x7F, 4 * n1 + 4, c.s));
+    DMS_CUDA(cudaMemsetAsync(P.d1_len.p, 0, 4 * ncols + 4, c.s));
+    int64_t pool_cap = std::max<int64_t>(1 << 20, 64 * ncols + 1024);
+    DMS_ALLOC(P.d1_pool, 4 * pool_cap);
+    P.rounds_d1 = 0;
+    if (ncols > 0) {
+        uint8_t *ovf = P.d1_ovf.as<uint8_t>();
+        DMS_CUDA(cudaMemsetAsync(ovf, 0, ncols, c.s));
+        DMS_CUDA(cudaMemsetAsync(&c.st->pool_top, 0, sizeof(unsigned long long), c.s));
+        int hcap = 256, hashcap = 512, rcap = 256;
+        int64_t nthreads = 152 * 2 * 128;
+        if (ncols < nthreads) nthreads = (ncols + 127) / 128 * 128;
+        size_t per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
+                     (size_t)rcap * 4;
+        DMS_ALLOC(P.d1_scratch, per * nthreads);
+        HeapEnt *heap = P.d1_scratch.as<HeapEnt>();
+        HashEnt *hash = (HashEnt *)(heap + (size_t)hcap * nthreads);
+        int32_t *rows = (int32_t *)(hash + (size_t)hashcap * nthreads);
+        DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nthreads * sizeof(HashEnt), c.s));
+        KEV(18);
+        k_d1_trace<T><<<(unsigned)(nthreads / 128), 128, 0, c.s>>>(
+            values, c.g, P.flags.as<uint8_t>(), P.vrank.as<int32_t>(), P.recs.as<CritRec>(),
+            P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
+            P.d1_colmap.as<int32_t>(), nullptr, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,
+            P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+            ovf, c.st);
+        c.launches++;
+        DMS_CUDA(cudaGetLastError());
+        // columns whose trace outgrew the scratch run again with 16x more
+        std::vector<uint8_t> hovf(ncols);
+        DMS_CUDA(cudaMemcpyAsync(hovf.data(), ovf, ncols, cudaMemcpyDeviceToHost, c.s));
+        DMS_TRY(sync_status(c));
+        std::vector<int32_t> todo;
+        for (int64_t q = 0; q < ncols; q++)
+            if (hovf[q]) todo.push_back((int32_t)q);
+        int32_t gen = (int32_t)ncols;
+        while (!todo.empty()) {
+            hcap *= 16; hashcap *= 16; rcap *= 16;
+            if (hashcap > (1 << 24)) return DMS_ERR_CAPACITY;
+            per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
+                  (size_t)rcap * 4;
+            int64_t nt = std::min<int64_t>((int64_t)todo.size(),
+                                           std::max<int64_t>(32, ((int64_t)4 << 30) / (int64_t)per));
+            nt = (nt + 31) / 32 * 32;
+            DMS_ALLOC(P.d1_scratch, per * nt);
+            heap = P.d1_scratch.as<HeapEnt>();
+            hash = (HashEnt *)(heap + (size_t)hcap * nt);
+            rows = (int32_t *)(hash + (size_t)hashcap * nt);
+            DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nt * sizeof(HashEnt), c.s));
+            DMS_ALLOC(P.d1_todo, 4 * todo.size());
+            DMS_CUDA(cudaMemcpyAsync(P.d1_todo.p, todo.data(), 4 * todo.size(),
+                                     cudaMemcpyHostToDevice, c.s));
+            k_d1_trace<T><<<(unsigned)(nt / 32), 32, 0, c.s>>>(
+                values, c.g, P.flags.as<uint8_t>(), P.vrank.as<int32_t>(), P.recs.as<CritRec>(),
+                P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(),
+                P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), P.d1_todo.as<int32_t>(),
+                (int64_t)todo.size(), heap, hash, rows, hcap, hashcap, rcap, gen,
+                P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(),
+                P.d1_len.as<int32_t>(), ovf, c.st);
+            c.launches++;
+            DMS_CUDA(cudaGetLastError());
+            gen += (int32_t)ncols;
+            DMS_CUDA(cudaMemcpyAsync(hovf.data(), ovf, ncols, cudaMemcpyDeviceToHost, c.s));
+            DMS_TRY(sync_status(c));
+            std::vector<int32_t> next;
+            for (int32_t q : todo)
+                if (hovf[q]) next.push_back(q);
+            todo.swap(next);
+        }
+        KEV(19);
+        // reduction rounds
+        KEV(20);
+        const int64_t limit = P.max_iters > 0 ? P.max_iters : ((int64_t)1 << 22);
+        bool done = false;
+        for (int64_t r = 0; r < limit && !done; r++) {
+            DMS_CUDA(cudaMemsetAsync(&c.st->changed, 0, sizeof(int), c.s));
+            DMS_LAUNCH(ncols, 256, k_red_claim, ncols, P.d1_start.as<int64_t>(),
+                       P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), P.d1_owner.as<int32_t>());
+            DMS_LAUNCH(ncols, 256, k_red_add, ncols, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+                       P.d1_pool.as<int32_t>(), P.d1_owner.as<int32_t>(), pool_cap, c.st);
+            DMS_TRY(sync_status(c));
+            P.rounds_d1 = r + 1;
+            done = c.hst->changed == 0;
+        }
+        if (!done) return DMS_ERR_ITER_LIMIT;
+        KEV(21);
+    }
+    cudaEventRecord(ev[6], c.s);
+    KEV(22);
+
+    // ---- output: per dimension, finite pairs (ordered by the simplex that
+    // indexes them) then the infinite classes
+    OutArgs a;
+    a.vc = P.vc.as<int32_t>();
+    a.v0 = P.c_vert[0].as<int32_t>();
+    a.v1 = P.c_vert[1].as<int32_t>(); a.l1 = P.c_loc[1].as<uint8_t>();
+    a.v2 = P.c_vert[2].as<int32_t>(); a.l2 = P.c_loc[2].as<uint8_t>();
+    a.v3 = P.c_vert[3].as<int32_t>(); a.l3 = P.c_loc[3].as<uint8_t>();
+    a.young0 = young0; a.young2 = young2; a.died0 = died0; a.died3 = died3;
+    a.colmap = P.d1_colmap.as<int32_t>();
+    a.col_start = P.d1_start.as<int64_t>(); a.col_len = P.d1_len.as<int32_t>();
+    a.pool = P.d1_pool.as<int32_t>(); a.owner1 = P.d1_owner.as<int32_t>();
+    a.is_row = is_row; a.is_col = is_col;
+    // parts: 0 D0 finite (over C1), 1 D0 infinite (C0), 2 D1 finite (columns),
+    // 3 D1 infinite (C1), 4 D2 finite (C2), 5 D2 infinite (columns), 6 D3 infinite (C3)
+    const int64_t part_n[7] = {n1, n0, ncols, n1, n2, ncols, n3};
+    const int part_dim[7] = {0, 0, 1, 1, 2, 2, 3};
+    int64_t foff[8] = {0};
+    for (int q = 0; q < 7; q++) foff[q + 1] = foff[q] + part_n[q] + 1;
+    DMS_ALLOC(P.flag_a, 4 * foff[7] + 4);
+    DMS_ALLOC(P.flag_b, 4 * foff[7] + 4);
+    int32_t *fl = P.flag_a.as<int32_t>(), *ps = P.flag_b.as<int32_t>();
+    for (int q = 0; q < 7; q++) {
+        if (q == 1)
+            DMS_LAUNCH(part_n[q], 256, k_flag_min, a.v0, part_n[q], P.vrank.as<int32_t>(), died0,
+                       fl + foff[q]);
+        else
+            DMS_LAUNCH(part_n[q], 256, k_flag, q, a, part_n[q], fl + foff[q]);
+        DMS_TRY(scan(c, fl + foff[q], ps + foff[q], part_n[q], &c.st->parts[q]));
+    }
+    DMS_TRY(sync_status(c));
+    int64_t cntp[7];
+    for (int q = 0; q < 7; q++) cntp[q] = c.hst->parts[q];
+    for (int d = 0; d < 3; d++) {
+        int64_t rows = cntp[2 * d] + cntp[2 * d + 1];
+        DMS_ALLOC(P.out_pairs[d], sizeof(dms_pair) * (rows + 1));
+    }
+    for (int q = 0; q < 6; q++) {
+        int d = part_dim[q];
+        int64_t off = (q & 1) ? cntp[q - 1] : 0;
+        DMS_LAUNCH(part_n[q], 128, k_write<T>, q, a, values, c.g, part_n[q], fl + foff[q],
+                   ps + foff[q], off, P.vrank.as<int32_t>(), c.hst->maxkey,
+                   P.out_pairs[d].as<dms_pair>());
+    }
+    P.n_pairs[0] = cntp[0]; P.n_pairs[1] = cntp[2]; P.n_pairs[2] = cntp[4];
+    P.n_ess[0] = cntp[1]; P.n_ess[1] = cntp[3]; P.n_ess[2] = cntp[5]; P.n_ess[3] = cntp[6];
+    KEV(23);
+    cudaEventRecord(ev[7], c.s);
+    DMS_TRY(sync_status(c));
+    return DMS_OK;
+}
+
+}  // namespace
+
+dms_status Pipeline::init(int64_t nx_, int64_t ny_, int64_t nz_, dms_dtype dt,
+                          const dms_options *o) {
+    if (nx_ < 1 || ny_ < 1 || nz_ < 1 || nx_ > (1 << 30) || ny_ > (1 << 30) || nz_ > (1 << 30))
+        return DMS_ERR_INVALID_ARG;
+    if (nx_ * ny_ >= ((int64_t)1 << 31) || nx_ * ny_ * nz_ >= ((int64_t)1 << 31))
+        return DMS_ERR_INVALID_ARG;
+    if (dt != DMS_U16 && dt != DMS_F32 && dt != DMS_F64) return DMS_ERR_INVALID_ARG;
+    if (o && o->virtual_max != 1) return DMS_ERR_INVALID_ARG;
+    if (o && o->max_iters < 0) return DMS_ERR_INVALID_ARG;
+    nx = nx_; ny = ny_; nz = nz_; n = nx * ny * nz; dtype = dt;
+    max_iters = o ? o->max_iters : 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return DMS_ERR_CUDA;
+    dms_status s = ensure_tables(device);
+    if (s != DMS_OK) return s;
+    const int64_t ntiles = (n + kClsTile - 1) / kClsTile;
+    if (!flags.ensure(n) || !vrank.ensure(4 * n) || !tile_cnt.ensure(4 * ntiles) ||
+        !tile_off.ensure(4 * ntiles) || !dstat.ensure(sizeof(DevStatus)))
+        return DMS_ERR_OOM;
+    if (cudaMallocHost(&hstat, sizeof(DevStatus)) != cudaSuccess) {
+        hstat = nullptr;
+        return DMS_ERR_OOM;
+    }
+    for (int i = 0; i < 24; i++)
+        if (cudaEventCreate((cudaEvent_t *)&kev[i]) != cudaSuccess) return DMS_ERR_CUDA;
+    for (int i = 0; i < 8; i++)
+        if (cudaEventCreate((cudaEvent_t *)&sev[i]) != cudaSuccess) return DMS_ERR_CUDA;
+    return DMS_OK;
+}
+
+void Pipeline::destroy() {
+    DevBuf *all[] = {&values_dev, &flags,    &vrank,     &tile_cnt,  &tile_off,   &vc,
+                     &vc_tmp,     &keys,     &keys_tmp,  &recs,      &arc_a,      &arc_b,
+                     &dc_keys,    &dc_par,   &dc_lab,    &young,     &died,       &rowcol,
+                     &flag_a,     &flag_b,   &d1_colmap, &d1_start,  &d1_len,     &d1_owner,
+                     &d1_ovf,     &d1_pool,  &d1_scratch, &d1_todo,  &scan_tmp,   &dstat};
+    for (DevBuf *b : all) b->release();
+    for (int d = 0; d < 4; d++) {
+        cnt[d].release(); base[d].release(); c_vert[d].release(); c_loc[d].release();
+    }
+    for (int d = 0; d < 3; d++) out_pairs[d].release();
+    if (hstat) cudaFreeHost(hstat);
+    hstat = nullptr;
+    for (int i = 0; i < 24; i++) if (kev[i]) cudaEventDestroy((cudaEvent_t)kev[i]);
+    for (int i = 0; i < 8; i++) if (sev[i]) cudaEventDestroy((cudaEvent_t)sev[i]);
+    for (int i = 0; i < 24; i++) kev[i] = nullptr;
+    for (int i = 0; i < 8; i++) sev[i] = nullptr;
+}
+
+dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
+    has_result = false;
+    if (!values || (on_host != 0 && on_host != 1)) return DMS_ERR_INVALID_ARG;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return DMS_ERR_CUDA;
+    if (cur != device && cudaSetDevice(device) != cudaSuccess) return DMS_ERR_CUDA;
+    cudaEvent_t *ev = (cudaEvent_t *)sev, *kv = (cudaEvent_t *)kev;
+    Ctx c{*this, (cudaStream_t)stream};
+    c.kev = kv;
+    c.st = dstat.as<DevStatus>();
+    c.hst = (DevStatus *)hstat;
+    c.ev = ev;
+    c.g.nx = (int32_t)nx; c.g.ny = (int32_t)ny; c.g.nz = (int32_t)nz; c.g.n = n;
+    for (int l = 0; l < kLinks; l++) {
+        int o = l % 7 + 1, sg = l < 7 ? 1 : -1;
+        c.g.dlin[l] = sg * ((o & 1) + (int32_t)nx * (((o >> 1) & 1) + (int32_t)ny * ((o >> 2) & 1)));
+    }
+    const size_t esz = dtype == DMS_U16 ? 2 : dtype == DMS_F32 ? 4 : 8;
+    dms_status s = DMS_OK;
+    cudaEventRecord(ev[0], c.s);
+    const void *dv = values;
+    if (on_host) {
+        if (!values_dev.ensure(n * esz)) s = DMS_ERR_OOM;
+        else if (cudaMemcpyAsync(values_dev.p, values, n * esz, cudaMemcpyHostToDevice, c.s) !=
+                 cudaSuccess)
+            s = DMS_ERR_CUDA;
+        dv = values_dev.p;
+    }
+    cudaEventRecord(ev[1], c.s);
+    if (s == DMS_OK) {
+        if (dtype == DMS_U16) s = run<uint16_t>(c, (const uint16_t *)dv);
+        else if (dtype == DMS_F32) s = run<float>(c, (const float *)dv);
+        else s = run<double>(c, (const double *)dv);
+    }
+    launches = c.launches;
+    if (s == DMS_OK) {
+        cudaEventSynchronize(ev[7]);
+        float t = 0;
+        // 0 start, 1 after H2D, 2 gradient, 3 sort, 4 D0, 5 D2, 6 D1, 7 output
+        const int from[8] = {1, 2, 3, 4, 5, 6, 1, 0}, to[8] = {2, 3, 4, 5, 6, 7, 7, 1};
+        for (int k = 0; k < 8; k++) {
+            cudaEventElapsedTime(&t, ev[from[k]], ev[to[k]]);
+            stage_ms[k] = t;
+        }
+        if (!on_host) stage_ms[7] = 0.f;
+        for (int k = 0; k < 12; k++) {
+            cudaEventElapsedTime(&t, kv[2 * k], kv[2 * k + 1]);
+            kernel_ms[k] = t;
+        }
+        has_result = true;
+    } else {
+        cudaStreamSynchronize(c.s);
+        cudaGetLastError();
+    }
+    return s;
+}
+
+dms_status Pipeline::fetch(int dim, dms_pair *out, int64_t cap, int64_t *written,
+                           int out_is_device) {
+    if (!written) return DMS_ERR_INVALID_ARG;
+    *written = 0;
+    if (!has_result) return DMS_ERR_STATE;
+    if (dim < 0 || dim > 2) return DMS_ERR_INVALID_ARG;
+    const int64_t total = n_pairs[dim] + n_ess[dim];
+    if (total > cap) return DMS_ERR_CAPACITY;
+    if (total == 0) return DMS_OK;
+    if (!out) return DMS_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpy(out, out_pairs[dim].p, sizeof(dms_pair) * total,
+                               out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return DMS_ERR_CUDA;
+    *written = total;
+    return DMS_OK;
+}
+
+}  // namespace dms

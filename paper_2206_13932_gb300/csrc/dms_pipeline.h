@@ -1,0 +1,59 @@
+// dms_pipeline.h -- host-side pipeline of libdms (one grid, one stream).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/dms.h"
+
+namespace dms {
+
+// A growable device allocation owned by the pipeline.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    bool ensure(size_t need);          // grows (never shrinks); false on OOM
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct Pipeline {
+    int64_t nx = 0, ny = 0, nz = 0, n = 0;
+    dms_dtype dtype = DMS_F32;
+    int64_t max_iters = 0;
+    int device = 0;
+
+    // grid-sized state
+    DevBuf values_dev;      // copy of host values (values_on_host = 1)
+    DevBuf flags;           // u8 per vertex: descent link | critical flag
+    DevBuf vrank;           // i32 per vertex: position among sorted critical vertices
+    DevBuf tile_cnt, tile_off;
+    // critical-count-sized state
+    DevBuf vc, vc_tmp, keys, keys_tmp, recs;
+    DevBuf cnt[4], base[4];
+    DevBuf c_vert[4], c_loc[4];
+    DevBuf arc_a, arc_b, young, died, rowcol, flag_a, flag_b;
+    DevBuf dc_keys, dc_par, dc_lab;   // elder-rule halving levels
+    DevBuf d1_colmap, d1_start, d1_len, d1_owner, d1_ovf, d1_pool, d1_scratch, d1_todo;
+    DevBuf out_pairs[3];
+    DevBuf scan_tmp;
+    DevBuf dstat;           // device status words
+    void *hstat = nullptr;  // pinned host mirror
+
+    int64_t n_crit = 0, n_c[4] = {0, 0, 0, 0};
+    int64_t n_pairs[3] = {0, 0, 0}, n_ess[4] = {0, 0, 0, 0};
+    int64_t launches = 0, rounds_d0 = 0, rounds_d2 = 0, rounds_d1 = 0  /* D0/D2: halving levels */, d1_cols = 0;
+    float stage_ms[8] = {0};
+    float kernel_ms[12] = {0};
+    void *kev[24] = {nullptr};   // cudaEvent_t pairs per kernel family
+    void *sev[8] = {nullptr};    // cudaEvent_t stage boundaries
+    bool has_result = false;
+
+    dms_status init(int64_t nx, int64_t ny, int64_t nz, dms_dtype dt, const dms_options *o);
+    dms_status compute(const void *values, int on_host, void *stream);
+    dms_status fetch(int dim, dms_pair *out, int64_t cap, int64_t *written, int out_is_device);
+    void destroy();
+};
+
+}  // namespace dms
