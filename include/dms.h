@@ -54,7 +54,11 @@ typedef enum { DMS_U16 = 0, DMS_F32 = 1, DMS_F64 = 2 } dms_dtype;
 typedef struct {
     int virtual_max;      /* 1 (the only supported value): Sec. 5.2 virtual
                              maximum on the outer boundary                   */
-    int64_t max_iters;    /* cap on device round loops; 0 = default          */
+    int64_t max_iters;    /* cap on device loops and path lengths; 0 = default */
+    int d1_mode;          /* D1 reduction: 0 = default (1), 1 = reduce the
+                             2-saddle columns (Alg. 3 order), 2 = reduce their
+                             anti-transpose (persistent cohomology; the same
+                             pairs)                                           */
 } dms_options;
 
 /* One persistence pair (or infinite class) of the result.
@@ -115,9 +119,12 @@ dms_status dms_fetch_pairs(dms_grid grid, int dim, dms_pair *out, int64_t cap,
 dms_status dms_get_stage_ms(dms_grid grid, float ms[8]);
 
 /* Statistics of the last compute: [0] critical vertices, [1..4] critical
- * simplices of dimension 0..3, [5] kernel launches, [6] D0 rounds,
- * [7] D2 rounds, [8] D1 reduction rounds, [9] D1 columns. */
-dms_status dms_get_stats(dms_grid grid, int64_t stats[10]);
+ * simplices of dimension 0..3, [5] kernel launches, [6] D0 halving levels,
+ * [7] D2 halving levels, [8] D1 reduction rounds, [9] D1 columns, [10] D1
+ * columns whose boundary outgrew the first scratch pass, [11] D1 column
+ * additions, [12] D1 column-pool entries used, [13] D1 pool regrowths,
+ * [14..15] reserved (0). */
+dms_status dms_get_stats(dms_grid grid, int64_t stats[16]);
 
 /* Device milliseconds of the last compute per kernel family, from CUDA event
  * pairs recorded on the compute stream around the launches (host round trips

@@ -38,7 +38,8 @@ class DmsError(RuntimeError):
 
 
 class _Options(ctypes.Structure):
-    _fields_ = [("virtual_max", ctypes.c_int), ("max_iters", ctypes.c_int64)]
+    _fields_ = [("virtual_max", ctypes.c_int), ("max_iters", ctypes.c_int64),
+                ("d1_mode", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -83,13 +84,13 @@ def _check(st: int, where: str):
 class Grid:
     """A handle of ``dms_grid``: one grid shape and dtype, reusable across fields."""
 
-    def __init__(self, shape_xyz, dtype, max_iters: int = 0):
+    def __init__(self, shape_xyz, dtype, max_iters: int = 0, d1_mode: int = 0):
         self._lib = load()
         self.shape_xyz = tuple(int(s) for s in shape_xyz)
         self.dtype = np.dtype(dtype)
         if self.dtype not in _DTYPE_CODE:
             raise TypeError(f"unsupported dtype {self.dtype}")
-        opts = _Options(1, int(max_iters))
+        opts = _Options(1, int(max_iters), int(d1_mode))
         h = ctypes.c_void_p()
         nx, ny, nz = self.shape_xyz
         _check(self._lib.dms_grid_create(nx, ny, nz, _DTYPE_CODE[self.dtype],
@@ -185,10 +186,11 @@ class Grid:
         return dict(zip(self.KERNELS, [float(x) for x in ms]))
 
     def stats(self):
-        s = (ctypes.c_int64 * 10)()
+        s = (ctypes.c_int64 * 16)()
         _check(self._lib.dms_get_stats(self._h, s), "dms_get_stats")
-        names = ("critical_vertices", "c0", "c1", "c2", "c3", "launches", "rounds_d0",
-                 "rounds_d2", "rounds_d1", "d1_columns")
+        names = ("critical_vertices", "c0", "c1", "c2", "c3", "launches", "levels_d0",
+                 "levels_d2", "rounds_d1", "d1_columns", "d1_trace_overflow", "d1_additions",
+                 "d1_pool_used", "d1_pool_grows")
         return dict(zip(names, [int(x) for x in s]))
 
 

@@ -53,7 +53,7 @@ dms_status dms_get_stage_ms(dms_grid grid, float ms[8]) {
     return DMS_OK;
 }
 
-dms_status dms_get_stats(dms_grid grid, int64_t stats[10]) {
+dms_status dms_get_stats(dms_grid grid, int64_t stats[16]) {
     if (!grid || !stats) return DMS_ERR_INVALID_ARG;
     if (!grid->p.has_result) return DMS_ERR_STATE;
     const dms::Pipeline &p = grid->p;
@@ -64,6 +64,11 @@ dms_status dms_get_stats(dms_grid grid, int64_t stats[10]) {
     stats[7] = p.rounds_d2;
     stats[8] = p.rounds_d1;
     stats[9] = p.d1_cols;
+    stats[10] = p.d1_overflow;
+    stats[11] = p.d1_additions;
+    stats[12] = p.d1_pool_used;
+    stats[13] = p.d1_pool_grows;
+    for (int k = 14; k < 16; k++) stats[k] = 0;
     return DMS_OK;
 }
 

@@ -22,6 +22,7 @@ constexpr uint64_t kAllTris = (1ull << kTris) - 1;
 constexpr uint32_t kAllTets = (1u << kTets) - 1;
 constexpr uint8_t kNoDescent = 0xF;   // flags low nibble of a minimum
 constexpr uint8_t kFlagCritical = 0x10;
+constexpr uint8_t kFlagGradient = 0x20;   // the vertex's GradRec is filled
 
 struct StarTables {
     int8_t dx[kLinks], dy[kLinks], dz[kLinks];
@@ -177,11 +178,35 @@ struct PLSResult {
     uint32_t crit_h;       // critical star tets
     uint64_t crit_t;       // critical star triangles
     bool is_min;
-    int8_t q_pair;         // query answer (see pls())
-    int8_t q_order;        // query: classification order of the queried edge
 };
 
-enum { kQueryNone = 0, kQueryTet = 1, kQueryEdge = 2 };
+// The gradient of one lower star, packed (40 bytes):
+//   tet h of the lower star  -> the star triangle it is paired with (6 bits,
+//                               kNone if critical or not in the lower star)
+//   edge n of the lower star -> the star triangle it is paired with, kHead
+//                               if it is paired with the vertex, kNone if
+//                               critical or not lower; plus the order (4 bits)
+//                               in which the lower star's edges were
+//                               classified.
+// Layout: w[0] tets 0-9, w[1] tets 10-19, w[2] tets 20-23 (bits 0-23) and
+// edge pairs 0-5 (bits 24-59), w[3] edge pairs 6-13, w[4] edge orders 0-13.
+constexpr int kNone = 63, kHead = 62;
+struct GradRec {
+    uint64_t w[5];
+};
+
+__device__ __forceinline__ int grad_tet_pair(const GradRec &g, int h) {
+    int word = h < 10 ? 0 : h < 20 ? 1 : 2;
+    int bit = 6 * (h - 10 * word);
+    return (int)((g.w[word] >> bit) & 63);
+}
+__device__ __forceinline__ int grad_edge_pair(const GradRec &g, int n) {
+    if (n < 6) return (int)((g.w[2] >> (24 + 6 * n)) & 63);
+    return (int)((g.w[3] >> (6 * (n - 6))) & 63);
+}
+__device__ __forceinline__ int grad_edge_order(const GradRec &g, int n) {
+    return (int)((g.w[4] >> (4 * n)) & 15);
+}
 
 __device__ __forceinline__ uint16_t code_edge(const uint8_t *r, int n) {
     return (uint16_t)((r[n] + 1) << 8);
@@ -200,16 +225,30 @@ __device__ __forceinline__ uint16_t code_tet(const StarTables &S, const uint8_t 
     return (uint16_t)(((a + 1) << 8) | ((b + 1) << 4) | (c + 1));
 }
 
-// Query kQueryTet (cell = star tet h): q_pair = the star triangle paired with
-// h, or -1 if h is critical.  kQueryEdge (cell = link n): q_pair = the star
-// triangle paired with edge n, -2 if n is paired with the vertex, -1 if
-// critical; q_order = the order in which the edges of the lower star were
-// classified (0 = first).
-__device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank, int qkind,
-                           int qcell, PLSResult &R) {
+// With G non-null the whole pairing of the lower star is packed into *G.
+__device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank, PLSResult &R,
+                           GradRec *G) {
     R.crit_e = 0; R.crit_h = 0; R.crit_t = 0; R.is_min = false;
-    R.q_pair = -1; R.q_order = -1;
-    if (L == 0) { R.is_min = true; return; }
+    uint8_t tpair[kTets], epair[kLinks], eord[kLinks];
+    if (G) {
+        for (int h = 0; h < kTets; h++) tpair[h] = kNone;
+        for (int n = 0; n < kLinks; n++) { epair[n] = kNone; eord[n] = 0; }
+    }
+    auto pack = [&]() {
+        if (!G) return;
+        uint64_t w[5] = {0, 0, 0, 0, 0};
+        for (int h = 0; h < kTets; h++) {
+            int word = h < 10 ? 0 : h < 20 ? 1 : 2;
+            w[word] |= (uint64_t)tpair[h] << (6 * (h - 10 * word));
+        }
+        for (int n = 0; n < kLinks; n++) {
+            if (n < 6) w[2] |= (uint64_t)epair[n] << (24 + 6 * n);
+            else w[3] |= (uint64_t)epair[n] << (6 * (n - 6));
+            w[4] |= (uint64_t)(eord[n] & 15) << (4 * n);
+        }
+        for (int k = 0; k < 5; k++) G->w[k] = w[k];
+    };
+    if (L == 0) { R.is_min = true; pack(); return; }
 
     // lower star cells
     uint64_t LT = kAllTris;
@@ -252,7 +291,7 @@ __device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank,
     int n0 = -1;
     for (uint16_t m = L; m; m &= m - 1) { int n = __ffs(m) - 1; if (rank[n] == 0) n0 = n; }
     cE = (uint16_t)(1u << n0);
-    if (qkind == kQueryEdge && qcell == n0) { R.q_pair = -2; R.q_order = (int8_t)eorder; }
+    if (G) { epair[n0] = kHead; eord[n0] = (uint8_t)eorder; }
     eorder++;
     zE = (uint16_t)(L & ~cE);
     push_cof_edge(n0);
@@ -277,7 +316,7 @@ __device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank,
                 if (u == 0) { zT |= 1ull << s; continue; }
                 int n = __ffs(u) - 1;                  // the unique unclassified edge
                 cE |= (uint16_t)(1u << n); cT |= 1ull << s; zE &= (uint16_t)~(1u << n);
-                if (qkind == kQueryEdge && qcell == n) { R.q_pair = (int8_t)s; R.q_order = (int8_t)eorder; }
+                if (G) { epair[n] = (uint8_t)s; eord[n] = (uint8_t)eorder; }
                 eorder++;
                 push_cof_tri(s);
                 push_cof_edge(n);
@@ -289,7 +328,7 @@ __device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank,
                 if (u == 0) { zH |= 1u << h; continue; }
                 int s = __ffsll(u) - 1;                // the unique unclassified face
                 cT |= 1ull << s; cH |= 1u << h; zT &= ~(1ull << s);
-                if (qkind == kQueryTet && qcell == h) R.q_pair = (int8_t)s;
+                if (G) tpair[h] = (uint8_t)s;
                 push_cof_tri(s);
             }
         }
@@ -311,7 +350,7 @@ __device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank,
         }
         if (bd == 1) {
             zE &= (uint16_t)~(1u << bi); cE |= (uint16_t)(1u << bi); R.crit_e |= (uint16_t)(1u << bi);
-            if (qkind == kQueryEdge && qcell == bi) { R.q_pair = -1; R.q_order = (int8_t)eorder; }
+            if (G) eord[bi] = (uint8_t)eorder;
             eorder++;
             push_cof_edge(bi);
         } else if (bd == 2) {
@@ -321,6 +360,7 @@ __device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank,
             zH &= ~(1u << bi); cH |= 1u << bi; R.crit_h |= 1u << bi;
         }
     }
+    pack();
 }
 
 // Code of a critical cell of a lower star from packed 4-bit ranks.

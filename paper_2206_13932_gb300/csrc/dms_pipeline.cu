@@ -17,6 +17,7 @@
 //   output     pairs and infinite classes (Sec. 6).
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -467,7 +468,7 @@ template <typename T>
 __global__ void k_pls(const T *__restrict__ values, GridParams g,
                       const int32_t *__restrict__ vc, int64_t nc, CritRec *recs,
                       int32_t *cnt0, int32_t *cnt1, int32_t *cnt2, int32_t *cnt3,
-                      int32_t *vrank) {
+                      int32_t *vrank, uint8_t *flags, GradRec *grad) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     const StarTables &S = g_star;
@@ -475,7 +476,10 @@ __global__ void k_pls(const T *__restrict__ values, GridParams g,
     StarView sv;
     load_star(S, g, values, x, sv);
     PLSResult R;
-    pls(S, sv.lower, sv.rank, kQueryNone, 0, R);
+    GradRec G;
+    pls(S, sv.lower, sv.rank, R, &G);
+    grad[x] = G;
+    flags[x] = (uint8_t)(flags[x] | kFlagGradient);
     uint64_t packed = 0;
     for (int n = 0; n < kLinks; n++)
         packed |= (uint64_t)((sv.lower >> n & 1) ? sv.rank[n] : 0xF) << (4 * n);
@@ -707,6 +711,35 @@ __global__ void k_dc_decide(int64_t narcs, int older_is_larger, const int32_t *A
     died[y] = 1;
 }
 
+// ------------------------------------------- the gradient, memoised lazily
+//
+// The pairing of a lower star is computed once per vertex and per compute:
+// by k_pls for the critical vertices, on first use for the others.  Two
+// threads may fill the same record; they write identical bytes.  The record
+// is stored before the flag bit is set (with a fence) and read through L2,
+// so a reader that sees the bit sees the record.
+template <typename T>
+__device__ __forceinline__ GradRec grad_get(const StarTables &S, const GridParams &g,
+                                            const T *__restrict__ values, uint8_t *flags,
+                                            GradRec *grad, int64_t y) {
+    GradRec G;
+    if (((volatile const uint8_t *)flags)[y] & kFlagGradient) {
+        const unsigned long long *src = (const unsigned long long *)&grad[y];
+        for (int k = 0; k < 5; k++) G.w[k] = __ldcg(src + k);
+        return G;
+    }
+    StarView sv;
+    load_star(S, g, values, y, sv);
+    PLSResult R;
+    pls(S, sv.lower, sv.rank, R, &G);
+    unsigned long long *dst = (unsigned long long *)&grad[y];
+    for (int k = 0; k < 5; k++) __stcg(dst + k, G.w[k]);
+    __threadfence();
+    volatile uint8_t *f = (volatile uint8_t *)flags;
+    f[y] = (uint8_t)(f[y] | kFlagGradient);
+    return G;
+}
+
 // ------------------------------------------------------ stage 5: D2 arcs
 
 // The critical tet (node index) or the virtual maximum reached from tet h of
@@ -715,7 +748,7 @@ __global__ void k_dc_decide(int64_t narcs, int older_is_larger, const int32_t *A
 // its other tet; the outer boundary is the virtual maximum.
 template <typename T>
 __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__restrict__ values,
-                          const uint8_t *__restrict__ flags, const int32_t *__restrict__ vrank,
+                          uint8_t *flags, GradRec *grad, const int32_t *__restrict__ vrank,
                           const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
                           int64_t y, int h, int32_t vmax, int64_t max_steps, DevStatus *st) {
     using K = typename Key<T>::K;
@@ -759,17 +792,16 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
             CritRec rec = recs[i];
             if (rec.crit_h >> h & 1) return base3[i] + local_index(S, rec, 3, h);
         }
-        StarView sv;
-        load_star(S, g, values, y, sv);
-        PLSResult R;
-        pls(S, sv.lower, sv.rank, kQueryTet, h, R);
-        int s2 = R.q_pair;
-        if (s2 < 0) { atomicOr(&st->err, kErrState); return vmax; }
+        GradRec G = grad_get(S, g, values, flags, grad, y);
+        int s2 = grad_tet_pair(G, h);
+        if (s2 >= kTris) { atomicOr(&st->err, kErrState); return vmax; }
         uint32_t other = S.tets_of_tri[s2] & ~(1u << h);
         if (!other) { atomicOr(&st->err, kErrState); return vmax; }
         int h2 = __ffs(other) - 1;
         int w = __ffs(S.tet_mask[h2] & ~S.tri_mask[s2]) - 1;
-        if (!(sv.present >> w & 1)) return vmax;   // the outer boundary
+        int cx, cy, cz;
+        coords(g, y, cx, cy, cz);
+        if (!(present_links(S, g, cx, cy, cz) >> w & 1)) return vmax;   // the outer boundary
         h = h2;
     }
     atomicOr(&st->err, kErrIter);
@@ -777,8 +809,8 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
 }
 
 template <typename T>
-__global__ void k_d2_arcs(const T *__restrict__ values, GridParams g,
-                          const uint8_t *__restrict__ flags, const int32_t *__restrict__ vrank,
+__global__ void k_d2_arcs(const T *__restrict__ values, GridParams g, uint8_t *flags,
+                          GradRec *grad, const int32_t *__restrict__ vrank,
                           const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
                           const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
                           int64_t n2, int32_t vmax, int32_t *A, int32_t *B,
@@ -797,8 +829,8 @@ __global__ void k_d2_arcs(const T *__restrict__ values, GridParams g,
         int h = __ffs(m) - 1;
         m &= m - 1;
         int w = __ffs(S.tet_mask[h] & ~S.tri_mask[s]) - 1;
-        ends[e] = (pres >> w & 1) ? ascend(S, g, values, flags, vrank, recs, base3, x, h, vmax,
-                                           max_steps, st)
+        ends[e] = (pres >> w & 1) ? ascend(S, g, values, flags, grad, vrank, recs, base3, x, h,
+                                           vmax, max_steps, st)
                                   : vmax;
     }
     A[j] = ends[0];
@@ -866,7 +898,7 @@ __device__ HeapEnt heap_pop(TraceCtx &c) {
 // expanded at most once.
 template <typename T>
 __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams &g,
-                             const T *__restrict__ values, const uint8_t *__restrict__ flags,
+                             const T *__restrict__ values, uint8_t *flags, GradRec *grad,
                              const int32_t *__restrict__ vrank, const CritRec *__restrict__ recs,
                              const int32_t *__restrict__ base1, const uint8_t *__restrict__ is_row,
                              int64_t y, int m, DevStatus *st) {
@@ -898,16 +930,15 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
         }
     }
     {
-        StarView sv;
-        load_star(S, g, values, y, sv);
-        PLSResult R;
-        pls(S, sv.lower, sv.rank, kQueryEdge, m, R);
-        if (R.q_pair < 0) { atomicOr(&st->err, kErrState); return; }
-        pair = (uint8_t)R.q_pair;
+        GradRec G = grad_get(S, g, values, flags, grad, y);
+        int sp = grad_edge_pair(G, m);
+        if (sp >= kTris) { atomicOr(&st->err, kErrState); return; }
+        pair = (uint8_t)sp;
         kind = kKindReg;
         HeapEnt he;
         he.hi = (unsigned long long)Key<T>::of(values[y]);
-        he.lo = ((unsigned long long)y << 12) | ((unsigned long long)R.q_order << 4) | (unsigned)m;
+        he.lo = ((unsigned long long)y << 12) | ((unsigned long long)grad_edge_order(G, m) << 4) |
+                (unsigned)m;
         heap_push(c, he);
         if (c.overflow) return;
     }
@@ -937,8 +968,8 @@ __device__ HashEnt *trace_find(TraceCtx &c, int64_t y, int m) {
 // to the rows (1-saddles not paired in D0), as a descending list of C1
 // indices appended to the column pool.
 template <typename T>
-__global__ void k_d1_trace(const T *__restrict__ values, GridParams g,
-                           const uint8_t *__restrict__ flags, const int32_t *__restrict__ vrank,
+__global__ void k_d1_trace(const T *__restrict__ values, GridParams g, uint8_t *flags,
+                           GradRec *grad, const int32_t *__restrict__ vrank,
                            const CritRec *__restrict__ recs, const int32_t *__restrict__ base1,
                            const uint8_t *__restrict__ is_row, const int32_t *__restrict__ v2,
                            const uint8_t *__restrict__ l2, const int32_t *__restrict__ colmap,
@@ -963,8 +994,8 @@ __global__ void k_d1_trace(const T *__restrict__ values, GridParams g,
         c.gen = gen_base + cj;
         int a = S.tri_v[s][0], b = S.tri_v[s][1];
         // boundary: (x,a), (x,b) and the edge between x+a and x+b
-        trace_toggle<T>(c, S, g, values, flags, vrank, recs, base1, is_row, x, a, st);
-        trace_toggle<T>(c, S, g, values, flags, vrank, recs, base1, is_row, x, b, st);
+        trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, x, a, st);
+        trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, x, b, st);
         {
             int64_t va = x + g.dlin[a], vb = x + g.dlin[b];
             auto ka = Key<T>::of(values[va]), kb = Key<T>::of(values[vb]);
@@ -972,7 +1003,7 @@ __global__ void k_d1_trace(const T *__restrict__ values, GridParams g,
             int hi = aup ? a : b, lo = aup ? b : a;
             int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
                                  9 * (S.dz[lo] - S.dz[hi] + 1)];
-            trace_toggle<T>(c, S, g, values, flags, vrank, recs, base1, is_row,
+            trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row,
                             x + g.dlin[hi], l, st);
         }
         while (c.hn > 0 && !c.overflow) {
@@ -985,14 +1016,14 @@ __global__ void k_d1_trace(const T *__restrict__ values, GridParams g,
             int sp = e->pair;
             int ta = S.tri_v[sp][0], tb = S.tri_v[sp][1];
             int other = ta == m ? tb : ta;
-            trace_toggle<T>(c, S, g, values, flags, vrank, recs, base1, is_row, y, other, st);
+            trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, y, other, st);
             int64_t va = y + g.dlin[ta], vb = y + g.dlin[tb];
             auto ka = Key<T>::of(values[va]), kb = Key<T>::of(values[vb]);
             bool aup = ka > kb || (ka == kb && va > vb);
             int hi = aup ? ta : tb, lo = aup ? tb : ta;
             int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
                                  9 * (S.dz[lo] - S.dz[hi] + 1)];
-            trace_toggle<T>(c, S, g, values, flags, vrank, recs, base1, is_row,
+            trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row,
                             y + g.dlin[hi], l, st);
         }
         if (c.overflow) {
@@ -1037,38 +1068,252 @@ __global__ void k_d1_trace(const T *__restrict__ values, GridParams g,
 // owner of a row is always a column whose pivot is that row (the CAS
 // "temporary pairs" of Sec. 7.2, made round-synchronous).
 
-__global__ void k_red_claim(int64_t ncols, const int64_t *__restrict__ start,
-                            const int32_t *__restrict__ len, const int32_t *__restrict__ pool,
-                            int32_t *owner) {
-    int64_t cj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cj >= ncols || len[cj] == 0) return;
-    atomicMin(&owner[pool[start[cj]]], (int32_t)cj);
+// Appends v to list[*count] with one atomic per warp (all active lanes call).
+__device__ __forceinline__ void warp_append(bool take, int32_t v, int32_t *list,
+                                            unsigned long long *count) {
+    unsigned m = __ballot_sync(__activemask(), take);
+    if (!m) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
+    base = __shfl_sync(__activemask(), base, leader);
+    if (take) list[base + __popc(m & lanemask_lt())] = v;
 }
 
-__global__ void k_red_add(int64_t ncols, int64_t *start, int32_t *len, int32_t *pool,
-                          const int32_t *__restrict__ owner, int64_t pool_cap, DevStatus *st) {
-    int64_t cj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cj >= ncols) return;
-    int la = len[cj];
-    if (la == 0) return;
-    int64_t sa = start[cj];
-    int32_t k = owner[pool[sa]];
-    if (k == cj) return;
-    int64_t sb = start[k];
-    int lb = len[k];
-    unsigned long long pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
-    if ((int64_t)(pos + la + lb) > pool_cap) { atomicOr(&st->err, kErrCap); return; }
-    int i = 0, q = 0, o = 0;
-    while (i < la || q < lb) {
-        int32_t x = i < la ? pool[sa + i] : -1, y = q < lb ? pool[sb + q] : -1;
-        if (x > y) { pool[pos + o++] = x; i++; }
-        else if (y > x) { pool[pos + o++] = y; q++; }
-        else { i++; q++; }                      // 1 + 1 = 0 (mod 2)
+// Active columns (new pivots since the previous round) claim their pivots;
+// a claim that displaces a later owner queues that owner for a recheck.
+__global__ void k_red_claim(const int32_t *__restrict__ active, int64_t nactive,
+                            const int64_t *__restrict__ start, const int32_t *__restrict__ len,
+                            const int32_t *__restrict__ pool, int32_t *owner, int32_t *recheck,
+                            DevStatus *st) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool take = false;
+    int32_t old = 0;
+    if (q < nactive) {
+        int32_t cj = active[q];
+        if (len[cj] > 0) {
+            old = atomicMin(&owner[pool[start[cj]]], cj);
+            take = old != kNoOwner && old > cj;
+        }
     }
-    start[cj] = (int64_t)pos;
-    len[cj] = o;
-    atomicAdd(&st->changed, 1);
+    warp_append(take, old, recheck, (unsigned long long *)&st->misc[0]);
 }
+
+// Merge path split of two decreasing lists: how many of the first d
+// elements of their merge (ties: A first) come from A.  A tie that would
+// straddle the split is moved to the earlier side, so that equal entries of A
+// and B always meet in the same segment.
+__device__ __forceinline__ void merge_split(const int32_t *A, int la, const int32_t *B, int lb,
+                                            int d, int &i, int &j) {
+    int lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (A[mid] >= B[d - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    i = lo;
+    j = d - lo;
+    if (i > 0 && j < lb && A[i - 1] == B[j]) j++;
+}
+
+// out = A + B (mod 2) for decreasing lists, by one warp; returns the length.
+__device__ int warp_symdiff(const int32_t *A, int la, const int32_t *B, int lb, int32_t *out) {
+    const int lane = threadIdx.x & 31;
+    const int L = la + lb, per = (L + 31) >> 5;
+    int i0, j0, i1, j1;
+    merge_split(A, la, B, lb, min(lane * per, L), i0, j0);
+    merge_split(A, la, B, lb, min(lane * per + per, L), i1, j1);
+    int cnt = 0;
+    {
+        int i = i0, j = j0;
+        while (i < i1 || j < j1) {
+            int32_t x = i < i1 ? A[i] : -1, y = j < j1 ? B[j] : -1;
+            if (x > y) { cnt++; i++; }
+            else if (y > x) { cnt++; j++; }
+            else { i++; j++; }
+        }
+    }
+    int inc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    int total = __shfl_sync(0xffffffffu, inc, 31);
+    int o = inc - cnt;
+    int i = i0, j = j0;
+    while (i < i1 || j < j1) {
+        int32_t x = i < i1 ? A[i] : -1, y = j < j1 ? B[j] : -1;
+        if (x > y) { out[o++] = x; i++; }
+        else if (y > x) { out[o++] = y; j++; }
+        else { i++; j++; }                      // 1 + 1 = 0 (mod 2)
+    }
+    return total;
+}
+
+// One warp per listed column (active or displaced): while its pivot is owned
+// by an earlier column, add that column (mod 2).  Owners never change inside
+// this kernel (a column owns a row only while the row is its pivot, and
+// claims happen in k_red_claim), so every column added is stable.  Stops at
+// its own pivot, an unclaimed pivot or one claimed by a later column (those
+// claim it in the next round).  A column listed twice is processed once.
+__global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
+                          const int32_t *__restrict__ recheck, int64_t *start, int32_t *len,
+                          int32_t *pool, const int32_t *__restrict__ owner, int32_t *stamp,
+                          int32_t round, int32_t *next, int64_t pool_cap, DevStatus *st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nre = *(volatile long long *)&st->misc[0];
+    unsigned adds = 0, longest = 0;
+    for (int64_t q = warp; q < nactive + nre; q += nwarps) {
+        int32_t cj = q < nactive ? active[q] : recheck[q - nactive];
+        int fresh = 0;
+        if (lane == 0) fresh = atomicExch(&stamp[cj], round) != round;
+        if (!__shfl_sync(0xffffffffu, fresh, 0)) continue;
+        int la = len[cj];
+        int64_t sa = start[cj];
+        bool changed = false;
+        unsigned chain = 0;
+        for (int it = 0; la > 0 && it < (1 << 24); it++) {
+            int32_t k = owner[pool[sa]];
+            if (k == cj || k == kNoOwner || k > cj) break;
+            int64_t sb = start[k];
+            int lb = len[k];
+            unsigned long long pos = 0;
+            if (lane == 0) pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if ((int64_t)(pos + la + lb) > pool_cap) {
+                if (lane == 0) atomicOr(&st->err, kErrCap);
+                break;
+            }
+            la = warp_symdiff(pool + sa, la, pool + sb, lb, pool + pos);
+            sa = (int64_t)pos;
+            changed = true;
+            chain++;
+        }
+        adds += chain;
+        longest = max(longest, chain);
+        if (changed && lane == 0) {
+            start[cj] = sa;
+            len[cj] = la;
+            if (la > 0) next[atomicAdd((unsigned long long *)&st->misc[1], 1ull)] = cj;
+        }
+    }
+    if (lane == 0 && adds) {
+        atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)adds);
+        atomicMax((unsigned long long *)&st->misc[3], (unsigned long long)longest);
+    }
+}
+
+__global__ void k_iota32(int32_t *p, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (int32_t)i;
+}
+
+// ---- the anti-transpose of the column set (persistent cohomology): the
+// rows, in decreasing order, become columns whose entries are the original
+// columns, also reversed (entry kappa = ncols-1-c), so that the pivot (the
+// largest entry) is the oldest column.  Reducing it yields the same pairs.
+
+// rho(r) = nrows-1-rowpos[r] for the rows (critical edges not paired in D0)
+__global__ void k_co_count(int64_t ncols, const int64_t *__restrict__ start,
+                           const int32_t *__restrict__ len, const int32_t *__restrict__ pool,
+                           const int32_t *__restrict__ rowpos, int64_t nrows, int32_t *cnt) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    int64_t s0 = start[c];
+    for (int k = 0; k < len[c]; k++) atomicAdd(&cnt[nrows - 1 - rowpos[pool[s0 + k]]], 1);
+}
+
+__global__ void k_co_scatter(int64_t ncols, const int64_t *__restrict__ start,
+                             const int32_t *__restrict__ len, const int32_t *__restrict__ pool,
+                             const int32_t *__restrict__ rowpos, int64_t nrows,
+                             const int32_t *__restrict__ costart, int32_t *fill, int32_t *copool) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    int64_t s0 = start[c];
+    int32_t kappa = (int32_t)(ncols - 1 - c);
+    for (int k = 0; k < len[c]; k++) {
+        int64_t rho = nrows - 1 - rowpos[pool[s0 + k]];
+        int32_t at = atomicAdd(&fill[rho], 1);
+        copool[costart[rho] + at] = kappa;
+    }
+}
+
+// sorts each cocolumn decreasingly (heap sort in place)
+__global__ void k_co_sort(int64_t nrows, const int32_t *__restrict__ costart,
+                          const int32_t *__restrict__ cnt, int32_t *copool, int64_t *start) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    int32_t *a = copool + costart[r];
+    int n = cnt[r];
+    start[r] = costart[r];
+    if (n <= 16) {
+        for (int i = 1; i < n; i++) {
+            int32_t v = a[i];
+            int p = i;
+            while (p > 0 && a[p - 1] < v) { a[p] = a[p - 1]; p--; }
+            a[p] = v;
+        }
+        return;
+    }
+    // min-heap sort gives decreasing order
+    auto sift = [&](int i, int m) {
+        while (true) {
+            int l = 2 * i + 1, b = i;
+            if (l < m && a[l] < a[b]) b = l;
+            if (l + 1 < m && a[l + 1] < a[b]) b = l + 1;
+            if (b == i) return;
+            int32_t t = a[i]; a[i] = a[b]; a[b] = t;
+            i = b;
+        }
+    };
+    for (int i = n / 2 - 1; i >= 0; i--) sift(i, n);
+    for (int m = n - 1; m > 0; m--) {
+        int32_t t = a[0]; a[0] = a[m]; a[m] = t;
+        sift(0, m);
+    }
+}
+
+// per-column D1 partner row (-1: the column stays unpaired) and row flags
+__global__ void k_d1_result_homology(int64_t ncols, const int64_t *__restrict__ start,
+                                     const int32_t *__restrict__ len,
+                                     const int32_t *__restrict__ pool, int32_t *d1_row,
+                                     uint8_t *row_paired) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    int32_t r = len[c] > 0 ? pool[start[c]] : -1;
+    d1_row[c] = r;
+    if (r >= 0) row_paired[r] = 1;
+}
+
+__global__ void k_d1_result_cohomology(int64_t nrows, int64_t ncols,
+                                       const int64_t *__restrict__ start,
+                                       const int32_t *__restrict__ len,
+                                       const int32_t *__restrict__ pool,
+                                       const int32_t *__restrict__ rowmap, int32_t *d1_row,
+                                       uint8_t *row_paired) {
+    int64_t rho = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rho >= nrows || len[rho] == 0) return;
+    int32_t kappa = pool[start[rho]];
+    int32_t r = rowmap[nrows - 1 - rho];
+    d1_row[ncols - 1 - kappa] = r;
+    row_paired[r] = 1;
+}
+
+// copies the live columns into a fresh pool (after an overflow)
+__global__ void k_pool_compact(int64_t ncol, int64_t *start, const int32_t *__restrict__ len,
+                               const int32_t *__restrict__ off, const int32_t *__restrict__ src,
+                               int32_t *dst) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncol) return;
+    int64_t s0 = start[c];
+    int32_t o = off[c];
+    for (int k = 0; k < len[c]; k++) dst[o + k] = src[s0 + k];
+    start[c] = o;
+}
+
 
 // ------------------------------------------------------ stage 8: output
 
@@ -1096,8 +1341,8 @@ struct OutArgs {
     const int32_t *young0, *young2;
     const uint8_t *died0, *died3;
     const int32_t *colmap;
-    const int64_t *col_start; const int32_t *col_len;
-    const int32_t *pool, *owner1;
+    const int32_t *d1_row;          // per column: paired row (C1 index) or -1
+    const uint8_t *row_paired;      // per C1 index: paired in D1
     const uint8_t *is_row, *is_col;
 };
 
@@ -1108,10 +1353,10 @@ __global__ void k_flag(int kind, OutArgs a, int64_t n, int32_t *flag) {
     int f = 0;
     switch (kind) {
         case 0: f = a.young0[i] >= 0; break;                          // D0 finite (C1)
-        case 2: f = a.col_len[i] > 0; break;                          // D1 finite (cols)
-        case 3: f = a.is_row[i] && a.owner1[i] == kNoOwner; break;    // D1 infinite (C1)
+        case 2: f = a.d1_row[i] >= 0; break;                          // D1 finite (cols)
+        case 3: f = a.is_row[i] && !a.row_paired[i]; break;           // D1 infinite (C1)
         case 4: f = a.young2[i] >= 0; break;                          // D2 finite (C2)
-        case 5: f = a.col_len[i] == 0; break;                         // D2 infinite (cols)
+        case 5: f = a.d1_row[i] < 0; break;                           // D2 infinite (cols)
         case 6: f = !a.died3[i]; break;                               // D3 infinite (C3)
     }
     flag[i] = f;
@@ -1146,7 +1391,7 @@ __global__ void k_write(int kind, OutArgs a, const T *__restrict__ values, GridP
             bv = a.v0[i]; bs = bv; dim = 0; ess = 1; break;
         }
         case 2: {   // D1: (critical edge = pivot row, critical triangle)
-            int32_t row = a.pool[a.col_start[i]];
+            int32_t row = a.d1_row[i];
             bv = a.v1[row]; bs = edge_id(S, g, bv, a.l1[row]);
             int32_t j2 = a.colmap[i];
             dv = a.v2[j2]; ds = tri_id(S, g, dv, a.l2[j2]);
@@ -1181,6 +1426,10 @@ __global__ void k_write(int kind, OutArgs a, const T *__restrict__ values, GridP
 __global__ void k_unpaired(const int32_t *young, int64_t n, uint8_t *flag, int32_t *flag32) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) { uint8_t f = young[i] < 0; flag[i] = f; if (flag32) flag32[i] = f; }
+}
+__global__ void k_u8_to_i32(const uint8_t *in, int64_t n, int32_t *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i];
 }
 __global__ void k_compact_idx(const uint8_t *flag, const int32_t *pos, int64_t n, int32_t *out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1352,6 +1601,141 @@ dms_status elder_rule(Ctx &c, int64_t narcs, int descending, int older_is_larger
     return DMS_OK;
 }
 
+// Reduces a set of columns (entries sorted decreasingly, pivot first) stored
+// in P.d1_pool at P.d1_start/P.d1_len, claiming pivots in owner[0..nent).
+// Rounds continue until no column changes; on a pool overflow the live
+// columns are compacted into a larger pool and the round is repeated.
+dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used) {
+    Pipeline &P = c.P;
+    DMS_ALLOC(P.d1_owner, 4 * nent + 4);
+    DMS_ALLOC(P.d1_act, 4 * ncol + 4);
+    DMS_ALLOC(P.d1_next, 4 * ncol + 4);
+    DMS_ALLOC(P.d1_re, 4 * ncol + 4);
+    DMS_ALLOC(P.d1_stamp, 4 * ncol + 4);
+    DMS_CUDA(cudaMemsetAsync(P.d1_owner.p, 0x7F, 4 * nent + 4, c.s));
+    DMS_CUDA(cudaMemsetAsync(P.d1_stamp.p, 0xFF, 4 * ncol + 4, c.s));
+    DMS_LAUNCH(ncol, 256, k_iota32, P.d1_act.as<int32_t>(), ncol);
+    DMS_CUDA(cudaMemsetAsync(&c.st->misc[2], 0, 2 * sizeof(long long), c.s));
+    c.hst->pool_top = (unsigned long long)pool_used;
+    DMS_CUDA(cudaMemcpyAsync(&c.st->pool_top, &c.hst->pool_top, sizeof(unsigned long long),
+                             cudaMemcpyHostToDevice, c.s));
+    int64_t pool_cap = (int64_t)(P.d1_pool.bytes / 4);
+    int64_t nactive = ncol, stamp = 0;
+    const int64_t limit = P.max_iters > 0 ? P.max_iters : ((int64_t)1 << 22);
+    for (int64_t r = 0; r < limit; r++, stamp++) {
+        DMS_CUDA(cudaMemsetAsync(&c.st->misc[0], 0, 2 * sizeof(long long), c.s));
+        DMS_LAUNCH(nactive, 256, k_red_claim, P.d1_act.as<int32_t>(), nactive,
+                   P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
+                   P.d1_owner.as<int32_t>(), P.d1_re.as<int32_t>(), c.st);
+        DMS_LAUNCH(std::min<int64_t>(64 * nactive, (int64_t)152 * 64 * 256), 256, k_red_add,
+                   P.d1_act.as<int32_t>(), nactive,
+                   P.d1_re.as<int32_t>(), P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+                   P.d1_pool.as<int32_t>(), P.d1_owner.as<int32_t>(), P.d1_stamp.as<int32_t>(),
+                   (int32_t)stamp, P.d1_next.as<int32_t>(), pool_cap, c.st);
+        dms_status s = sync_status(c);
+        P.rounds_d1 = r + 1;
+        if (getenv("DMS_DEBUG"))
+            fprintf(stderr, "d1 round %lld: active %lld rechecked %lld next %lld adds %lld "
+                    "max-chain %lld pool %llu\n", (long long)r, (long long)nactive,
+                    c.hst->misc[0], c.hst->misc[1], c.hst->misc[2], c.hst->misc[3],
+                    c.hst->pool_top);
+        if (s == DMS_ERR_CAPACITY) {
+            // compact the live columns into a pool twice as large, then sweep all columns
+            DMS_ALLOC(P.flag_a, 4 * ncol + 4);
+            DMS_ALLOC(P.flag_b, 4 * ncol + 4);
+            DMS_CUDA(cudaMemcpyAsync(P.flag_a.p, P.d1_len.p, 4 * ncol, cudaMemcpyDeviceToDevice, c.s));
+            DMS_TRY(scan(c, P.flag_a.as<int32_t>(), P.flag_b.as<int32_t>(), ncol, &c.st->total[3]));
+            DMS_CUDA(cudaMemcpyAsync(c.hst, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.s));
+            DMS_CUDA(cudaStreamSynchronize(c.s));
+            int64_t live = c.hst->total[3];
+            int64_t cap2 = std::max<int64_t>(2 * pool_cap, 4 * live + (1 << 20));
+            if (cap2 >= ((int64_t)1 << 31)) return DMS_ERR_CAPACITY;
+            DevBuf fresh;
+            if (!fresh.ensure(4 * (size_t)cap2)) return DMS_ERR_OOM;
+            DMS_LAUNCH(ncol, 256, k_pool_compact, ncol, P.d1_start.as<int64_t>(),
+                       P.d1_len.as<int32_t>(), P.flag_b.as<int32_t>(), P.d1_pool.as<int32_t>(),
+                       fresh.as<int32_t>());
+            DMS_CUDA(cudaStreamSynchronize(c.s));
+            P.d1_pool.release();
+            P.d1_pool = fresh;
+            pool_cap = cap2;
+            c.hst->err = 0;
+            c.hst->pool_top = (unsigned long long)live;
+            DMS_CUDA(cudaMemcpyAsync(c.st, c.hst, sizeof(DevStatus), cudaMemcpyHostToDevice, c.s));
+            DMS_LAUNCH(ncol, 256, k_iota32, P.d1_act.as<int32_t>(), ncol);
+            nactive = ncol;
+            P.d1_pool_grows++;
+            continue;
+        }
+        if (s != DMS_OK) return s;
+        nactive = c.hst->misc[1];
+        std::swap(P.d1_act, P.d1_next);
+        if (nactive == 0) {
+            P.d1_additions = c.hst->misc[2];
+            P.d1_pool_used = (int64_t)c.hst->pool_top;
+            return DMS_OK;
+        }
+    }
+    return DMS_ERR_ITER_LIMIT;
+}
+
+// D1 from the traced columns: reduce them directly (homology) or reduce
+// their anti-transpose (cohomology); both give the pairs of Alg. 3.
+dms_status reduce_d1(Ctx &c, int64_t ncols, int64_t n1, const uint8_t *is_row) {
+    Pipeline &P = c.P;
+    DMS_CUDA(cudaMemcpyAsync(c.hst, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.s));
+    DMS_CUDA(cudaStreamSynchronize(c.s));
+    const int64_t traced = (int64_t)c.hst->pool_top;
+    if (P.d1_mode == 1) {
+        DMS_TRY(reduce_columns(c, ncols, n1, traced));
+        DMS_LAUNCH(ncols, 256, k_d1_result_homology, ncols, P.d1_start.as<int64_t>(),
+                   P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), P.d1_row.as<int32_t>(),
+                   P.d1_rowpaired.as<uint8_t>());
+        return DMS_OK;
+    }
+    // rows: their positions among the rows (scan of the row flags)
+    DMS_ALLOC(P.flag_a, 4 * (n1 + 4));
+    DMS_ALLOC(P.d1_rowpos, 4 * (n1 + 4));
+    DMS_LAUNCH(n1, 256, k_u8_to_i32, is_row, n1, P.flag_a.as<int32_t>());
+    DMS_TRY(scan(c, P.flag_a.as<int32_t>(), P.d1_rowpos.as<int32_t>(), n1, &c.st->total[3]));
+    DMS_CUDA(cudaMemcpyAsync(c.hst, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.s));
+    DMS_CUDA(cudaStreamSynchronize(c.s));
+    const int64_t nrows = c.hst->total[3];
+    DMS_ALLOC(P.d1_rowmap, 4 * (nrows + 4));
+    DMS_LAUNCH(n1, 256, k_compact_idx, is_row, P.d1_rowpos.as<int32_t>(), n1,
+               P.d1_rowmap.as<int32_t>());
+    // transpose: count, scan, scatter, sort
+    DMS_ALLOC(P.d1_cocnt, 4 * (nrows + 4));
+    DMS_ALLOC(P.d1_costart, 4 * (nrows + 4));
+    DMS_ALLOC(P.d1_cofill, 4 * (nrows + 4));
+    DMS_CUDA(cudaMemsetAsync(P.d1_cocnt.p, 0, 4 * (nrows + 4), c.s));
+    DMS_CUDA(cudaMemsetAsync(P.d1_cofill.p, 0, 4 * (nrows + 4), c.s));
+    DMS_LAUNCH(ncols, 256, k_co_count, ncols, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+               P.d1_pool.as<int32_t>(), P.d1_rowpos.as<int32_t>(), nrows, P.d1_cocnt.as<int32_t>());
+    DMS_TRY(scan(c, P.d1_cocnt.as<int32_t>(), P.d1_costart.as<int32_t>(), nrows, &c.st->total[3]));
+    int64_t cap = std::max<int64_t>(1 << 22, 8 * traced + 1024);
+    DevBuf copool;
+    if (!copool.ensure(4 * (size_t)cap)) return DMS_ERR_OOM;
+    DMS_LAUNCH(ncols, 256, k_co_scatter, ncols, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+               P.d1_pool.as<int32_t>(), P.d1_rowpos.as<int32_t>(), nrows,
+               P.d1_costart.as<int32_t>(), P.d1_cofill.as<int32_t>(), copool.as<int32_t>());
+    // the cocolumns replace the columns in the reduction buffers
+    DMS_CUDA(cudaStreamSynchronize(c.s));
+    DMS_ALLOC(P.d1_start, 8 * (nrows + 4));
+    DMS_ALLOC(P.d1_len, 4 * (nrows + 4));
+    DMS_CUDA(cudaMemcpyAsync(P.d1_len.p, P.d1_cocnt.p, 4 * nrows, cudaMemcpyDeviceToDevice, c.s));
+    DMS_LAUNCH(nrows, 128, k_co_sort, nrows, P.d1_costart.as<int32_t>(), P.d1_cocnt.as<int32_t>(),
+               copool.as<int32_t>(), P.d1_start.as<int64_t>());
+    DMS_CUDA(cudaStreamSynchronize(c.s));
+    P.d1_pool.release();
+    P.d1_pool = copool;
+    DMS_TRY(reduce_columns(c, nrows, ncols, traced));
+    DMS_LAUNCH(nrows, 256, k_d1_result_cohomology, nrows, ncols, P.d1_start.as<int64_t>(),
+               P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), P.d1_rowmap.as<int32_t>(),
+               P.d1_row.as<int32_t>(), P.d1_rowpaired.as<uint8_t>());
+    return DMS_OK;
+}
+
 template <typename T> dms_status run(Ctx &c, const T *values) {
     using K = typename Key<T>::K;
     Pipeline &P = c.P;
@@ -1419,7 +1803,8 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
         KEV(6);
         DMS_LAUNCH(nc, 128, k_pls<T>, values, c.g, P.vc.as<int32_t>(), nc, P.recs.as<CritRec>(),
                    P.cnt[0].as<int32_t>(), P.cnt[1].as<int32_t>(), P.cnt[2].as<int32_t>(),
-                   P.cnt[3].as<int32_t>(), P.vrank.as<int32_t>());
+                   P.cnt[3].as<int32_t>(), P.vrank.as<int32_t>(), P.flags.as<uint8_t>(),
+                   P.grad.as<GradRec>());
         KEV(7);
     }
     cudaEventRecord(ev[2], c.s);
@@ -1467,7 +1852,8 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
     // ---- D2: arcs between maxima (node n3 = the virtual maximum), decreasing
     const int32_t vmax = (int32_t)n3;
     KEV(14);
-    DMS_LAUNCH(n2, 128, k_d2_arcs<T>, values, c.g, P.flags.as<uint8_t>(), P.vrank.as<int32_t>(),
+    DMS_LAUNCH(n2, 128, k_d2_arcs<T>, values, c.g, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
+               P.vrank.as<int32_t>(),
                P.recs.as<CritRec>(), P.base[3].as<int32_t>(), P.c_vert[2].as<int32_t>(),
                P.c_loc[2].as<uint8_t>(), n2, vmax, P.arc_a.as<int32_t>(), P.arc_b.as<int32_t>(),
                young2, max_steps, c.st);
@@ -1492,19 +1878,22 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
     DMS_ALLOC(P.d1_colmap, 4 * ncols + 4);
     DMS_ALLOC(P.d1_start, 8 * ncols + 8);
     DMS_ALLOC(P.d1_len, 4 * ncols + 4);
-    DMS_ALLOC(P.d1_owner, 4 * n1 + 4);
     DMS_ALLOC(P.d1_ovf, ncols + 4);
     DMS_LAUNCH(n2, 256, k_compact_idx, is_col, P.flag_b.as<int32_t>(), n2, P.d1_colmap.as<int32_t>());
-    DMS_CUDA(cudaMemsetAsync(P.d1_owner.p, 0x7F, 4 * n1 + 4, c.s));
     DMS_CUDA(cudaMemsetAsync(P.d1_len.p, 0, 4 * ncols + 4, c.s));
-    int64_t pool_cap = std::max<int64_t>(1 << 20, 64 * ncols + 1024);
+    int64_t pool_cap = std::max<int64_t>(1 << 22, 32 * ncols + 1024);
     DMS_ALLOC(P.d1_pool, 4 * pool_cap);
     P.rounds_d1 = 0;
+    DMS_ALLOC(P.d1_row, 4 * ncols + 4);
+    DMS_ALLOC(P.d1_rowpaired, n1 + 4);
+    DMS_CUDA(cudaMemsetAsync(P.d1_rowpaired.p, 0, n1 + 4, c.s));
+    DMS_CUDA(cudaMemsetAsync(P.d1_row.p, 0xFF, 4 * ncols + 4, c.s));
     if (ncols > 0) {
         uint8_t *ovf = P.d1_ovf.as<uint8_t>();
         DMS_CUDA(cudaMemsetAsync(ovf, 0, ncols, c.s));
         DMS_CUDA(cudaMemsetAsync(&c.st->pool_top, 0, sizeof(unsigned long long), c.s));
-        int hcap = 256, hashcap = 512, rcap = 256;
+        // first pass: small per-thread scratch that stays in L2
+        int hcap = 48, hashcap = 64, rcap = 48;
         int64_t nthreads = 152 * 2 * 128;
         if (ncols < nthreads) nthreads = (ncols + 127) / 128 * 128;
         size_t per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
@@ -1516,8 +1905,8 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
         DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nthreads * sizeof(HashEnt), c.s));
         KEV(18);
         k_d1_trace<T><<<(unsigned)(nthreads / 128), 128, 0, c.s>>>(
-            values, c.g, P.flags.as<uint8_t>(), P.vrank.as<int32_t>(), P.recs.as<CritRec>(),
-            P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
+            values, c.g, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
+            P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
             P.d1_colmap.as<int32_t>(), nullptr, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,
             P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
             ovf, c.st);
@@ -1530,6 +1919,7 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
         std::vector<int32_t> todo;
         for (int64_t q = 0; q < ncols; q++)
             if (hovf[q]) todo.push_back((int32_t)q);
+        P.d1_overflow = (int64_t)todo.size();
         int32_t gen = (int32_t)ncols;
         while (!todo.empty()) {
             hcap *= 16; hashcap *= 16; rcap *= 16;
@@ -1548,8 +1938,8 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
             DMS_CUDA(cudaMemcpyAsync(P.d1_todo.p, todo.data(), 4 * todo.size(),
                                      cudaMemcpyHostToDevice, c.s));
             k_d1_trace<T><<<(unsigned)(nt / 32), 32, 0, c.s>>>(
-                values, c.g, P.flags.as<uint8_t>(), P.vrank.as<int32_t>(), P.recs.as<CritRec>(),
-                P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(),
+                values, c.g, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
+                P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(),
                 P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), P.d1_todo.as<int32_t>(),
                 (int64_t)todo.size(), heap, hash, rows, hcap, hashcap, rcap, gen,
                 P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(),
@@ -1565,21 +1955,8 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
             todo.swap(next);
         }
         KEV(19);
-        // reduction rounds
         KEV(20);
-        const int64_t limit = P.max_iters > 0 ? P.max_iters : ((int64_t)1 << 22);
-        bool done = false;
-        for (int64_t r = 0; r < limit && !done; r++) {
-            DMS_CUDA(cudaMemsetAsync(&c.st->changed, 0, sizeof(int), c.s));
-            DMS_LAUNCH(ncols, 256, k_red_claim, ncols, P.d1_start.as<int64_t>(),
-                       P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), P.d1_owner.as<int32_t>());
-            DMS_LAUNCH(ncols, 256, k_red_add, ncols, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
-                       P.d1_pool.as<int32_t>(), P.d1_owner.as<int32_t>(), pool_cap, c.st);
-            DMS_TRY(sync_status(c));
-            P.rounds_d1 = r + 1;
-            done = c.hst->changed == 0;
-        }
-        if (!done) return DMS_ERR_ITER_LIMIT;
+        DMS_TRY(reduce_d1(c, ncols, n1, is_row));
         KEV(21);
     }
     cudaEventRecord(ev[6], c.s);
@@ -1595,8 +1972,7 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
     a.v3 = P.c_vert[3].as<int32_t>(); a.l3 = P.c_loc[3].as<uint8_t>();
     a.young0 = young0; a.young2 = young2; a.died0 = died0; a.died3 = died3;
     a.colmap = P.d1_colmap.as<int32_t>();
-    a.col_start = P.d1_start.as<int64_t>(); a.col_len = P.d1_len.as<int32_t>();
-    a.pool = P.d1_pool.as<int32_t>(); a.owner1 = P.d1_owner.as<int32_t>();
+    a.d1_row = P.d1_row.as<int32_t>(); a.row_paired = P.d1_rowpaired.as<uint8_t>();
     a.is_row = is_row; a.is_col = is_col;
     // parts: 0 D0 finite (over C1), 1 D0 infinite (C0), 2 D1 finite (columns),
     // 3 D1 infinite (C1), 4 D2 finite (C2), 5 D2 infinite (columns), 6 D3 infinite (C3)
@@ -1648,13 +2024,15 @@ dms_status Pipeline::init(int64_t nx_, int64_t ny_, int64_t nz_, dms_dtype dt,
     if (dt != DMS_U16 && dt != DMS_F32 && dt != DMS_F64) return DMS_ERR_INVALID_ARG;
     if (o && o->virtual_max != 1) return DMS_ERR_INVALID_ARG;
     if (o && o->max_iters < 0) return DMS_ERR_INVALID_ARG;
+    if (o && (o->d1_mode < 0 || o->d1_mode > 2)) return DMS_ERR_INVALID_ARG;
     nx = nx_; ny = ny_; nz = nz_; n = nx * ny * nz; dtype = dt;
     max_iters = o ? o->max_iters : 0;
+    d1_mode = (o && o->d1_mode == 2) ? 2 : 1;
     if (cudaGetDevice(&device) != cudaSuccess) return DMS_ERR_CUDA;
     dms_status s = ensure_tables(device);
     if (s != DMS_OK) return s;
     const int64_t ntiles = (n + kClsTile - 1) / kClsTile;
-    if (!flags.ensure(n) || !vrank.ensure(4 * n) || !tile_cnt.ensure(4 * ntiles) ||
+    if (!flags.ensure(n) || !vrank.ensure(4 * n) || !grad.ensure(sizeof(GradRec) * n) || !tile_cnt.ensure(4 * ntiles) ||
         !tile_off.ensure(4 * ntiles) || !dstat.ensure(sizeof(DevStatus)))
         return DMS_ERR_OOM;
     if (cudaMallocHost(&hstat, sizeof(DevStatus)) != cudaSuccess) {
@@ -1669,7 +2047,8 @@ dms_status Pipeline::init(int64_t nx_, int64_t ny_, int64_t nz_, dms_dtype dt,
 }
 
 void Pipeline::destroy() {
-    DevBuf *all[] = {&values_dev, &flags,    &vrank,     &tile_cnt,  &tile_off,   &vc,
+    DevBuf *all[] = {&d1_row, &d1_rowpaired, &d1_rowpos, &d1_rowmap, &d1_cocnt, &d1_costart,
+                     &d1_cofill, &d1_act, &d1_next, &d1_re, &d1_stamp, &grad, &values_dev, &flags,    &vrank,     &tile_cnt,  &tile_off,   &vc,
                      &vc_tmp,     &keys,     &keys_tmp,  &recs,      &arc_a,      &arc_b,
                      &dc_keys,    &dc_par,   &dc_lab,    &young,     &died,       &rowcol,
                      &flag_a,     &flag_b,   &d1_colmap, &d1_start,  &d1_len,     &d1_owner,

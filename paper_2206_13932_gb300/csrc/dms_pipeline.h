@@ -22,12 +22,14 @@ struct Pipeline {
     int64_t nx = 0, ny = 0, nz = 0, n = 0;
     dms_dtype dtype = DMS_F32;
     int64_t max_iters = 0;
+    int d1_mode = 1;        // 1: reduce columns (homology), 2: anti-transpose (cohomology)
     int device = 0;
 
     // grid-sized state
     DevBuf values_dev;      // copy of host values (values_on_host = 1)
     DevBuf flags;           // u8 per vertex: descent link | critical flag
     DevBuf vrank;           // i32 per vertex: position among sorted critical vertices
+    DevBuf grad;            // 40 B per vertex: memoised lower-star pairing
     DevBuf tile_cnt, tile_off;
     // critical-count-sized state
     DevBuf vc, vc_tmp, keys, keys_tmp, recs;
@@ -35,6 +37,9 @@ struct Pipeline {
     DevBuf c_vert[4], c_loc[4];
     DevBuf arc_a, arc_b, young, died, rowcol, flag_a, flag_b;
     DevBuf dc_keys, dc_par, dc_lab;   // elder-rule halving levels
+    DevBuf d1_act, d1_next, d1_re, d1_stamp;   // D1 reduction work lists
+    DevBuf d1_row, d1_rowpaired;               // D1 result per column / row
+    DevBuf d1_rowpos, d1_rowmap, d1_cocnt, d1_costart, d1_cofill;   // transpose
     DevBuf d1_colmap, d1_start, d1_len, d1_owner, d1_ovf, d1_pool, d1_scratch, d1_todo;
     DevBuf out_pairs[3];
     DevBuf scan_tmp;
@@ -44,6 +49,7 @@ struct Pipeline {
     int64_t n_crit = 0, n_c[4] = {0, 0, 0, 0};
     int64_t n_pairs[3] = {0, 0, 0}, n_ess[4] = {0, 0, 0, 0};
     int64_t launches = 0, rounds_d0 = 0, rounds_d2 = 0, rounds_d1 = 0  /* D0/D2: halving levels */, d1_cols = 0;
+    int64_t d1_overflow = 0, d1_additions = 0, d1_pool_used = 0, d1_pool_grows = 0;
     float stage_ms[8] = {0};
     float kernel_ms[12] = {0};
     void *kev[24] = {nullptr};   // cudaEvent_t pairs per kernel family
