@@ -189,11 +189,15 @@ struct PLSResult {
 //                               in which the lower star's edges were
 //                               classified.
 // Layout: w[0] tets 0-9, w[1] tets 10-19, w[2] tets 20-23 (bits 0-23) and
-// edge pairs 0-5 (bits 24-59), w[3] edge pairs 6-13, w[4] edge orders 0-13.
+// edge pairs 0-5 (bits 24-59), w[3] edge pairs 6-13, w[4] edge orders 0-13,
+// w[5] the 4-bit rank of each lower link vertex (0xF: not lower).
 constexpr int kNone = 63, kHead = 62;
-struct GradRec {
-    uint64_t w[5];
+struct __align__(16) GradRec {
+    uint64_t w[6];
 };
+__device__ __forceinline__ int grad_rank(const GradRec &g, int n) {
+    return (int)((g.w[5] >> (4 * n)) & 15);
+}
 
 __device__ __forceinline__ int grad_tet_pair(const GradRec &g, int h) {
     int word = h < 10 ? 0 : h < 20 ? 1 : 2;
@@ -246,7 +250,11 @@ __device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank,
             else w[3] |= (uint64_t)epair[n] << (6 * (n - 6));
             w[4] |= (uint64_t)(eord[n] & 15) << (4 * n);
         }
+        uint64_t rk = 0;
+        for (int n = 0; n < kLinks; n++)
+            rk |= (uint64_t)((L >> n & 1) ? rank[n] : 0xF) << (4 * n);
         for (int k = 0; k < 5; k++) G->w[k] = w[k];
+        G->w[5] = rk;
     };
     if (L == 0) { R.is_min = true; pack(); return; }
 

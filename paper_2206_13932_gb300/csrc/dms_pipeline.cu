@@ -16,6 +16,7 @@
 //              (Alg. 3 restricted, Sec. 4.2 (b), Sec. 6);
 //   output     pairs and infinite classes (Sec. 6).
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -55,9 +56,19 @@ struct CritRec {
 struct HeapEnt { unsigned long long hi, lo; };
 struct HashEnt {
     unsigned long long key;
-    int32_t gen, row;
-    uint8_t parity, kind, pair, pad[5];
+    int32_t gen;
+    uint32_t info;   // row (bits 0-23... see kRowBits), pair (6 bits), kind (2), parity (1)
 };
+// info packing: bits 0-22 unused when kind = reg; a row index needs up to 31
+// bits, so rows are kept apart in the per-thread row list and info holds the
+// position in that list
+__device__ __forceinline__ uint32_t hinfo(uint32_t aux, int pair, int kind, int parity) {
+    return (aux & 0x7FFFFF) | ((uint32_t)pair << 23) | ((uint32_t)kind << 29) | ((uint32_t)parity << 31);
+}
+__device__ __forceinline__ uint32_t hinfo_aux(uint32_t i) { return i & 0x7FFFFF; }
+__device__ __forceinline__ int hinfo_pair(uint32_t i) { return (i >> 23) & 63; }
+__device__ __forceinline__ int hinfo_kind(uint32_t i) { return (i >> 29) & 3; }
+__device__ __forceinline__ int hinfo_parity(uint32_t i) { return (i >> 31) & 1; }
 enum { kKindRow = 1, kKindReg = 2 };
 
 // ------------------------------------------------------------ host tables
@@ -462,17 +473,17 @@ __global__ void __launch_bounds__(kRsThreads)
     }
 }
 
-// -------------------------------- stage 3: ProcessLowerStars on critical ones
+// -------------------------------- stage 3: ProcessLowerStars
 
+// ProcessLowerStars of the vertices of an id-ordered list (or of every vertex
+// if list is null): the packed pairing of each lower star.
 template <typename T>
-__global__ void k_pls(const T *__restrict__ values, GridParams g,
-                      const int32_t *__restrict__ vc, int64_t nc, CritRec *recs,
-                      int32_t *cnt0, int32_t *cnt1, int32_t *cnt2, int32_t *cnt3,
-                      int32_t *vrank, uint8_t *flags, GradRec *grad) {
+__global__ void k_pls(const T *__restrict__ values, GridParams g, const int32_t *__restrict__ list,
+                      int64_t count, uint8_t *flags, GradRec *grad) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nc) return;
+    if (i >= count) return;
     const StarTables &S = g_star;
-    int64_t x = vc[i];
+    int64_t x = list ? list[i] : i;
     StarView sv;
     load_star(S, g, values, x, sv);
     PLSResult R;
@@ -480,17 +491,56 @@ __global__ void k_pls(const T *__restrict__ values, GridParams g,
     pls(S, sv.lower, sv.rank, R, &G);
     grad[x] = G;
     flags[x] = (uint8_t)(flags[x] | kFlagGradient);
-    uint64_t packed = 0;
-    for (int n = 0; n < kLinks; n++)
-        packed |= (uint64_t)((sv.lower >> n & 1) ? sv.rank[n] : 0xF) << (4 * n);
+}
+
+// The critical cells of the lower star of each sorted critical vertex, read
+// off its packed pairing: the critical edges and tets are the lower ones left
+// unpaired, the critical triangles those paired with neither an edge nor a
+// tet, a vertex without lower edge is a minimum.
+__global__ void k_critrec(const int32_t *__restrict__ vc, int64_t nc,
+                          const GradRec *__restrict__ grad, CritRec *recs, int32_t *cnt0,
+                          int32_t *cnt1, int32_t *cnt2, int32_t *cnt3, int32_t *vrank) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const StarTables &S = g_star;
+    int64_t x = vc[i];
+    GradRec G = grad[x];
+    uint16_t L = 0;
+    for (int n = 0; n < kLinks; n++) L |= (uint16_t)((grad_rank(G, n) != 0xF) << n);
+    uint64_t LT = kAllTris;
+    uint32_t LH = kAllTets;
+    for (uint16_t out = (uint16_t)(~L & kAllLinks); out; out &= out - 1) {
+        int n = __ffs(out) - 1;
+        LT &= ~S.tris_of_link[n];
+        LH &= ~S.tets_of_link[n];
+    }
+    uint16_t ce = 0;
+    uint64_t paired_t = 0;
+    uint32_t ch = 0;
+    for (uint16_t m = L; m; m &= m - 1) {
+        int n = __ffs(m) - 1;
+        int p = grad_edge_pair(G, n);
+        if (p == kNone) ce |= (uint16_t)(1u << n);
+        else if (p < kTris) paired_t |= 1ull << p;
+    }
+    for (uint32_t m = LH; m; m &= m - 1) {
+        int h = __ffs(m) - 1;
+        int p = grad_tet_pair(G, h);
+        if (p == kNone) ch |= 1u << h;
+        else paired_t |= 1ull << p;
+    }
     CritRec rec;
-    rec.crit_t = R.crit_t; rec.ranks = packed; rec.crit_h = R.crit_h; rec.crit_e = R.crit_e;
-    rec.is_min = R.is_min; rec.pad = 0;
+    rec.crit_t = LT & ~paired_t;
+    rec.ranks = G.w[5];
+    rec.crit_h = ch;
+    rec.crit_e = ce;
+    rec.is_min = L == 0;
+    rec.pad = 0;
     recs[i] = rec;
-    cnt0[i] = R.is_min;
-    cnt1[i] = __popc(R.crit_e);
-    cnt2[i] = __popcll(R.crit_t);
-    cnt3[i] = __popc(R.crit_h);
+    cnt0[i] = rec.is_min;
+    cnt1[i] = __popc(ce);
+    cnt2[i] = __popcll(rec.crit_t);
+    cnt3[i] = __popc(ch);
     vrank[x] = (int32_t)i;
 }
 
@@ -719,21 +769,40 @@ __global__ void k_dc_decide(int64_t narcs, int older_is_larger, const int32_t *A
 // is stored before the flag bit is set (with a fence) and read through L2,
 // so a reader that sees the bit sees the record.
 template <typename T>
+__device__ __noinline__ GradRec grad_fill(const StarTables &S, const GridParams &g,
+                                          const T *__restrict__ values, uint8_t *flags,
+                                          GradRec *grad, int64_t y);
+
+template <typename T>
 __device__ __forceinline__ GradRec grad_get(const StarTables &S, const GridParams &g,
                                             const T *__restrict__ values, uint8_t *flags,
                                             GradRec *grad, int64_t y) {
-    GradRec G;
     if (((volatile const uint8_t *)flags)[y] & kFlagGradient) {
-        const unsigned long long *src = (const unsigned long long *)&grad[y];
-        for (int k = 0; k < 5; k++) G.w[k] = __ldcg(src + k);
+        GradRec G;
+        const ulonglong2 *src = (const ulonglong2 *)&grad[y];
+        for (int k = 0; k < 3; k++) {
+            ulonglong2 v = __ldcg(src + k);
+            G.w[2 * k] = v.x;
+            G.w[2 * k + 1] = v.y;
+        }
         return G;
     }
+    return grad_fill(S, g, values, flags, grad, y);
+}
+
+// Computes and stores the record of vertex y (out of line: one copy of
+// ProcessLowerStars per kernel instead of one per call site).
+template <typename T>
+__device__ __noinline__ GradRec grad_fill(const StarTables &S, const GridParams &g,
+                                          const T *__restrict__ values, uint8_t *flags,
+                                          GradRec *grad, int64_t y) {
+    GradRec G;
     StarView sv;
     load_star(S, g, values, y, sv);
     PLSResult R;
     pls(S, sv.lower, sv.rank, R, &G);
-    unsigned long long *dst = (unsigned long long *)&grad[y];
-    for (int k = 0; k < 5; k++) __stcg(dst + k, G.w[k]);
+    ulonglong2 *dst = (ulonglong2 *)&grad[y];
+    for (int k = 0; k < 3; k++) __stcg(dst + k, make_ulonglong2(G.w[2 * k], G.w[2 * k + 1]));
     __threadfence();
     volatile uint8_t *f = (volatile uint8_t *)flags;
     f[y] = (uint8_t)(f[y] | kFlagGradient);
@@ -843,7 +912,8 @@ __global__ void k_d2_arcs(const T *__restrict__ values, GridParams g, uint8_t *f
 struct TraceCtx {
     HeapEnt *heap;
     HashEnt *hash;
-    int32_t *rows;
+    int32_t *rows;     // C1 index of each row met (in order of first contact)
+    int32_t *rslot;    // its hash slot
     int hcap, hashmask, rcap;
     int hn, rn, used;
     int32_t gen;
@@ -911,11 +981,10 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
     for (int p = 0; p <= c.hashmask; p++) {
         HashEnt *e = &c.hash[(hpos + p) & c.hashmask];
         if (e->gen != c.gen) { slot = e; break; }
-        if (e->key == key) { e->parity ^= 1; return; }
+        if (e->key == key) { e->info ^= 1u << 31; return; }
     }
     if (!slot || c.used * 4 >= (c.hashmask + 1) * 3) { c.overflow = true; return; }
-    int32_t row = -1;
-    uint8_t kind, pair = 0;
+    uint32_t info;
     if (fy & kFlagCritical) {
         int32_t i = vrank[y];
         CritRec rec = recs[i];
@@ -923,37 +992,33 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
             int32_t j1 = base1[i] + local_index(S, rec, 1, m);
             if (!is_row[j1]) return;            // paired in D0: dropped
             if (c.rn >= c.rcap) { c.overflow = true; return; }
-            row = j1;
-            kind = kKindRow;
-            c.rows[c.rn++] = (int32_t)(slot - c.hash);
-            goto insert;
+            c.rows[c.rn] = j1;
+            c.rslot[c.rn] = (int32_t)(slot - c.hash);
+            info = hinfo((uint32_t)c.rn, 0, kKindRow, 1);
+            c.rn++;
+            slot->key = key;
+            slot->gen = c.gen;
+            slot->info = info;
+            c.used++;
+            return;
         }
     }
-    {
-        GradRec G = grad_get(S, g, values, flags, grad, y);
-        int sp = grad_edge_pair(G, m);
-        if (sp >= kTris) { atomicOr(&st->err, kErrState); return; }
-        pair = (uint8_t)sp;
-        kind = kKindReg;
-        HeapEnt he;
-        he.hi = (unsigned long long)Key<T>::of(values[y]);
-        he.lo = ((unsigned long long)y << 12) | ((unsigned long long)grad_edge_order(G, m) << 4) |
-                (unsigned)m;
-        heap_push(c, he);
-        if (c.overflow) return;
-    }
-insert:
+    GradRec G = grad_get(S, g, values, flags, grad, y);
+    int sp = grad_edge_pair(G, m);
+    if (sp >= kTris) { atomicOr(&st->err, kErrState); return; }
+    HeapEnt he;
+    he.hi = (unsigned long long)Key<T>::of(values[y]);
+    he.lo = ((unsigned long long)y << 12) | ((unsigned long long)grad_edge_order(G, m) << 4) |
+            (unsigned)m;
+    heap_push(c, he);
+    if (c.overflow) return;
     slot->key = key;
     slot->gen = c.gen;
-    slot->row = row;
-    slot->parity = 1;
-    slot->kind = kind;
-    slot->pair = pair;
+    slot->info = hinfo(0, sp, kKindReg, 1);
     c.used++;
 }
 
-template <typename T>
-__device__ HashEnt *trace_find(TraceCtx &c, int64_t y, int m) {
+__device__ __forceinline__ HashEnt *trace_find(TraceCtx &c, int64_t y, int m) {
     unsigned long long key = (((unsigned long long)y << 4) | (unsigned)m) + 1;
     uint32_t hpos = hash64(key) & c.hashmask;
     for (int p = 0; p <= c.hashmask; p++) {
@@ -962,6 +1027,29 @@ __device__ HashEnt *trace_find(TraceCtx &c, int64_t y, int m) {
         if (e->key == key) return e;
     }
     return nullptr;
+}
+
+// The two further edges of star triangle s of y when edge (y, m) is expanded
+// through it: (y, other) and the edge between the triangle's two link
+// vertices, expressed in the star of the higher of them (by the ranks of the
+// lower star of y).
+template <typename T>
+__device__ __forceinline__ void trace_expand(TraceCtx &c, const StarTables &S, const GridParams &g,
+                                             const T *__restrict__ values, uint8_t *flags,
+                                             GradRec *grad, const int32_t *__restrict__ vrank,
+                                             const CritRec *__restrict__ recs,
+                                             const int32_t *__restrict__ base1,
+                                             const uint8_t *__restrict__ is_row, int64_t y, int s,
+                                             int m, const GradRec &G, DevStatus *st) {
+    int ta = S.tri_v[s][0], tb = S.tri_v[s][1];
+    if (m >= 0) trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, y,
+                                ta == m ? tb : ta, st);
+    bool aup = grad_rank(G, ta) > grad_rank(G, tb);
+    int hi = aup ? ta : tb, lo = aup ? tb : ta;
+    int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
+                         9 * (S.dz[lo] - S.dz[hi] + 1)];
+    trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, y + g.dlin[hi], l,
+                    st);
 }
 
 // One thread per column: the Morse boundary of a critical triangle restricted
@@ -983,7 +1071,8 @@ __global__ void k_d1_trace(const T *__restrict__ values, GridParams g, uint8_t *
     TraceCtx c;
     c.heap = heap_all + tid * hcap;
     c.hash = hash_all + tid * hashcap;
-    c.rows = rows_all + tid * rcap;
+    c.rows = rows_all + tid * 2 * rcap;
+    c.rslot = c.rows + rcap;
     c.hcap = hcap; c.hashmask = hashcap - 1; c.rcap = rcap;
     for (int64_t q = tid; q < ntodo; q += nth) {
         int32_t cj = todo ? todo[q] : (int32_t)q;
@@ -992,51 +1081,32 @@ __global__ void k_d1_trace(const T *__restrict__ values, GridParams g, uint8_t *
         int s = l2[j2];
         c.hn = 0; c.rn = 0; c.used = 0; c.overflow = false;
         c.gen = gen_base + cj;
-        int a = S.tri_v[s][0], b = S.tri_v[s][1];
         // boundary: (x,a), (x,b) and the edge between x+a and x+b
-        trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, x, a, st);
-        trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, x, b, st);
-        {
-            int64_t va = x + g.dlin[a], vb = x + g.dlin[b];
-            auto ka = Key<T>::of(values[va]), kb = Key<T>::of(values[vb]);
-            bool aup = ka > kb || (ka == kb && va > vb);
-            int hi = aup ? a : b, lo = aup ? b : a;
-            int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
-                                 9 * (S.dz[lo] - S.dz[hi] + 1)];
-            trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row,
-                            x + g.dlin[hi], l, st);
-        }
+        GradRec Gx = grad_get(S, g, values, flags, grad, x);
+        trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, x,
+                        S.tri_v[s][0], st);
+        trace_expand<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, x, s,
+                        S.tri_v[s][0], Gx, st);
         while (c.hn > 0 && !c.overflow) {
             HeapEnt top = heap_pop(c);
             int64_t y = (int64_t)(top.lo >> 12);
             int m = (int)(top.lo & 0xF);
-            HashEnt *e = trace_find<T>(c, y, m);
-            if (!e || !e->parity) continue;
-            e->parity = 0;
-            int sp = e->pair;
-            int ta = S.tri_v[sp][0], tb = S.tri_v[sp][1];
-            int other = ta == m ? tb : ta;
-            trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, y, other, st);
-            int64_t va = y + g.dlin[ta], vb = y + g.dlin[tb];
-            auto ka = Key<T>::of(values[va]), kb = Key<T>::of(values[vb]);
-            bool aup = ka > kb || (ka == kb && va > vb);
-            int hi = aup ? ta : tb, lo = aup ? tb : ta;
-            int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
-                                 9 * (S.dz[lo] - S.dz[hi] + 1)];
-            trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row,
-                            y + g.dlin[hi], l, st);
+            HashEnt *e = trace_find(c, y, m);
+            if (!e || !hinfo_parity(e->info)) continue;
+            e->info &= ~(1u << 31);
+            GradRec G = grad_get(S, g, values, flags, grad, y);
+            trace_expand<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, y,
+                            hinfo_pair(e->info), m, G, st);
         }
         if (c.overflow) {
             overflow[cj] = 1;
             col_len[cj] = 0;
             continue;
         }
-        // collect the rows with odd multiplicity, sorted decreasingly
+        // the rows with odd multiplicity, sorted decreasingly
         int len = 0;
-        for (int k = 0; k < c.rn; k++) {
-            HashEnt *e = &c.hash[c.rows[k]];
-            if (e->parity) c.rows[len++] = e->row;
-        }
+        for (int k = 0; k < c.rn; k++)
+            if (hinfo_parity(c.hash[c.rslot[k]].info)) c.rows[len++] = c.rows[k];
         for (int k = 1; k < len; k++) {
             int32_t v = c.rows[k];
             int p = k;
@@ -1203,6 +1273,115 @@ __global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
     if (lane == 0 && adds) {
         atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)adds);
         atomicMax((unsigned long long *)&st->misc[3], (unsigned long long)longest);
+    }
+}
+
+// out = A + B (mod 2) by a block of NT threads; both lists are staged in
+// shared memory when they fit (cap entries each).  Returns the length.
+template <int NT>
+__device__ int block_symdiff(const int32_t *A, int la, const int32_t *B, int lb, int32_t *out,
+                             int32_t *sA, int32_t *sB, int cap, int *sscan) {
+    const int t = threadIdx.x;
+    if (la <= cap && lb <= cap) {
+        for (int k = t; k < la; k += NT) sA[k] = A[k];
+        for (int k = t; k < lb; k += NT) sB[k] = B[k];
+        __syncthreads();
+        A = sA;
+        B = sB;
+    }
+    const int L = la + lb, per = (L + NT - 1) / NT;
+    int i0, j0, i1, j1;
+    merge_split(A, la, B, lb, min(t * per, L), i0, j0);
+    merge_split(A, la, B, lb, min(t * per + per, L), i1, j1);
+    int cnt = 0;
+    {
+        int i = i0, j = j0;
+        while (i < i1 || j < j1) {
+            int32_t x = i < i1 ? A[i] : -1, y = j < j1 ? B[j] : -1;
+            if (x > y) { cnt++; i++; }
+            else if (y > x) { cnt++; j++; }
+            else { i++; j++; }
+        }
+    }
+    // block exclusive scan of cnt
+    const int lane = t & 31, w = t >> 5;
+    int inc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) sscan[w] = inc;
+    __syncthreads();
+    int pre = 0, total = 0;
+    for (int q = 0; q < NT / 32; q++) { if (q < w) pre += sscan[q]; total += sscan[q]; }
+    int o = pre + inc - cnt;
+    int i = i0, j = j0;
+    while (i < i1 || j < j1) {
+        int32_t x = i < i1 ? A[i] : -1, y = j < j1 ? B[j] : -1;
+        if (x > y) { out[o++] = x; i++; }
+        else if (y > x) { out[o++] = y; j++; }
+        else { i++; j++; }
+    }
+    __syncthreads();   // smem reused by the next addition
+    return total;
+}
+
+// The same as k_red_add with one block per listed column, for the last rounds
+// where few columns remain and their additions are long.
+constexpr int kRedBlock = 256, kRedStage = 6144;
+__global__ void __launch_bounds__(kRedBlock)
+    k_red_add_block(const int32_t *__restrict__ active, int64_t nactive,
+                    const int32_t *__restrict__ recheck, int64_t *start, int32_t *len,
+                    int32_t *pool, const int32_t *__restrict__ owner, int32_t *stamp,
+                    int32_t round, int32_t *next, int64_t pool_cap, DevStatus *st) {
+    __shared__ int32_t sA[kRedStage], sB[kRedStage];
+    __shared__ int sscan[kRedBlock / 32];
+    __shared__ int32_t s_cj, s_k, s_fresh;
+    __shared__ unsigned long long s_pos;
+    const int64_t nre = *(volatile long long *)&st->misc[0];
+    const int64_t q = blockIdx.x;
+    if (q >= nactive + nre) return;
+    if (threadIdx.x == 0) {
+        s_cj = q < nactive ? active[q] : recheck[q - nactive];
+        s_fresh = atomicExch(&stamp[s_cj], round) != round;
+    }
+    __syncthreads();
+    if (!s_fresh) return;
+    const int32_t cj = s_cj;
+    int la = len[cj];
+    int64_t sa = start[cj];
+    bool changed = false;
+    unsigned chain = 0;
+    for (int it = 0; la > 0 && it < (1 << 24); it++) {
+        if (threadIdx.x == 0) s_k = owner[pool[sa]];
+        __syncthreads();
+        int32_t k = s_k;
+        if (k == cj || k == kNoOwner || k > cj) break;
+        int64_t sb = start[k];
+        int lb = len[k];
+        if (threadIdx.x == 0) s_pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
+        __syncthreads();
+        unsigned long long pos = s_pos;
+        if ((int64_t)(pos + la + lb) > pool_cap) {
+            if (threadIdx.x == 0) atomicOr(&st->err, kErrCap);
+            break;
+        }
+        la = block_symdiff<kRedBlock>(pool + sa, la, pool + sb, lb, pool + pos, sA, sB, kRedStage,
+                                      sscan);
+        sa = (int64_t)pos;
+        changed = true;
+        chain++;
+    }
+    if (threadIdx.x == 0) {
+        if (changed) {
+            start[cj] = sa;
+            len[cj] = la;
+            if (la > 0) next[atomicAdd((unsigned long long *)&st->misc[1], 1ull)] = cj;
+        }
+        if (chain) {
+            atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)chain);
+            atomicMax((unsigned long long *)&st->misc[3], (unsigned long long)chain);
+        }
     }
 }
 
@@ -1605,11 +1784,13 @@ dms_status elder_rule(Ctx &c, int64_t narcs, int descending, int older_is_larger
 // in P.d1_pool at P.d1_start/P.d1_len, claiming pivots in owner[0..nent).
 // Rounds continue until no column changes; on a pool overflow the live
 // columns are compacted into a larger pool and the round is repeated.
+constexpr int64_t kBlockModeBelow = 8192;   // active columns below which a block adds
+
 dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used) {
     Pipeline &P = c.P;
     DMS_ALLOC(P.d1_owner, 4 * nent + 4);
-    DMS_ALLOC(P.d1_act, 4 * ncol + 4);
-    DMS_ALLOC(P.d1_next, 4 * ncol + 4);
+    DMS_ALLOC(P.d1_act, 4 * 3 * ncol + 4);
+    DMS_ALLOC(P.d1_next, 4 * 3 * ncol + 4);
     DMS_ALLOC(P.d1_re, 4 * ncol + 4);
     DMS_ALLOC(P.d1_stamp, 4 * ncol + 4);
     DMS_CUDA(cudaMemsetAsync(P.d1_owner.p, 0x7F, 4 * nent + 4, c.s));
@@ -1627,18 +1808,33 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
         DMS_LAUNCH(nactive, 256, k_red_claim, P.d1_act.as<int32_t>(), nactive,
                    P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
                    P.d1_owner.as<int32_t>(), P.d1_re.as<int32_t>(), c.st);
-        DMS_LAUNCH(std::min<int64_t>(64 * nactive, (int64_t)152 * 64 * 256), 256, k_red_add,
-                   P.d1_act.as<int32_t>(), nactive,
-                   P.d1_re.as<int32_t>(), P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
-                   P.d1_pool.as<int32_t>(), P.d1_owner.as<int32_t>(), P.d1_stamp.as<int32_t>(),
-                   (int32_t)stamp, P.d1_next.as<int32_t>(), pool_cap, c.st);
+        if (nactive > kBlockModeBelow) {
+            DMS_LAUNCH(std::min<int64_t>(64 * nactive, (int64_t)152 * 64 * 256), 256, k_red_add,
+                       P.d1_act.as<int32_t>(), nactive, P.d1_re.as<int32_t>(),
+                       P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
+                       P.d1_owner.as<int32_t>(), P.d1_stamp.as<int32_t>(), (int32_t)stamp,
+                       P.d1_next.as<int32_t>(), pool_cap, c.st);
+        } else {
+            // one block per column (grid covers active + displaced, <= 2x active)
+            k_red_add_block<<<(unsigned)(2 * nactive), kRedBlock, 0, c.s>>>(
+                P.d1_act.as<int32_t>(), nactive, P.d1_re.as<int32_t>(), P.d1_start.as<int64_t>(),
+                P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), P.d1_owner.as<int32_t>(),
+                P.d1_stamp.as<int32_t>(), (int32_t)stamp, P.d1_next.as<int32_t>(), pool_cap, c.st);
+            c.launches++;
+            DMS_CUDA(cudaGetLastError());
+        }
         dms_status s = sync_status(c);
         P.rounds_d1 = r + 1;
-        if (getenv("DMS_DEBUG"))
+        if (getenv("DMS_DEBUG")) {
+            static std::chrono::steady_clock::time_point t_last;
+            auto now = std::chrono::steady_clock::now();
+            double ms = r ? std::chrono::duration<double, std::milli>(now - t_last).count() : 0.0;
+            t_last = now;
             fprintf(stderr, "d1 round %lld: active %lld rechecked %lld next %lld adds %lld "
-                    "max-chain %lld pool %llu\n", (long long)r, (long long)nactive,
+                    "max-chain %lld pool %llu (%.3f ms)\n", (long long)r, (long long)nactive,
                     c.hst->misc[0], c.hst->misc[1], c.hst->misc[2], c.hst->misc[3],
-                    c.hst->pool_top);
+                    c.hst->pool_top, ms);
+        }
         if (s == DMS_ERR_CAPACITY) {
             // compact the live columns into a pool twice as large, then sweep all columns
             DMS_ALLOC(P.flag_a, 4 * ncol + 4);
@@ -1659,11 +1855,16 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
             P.d1_pool.release();
             P.d1_pool = fresh;
             pool_cap = cap2;
+            // every column the interrupted round listed or changed is listed again
+            const int64_t nre = c.hst->misc[0], nnext = c.hst->misc[1];
+            DMS_CUDA(cudaMemcpyAsync(P.d1_act.as<int32_t>() + nactive, P.d1_re.p, 4 * nre,
+                                     cudaMemcpyDeviceToDevice, c.s));
+            DMS_CUDA(cudaMemcpyAsync(P.d1_act.as<int32_t>() + nactive + nre, P.d1_next.p,
+                                     4 * nnext, cudaMemcpyDeviceToDevice, c.s));
+            nactive += nre + nnext;
             c.hst->err = 0;
             c.hst->pool_top = (unsigned long long)live;
             DMS_CUDA(cudaMemcpyAsync(c.st, c.hst, sizeof(DevStatus), cudaMemcpyHostToDevice, c.s));
-            DMS_LAUNCH(ncol, 256, k_iota32, P.d1_act.as<int32_t>(), ncol);
-            nactive = ncol;
             P.d1_pool_grows++;
             continue;
         }
@@ -1774,6 +1975,17 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
     DMS_CUDA(cudaGetLastError());
     KEV(3);
     if (nc > 0) {
+        // ProcessLowerStars in id order (coalesced stencils): on every vertex
+        // when critical vertices are dense (the walks of D2 and D1 then visit
+        // most vertices), otherwise on the critical ones, the rest on demand
+        KEV(6);
+        if (nc * 4 > n)
+            DMS_LAUNCH(n, 128, k_pls<T>, values, c.g, (const int32_t *)nullptr, n,
+                       P.flags.as<uint8_t>(), P.grad.as<GradRec>());
+        else
+            DMS_LAUNCH(nc, 128, k_pls<T>, values, c.g, P.vc.as<int32_t>(), nc,
+                       P.flags.as<uint8_t>(), P.grad.as<GradRec>());
+        KEV(7);
         // stable LSD radix sort of the critical vertices (in id order) by value
         KEV(4);
         DMS_LAUNCH(nc, 256, k_gather_keys<T>, values, P.vc.as<int32_t>(), nc, P.keys.as<K>());
@@ -1800,12 +2012,9 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
             std::swap(P.keys, P.keys_tmp);
         }
         KEV(5);
-        KEV(6);
-        DMS_LAUNCH(nc, 128, k_pls<T>, values, c.g, P.vc.as<int32_t>(), nc, P.recs.as<CritRec>(),
-                   P.cnt[0].as<int32_t>(), P.cnt[1].as<int32_t>(), P.cnt[2].as<int32_t>(),
-                   P.cnt[3].as<int32_t>(), P.vrank.as<int32_t>(), P.flags.as<uint8_t>(),
-                   P.grad.as<GradRec>());
-        KEV(7);
+        DMS_LAUNCH(nc, 256, k_critrec, P.vc.as<int32_t>(), nc, P.grad.as<GradRec>(),
+                   P.recs.as<CritRec>(), P.cnt[0].as<int32_t>(), P.cnt[1].as<int32_t>(),
+                   P.cnt[2].as<int32_t>(), P.cnt[3].as<int32_t>(), P.vrank.as<int32_t>());
     }
     cudaEventRecord(ev[2], c.s);
 
@@ -1881,7 +2090,7 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
     DMS_ALLOC(P.d1_ovf, ncols + 4);
     DMS_LAUNCH(n2, 256, k_compact_idx, is_col, P.flag_b.as<int32_t>(), n2, P.d1_colmap.as<int32_t>());
     DMS_CUDA(cudaMemsetAsync(P.d1_len.p, 0, 4 * ncols + 4, c.s));
-    int64_t pool_cap = std::max<int64_t>(1 << 22, 32 * ncols + 1024);
+    int64_t pool_cap = std::max<int64_t>(1 << 24, 128 * ncols + 1024);
     DMS_ALLOC(P.d1_pool, 4 * pool_cap);
     P.rounds_d1 = 0;
     DMS_ALLOC(P.d1_row, 4 * ncols + 4);
@@ -1894,16 +2103,17 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
         DMS_CUDA(cudaMemsetAsync(&c.st->pool_top, 0, sizeof(unsigned long long), c.s));
         // first pass: small per-thread scratch that stays in L2
         int hcap = 48, hashcap = 64, rcap = 48;
-        int64_t nthreads = 152 * 2 * 128;
+        int64_t nthreads = 152 * 16 * 128;
         if (ncols < nthreads) nthreads = (ncols + 127) / 128 * 128;
         size_t per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
-                     (size_t)rcap * 4;
+                     (size_t)rcap * 8;
         DMS_ALLOC(P.d1_scratch, per * nthreads);
         HeapEnt *heap = P.d1_scratch.as<HeapEnt>();
         HashEnt *hash = (HashEnt *)(heap + (size_t)hcap * nthreads);
         int32_t *rows = (int32_t *)(hash + (size_t)hashcap * nthreads);
         DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nthreads * sizeof(HashEnt), c.s));
         KEV(18);
+        auto dbg_p1 = std::chrono::steady_clock::now();
         k_d1_trace<T><<<(unsigned)(nthreads / 128), 128, 0, c.s>>>(
             values, c.g, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
             P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
@@ -1920,12 +2130,18 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
         for (int64_t q = 0; q < ncols; q++)
             if (hovf[q]) todo.push_back((int32_t)q);
         P.d1_overflow = (int64_t)todo.size();
+        auto dbg_t0 = std::chrono::steady_clock::now();
+        if (getenv("DMS_DEBUG")) {
+            fprintf(stderr, "d1 trace pass 1: %lld columns, %zu overflow, pool %llu, %.3f ms\n",
+                    (long long)ncols, todo.size(), c.hst->pool_top,
+                    std::chrono::duration<double, std::milli>(dbg_t0 - dbg_p1).count());
+        }
         int32_t gen = (int32_t)ncols;
         while (!todo.empty()) {
             hcap *= 16; hashcap *= 16; rcap *= 16;
             if (hashcap > (1 << 24)) return DMS_ERR_CAPACITY;
             per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
-                  (size_t)rcap * 4;
+                  (size_t)rcap * 8;
             int64_t nt = std::min<int64_t>((int64_t)todo.size(),
                                            std::max<int64_t>(32, ((int64_t)4 << 30) / (int64_t)per));
             nt = (nt + 31) / 32 * 32;
@@ -1954,6 +2170,10 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
                 if (hovf[q]) next.push_back(q);
             todo.swap(next);
         }
+        if (getenv("DMS_DEBUG"))
+            fprintf(stderr, "d1 trace retries: %.3f ms\n",
+                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                              dbg_t0).count());
         KEV(19);
         KEV(20);
         DMS_TRY(reduce_d1(c, ncols, n1, is_row));
