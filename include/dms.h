@@ -123,7 +123,7 @@ dms_status dms_get_stage_ms(dms_grid grid, float ms[8]);
  * [7] D2 halving levels, [8] D1 reduction rounds, [9] D1 columns, [10] D1
  * columns whose boundary outgrew the first scratch pass, [11] D1 column
  * additions, [12] D1 column-pool entries used, [13] D1 pool regrowths,
- * [14..15] reserved (0). */
+ * [14] D1 entries read by additions, [15] D1 entries written by additions. */
 dms_status dms_get_stats(dms_grid grid, int64_t stats[16]);
 
 /* Device milliseconds of the last compute per kernel family, from CUDA event

@@ -68,7 +68,8 @@ dms_status dms_get_stats(dms_grid grid, int64_t stats[16]) {
     stats[11] = p.d1_additions;
     stats[12] = p.d1_pool_used;
     stats[13] = p.d1_pool_grows;
-    for (int k = 14; k < 16; k++) stats[k] = 0;
+    stats[14] = p.d1_io_read;
+    stats[15] = p.d1_io_written;
     return DMS_OK;
 }
 

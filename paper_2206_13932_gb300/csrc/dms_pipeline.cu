@@ -39,6 +39,7 @@ struct DevStatus {
     unsigned long long maxkey;     // largest vertex key
     long long total[4];            // scan totals
     long long parts[8];            // output part sizes
+    long long red_io[2];           // D1 additions: entries read, entries written
     int changed;                   // D1: columns changed this round
     unsigned long long pool_top;   // D1 column pool bump pointer
     long long misc[4];
@@ -1236,6 +1237,7 @@ __global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nre = *(volatile long long *)&st->misc[0];
     unsigned adds = 0, longest = 0;
+    unsigned long long io_r = 0, io_w = 0;
     for (int64_t q = warp; q < nactive + nre; q += nwarps) {
         int32_t cj = q < nactive ? active[q] : recheck[q - nactive];
         int fresh = 0;
@@ -1257,7 +1259,9 @@ __global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
                 if (lane == 0) atomicOr(&st->err, kErrCap);
                 break;
             }
+            io_r += (unsigned long long)(la + lb);
             la = warp_symdiff(pool + sa, la, pool + sb, lb, pool + pos);
+            io_w += (unsigned long long)la;
             sa = (int64_t)pos;
             changed = true;
             chain++;
@@ -1273,6 +1277,8 @@ __global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
     if (lane == 0 && adds) {
         atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)adds);
         atomicMax((unsigned long long *)&st->misc[3], (unsigned long long)longest);
+        atomicAdd((unsigned long long *)&st->red_io[0], io_r);
+        atomicAdd((unsigned long long *)&st->red_io[1], io_w);
     }
 }
 
@@ -1352,6 +1358,7 @@ __global__ void __launch_bounds__(kRedBlock)
     int64_t sa = start[cj];
     bool changed = false;
     unsigned chain = 0;
+    unsigned long long io_r = 0, io_w = 0;
     for (int it = 0; la > 0 && it < (1 << 24); it++) {
         if (threadIdx.x == 0) s_k = owner[pool[sa]];
         __syncthreads();
@@ -1366,8 +1373,10 @@ __global__ void __launch_bounds__(kRedBlock)
             if (threadIdx.x == 0) atomicOr(&st->err, kErrCap);
             break;
         }
+        io_r += (unsigned long long)(la + lb);
         la = block_symdiff<kRedBlock>(pool + sa, la, pool + sb, lb, pool + pos, sA, sB, kRedStage,
                                       sscan);
+        io_w += (unsigned long long)la;
         sa = (int64_t)pos;
         changed = true;
         chain++;
@@ -1381,6 +1390,8 @@ __global__ void __launch_bounds__(kRedBlock)
         if (chain) {
             atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)chain);
             atomicMax((unsigned long long *)&st->misc[3], (unsigned long long)chain);
+            atomicAdd((unsigned long long *)&st->red_io[0], io_r);
+            atomicAdd((unsigned long long *)&st->red_io[1], io_w);
         }
     }
 }
@@ -1872,6 +1883,8 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
         nactive = c.hst->misc[1];
         std::swap(P.d1_act, P.d1_next);
         if (nactive == 0) {
+            P.d1_io_read = c.hst->red_io[0];
+            P.d1_io_written = c.hst->red_io[1];
             P.d1_additions = c.hst->misc[2];
             P.d1_pool_used = (int64_t)c.hst->pool_top;
             return DMS_OK;
