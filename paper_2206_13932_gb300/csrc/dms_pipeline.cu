@@ -1288,7 +1288,7 @@ template <int NT>
 __device__ int block_symdiff(const int32_t *A, int la, const int32_t *B, int lb, int32_t *out,
                              int32_t *sA, int32_t *sB, int cap, int *sscan) {
     const int t = threadIdx.x;
-    if (la <= cap && lb <= cap) {
+    if (sA && la <= cap && lb <= cap) {
         for (int k = t; k < la; k += NT) sA[k] = A[k];
         for (int k = t; k < lb; k += NT) sB[k] = B[k];
         __syncthreads();
@@ -1333,14 +1333,21 @@ __device__ int block_symdiff(const int32_t *A, int la, const int32_t *B, int lb,
 }
 
 // The same as k_red_add with one block per listed column, for the last rounds
-// where few columns remain and their additions are long.
-constexpr int kRedBlock = 256, kRedStage = 6144;
+// where few columns remain and their chains of additions are long.  The
+// column being reduced stays in shared memory (two buffers) while it fits:
+// an addition reads only the added column from global memory; the result is
+// written back once at the end.  A column that outgrows the buffers continues
+// with merges through the global pool.
+constexpr int kRedBlock = 512, kRedAcc = 6144, kRedStage = 6144;
+constexpr size_t kRedSmem = sizeof(int32_t) * (2 * kRedAcc + kRedStage);
 __global__ void __launch_bounds__(kRedBlock)
     k_red_add_block(const int32_t *__restrict__ active, int64_t nactive,
                     const int32_t *__restrict__ recheck, int64_t *start, int32_t *len,
                     int32_t *pool, const int32_t *__restrict__ owner, int32_t *stamp,
                     int32_t round, int32_t *next, int64_t pool_cap, DevStatus *st) {
-    __shared__ int32_t sA[kRedStage], sB[kRedStage];
+    extern __shared__ int32_t smem[];
+    int32_t *acc[2] = {smem, smem + kRedAcc};
+    int32_t *sB = smem + 2 * kRedAcc;
     __shared__ int sscan[kRedBlock / 32];
     __shared__ int32_t s_cj, s_k, s_fresh;
     __shared__ unsigned long long s_pos;
@@ -1356,30 +1363,64 @@ __global__ void __launch_bounds__(kRedBlock)
     const int32_t cj = s_cj;
     int la = len[cj];
     int64_t sa = start[cj];
-    bool changed = false;
+    // resident: the column lives in acc[cur]; otherwise at pool[sa]
+    bool resident = la <= kRedAcc;
+    int cur = 0;
+    if (resident) {
+        for (int k = threadIdx.x; k < la; k += kRedBlock) acc[0][k] = pool[sa + k];
+        __syncthreads();
+    }
+    bool changed = false, failed = false;
     unsigned chain = 0;
     unsigned long long io_r = 0, io_w = 0;
     for (int it = 0; la > 0 && it < (1 << 24); it++) {
-        if (threadIdx.x == 0) s_k = owner[pool[sa]];
+        if (threadIdx.x == 0) s_k = owner[resident ? acc[cur][0] : pool[sa]];
         __syncthreads();
-        int32_t k = s_k;
+        const int32_t k = s_k;
         if (k == cj || k == kNoOwner || k > cj) break;
-        int64_t sb = start[k];
-        int lb = len[k];
-        if (threadIdx.x == 0) s_pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
-        __syncthreads();
-        unsigned long long pos = s_pos;
-        if ((int64_t)(pos + la + lb) > pool_cap) {
-            if (threadIdx.x == 0) atomicOr(&st->err, kErrCap);
-            break;
+        const int64_t sb = start[k];
+        const int lb = len[k];
+        const int32_t *B = pool + sb;
+        if (lb <= kRedStage) {
+            for (int t = threadIdx.x; t < lb; t += kRedBlock) sB[t] = B[t];
+            B = sB;
         }
         io_r += (unsigned long long)(la + lb);
-        la = block_symdiff<kRedBlock>(pool + sa, la, pool + sb, lb, pool + pos, sA, sB, kRedStage,
-                                      sscan);
+        if (resident && la + lb <= kRedAcc) {
+            __syncthreads();
+            la = block_symdiff<kRedBlock>(acc[cur], la, B, lb, acc[cur ^ 1], nullptr, nullptr, 0,
+                                          sscan);
+            cur ^= 1;
+        } else {
+            if (threadIdx.x == 0) s_pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
+            __syncthreads();
+            const unsigned long long pos = s_pos;
+            if ((int64_t)(pos + la + lb) > pool_cap) {
+                if (threadIdx.x == 0) atomicOr(&st->err, kErrCap);
+                failed = true;
+                break;
+            }
+            la = block_symdiff<kRedBlock>(resident ? acc[cur] : pool + sa, la, B, lb, pool + pos,
+                                          nullptr, nullptr, 0, sscan);
+            sa = (int64_t)pos;
+            resident = false;
+        }
         io_w += (unsigned long long)la;
-        sa = (int64_t)pos;
         changed = true;
         chain++;
+    }
+    if (changed && resident && !failed) {
+        // write the reduced column back to the pool
+        if (threadIdx.x == 0) s_pos = la ? atomicAdd(&st->pool_top, (unsigned long long)la) : 0;
+        __syncthreads();
+        const unsigned long long pos = s_pos;
+        if ((int64_t)(pos + la) > pool_cap) {
+            if (threadIdx.x == 0) atomicOr(&st->err, kErrCap);
+            changed = false;    // the column keeps its previous state
+        } else {
+            for (int t = threadIdx.x; t < la; t += kRedBlock) pool[pos + t] = acc[cur][t];
+            sa = (int64_t)pos;
+        }
     }
     if (threadIdx.x == 0) {
         if (changed) {
@@ -1700,6 +1741,8 @@ dms_status ensure_tables(int device) {
     build_regular_lut(S, lut);
     DMS_CUDA(cudaMemcpyToSymbol(g_star, &S, sizeof S));
     DMS_CUDA(cudaMemcpyToSymbol(g_regular, lut.data(), lut.size() * sizeof(uint32_t)));
+    DMS_CUDA(cudaFuncSetAttribute(k_red_add_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kRedSmem));
     if (device < 32) g_tables_ready |= 1u << device;
     return DMS_OK;
 }
@@ -1827,7 +1870,7 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
                        P.d1_next.as<int32_t>(), pool_cap, c.st);
         } else {
             // one block per column (grid covers active + displaced, <= 2x active)
-            k_red_add_block<<<(unsigned)(2 * nactive), kRedBlock, 0, c.s>>>(
+            k_red_add_block<<<(unsigned)(2 * nactive), kRedBlock, kRedSmem, c.s>>>(
                 P.d1_act.as<int32_t>(), nactive, P.d1_re.as<int32_t>(), P.d1_start.as<int64_t>(),
                 P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), P.d1_owner.as<int32_t>(),
                 P.d1_stamp.as<int32_t>(), (int32_t)stamp, P.d1_next.as<int32_t>(), pool_cap, c.st);
