@@ -135,6 +135,39 @@ dms_status dms_get_stats(dms_grid grid, int64_t stats[16]);
  * reduction, [11] output. */
 dms_status dms_get_kernel_ms(dms_grid grid, float ms[12]);
 
+/* Lower-link classification of every vertex and the id-ordered list of the
+ * PL-critical vertices (the first step of the gradient), computed without
+ * allocating any memory.  The paper has no counterpart: this entry point
+ * exists for callers that cannot let a library call cudaMalloc -- for
+ * example a process whose device memory is all handed to its own pool
+ * allocator at start-up, a service running under a fixed per-request memory
+ * budget, or a latency-critical pipeline where an allocation (which may
+ * synchronise the device) would stall its other streams.
+ *
+ * Its scratch is one fixed array in the library's device memory, sized for
+ * at most 2^28 vertices (about 1 MB); every GPU that loads the library holds
+ * it until the process exits.  Grids with more vertices are rejected with
+ * DMS_ERR_INVALID_ARG.  All calls share that array: calls that overlap on
+ * the GPU (from several streams or threads) race and must be serialised by
+ * the caller.  The first call on a device (with that device current) looks
+ * up the array's address and uploads the star tables; make that first call
+ * before any stream capture.
+ *
+ * values:       device pointer, nx*ny*nz elements of dtype, x fastest.
+ * flags_out:    device pointer, nx*ny*nz bytes: low nibble = link index of
+ *               the lowest lower neighbour (0xF: a minimum), bit 4 set for
+ *               a PL-critical vertex (other bits 0).
+ * critical_out: device pointer with room for cap int32: the ids of the
+ *               PL-critical vertices in increasing order.
+ * n_critical:   host pointer: their number (also set when cap is too small,
+ *               in which case DMS_ERR_CAPACITY is returned and critical_out
+ *               is not written).
+ * stream:       cudaStream_t (NULL = legacy default); the call synchronises
+ *               it.  NaN in the field -> DMS_ERR_NAN. */
+dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, int64_t ny,
+                               int64_t nz, uint8_t *flags_out, int32_t *critical_out,
+                               int64_t cap, int64_t *n_critical, void *stream);
+
 /* Frees every device and host resource of the handle. */
 dms_status dms_grid_destroy(dms_grid grid);
 

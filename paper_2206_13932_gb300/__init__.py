@@ -17,7 +17,8 @@ import numpy as np
 from ._build_lib import LIB as _LIB_PATH
 from ._build_lib import build
 
-__all__ = ["build", "load", "Grid", "diagram", "PAIR_DTYPE", "DmsError", "STATUS"]
+__all__ = ["build", "load", "Grid", "diagram", "classify_static", "PAIR_DTYPE", "DmsError",
+           "STATUS"]
 
 PAIR_DTYPE = np.dtype([("birth_simplex", "<i8"), ("death_simplex", "<i8"),
                        ("birth_vertex", "<i8"), ("death_vertex", "<i8"),
@@ -65,6 +66,9 @@ def load(build_if_missing: bool = False):
             lib.dms_get_stage_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
             lib.dms_get_stats.argtypes = [vp, p64]
             lib.dms_get_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+            lib.dms_classify_static.argtypes = [vp, ctypes.c_int, i64, i64, i64, vp, vp, i64,
+                                                p64, vp]
+            lib.dms_classify_static.restype = ctypes.c_int
             lib.dms_grid_destroy.argtypes = [vp]
             lib.dms_status_string.argtypes = [ctypes.c_int]
             lib.dms_status_string.restype = ctypes.c_char_p
@@ -192,6 +196,27 @@ class Grid:
                  "levels_d2", "rounds_d1", "d1_columns", "d1_trace_overflow", "d1_additions",
                  "d1_pool_used", "d1_pool_grows", "d1_entries_read", "d1_entries_written")
         return dict(zip(names, [int(x) for x in s]))
+
+
+def classify_static(values, flags_out, critical_out, stream=None) -> int:
+    """Binding of ``dms_classify_static`` (allocates nothing on the device).
+
+    ``values``: CUDA tensor indexed [z, y, x]; ``flags_out``: CUDA uint8
+    tensor of values.numel() bytes; ``critical_out``: CUDA int32 tensor whose
+    length is the capacity.  Returns the number of PL-critical vertices."""
+    import torch
+    lib = load()
+    nz, ny, nx = values.shape
+    dt = np.dtype(str(values.dtype).replace("torch.", ""))
+    n = ctypes.c_int64(0)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib.dms_classify_static(ctypes.c_void_p(values.data_ptr()), _DTYPE_CODE[dt], nx, ny,
+                                   nz, ctypes.c_void_p(flags_out.data_ptr()),
+                                   ctypes.c_void_p(critical_out.data_ptr()),
+                                   critical_out.numel(), ctypes.byref(n),
+                                   ctypes.c_void_p(int(stream))), "dms_classify_static")
+    return n.value
 
 
 def diagram(values, shape_xyz=None, stream=None) -> dict:

@@ -17,6 +17,7 @@
 //   output     pairs and infinite classes (Sec. 6).
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -2291,6 +2292,86 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
 
 }  // namespace
 
+// ------------------------------------------------------------------------
+// Classification without allocation (dms_classify_static).
+//
+// Its scratch is a file-scope device array of fixed size, sized for grids of
+// up to kStaticMaxVertices vertices: the per-tile counts and offsets of the
+// ordered compaction, the partial sums of their scan and a status block.
+// Every device that loads this library holds the array until the process
+// exits.  Host code cannot use the array's name as a device address, so its
+// address is looked up once per device with cudaGetSymbolAddress and passed
+// to the kernels.
+constexpr int64_t kStaticMaxVertices = (int64_t)1 << 28;
+constexpr int64_t kStaticTiles = kStaticMaxVertices / kClsTile;           // 131072
+constexpr int64_t kStaticParts = (kStaticTiles + kScanTile - 1) / kScanTile;  // 64
+struct StaticScratch {
+    int32_t tile_cnt[kStaticTiles];
+    int32_t tile_off[kStaticTiles];
+    int32_t part[kStaticParts];
+    int32_t part_off[kStaticParts];
+    DevStatus status;
+};
+static __device__ __align__(256) StaticScratch g_static_scratch;
+
+namespace {
+std::mutex g_static_mutex;
+StaticScratch *g_static_ptr[64] = {nullptr};   // per device, from cudaGetSymbolAddress
+
+// Set-up on first use on a device (that device current): the star tables and
+// the address of the scratch array.  Must run before any stream capture.
+dms_status static_setup(int device, StaticScratch **out) {
+    if (device < 0 || device >= 64) return DMS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[device]) {
+        dms_status s = ensure_tables(device);
+        if (s != DMS_OK) return s;
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr) {
+            fprintf(stderr, "libdms: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+            return DMS_ERR_CUDA;
+        }
+        g_static_ptr[device] = (StaticScratch *)ptr;
+    }
+    *out = g_static_ptr[device];
+    return DMS_OK;
+}
+
+template <typename T>
+dms_status classify_static(const T *values, GridParams g, uint8_t *flags, int32_t *critical,
+                           int64_t cap, int64_t *n_critical, cudaStream_t s, StaticScratch *scr) {
+    const int64_t ntiles = (g.n + kClsTile - 1) / kClsTile;
+    DevStatus *st = &scr->status;
+    DMS_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));   // starts at zero every call
+    k_classify<T><<<(unsigned)ntiles, kClsThreads, 0, s>>>(values, g, flags, scr->tile_cnt, st);
+    DMS_CUDA(cudaGetLastError());
+    if (ntiles <= kScanTile) {
+        k_scan_apply<<<1, kScanThreads, 0, s>>>(scr->tile_cnt, scr->tile_off, ntiles, nullptr,
+                                                &st->total[0]);
+    } else {
+        const int64_t m = (ntiles + kScanTile - 1) / kScanTile;
+        k_scan_partial<<<(unsigned)m, kScanThreads, 0, s>>>(scr->tile_cnt, ntiles, scr->part);
+        k_scan_apply<<<1, kScanThreads, 0, s>>>(scr->part, scr->part_off, m, nullptr, nullptr);
+        k_scan_apply<<<(unsigned)m, kScanThreads, 0, s>>>(scr->tile_cnt, scr->tile_off, ntiles,
+                                                          scr->part_off, &st->total[0]);
+    }
+    DMS_CUDA(cudaGetLastError());
+    long long total = 0;
+    uint32_t err = 0;
+    DMS_CUDA(cudaMemcpyAsync(&total, &st->total[0], sizeof total, cudaMemcpyDeviceToHost, s));
+    DMS_CUDA(cudaMemcpyAsync(&err, &st->err, sizeof err, cudaMemcpyDeviceToHost, s));
+    DMS_CUDA(cudaStreamSynchronize(s));
+    if (err & kErrNan) return DMS_ERR_NAN;
+    *n_critical = total;
+    if (total > cap) return DMS_ERR_CAPACITY;
+    k_compact<<<(unsigned)ntiles, kClsThreads, 0, s>>>(flags, g.n, scr->tile_off, critical);
+    DMS_CUDA(cudaGetLastError());
+    DMS_CUDA(cudaStreamSynchronize(s));
+    return DMS_OK;
+}
+}  // namespace
+
 dms_status Pipeline::init(int64_t nx_, int64_t ny_, int64_t nz_, dms_dtype dt,
                           const dms_options *o) {
     if (nx_ < 1 || ny_ < 1 || nz_ < 1 || nx_ > (1 << 30) || ny_ > (1 << 30) || nz_ > (1 << 30))
@@ -2417,3 +2498,39 @@ dms_status Pipeline::fetch(int dim, dms_pair *out, int64_t cap, int64_t *written
 }
 
 }  // namespace dms
+
+extern "C" dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx,
+                                          int64_t ny, int64_t nz, uint8_t *flags_out,
+                                          int32_t *critical_out, int64_t cap,
+                                          int64_t *n_critical, void *stream) {
+    using namespace dms;
+    if (!values || !flags_out || !n_critical || cap < 0 || (cap > 0 && !critical_out))
+        return DMS_ERR_INVALID_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > kStaticMaxVertices || ny > kStaticMaxVertices ||
+        nz > kStaticMaxVertices || nx * ny > kStaticMaxVertices ||
+        nx * ny * nz > kStaticMaxVertices)
+        return DMS_ERR_INVALID_ARG;   // beyond the fixed scratch
+    if (dtype != DMS_U16 && dtype != DMS_F32 && dtype != DMS_F64) return DMS_ERR_INVALID_ARG;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return DMS_ERR_CUDA;
+    StaticScratch *scr = nullptr;
+    dms_status st = static_setup(device, &scr);
+    if (st != DMS_OK) return st;
+    GridParams g;
+    g.nx = (int32_t)nx; g.ny = (int32_t)ny; g.nz = (int32_t)nz; g.n = nx * ny * nz;
+    for (int l = 0; l < kLinks; l++) {
+        int o = l % 7 + 1, sg = l < 7 ? 1 : -1;
+        g.dlin[l] = sg * ((o & 1) + (int32_t)nx * (((o >> 1) & 1) + (int32_t)ny * ((o >> 2) & 1)));
+    }
+    *n_critical = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == DMS_U16)
+        return classify_static<uint16_t>((const uint16_t *)values, g, flags_out, critical_out, cap,
+                                         n_critical, s, scr);
+    if (dtype == DMS_F32)
+        return classify_static<float>((const float *)values, g, flags_out, critical_out, cap,
+                                      n_critical, s, scr);
+    return classify_static<double>((const double *)values, g, flags_out, critical_out, cap,
+                                   n_critical, s, scr);
+}
+
