@@ -1339,7 +1339,7 @@ __device__ int block_symdiff(const int32_t *A, int la, const int32_t *B, int lb,
 // an addition reads only the added column from global memory; the result is
 // written back once at the end.  A column that outgrows the buffers continues
 // with merges through the global pool.
-constexpr int kRedBlock = 512, kRedAcc = 6144, kRedStage = 6144;
+constexpr int kRedBlock = 512, kRedAcc = 24576, kRedStage = 4096;
 constexpr size_t kRedSmem = sizeof(int32_t) * (2 * kRedAcc + kRedStage);
 __global__ void __launch_bounds__(kRedBlock)
     k_red_add_block(const int32_t *__restrict__ active, int64_t nactive,

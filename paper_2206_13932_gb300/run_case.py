@@ -27,6 +27,8 @@ def main():
     ap.add_argument("--edge", type=int, default=128)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--d1-mode", type=int, default=0)
+    ap.add_argument("--op", default="diagram", choices=["diagram", "classify"],
+                    help="classify: only dms_classify_static (allocates nothing but the outputs)")
     a = ap.parse_args()
     e = a.edge
     if a.workload == "noise":
@@ -36,6 +38,19 @@ def main():
     else:
         v = sf.config_field("mixture32_f32", shape_xyz=(e, e, e))
     t = torch.from_numpy(v).cuda()
+    if a.op == "classify":
+        flags = torch.empty(t.numel(), dtype=torch.uint8, device="cuda")
+        crit = torch.empty(t.numel(), dtype=torch.int32, device="cuda")
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(a.repeat):
+            start.record()
+            n = dms.classify_static(t, flags, crit)
+            end.record()
+            torch.cuda.synchronize()
+            ms.append(start.elapsed_time(end))
+        print(json.dumps({"critical_vertices": n, "classify_call_ms": ms}))
+        return
     with dms.Grid((e, e, e), v.dtype, d1_mode=a.d1_mode) as g:
         for _ in range(a.repeat):
             g.compute(t)
