@@ -319,53 +319,175 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t *__re
 
 constexpr int kClsThreads = 256, kClsItems = 8, kClsTile = kClsThreads * kClsItems;
 
+// ---- the tier-1 stencil, register-tiled
+//
+// A thread classifies a run of K = 16/sizeof(T) consecutive vertices of one
+// row (x fastest).  Interior runs (all 14 neighbours present, 16-byte
+// aligned rows) load the 7 rows they need as 16-byte vectors plus the two
+// edge values and index every neighbour statically; other runs use the
+// per-vertex path.  A block covers R whole consecutive rows, i.e. a
+// contiguous id range (a tile of R*nx vertices), so that the ordered
+// compaction can follow.  Link id order (used for ties): -7..-1, +1..+7.
+
+// per-vertex path (boundary runs)
+template <typename T>
+__device__ __forceinline__ uint8_t classify_vertex(const StarTables &S, const GridParams &g,
+                                                   const uint32_t *lut, const T *__restrict__ values,
+                                                   int64_t v, int cx, int cy, int cz,
+                                                   typename Key<T>::K &kv) {
+    using K = typename Key<T>::K;
+    uint16_t pres = present_links(S, g, cx, cy, cz);
+    kv = Key<T>::of(values[v]);
+    uint16_t lower = 0;
+    K best = 0;
+    int bn = -1;
+#pragma unroll
+    for (int n = 0; n < kLinks; n++) {
+        if (pres >> n & 1) {
+            K kn = Key<T>::of(values[v + g.dlin[n]]);
+            bool lo = kn < kv || (kn == kv && n >= 7);
+            if (lo) {
+                lower |= (uint16_t)(1u << n);
+                if (bn < 0 || kn < best || (kn == best && g.dlin[n] < g.dlin[bn])) {
+                    best = kn;
+                    bn = n;
+                }
+            }
+        }
+    }
+    bool crit = !((lut[lower >> 5] >> (lower & 31)) & 1);
+    return (uint8_t)((bn < 0 ? kNoDescent : bn) | (crit ? kFlagCritical : 0));
+}
+
+template <typename T> struct VecOf;
+template <> struct VecOf<uint16_t> { static constexpr int K = 8; };
+template <> struct VecOf<float> { static constexpr int K = 4; };
+template <> struct VecOf<double> { static constexpr int K = 2; };
+
 template <typename T>
 __global__ void __launch_bounds__(kClsThreads)
-    k_classify(const T *__restrict__ values, GridParams g, uint8_t *__restrict__ flags,
-               int32_t *__restrict__ tile_cnt, DevStatus *st) {
-    using K = typename Key<T>::K;
+    k_classify2(const T *__restrict__ values, GridParams g, int rows_per_block, int runs_per_row,
+                int aligned, uint8_t *__restrict__ flags, int32_t *__restrict__ tile_cnt,
+                DevStatus *st) {
+    using Kt = typename Key<T>::K;
+    constexpr int K = VecOf<T>::K;
     __shared__ uint32_t lut[(1 << kLinks) / 32];
     __shared__ int scnt[kClsThreads / 32];
     __shared__ unsigned long long smax[kClsThreads / 32];
     for (int i = threadIdx.x; i < (1 << kLinks) / 32; i += kClsThreads) lut[i] = g_regular[i];
     __syncthreads();
     const StarTables &S = g_star;
-    int64_t base = (int64_t)blockIdx.x * kClsTile;
+    const int64_t nrows = (int64_t)g.ny * g.nz;
+    const int64_t row0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t plane = (int64_t)g.nx * g.ny;
     int cnt = 0;
-    K kmax = 0;
+    Kt kmax = 0;
     bool bad = false;
-    for (int k = 0; k < kClsItems; k++) {
-        int64_t v = base + k * kClsThreads + threadIdx.x;
-        if (v >= g.n) break;
-        int cx, cy, cz;
-        coords(g, v, cx, cy, cz);
-        uint16_t pres = present_links(S, g, cx, cy, cz);
-        T xv = values[v];
-        bad |= Key<T>::nan(xv);
-        K kv = Key<T>::of(xv);
-        uint16_t lower = 0;
-        K best = 0;
-        int bn = -1;
+    for (int s = threadIdx.x; s < rows_per_block * runs_per_row; s += kClsThreads) {
+        const int64_t row = row0 + s / runs_per_row;
+        if (row >= nrows) break;
+        const int x0 = (s % runs_per_row) * K;
+        const int cy = (int)(row % g.ny), cz = (int)(row / g.ny);
+        const int64_t base = row * g.nx + x0;
+        // y/z-interior rows take the fast path (uniform across a warp, which
+        // covers one row); x-edge vertices are masked inside it
+        const bool interior = aligned && cy >= 1 && cy <= g.ny - 2 && cz >= 1 && cz <= g.nz - 2;
+        const bool xlo = x0 == 0, xhi = x0 + K >= g.nx;
+        uint8_t f[K];
+        if (interior) {
+            // rows: 0 (0,0) 1 (+y) 2 (-y) 3 (+z) 4 (-z) 5 (+y+z) 6 (-y-z); values x0-1 .. x0+K
+            Kt r[7][K + 2];
+            const int64_t roff[7] = {0, g.nx, -(int64_t)g.nx, plane, -plane, g.nx + plane,
+                                     -(int64_t)g.nx - plane};
 #pragma unroll
-        for (int n = 0; n < kLinks; n++) {
-            if (pres >> n & 1) {
-                K kn = Key<T>::of(values[v + g.dlin[n]]);
-                bool lo = kn < kv || (kn == kv && n >= 7);
-                if (lo) {
-                    lower |= (uint16_t)(1u << n);
-                    if (bn < 0 || kn < best || (kn == best && g.dlin[n] < g.dlin[bn])) {
-                        best = kn;
-                        bn = n;
+            for (int q = 0; q < 7; q++) {
+                const T *p = values + base + roff[q];
+                union { uint4 u; T t[K]; } vec;
+                vec.u = __ldg((const uint4 *)p);
+                r[q][0] = xlo ? Kt(0) : Key<T>::of(__ldg(p - 1));
+#pragma unroll
+                for (int i = 0; i < K; i++) {
+                    r[q][i + 1] = Key<T>::of(vec.t[i]);
+                    if (q == 0) bad |= Key<T>::nan(vec.t[i]);
+                }
+                r[q][K + 1] = xhi ? Kt(0) : Key<T>::of(__ldg(p + K));
+            }
+#pragma unroll
+            for (int i = 0; i < K; i++) {
+                const Kt kv = r[0][i + 1];
+                // neighbours in id order -7 -6 -5 -4 -3 -2 -1 +1 .. +7 with their link
+                // index (o-1 for +o, o+6 for -o)
+                const Kt nb[14] = {r[6][i], r[6][i + 1], r[4][i], r[4][i + 1], r[2][i], r[2][i + 1],
+                                   r[0][i], r[0][i + 2], r[1][i + 1], r[1][i + 2], r[3][i + 1],
+                                   r[3][i + 2], r[5][i + 1], r[5][i + 2]};
+                constexpr int link[14] = {13, 12, 11, 10, 9, 8, 7, 0, 1, 2, 3, 4, 5, 6};
+                uint32_t lower = 0;
+                int bn = kNoDescent;
+                // absent x neighbours: -x links (q 0 2 4 6) at x = 0, +x links
+                // (q 7 9 11 13) at x = nx-1
+                const bool nox_lo = xlo && i == 0, nox_hi = xhi && x0 + i == g.nx - 1;
+                if constexpr (sizeof(Kt) == 4 && sizeof(T) == 2) {
+                    // 16-bit values: key = value << 4 | position in id order (-7..-1 at
+                    // 0..6, +1..+7 at 8..14), centre = value << 4 | 7.  A neighbour is
+                    // lower iff its key is smaller (ties resolved by id), and the lowest
+                    // lower neighbour is the smallest key.
+                    const uint32_t c = (kv << 4) | 7u;
+                    uint32_t mn = 0xFFFFFFFFu;
+#pragma unroll
+                    for (int q = 0; q < 14; q++) {
+                        const bool absent = ((q == 0 || q == 2 || q == 4 || q == 6) && nox_lo) ||
+                                            ((q == 7 || q == 9 || q == 11 || q == 13) && nox_hi);
+                        const uint32_t key = absent ? 0xFFFFFFFFu
+                                                    : (((uint32_t)nb[q] << 4) | (uint32_t)(q < 7 ? q : q + 1));
+                        lower |= (uint32_t)(key < c) << link[q];
+                        mn = key < mn ? key : mn;
+                    }
+                    if (mn < c) {
+                        const uint32_t pos = mn & 15u;
+                        // position -> link index: 0..6 -> 13..7, 8..14 -> 0..6
+                        bn = pos < 7 ? 13 - (int)pos : (int)pos - 8;
+                    }
+                } else {
+                    Kt best = kv;
+#pragma unroll
+                    for (int q = 0; q < 14; q++) {
+                        const bool absent = ((q == 0 || q == 2 || q == 4 || q == 6) && nox_lo) ||
+                                            ((q == 7 || q == 9 || q == 11 || q == 13) && nox_hi);
+                        const bool lo = !absent && (q < 7 ? nb[q] <= kv : nb[q] < kv);
+                        lower |= (uint32_t)lo << link[q];
+                        // in id order, strict-less keeps the smallest id among equal values
+                        const bool take = lo && (bn == kNoDescent || nb[q] < best);
+                        best = take ? nb[q] : best;
+                        bn = take ? link[q] : bn;
                     }
                 }
+                const bool crit = !((lut[lower >> 5] >> (lower & 31)) & 1);
+                f[i] = (uint8_t)(bn | (crit ? kFlagCritical : 0));
+                cnt += crit;
+                kmax = kv > kmax ? kv : kmax;
+            }
+            if constexpr (K == 8) {
+                *(uint2 *)(flags + base) = make_uint2(
+                    f[0] | (f[1] << 8) | (f[2] << 16) | ((uint32_t)f[3] << 24),
+                    f[4] | (f[5] << 8) | (f[6] << 16) | ((uint32_t)f[7] << 24));
+            } else if constexpr (K == 4) {
+                *(uint32_t *)(flags + base) =
+                    f[0] | (f[1] << 8) | (f[2] << 16) | ((uint32_t)f[3] << 24);
+            } else {
+                *(uint16_t *)(flags + base) = (uint16_t)(f[0] | (f[1] << 8));
+            }
+        } else {
+            for (int i = 0; i < K && x0 + i < g.nx; i++) {
+                Kt kv;
+                const uint8_t fl = classify_vertex<T>(S, g, lut, values, base + i, x0 + i, cy, cz, kv);
+                bad |= Key<T>::nan(values[base + i]);
+                flags[base + i] = fl;
+                cnt += (fl & kFlagCritical) != 0;
+                kmax = kv > kmax ? kv : kmax;
             }
         }
-        bool crit = !((lut[lower >> 5] >> (lower & 31)) & 1);
-        flags[v] = (uint8_t)((bn < 0 ? kNoDescent : bn) | (crit ? kFlagCritical : 0));
-        cnt += crit;
-        kmax = kv > kmax ? kv : kmax;
     }
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned long long km = kmax;
     for (int o = 16; o; o >>= 1) {
         cnt += __shfl_down_sync(0xffffffffu, cnt, o);
@@ -384,18 +506,20 @@ __global__ void __launch_bounds__(kClsThreads)
     }
 }
 
-// Critical vertex ids in increasing id order.
+// Critical vertex ids of a tile of `tile` consecutive ids, in increasing id
+// order, at the tile's offset.
 __global__ void __launch_bounds__(kClsThreads)
-    k_compact(const uint8_t *__restrict__ flags, int64_t n, const int32_t *__restrict__ tile_off,
-              int32_t *__restrict__ vc) {
+    k_compact2(const uint8_t *__restrict__ flags, int64_t n, int64_t tile,
+               const int32_t *__restrict__ tile_off, int32_t *__restrict__ vc) {
     __shared__ int ws[kClsThreads / 32];
-    int64_t base = (int64_t)blockIdx.x * kClsTile;
+    const int64_t base = (int64_t)blockIdx.x * tile;
+    const int64_t end = base + tile < n ? base + tile : n;
     int off = tile_off[blockIdx.x];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int k = 0; k < kClsItems; k++) {
-        int64_t v = base + k * kClsThreads + threadIdx.x;
-        bool c = v < n && (flags[v] & kFlagCritical);
-        unsigned b = __ballot_sync(0xffffffffu, c);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t v0 = base; v0 < end; v0 += kClsThreads) {
+        const int64_t v = v0 + threadIdx.x;
+        const bool c = v < end && (flags[v] & kFlagCritical);
+        const unsigned b = __ballot_sync(0xffffffffu, c);
         if (lane == 0) ws[w] = __popc(b);
         __syncthreads();
         int pre = 0, tot = 0;
@@ -1688,6 +1812,24 @@ namespace {
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Tiling of the tier-1 stencil: R whole rows per block, at least 2048
+// vertices per tile.
+struct ClsTiling {
+    int rows_per_block, runs_per_row, aligned;
+    int64_t tile, ntiles;
+};
+template <typename T> ClsTiling cls_tiling(const GridParams &g, const void *values) {
+    constexpr int K = VecOf<T>::K;
+    ClsTiling t;
+    t.runs_per_row = (g.nx + K - 1) / K;
+    t.rows_per_block = std::max(1, (2048 + g.nx - 1) / g.nx);
+    t.tile = (int64_t)t.rows_per_block * g.nx;
+    const int64_t rows = (int64_t)g.ny * g.nz;
+    t.ntiles = (rows + t.rows_per_block - 1) / t.rows_per_block;
+    t.aligned = ((uintptr_t)values % 16 == 0) && ((int64_t)g.nx * sizeof(T)) % 16 == 0;
+    return t;
+}
+
 struct Ctx {
     Pipeline &P;
     cudaStream_t s;
@@ -2003,11 +2145,15 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
     DMS_CUDA(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s));
 
     // ---- gradient: classification, compaction, sort, ProcessLowerStars
-    const int64_t ntiles = (n + kClsTile - 1) / kClsTile;
+    const ClsTiling ct = cls_tiling<T>(c.g, values);
+    const int64_t ntiles = ct.ntiles;
+    DMS_ALLOC(P.tile_cnt, 4 * ntiles + 4);
+    DMS_ALLOC(P.tile_off, 4 * ntiles + 4);
     for (int i = 0; i < 24; i++) KEV(i);   // families that do not run read 0 ms
     KEV(0);
-    k_classify<T><<<(unsigned)ntiles, kClsThreads, 0, c.s>>>(values, c.g, P.flags.as<uint8_t>(),
-                                                            P.tile_cnt.as<int32_t>(), c.st);
+    k_classify2<T><<<(unsigned)ntiles, kClsThreads, 0, c.s>>>(
+        values, c.g, ct.rows_per_block, ct.runs_per_row, ct.aligned, P.flags.as<uint8_t>(),
+        P.tile_cnt.as<int32_t>(), c.st);
     c.launches++;
     DMS_CUDA(cudaGetLastError());
     KEV(1);
@@ -2025,9 +2171,9 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
         DMS_ALLOC(P.base[d], 4 * nc + 4);
     }
     KEV(2);
-    k_compact<<<(unsigned)ntiles, kClsThreads, 0, c.s>>>(P.flags.as<uint8_t>(), n,
-                                                        P.tile_off.as<int32_t>(),
-                                                        P.vc.as<int32_t>());
+    k_compact2<<<(unsigned)ntiles, kClsThreads, 0, c.s>>>(P.flags.as<uint8_t>(), n, ct.tile,
+                                                         P.tile_off.as<int32_t>(),
+                                                         P.vc.as<int32_t>());
     c.launches++;
     DMS_CUDA(cudaGetLastError());
     KEV(3);
@@ -2341,10 +2487,14 @@ dms_status static_setup(int device, StaticScratch **out) {
 template <typename T>
 dms_status classify_static(const T *values, GridParams g, uint8_t *flags, int32_t *critical,
                            int64_t cap, int64_t *n_critical, cudaStream_t s, StaticScratch *scr) {
-    const int64_t ntiles = (g.n + kClsTile - 1) / kClsTile;
+    const ClsTiling ct = cls_tiling<T>(g, values);
+    const int64_t ntiles = ct.ntiles;
+    if (ntiles > kStaticTiles) return DMS_ERR_INVALID_ARG;
     DevStatus *st = &scr->status;
     DMS_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));   // starts at zero every call
-    k_classify<T><<<(unsigned)ntiles, kClsThreads, 0, s>>>(values, g, flags, scr->tile_cnt, st);
+    k_classify2<T><<<(unsigned)ntiles, kClsThreads, 0, s>>>(values, g, ct.rows_per_block,
+                                                           ct.runs_per_row, ct.aligned, flags,
+                                                           scr->tile_cnt, st);
     DMS_CUDA(cudaGetLastError());
     if (ntiles <= kScanTile) {
         k_scan_apply<<<1, kScanThreads, 0, s>>>(scr->tile_cnt, scr->tile_off, ntiles, nullptr,
@@ -2365,7 +2515,8 @@ dms_status classify_static(const T *values, GridParams g, uint8_t *flags, int32_
     if (err & kErrNan) return DMS_ERR_NAN;
     *n_critical = total;
     if (total > cap) return DMS_ERR_CAPACITY;
-    k_compact<<<(unsigned)ntiles, kClsThreads, 0, s>>>(flags, g.n, scr->tile_off, critical);
+    k_compact2<<<(unsigned)ntiles, kClsThreads, 0, s>>>(flags, g.n, ct.tile, scr->tile_off,
+                                                       critical);
     DMS_CUDA(cudaGetLastError());
     DMS_CUDA(cudaStreamSynchronize(s));
     return DMS_OK;
