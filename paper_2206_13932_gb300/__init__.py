@@ -69,6 +69,8 @@ def load(build_if_missing: bool = False):
             lib.dms_classify_static.argtypes = [vp, ctypes.c_int, i64, i64, i64, vp, vp, i64,
                                                 p64, vp]
             lib.dms_classify_static.restype = ctypes.c_int
+            lib.dms_backward_pairs.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
+            lib.dms_backward_pairs.restype = ctypes.c_int
             lib.dms_grid_destroy.argtypes = [vp]
             lib.dms_status_string.argtypes = [ctypes.c_int]
             lib.dms_status_string.restype = ctypes.c_char_p

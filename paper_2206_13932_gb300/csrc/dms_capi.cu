@@ -46,6 +46,12 @@ dms_status dms_fetch_pairs(dms_grid grid, int dim, dms_pair *out, int64_t cap, i
     return grid->p.fetch(dim, out, cap, written, out_is_device);
 }
 
+dms_status dms_backward_pairs(dms_grid grid, int dim, const double *grad_birth,
+                              const double *grad_death, double *grad_field, void *stream) {
+    if (!grid) return DMS_ERR_INVALID_ARG;
+    return grid->p.backward(dim, grad_birth, grad_death, grad_field, stream);
+}
+
 dms_status dms_get_stage_ms(dms_grid grid, float ms[8]) {
     if (!grid || !ms) return DMS_ERR_INVALID_ARG;
     if (!grid->p.has_result) return DMS_ERR_STATE;

@@ -1792,6 +1792,24 @@ __global__ void k_compact_idx(const uint8_t *flag, const int32_t *pos, int64_t n
     if (i < n && flag[i]) out[pos[i]] = (int32_t)i;
 }
 
+// ------------------------------------------------ backward (differentiation)
+//
+// For a loss of the diagram, the value of a pair is the value of its maximum
+// vertices (Sec. 2.4: persistence = f(max vertex of the death simplex) -
+// f(max vertex of the birth simplex)), so d loss / d f(v) collects the
+// gradients of the births and deaths whose maximum vertex is v.  FP64
+// atomics accumulate them (a vertex is the maximum vertex of a few pairs at
+// most); the caller casts.
+__global__ void k_scatter_pair_grads(const dms_pair *__restrict__ pairs, int64_t n,
+                                     const double *__restrict__ gbirth,
+                                     const double *__restrict__ gdeath, double *grad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const dms_pair p = pairs[i];
+    if (gbirth && gbirth[i] != 0.0) atomicAdd(&grad[p.birth_vertex], gbirth[i]);
+    if (gdeath && !p.essential && gdeath[i] != 0.0) atomicAdd(&grad[p.death_vertex], gdeath[i]);
+}
+
 // ------------------------------------------------------------- host side
 
 bool DevBuf::ensure(size_t need) {
@@ -2629,6 +2647,17 @@ dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
         cudaGetLastError();
     }
     return s;
+}
+
+dms_status Pipeline::backward(int dim, const double *gbirth, const double *gdeath, double *grad,
+                              void *stream) {
+    if (!has_result) return DMS_ERR_STATE;
+    if (dim < 0 || dim > 2 || !grad) return DMS_ERR_INVALID_ARG;
+    const int64_t total = n_pairs[dim] + n_ess[dim];
+    if (total == 0) return DMS_OK;
+    k_scatter_pair_grads<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
+        out_pairs[dim].as<dms_pair>(), total, gbirth, gdeath, grad);
+    return cudaGetLastError() == cudaSuccess ? DMS_OK : DMS_ERR_CUDA;
 }
 
 dms_status Pipeline::fetch(int dim, dms_pair *out, int64_t cap, int64_t *written,
