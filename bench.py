@@ -34,6 +34,7 @@ METRIC = "full-diagram Mvertices/s"
 UNIT = "Mvertices/s"
 L2_BYTES = 129 * 2**20
 ORACLE_SAMPLE = 64          # edge of the cube cropped for the oracle (cpu_baseline)
+SERVE_REQUESTS = 128        # requests of the serving workload replayed per run
 REFERENCE_SAMPLE = 40       # edge of the crop per reference-arm step
 
 
@@ -139,6 +140,32 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def serving_section():
+    """Continuous batching vs one request at a time on the serving workload:
+    fields of log-uniform shapes in [16,128]^3 (16 Gaussians + 1e-3 noise,
+    float32), Poisson arrivals at 80 % of the one-at-a-time capacity."""
+    from paper_2206_13932_gb300 import serve
+    fields = sf.serving_fields(SERVE_REQUESTS)
+    nvert = sum(f.size for f in fields)
+    zeros = np.zeros(len(fields))
+    serve.run_stream(fields[:8], zeros[:8], slots=4)             # warm-up
+    r1, w1 = serve.run_stream(fields, zeros, slots=1)             # back to back, one at a time
+    cap = len(fields) / w1
+    r4, w4 = serve.run_stream(fields, zeros, slots=4)             # back to back, 4 slots
+    arr = sf.poisson_arrivals(len(fields), 0.8 * cap)
+    rb, wb = serve.run_stream(fields, arr, slots=4)
+    rs, ws = serve.run_stream(fields, arr, slots=1)
+    return {
+        "requests": len(fields), "mean_vertices": nvert / len(fields),
+        "saturated": {"one_at_a_time_rps": cap, "one_at_a_time_Mvertices_s": nvert / w1 / 1e6,
+                      "served_4_slots_rps": len(fields) / w4,
+                      "served_4_slots_Mvertices_s": nvert / w4 / 1e6},
+        "poisson_rho_0.8": {"rate_rps": 0.8 * cap,
+                            "served_4_slots": serve.latency_stats(rb),
+                            "one_at_a_time": serve.latency_stats(rs)},
+    }
+
+
 def run_ours(args):
     import torch
     import paper_2206_13932_gb300 as dms
@@ -236,6 +263,7 @@ def run_ours(args):
         roofline = dict(roof_grad) if dom == "classify" else {
             "bound": "latency", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s",
             "frac": None, "traffic": None, "peak_source": src}
+    serving = serving_section() if not args.no_serve else None
     # oracle on a bounded crop of the same field
     nv, dt, _ = _oracle_sample(field, ORACLE_SAMPLE)
     line = {
@@ -260,6 +288,7 @@ def run_ours(args):
                          "sample": f"{ORACLE_SAMPLE}^3 crop of the same field, standard reduction",
                          "seconds": dt},
         "clocks": clk.summary(),
+        "serving": serving,
     }
     print(json.dumps(line))
     g.close()
@@ -271,6 +300,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -90,6 +90,11 @@ typedef struct dms_grid_s *dms_grid;
 dms_status dms_grid_create(int64_t nx, int64_t ny, int64_t nz, dms_dtype dtype,
                            const dms_options *opts, dms_grid *out);
 
+/* Changes the grid dimensions of a handle (same dtype and options), keeping
+ * its device buffers and growing them only when the new grid is larger, so
+ * that one handle serves fields of many shapes.  Drops the last result. */
+dms_status dms_grid_reshape(dms_grid grid, int64_t nx, int64_t ny, int64_t nz);
+
 /* Computes D0, D1, D2 and the infinite classes of the field `values`
  * (nx*ny*nz elements, x fastest).  values_on_host = 0: a device pointer that
  * must stay valid until `stream` (a cudaStream_t, NULL = legacy default)

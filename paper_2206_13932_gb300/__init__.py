@@ -71,6 +71,8 @@ def load(build_if_missing: bool = False):
             lib.dms_classify_static.restype = ctypes.c_int
             lib.dms_backward_pairs.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
             lib.dms_backward_pairs.restype = ctypes.c_int
+            lib.dms_grid_reshape.argtypes = [vp, i64, i64, i64]
+            lib.dms_grid_reshape.restype = ctypes.c_int
             lib.dms_grid_destroy.argtypes = [vp]
             lib.dms_status_string.argtypes = [ctypes.c_int]
             lib.dms_status_string.restype = ctypes.c_char_p
@@ -103,6 +105,13 @@ class Grid:
                                          ctypes.byref(opts), ctypes.byref(h)),
                "dms_grid_create")
         self._h = h
+
+    def reshape(self, shape_xyz):
+        """Reuses this handle (and its device buffers) for another grid shape."""
+        shape_xyz = tuple(int(s) for s in shape_xyz)
+        _check(self._lib.dms_grid_reshape(self._h, *shape_xyz), "dms_grid_reshape")
+        self.shape_xyz = shape_xyz
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

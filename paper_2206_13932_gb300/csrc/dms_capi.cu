@@ -26,6 +26,11 @@ dms_status dms_grid_create(int64_t nx, int64_t ny, int64_t nz, dms_dtype dtype,
     return DMS_OK;
 }
 
+dms_status dms_grid_reshape(dms_grid grid, int64_t nx, int64_t ny, int64_t nz) {
+    if (!grid) return DMS_ERR_INVALID_ARG;
+    return grid->p.reshape(nx, ny, nz);
+}
+
 dms_status dms_compute_diagram(dms_grid grid, const void *values, int values_on_host,
                                void *stream) {
     if (!grid) return DMS_ERR_INVALID_ARG;

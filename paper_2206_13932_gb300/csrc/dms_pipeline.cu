@@ -1830,6 +1830,11 @@ namespace {
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Grids up to this many vertices get every gradient record computed densely
+// (cheap at this size; the D1 walls of smooth fields then never wait on a
+// single-threaded lazy ProcessLowerStars).
+constexpr int64_t kDenseGradientBelow = (int64_t)1 << 25;
+
 // Tiling of the tier-1 stencil: R whole rows per block, at least 2048
 // vertices per tile.
 struct ClsTiling {
@@ -2200,7 +2205,7 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
         // when critical vertices are dense (the walks of D2 and D1 then visit
         // most vertices), otherwise on the critical ones, the rest on demand
         KEV(6);
-        if (nc * 4 > n)
+        if (nc * 4 > n || n <= kDenseGradientBelow)
             DMS_LAUNCH(n, 128, k_pls<T>, values, c.g, (const int32_t *)nullptr, n,
                        P.flags.as<uint8_t>(), P.grad.as<GradRec>());
         else
@@ -2569,6 +2574,19 @@ dms_status Pipeline::init(int64_t nx_, int64_t ny_, int64_t nz_, dms_dtype dt,
         if (cudaEventCreate((cudaEvent_t *)&kev[i]) != cudaSuccess) return DMS_ERR_CUDA;
     for (int i = 0; i < 8; i++)
         if (cudaEventCreate((cudaEvent_t *)&sev[i]) != cudaSuccess) return DMS_ERR_CUDA;
+    return DMS_OK;
+}
+
+dms_status Pipeline::reshape(int64_t nx_, int64_t ny_, int64_t nz_) {
+    if (nx_ < 1 || ny_ < 1 || nz_ < 1 || nx_ > (1 << 30) || ny_ > (1 << 30) || nz_ > (1 << 30))
+        return DMS_ERR_INVALID_ARG;
+    if (nx_ * ny_ >= ((int64_t)1 << 31) || nx_ * ny_ * nz_ >= ((int64_t)1 << 31))
+        return DMS_ERR_INVALID_ARG;
+    const int64_t n2 = nx_ * ny_ * nz_;
+    if (!flags.ensure(n2) || !vrank.ensure(4 * n2) || !grad.ensure(sizeof(GradRec) * n2))
+        return DMS_ERR_OOM;
+    nx = nx_; ny = ny_; nz = nz_; n = n2;
+    has_result = false;
     return DMS_OK;
 }
 

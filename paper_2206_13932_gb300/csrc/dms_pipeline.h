@@ -59,6 +59,7 @@ struct Pipeline {
 
     dms_status init(int64_t nx, int64_t ny, int64_t nz, dms_dtype dt, const dms_options *o);
     dms_status compute(const void *values, int on_host, void *stream);
+    dms_status reshape(int64_t nx, int64_t ny, int64_t nz);
     dms_status fetch(int dim, dms_pair *out, int64_t cap, int64_t *written, int out_is_device);
     dms_status backward(int dim, const double *gbirth, const double *gdeath, double *grad,
                         void *stream);

@@ -19,7 +19,8 @@ import hashlib
 import numpy as np
 
 __all__ = ["gaussian_mixture", "white_noise", "quantize_u16", "ramp", "constant",
-           "config_field", "sha256", "CONFIGS", "blob_params"]
+           "config_field", "sha256", "CONFIGS", "blob_params", "serving_shapes", "serving_fields",
+           "poisson_arrivals"]
 
 
 def blob_params(n_blobs: int, rng: np.random.Generator):
@@ -134,3 +135,24 @@ def config_field(name: str, device=None, shape_xyz=None) -> np.ndarray:
                              device=device)
         return quantize_u16(g)
     raise KeyError(name)
+
+
+def serving_shapes(count: int, seed: int = 4000, lo: int = 16, hi: int = 128):
+    """Per-axis sizes round(exp(U(ln lo, ln hi))), drawn independently."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [tuple(int(round(np.exp(rng.uniform(np.log(lo), np.log(hi))))) for _ in range(3))
+            for _ in range(count)]
+
+
+def serving_fields(count: int, seed0: int = 4000, lo: int = 16, hi: int = 128):
+    """The serving workload: fields of log-uniform non-cubic shapes, each
+    16 Gaussians + U(-1e-3, 1e-3) noise in float32, seeds seed0 + i."""
+    shapes = serving_shapes(count, seed0, lo, hi)
+    return [gaussian_mixture(sh, 16, seed0 + i, noise=1e-3, dtype=np.float32)
+            for i, sh in enumerate(shapes)]
+
+
+def poisson_arrivals(count: int, rate_per_s: float, seed: int = 4100):
+    """Arrival times (seconds) of a Poisson process of the given rate."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, count))
