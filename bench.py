@@ -252,7 +252,7 @@ def run_ours(args):
                  "unit": "GB/s", "frac": cls_gbs / hbm, "traffic": None,
                  "algorithmic_bytes_per_launch": cls_bytes, "peak_source": src}
     if dom == "d1_reduce":
-        red_bytes = 4 * (stats["d1_entries_read"] + stats["d1_entries_written"])
+        red_bytes = stats["d1_bytes_read"] + stats["d1_bytes_written"]
         gbs = red_bytes / (kavg[dom] * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": "D1 reduction (k_red_claim, k_red_add, "
                     "k_red_add_block)", "achieved": gbs, "peak": hbm, "unit": "GB/s",

@@ -55,10 +55,15 @@ typedef struct {
     int virtual_max;      /* 1 (the only supported value): Sec. 5.2 virtual
                              maximum on the outer boundary                   */
     int64_t max_iters;    /* cap on device loops and path lengths; 0 = default */
-    int d1_mode;          /* D1 reduction: 0 = default (1), 1 = reduce the
+    int d1_mode;          /* D1 reduction: 0 = by density (3 when there are
+                             fewer 2-saddle columns than 1 per 32 vertices,
+                             else 1), 1 = reduce the
                              2-saddle columns (Alg. 3 order), 2 = reduce their
-                             anti-transpose (persistent cohomology; the same
-                             pairs)                                           */
+                             anti-transpose (persistent cohomology), 3 = lazy
+                             columns: each 2-saddle's Morse boundary is
+                             expanded only as far as its current pivot,
+                             between rounds of the reduction (Alg. 3's
+                             interleaving); all modes give the same pairs    */
 } dms_options;
 
 /* One persistence pair (or infinite class) of the result.
@@ -140,9 +145,10 @@ dms_status dms_get_stage_ms(dms_grid grid, float ms[8]);
 /* Statistics of the last compute: [0] critical vertices, [1..4] critical
  * simplices of dimension 0..3, [5] kernel launches, [6] D0 halving levels,
  * [7] D2 halving levels, [8] D1 reduction rounds, [9] D1 columns, [10] D1
- * columns whose boundary outgrew the first scratch pass, [11] D1 column
- * additions, [12] D1 column-pool entries used, [13] D1 pool regrowths,
- * [14] D1 entries read by additions, [15] D1 entries written by additions. */
+ * columns whose boundary outgrew the first scratch pass (lazy mode: column
+ * advances that did), [11] D1 column additions, [12] D1 column-pool entries
+ * used (4 B each; lazy mode 16 B), [13] D1 pool regrowths, [14] bytes read
+ * by D1 column additions, [15] bytes written by D1 column additions. */
 dms_status dms_get_stats(dms_grid grid, int64_t stats[16]);
 
 /* Device milliseconds of the last compute per kernel family, from CUDA event
@@ -151,7 +157,7 @@ dms_status dms_get_stats(dms_grid grid, int64_t stats[16]);
  * stencil), [1] compaction, [2] radix sort, [3] ProcessLowerStars, [4] emit
  * of the critical simplices, [5] D0 arcs, [6] D0 union-find rounds, [7] D2
  * arcs, [8] D2 union-find rounds, [9] D1 boundary tracing, [10] D1
- * reduction, [11] output. */
+ * reduction (lazy mode: [9] is 0, [10] covers both), [11] output. */
 dms_status dms_get_kernel_ms(dms_grid grid, float ms[12]);
 
 /* Lower-link classification of every vertex and the id-ordered list of the

@@ -205,7 +205,7 @@ class Grid:
         _check(self._lib.dms_get_stats(self._h, s), "dms_get_stats")
         names = ("critical_vertices", "c0", "c1", "c2", "c3", "launches", "levels_d0",
                  "levels_d2", "rounds_d1", "d1_columns", "d1_trace_overflow", "d1_additions",
-                 "d1_pool_used", "d1_pool_grows", "d1_entries_read", "d1_entries_written")
+                 "d1_pool_used", "d1_pool_grows", "d1_bytes_read", "d1_bytes_written")
         return dict(zip(names, [int(x) for x in s]))
 
 

@@ -40,7 +40,7 @@ struct DevStatus {
     unsigned long long maxkey;     // largest vertex key
     long long total[4];            // scan totals
     long long parts[8];            // output part sizes
-    long long red_io[2];           // D1 additions: entries read, entries written
+    long long red_io[2];           // D1 additions: bytes read, bytes written
     int changed;                   // D1: columns changed this round
     unsigned long long pool_top;   // D1 column pool bump pointer
     long long misc[4];
@@ -1402,8 +1402,8 @@ __global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
     if (lane == 0 && adds) {
         atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)adds);
         atomicMax((unsigned long long *)&st->misc[3], (unsigned long long)longest);
-        atomicAdd((unsigned long long *)&st->red_io[0], io_r);
-        atomicAdd((unsigned long long *)&st->red_io[1], io_w);
+        atomicAdd((unsigned long long *)&st->red_io[0], io_r * 4ull);
+        atomicAdd((unsigned long long *)&st->red_io[1], io_w * 4ull);
     }
 }
 
@@ -1556,8 +1556,8 @@ __global__ void __launch_bounds__(kRedBlock)
         if (chain) {
             atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)chain);
             atomicMax((unsigned long long *)&st->misc[3], (unsigned long long)chain);
-            atomicAdd((unsigned long long *)&st->red_io[0], io_r);
-            atomicAdd((unsigned long long *)&st->red_io[1], io_w);
+            atomicAdd((unsigned long long *)&st->red_io[0], io_r * 4ull);
+            atomicAdd((unsigned long long *)&st->red_io[1], io_w * 4ull);
         }
     }
 }
@@ -1666,6 +1666,499 @@ __global__ void k_pool_compact(int64_t ncol, int64_t *start, const int32_t *__re
     if (c >= ncol) return;
     int64_t s0 = start[c];
     int32_t o = off[c];
+    for (int k = 0; k < len[c]; k++) dst[o + k] = src[s0 + k];
+    start[c] = o;
+}
+
+
+// ------------------------------ D1, lazy: propagation interleaved with the reduction
+//
+// Alg. 3 as the paper states it: a column keeps its boundary only partially
+// expanded (the cached Boundary), and expands it only as far as the pivot.
+// Here a column is a set of star edges E with Morse boundary Phi(E), Phi
+// linear mod 2: a critical row maps to itself, a regular edge to the image of
+// the other two edges of its paired triangle, a vertex->edge head and a
+// critical edge paired in D0 to nothing.  E is kept sorted by decreasing
+// priority (the vertex order of the edge's maximum vertex y, then the edge's
+// classification order inside the lower star of y).  Expanding a regular
+// edge only yields edges of lower priority (the other edge of the triangle
+// was classified earlier in the same lower star, the third edge lies in the
+// lower star of a lower vertex), and the critical edges of one lower star are
+// classified in increasing lexicographic order.  So when the highest-priority
+// edge of E with odd multiplicity is critical, it is the largest row of
+// Phi(E): the pivot.  Advancing a column expands its top until that holds.
+// The reduction rounds are those of the eager path (claims by atomic minimum,
+// additions of stable owners), with E + E' (mod 2) in place of the sum of
+// the expanded boundaries; a column whose top turns regular is advanced at
+// the start of the next round.
+//
+// Entry: hi = key of the value at y; lo = y << 15 | order << 11 | m << 7 |
+// pair << 1 | critical (pair: the star triangle of y a regular edge is paired
+// with; 0 for a critical edge).  (hi, lo) orders by (key, y, order).
+struct Ent {
+    unsigned long long hi, lo;
+};
+__device__ __forceinline__ bool ent_gt(const Ent &a, const Ent &b) {
+    return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+}
+__device__ __forceinline__ bool ent_eq(const Ent &a, const Ent &b) {
+    return a.hi == b.hi && a.lo == b.lo;
+}
+__device__ __forceinline__ int64_t ent_y(const Ent &e) { return (int64_t)(e.lo >> 15); }
+__device__ __forceinline__ int ent_m(const Ent &e) { return (int)((e.lo >> 7) & 15); }
+__device__ __forceinline__ int ent_pair(const Ent &e) { return (int)((e.lo >> 1) & 63); }
+__device__ __forceinline__ bool ent_crit(const Ent &e) { return e.lo & 1; }
+
+// C1 index of the critical edge (y, link m)
+__device__ __forceinline__ int32_t crit_edge_row(const StarTables &S,
+                                                 const int32_t *__restrict__ vrank,
+                                                 const CritRec *__restrict__ recs,
+                                                 const int32_t *__restrict__ base1, int64_t y,
+                                                 int m) {
+    const int32_t i = vrank[y];
+    const CritRec rec = recs[i];
+    return base1[i] + local_index(S, rec, 1, m);
+}
+
+// Per-thread scratch of an advance: a max-heap of the edges produced by
+// expansions and a hash of their parities (the list's own entries are merged
+// in order, not hashed).
+struct LazyCtx {
+    HeapEnt *heap;
+    HashEnt *hash;
+    int hcap, hashmask, hn, used;
+    int32_t gen;
+    bool overflow;
+};
+
+__device__ __forceinline__ HashEnt *lz_find(LazyCtx &c, unsigned long long key) {
+    const uint32_t hpos = hash64(key) & c.hashmask;
+    for (int p = 0; p <= c.hashmask; p++) {
+        HashEnt *e = &c.hash[(hpos + p) & c.hashmask];
+        if (e->gen != c.gen) return nullptr;
+        if (e->key == key) return e;
+    }
+    return nullptr;
+}
+__device__ __forceinline__ unsigned long long lz_key(int64_t y, int m) {
+    return (((unsigned long long)y << 4) | (unsigned)m) + 1;
+}
+
+// Toggles edge (y, m) among the products; drops heads of vertex->edge vectors
+// and critical edges paired in D0.  A new edge is pushed with its entry.
+template <typename T>
+__device__ void lz_toggle(LazyCtx &c, const StarTables &S, const GridParams &g,
+                          const T *__restrict__ values, uint8_t *flags, GradRec *grad,
+                          const int32_t *__restrict__ vrank, const CritRec *__restrict__ recs,
+                          const int32_t *__restrict__ base1, const uint8_t *__restrict__ is_row,
+                          int64_t y, int m, DevStatus *st) {
+    if (m < 0 || m >= kLinks) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
+    const uint8_t fy = flags[y];
+    if ((fy & 0xF) == m) return;
+    bool crit = false;
+    if (fy & kFlagCritical) {
+        const int32_t i = vrank[y];
+        const CritRec rec = recs[i];
+        if (rec.crit_e >> m & 1) {
+            if (!is_row[base1[i] + local_index(S, rec, 1, m)]) return;   // paired in D0
+            crit = true;
+        }
+    }
+    const unsigned long long key = lz_key(y, m);
+    const uint32_t hpos = hash64(key) & c.hashmask;
+    HashEnt *slot = nullptr;
+    for (int p = 0; p <= c.hashmask; p++) {
+        HashEnt *e = &c.hash[(hpos + p) & c.hashmask];
+        if (e->gen != c.gen) { slot = e; break; }
+        if (e->key == key) { e->info ^= 1u; return; }
+    }
+    if (!slot || c.used * 4 >= (c.hashmask + 1) * 3 || c.hn >= c.hcap) {
+        c.overflow = true;
+        return;
+    }
+    const GradRec G = grad_get(S, g, values, flags, grad, y);
+    int pair = 0;
+    if (!crit) {
+        pair = grad_edge_pair(G, m);
+        if (pair >= kTris) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
+    }
+    HeapEnt he;
+    he.hi = (unsigned long long)Key<T>::of(values[y]);
+    he.lo = ((unsigned long long)y << 15) | ((unsigned long long)grad_edge_order(G, m) << 11) |
+            ((unsigned long long)m << 7) | ((unsigned long long)pair << 1) |
+            (crit ? 1ull : 0ull);
+    int i = c.hn++;
+    while (i > 0) {
+        const int p = (i - 1) >> 1;
+        if (!heap_less(c.heap[p], he)) break;
+        c.heap[i] = c.heap[p];
+        i = p;
+    }
+    c.heap[i] = he;
+    slot->key = key;
+    slot->gen = c.gen;
+    slot->info = 1u;
+    c.used++;
+}
+
+__device__ __forceinline__ HeapEnt lz_pop(LazyCtx &c) {
+    const HeapEnt top = c.heap[0];
+    const HeapEnt last = c.heap[--c.hn];
+    int i = 0;
+    while (true) {
+        const int l = 2 * i + 1;
+        if (l >= c.hn) break;
+        const int r = l + 1;
+        const int m = (r < c.hn && heap_less(c.heap[l], c.heap[r])) ? r : l;
+        if (!heap_less(last, c.heap[m])) break;
+        c.heap[i] = c.heap[m];
+        i = m;
+    }
+    if (c.hn > 0) c.heap[i] = last;
+    return top;
+}
+
+// Expansion of regular edge (y, m) through its paired star triangle s: the
+// other star edge of s and the edge between its two link vertices, in the
+// star of the higher one.
+template <typename T>
+__device__ __forceinline__ void lz_expand(LazyCtx &c, const StarTables &S, const GridParams &g,
+                                          const T *__restrict__ values, uint8_t *flags,
+                                          GradRec *grad, const int32_t *__restrict__ vrank,
+                                          const CritRec *__restrict__ recs,
+                                          const int32_t *__restrict__ base1,
+                                          const uint8_t *__restrict__ is_row, int64_t y, int s,
+                                          int m, DevStatus *st) {
+    const int ta = S.tri_v[s][0], tb = S.tri_v[s][1];
+    if (m >= 0) lz_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, y,
+                             ta == m ? tb : ta, st);
+    const GradRec G = grad_get(S, g, values, flags, grad, y);
+    const bool aup = grad_rank(G, ta) > grad_rank(G, tb);
+    const int hi = aup ? ta : tb, lo = aup ? tb : ta;
+    const int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
+                               9 * (S.dz[lo] - S.dz[hi] + 1)];
+    lz_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, y + g.dlin[hi], l, st);
+}
+
+// Advances column cj (list at sa, la entries; la < 0: no list yet, start
+// from the boundary of the critical triangle) until its top is a critical
+// row or it is zero, and writes it back as a new list.  Returns 0 when done
+// (col_start/col_len updated), 1 when the products outgrow the scratch, 2
+// when the pool is full; the column is unchanged then.
+template <typename T>
+__device__ int lz_advance_col(LazyCtx &c, const StarTables &S, const T *__restrict__ values,
+                              const GridParams &g, uint8_t *flags, GradRec *grad,
+                              const int32_t *__restrict__ vrank, const CritRec *__restrict__ recs,
+                              const int32_t *__restrict__ base1,
+                              const uint8_t *__restrict__ is_row, const int32_t *__restrict__ v2,
+                              const uint8_t *__restrict__ l2, const int32_t *__restrict__ colmap,
+                              int32_t cj, int la, int64_t sa, Ent *pool, int64_t pool_cap,
+                              int64_t *col_start, int32_t *col_len, DevStatus *st) {
+    c.hn = 0; c.used = 0; c.overflow = false;
+    const Ent *L = pool + sa;
+    int li = 0;
+    const int ln = la > 0 ? la : 0;
+    if (la < 0) {
+        // the boundary of the critical triangle: (x,a), (x,b), edge(x+a, x+b)
+        const int32_t j2 = colmap[cj];
+        const int64_t x = v2[j2];
+        const int s = l2[j2];
+        lz_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, x, S.tri_v[s][0],
+                     st);
+        lz_expand<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, x, s,
+                     S.tri_v[s][0], st);
+    }
+    Ent stop{0, 0};
+    bool have = false;
+    while (!c.overflow) {
+        const bool hl = li < ln;
+        if (!hl && c.hn == 0) break;
+        Ent e;
+        int par;
+        if (c.hn > 0 && (!hl || !ent_gt(L[li], Ent{c.heap[0].hi, c.heap[0].lo}))) {
+            const HeapEnt h = lz_pop(c);
+            e = Ent{h.hi, h.lo};
+            HashEnt *slot = lz_find(c, lz_key(ent_y(e), ent_m(e)));
+            par = slot ? (int)(slot->info & 1u) : 0;
+            if (hl && ent_eq(L[li], e)) { par ^= 1; li++; }
+        } else {
+            e = L[li++];
+            par = 1;
+        }
+        if (!par) continue;
+        if (ent_crit(e)) { stop = e; have = true; break; }
+        lz_expand<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, ent_y(e),
+                     ent_pair(e), ent_m(e), st);
+    }
+    if (c.overflow) return 1;
+    // write back: the stop row, then the rest of the list merged with the
+    // remaining products of odd parity
+    const int64_t room = (have ? 1 : 0) + (ln - li) + c.hn;
+    if (room == 0) { col_start[cj] = 0; col_len[cj] = 0; return 0; }
+    const unsigned long long pos = atomicAdd(&st->pool_top, (unsigned long long)room);
+    if ((int64_t)(pos + room) > pool_cap) { atomicOr(&st->err, kErrCap); return 2; }
+    Ent *out = pool + pos;
+    int o = 0;
+    if (have) out[o++] = stop;
+    while (li < ln || c.hn > 0) {
+        if (c.hn > 0 && (li >= ln || !ent_gt(L[li], Ent{c.heap[0].hi, c.heap[0].lo}))) {
+            const HeapEnt h = lz_pop(c);
+            const Ent e{h.hi, h.lo};
+            HashEnt *slot = lz_find(c, lz_key(ent_y(e), ent_m(e)));
+            int par = slot ? (int)(slot->info & 1u) : 0;
+            if (li < ln && ent_eq(L[li], e)) { par ^= 1; li++; }
+            if (par) out[o++] = e;
+        } else {
+            out[o++] = L[li++];
+        }
+    }
+    col_start[cj] = (int64_t)pos;
+    col_len[cj] = o;
+    return 0;
+}
+
+// The inputs every advance reads.
+template <typename T> struct LzArgs {
+    const T *values;
+    GridParams g;
+    uint8_t *flags;
+    GradRec *grad;
+    const int32_t *vrank;
+    const CritRec *recs;
+    const int32_t *base1;
+    const uint8_t *is_row;
+    const int32_t *v2;
+    const uint8_t *l2;
+    const int32_t *colmap;
+    HeapEnt *heap_all;
+    HashEnt *hash_all;
+    int32_t *tgen;
+    int hcap, hashcap;
+};
+
+template <typename T>
+__device__ __forceinline__ LazyCtx lz_ctx(const LzArgs<T> &a, int64_t slot) {
+    LazyCtx c;
+    c.heap = a.heap_all + slot * a.hcap;
+    c.hash = a.hash_all + slot * a.hashcap;
+    c.hcap = a.hcap;
+    c.hashmask = a.hashcap - 1;
+    c.hn = 0; c.used = 0; c.gen = 0; c.overflow = false;
+    return c;
+}
+
+// Advances the listed columns (one thread each) whose top is regular or that
+// have no list yet.  A column that outgrows the scratch, or finds the pool
+// full, is left as it was and queued on `retry`.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_lz_advance(LzArgs<T> a, const int32_t *__restrict__ todo, int64_t ntodo, int32_t *astamp,
+                 int32_t launch, Ent *pool, int64_t pool_cap, int64_t *col_start,
+                 int32_t *col_len, int32_t *retry, DevStatus *st) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    LazyCtx c = lz_ctx(a, tid);
+    int32_t gen = a.tgen[tid];
+    for (int64_t q = tid; q < ntodo; q += nth) {
+        const int32_t cj = todo[q];
+        const int la = col_len[cj];
+        const int64_t sa = col_start[cj];
+        if (la == 0) continue;                                   // zero column
+        if (la > 0 && (pool[sa].lo & 1)) continue;               // critical top
+        if (atomicExch(&astamp[cj], launch) == launch) continue; // listed twice
+        c.gen = ++gen;
+        const int r = lz_advance_col<T>(c, g_star, a.values, a.g, a.flags, a.grad, a.vrank,
+                                        a.recs, a.base1, a.is_row, a.v2, a.l2, a.colmap, cj, la,
+                                        sa, pool, pool_cap, col_start, col_len, st);
+        if (r) retry[atomicAdd((unsigned long long *)&st->misc[3], 1ull)] = cj;
+    }
+    a.tgen[tid] = gen;
+}
+
+// Listed columns with a critical top claim it (atomic minimum of the column
+// index); a claim that displaces a later owner queues it on `recheck`.
+__global__ void k_lz_claim(const int32_t *__restrict__ active, int64_t nactive,
+                           const int64_t *__restrict__ start, const int32_t *__restrict__ len,
+                           const Ent *__restrict__ pool, const int32_t *__restrict__ vrank,
+                           const CritRec *__restrict__ recs, const int32_t *__restrict__ base1,
+                           int32_t *owner, int32_t *recheck, DevStatus *st) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool take = false;
+    int32_t old = 0;
+    if (q < nactive) {
+        const int32_t cj = active[q];
+        if (len[cj] > 0) {
+            const Ent top = pool[start[cj]];
+            if (ent_crit(top)) {
+                const int32_t row =
+                    crit_edge_row(g_star, vrank, recs, base1, ent_y(top), ent_m(top));
+                old = atomicMin(&owner[row], cj);
+                take = old != kNoOwner && old > cj;
+            }
+        }
+    }
+    warp_append(take, old, recheck, (unsigned long long *)&st->misc[0]);
+}
+
+// Merge path split of two decreasing entry lists (ties: A first; an equal
+// pair never straddles the split).
+__device__ __forceinline__ void ent_split(const Ent *A, int la, const Ent *B, int lb, int d,
+                                          int &i, int &j) {
+    int lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (!ent_gt(B[d - 1 - mid], A[mid])) lo = mid + 1;
+        else hi = mid;
+    }
+    i = lo;
+    j = d - lo;
+    if (i > 0 && j < lb && ent_eq(A[i - 1], B[j])) j++;
+}
+
+// out = A + B (mod 2) for decreasing entry lists, by one warp; returns the length
+__device__ int ent_warp_symdiff(const Ent *A, int la, const Ent *B, int lb, Ent *out) {
+    const int lane = threadIdx.x & 31;
+    const int L = la + lb, per = (L + 31) >> 5;
+    int i0, j0, i1, j1;
+    ent_split(A, la, B, lb, min(lane * per, L), i0, j0);
+    ent_split(A, la, B, lb, min(lane * per + per, L), i1, j1);
+    int cnt = 0;
+    {
+        int i = i0, j = j0;
+        while (i < i1 || j < j1) {
+            if (j >= j1 || (i < i1 && ent_gt(A[i], B[j]))) { cnt++; i++; }
+            else if (i >= i1 || ent_gt(B[j], A[i])) { cnt++; j++; }
+            else { i++; j++; }
+        }
+    }
+    int inc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    int o = inc - cnt;
+    int i = i0, j = j0;
+    while (i < i1 || j < j1) {
+        if (j >= j1 || (i < i1 && ent_gt(A[i], B[j]))) out[o++] = A[i++];
+        else if (i >= i1 || ent_gt(B[j], A[i])) out[o++] = B[j++];
+        else { i++; j++; }                         // the same edge twice: 1 + 1 = 0
+    }
+    return total;
+}
+
+// One warp per listed column: while its top is a critical row owned by an
+// earlier (stable) column, add that column's list; when an addition leaves a
+// regular top, lane 0 advances the column in place (with the warp's slot of
+// the scratch) and the additions go on, so a column's whole chain runs in one
+// round.  A changed column is listed for the next round (for its claim, or
+// for an advance with larger scratch when the inline one did not fit).
+template <typename T>
+__global__ void k_lz_add(LzArgs<T> a, const int32_t *__restrict__ active, int64_t nactive,
+                         const int32_t *__restrict__ recheck, int64_t *start, int32_t *len,
+                         Ent *pool, const int32_t *__restrict__ owner, int32_t *stamp,
+                         int32_t round, int32_t *next, int64_t pool_cap, DevStatus *st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nre = *(volatile long long *)&st->misc[0];
+    LazyCtx c = lz_ctx(a, warp);
+    int32_t gen = lane == 0 ? a.tgen[warp] : 0;
+    unsigned adds = 0;
+    unsigned long long io_r = 0, io_w = 0;
+    for (int64_t q = warp; q < nactive + nre; q += nwarps) {
+        const int32_t cj = q < nactive ? active[q] : recheck[q - nactive];
+        int fresh = 0;
+        if (lane == 0) fresh = atomicExch(&stamp[cj], round) != round;
+        if (!__shfl_sync(0xffffffffu, fresh, 0)) continue;
+        int la = len[cj];
+        int64_t sa = start[cj];
+        bool changed = false;
+        for (int it = 0; la > 0 && it < (1 << 24); it++) {
+            const Ent top = pool[sa];
+            if (!ent_crit(top)) {
+                if (!changed) break;     // not advanced yet: the next round's advance
+                int r = 0, la2 = 0;
+                long long sa2 = 0;
+                if (lane == 0) {
+                    c.gen = ++gen;
+                    r = lz_advance_col<T>(c, g_star, a.values, a.g, a.flags, a.grad, a.vrank,
+                                          a.recs, a.base1, a.is_row, a.v2, a.l2, a.colmap, cj,
+                                          la, sa, pool, pool_cap, start, len, st);
+                    if (r == 0) { la2 = len[cj]; sa2 = start[cj]; }
+                }
+                r = __shfl_sync(0xffffffffu, r, 0);
+                if (r) break;
+                la = __shfl_sync(0xffffffffu, la2, 0);
+                sa = __shfl_sync(0xffffffffu, sa2, 0);
+                continue;
+            }
+            const int32_t row = crit_edge_row(g_star, a.vrank, a.recs, a.base1, ent_y(top),
+                                              ent_m(top));
+            const int32_t k = owner[row];
+            if (k == cj || k == kNoOwner || k > cj) break;
+            const int64_t sb = start[k];
+            const int lb = len[k];
+            unsigned long long pos = 0;
+            if (lane == 0) pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if ((int64_t)(pos + la + lb) > pool_cap) {
+                if (lane == 0) atomicOr(&st->err, kErrCap);
+                break;
+            }
+            io_r += (unsigned long long)(la + lb);
+            la = ent_warp_symdiff(pool + sa, la, pool + sb, lb, pool + pos);
+            io_w += (unsigned long long)la;
+            sa = (int64_t)pos;
+            changed = true;
+            adds++;
+        }
+        if (changed && lane == 0) {
+            start[cj] = sa;
+            len[cj] = la;
+            if (la > 0) next[atomicAdd((unsigned long long *)&st->misc[1], 1ull)] = cj;
+        }
+    }
+    if (lane == 0) {
+        a.tgen[warp] = gen;
+        if (adds) {
+            atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)adds);
+            atomicAdd((unsigned long long *)&st->red_io[0], io_r * sizeof(Ent));
+            atomicAdd((unsigned long long *)&st->red_io[1], io_w * sizeof(Ent));
+        }
+    }
+}
+
+// per-column D1 partner (the owned top row) once no column changes
+__global__ void k_lz_result(int64_t ncols, const int64_t *__restrict__ start,
+                            const int32_t *__restrict__ len, const Ent *__restrict__ pool,
+                            const int32_t *__restrict__ vrank, const CritRec *__restrict__ recs,
+                            const int32_t *__restrict__ base1, int32_t *d1_row,
+                            uint8_t *row_paired, DevStatus *st) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    if (len[c] <= 0) { if (len[c] < 0) atomicOr(&st->err, kErrState); d1_row[c] = -1; return; }
+    const Ent top = pool[start[c]];
+    if (!ent_crit(top)) { atomicOr(&st->err, kErrState); d1_row[c] = -1; return; }
+    const int32_t r = crit_edge_row(g_star, vrank, recs, base1, ent_y(top), ent_m(top));
+    d1_row[c] = r;
+    row_paired[r] = 1;
+}
+
+// live lengths (a column not yet listed, len < 0, holds nothing)
+__global__ void k_lz_live(int64_t ncol, const int32_t *__restrict__ len, int32_t *out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncol) out[c] = len[c] > 0 ? len[c] : 0;
+}
+
+// copies the live entry lists into a fresh pool (after the pool filled up)
+__global__ void k_lz_compact(int64_t ncol, int64_t *start, const int32_t *__restrict__ len,
+                             const int32_t *__restrict__ off, const Ent *__restrict__ src,
+                             Ent *dst) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncol || len[c] <= 0) return;
+    const int64_t s0 = start[c];
+    const int32_t o = off[c];
     for (int k = 0; k < len[c]; k++) dst[o + k] = src[s0 + k];
     start[c] = o;
 }
@@ -1834,6 +2327,10 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // (cheap at this size; the D1 walls of smooth fields then never wait on a
 // single-threaded lazy ProcessLowerStars).
 constexpr int64_t kDenseGradientBelow = (int64_t)1 << 25;
+
+// D1 mode 0 reduces lazily when there are fewer than one column per this
+// many vertices.
+constexpr int64_t kLazyBelowDensity = 32;
 
 // Tiling of the tier-1 stencil: R whole rows per block, at least 2048
 // vertices per tile.
@@ -2004,6 +2501,16 @@ dms_status elder_rule(Ctx &c, int64_t narcs, int descending, int older_is_larger
 // in P.d1_pool at P.d1_start/P.d1_len, claiming pivots in owner[0..nent).
 // Rounds continue until no column changes; on a pool overflow the live
 // columns are compacted into a larger pool and the round is repeated.
+// Initial capacity (entries) of the lazy D1 column pool: `dflt`, unless the
+// environment sets DMS_D1_POOL_ENTRIES (a smaller pool exercises the
+// compaction and regrowth path).
+int64_t d1_pool_entries(int64_t dflt) {
+    const char *e = getenv("DMS_D1_POOL_ENTRIES");
+    if (!e) return dflt;
+    const long long v = atoll(e);
+    return v >= 64 ? (int64_t)v : dflt;
+}
+
 constexpr int64_t kBlockModeBelow = 8192;   // active columns below which a block adds
 
 dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used) {
@@ -2109,7 +2616,7 @@ dms_status reduce_d1(Ctx &c, int64_t ncols, int64_t n1, const uint8_t *is_row) {
     DMS_CUDA(cudaMemcpyAsync(c.hst, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.s));
     DMS_CUDA(cudaStreamSynchronize(c.s));
     const int64_t traced = (int64_t)c.hst->pool_top;
-    if (P.d1_mode == 1) {
+    if (P.d1_mode_used == 1) {
         DMS_TRY(reduce_columns(c, ncols, n1, traced));
         DMS_LAUNCH(ncols, 256, k_d1_result_homology, ncols, P.d1_start.as<int64_t>(),
                    P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), P.d1_row.as<int32_t>(),
@@ -2157,6 +2664,229 @@ dms_status reduce_d1(Ctx &c, int64_t ncols, int64_t n1, const uint8_t *is_row) {
                P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), P.d1_rowmap.as<int32_t>(),
                P.d1_row.as<int32_t>(), P.d1_rowpaired.as<uint8_t>());
     return DMS_OK;
+}
+
+// D1 by the lazy reduction (d1_mode 3): no separate tracing; columns are
+// advanced only as far as their pivots, between rounds of claims and
+// additions of partially expanded columns.
+HeapEnt *lz_heap(LazyScratch &s) { return s.buf.as<HeapEnt>(); }
+HashEnt *lz_hash(LazyScratch &s) { return (HashEnt *)(lz_heap(s) + (size_t)s.hcap * s.nt); }
+int32_t *lz_tgen(LazyScratch &s) { return (int32_t *)(lz_hash(s) + (size_t)s.hashcap * s.nt); }
+
+dms_status lazy_scratch(Ctx &c, LazyScratch &s, int hcap, int hashcap, int64_t nt) {
+    if (s.buf.p && s.hcap == hcap && s.hashcap == hashcap && s.nt >= nt) return DMS_OK;
+    const size_t per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) + 4;
+    s.buf.release();
+    if (!s.buf.ensure(per * (size_t)nt + 16)) return DMS_ERR_OOM;
+    s.hcap = hcap; s.hashcap = hashcap; s.nt = nt;
+    DMS_CUDA(cudaMemsetAsync(lz_hash(s), 0xFF, (size_t)hashcap * nt * sizeof(HashEnt), c.s));
+    DMS_CUDA(cudaMemsetAsync(lz_tgen(s), 0, 4 * (size_t)nt, c.s));
+    return DMS_OK;
+}
+
+template <typename T>
+dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const uint8_t *is_row) {
+    Pipeline &P = c.P;
+    DMS_ALLOC(P.d1_owner, 4 * n1 + 4);
+    DMS_ALLOC(P.d1_act, 4 * 4 * ncols + 4);
+    DMS_ALLOC(P.d1_next, 4 * 4 * ncols + 4);
+    DMS_ALLOC(P.d1_re, 4 * ncols + 4);
+    DMS_ALLOC(P.d1_todo, 4 * ncols + 4);
+    DMS_ALLOC(P.d1_stamp, 4 * ncols + 4);
+    DMS_ALLOC(P.d1_astamp, 4 * ncols + 4);
+    DMS_CUDA(cudaMemsetAsync(P.d1_owner.p, 0x7F, 4 * n1 + 4, c.s));
+    DMS_CUDA(cudaMemsetAsync(P.d1_stamp.p, 0xFF, 4 * ncols + 4, c.s));
+    DMS_CUDA(cudaMemsetAsync(P.d1_astamp.p, 0xFF, 4 * ncols + 4, c.s));
+    DMS_CUDA(cudaMemsetAsync(P.d1_len.p, 0xFF, 4 * ncols + 4, c.s));   // -1: not yet listed
+    DMS_LAUNCH(ncols, 256, k_iota32, P.d1_act.as<int32_t>(), ncols);
+    DMS_CUDA(cudaMemsetAsync(&c.st->misc[0], 0, 4 * sizeof(long long), c.s));
+    DMS_CUDA(cudaMemsetAsync(&c.st->red_io[0], 0, 2 * sizeof(long long), c.s));
+    DMS_CUDA(cudaMemsetAsync(&c.st->pool_top, 0, sizeof(unsigned long long), c.s));
+    int64_t pool_cap = d1_pool_entries(std::max<int64_t>(1 << 18, 24 * ncols + 1024));
+    DMS_ALLOC(P.d1_pool, sizeof(Ent) * pool_cap);
+    Ent *pool = P.d1_pool.as<Ent>();
+
+    // scratch: the first pass small (stays in L2), retries 16x larger per level
+    const int64_t nt_small = std::min<int64_t>(152 * 16 * 128, (ncols + 127) / 128 * 128);
+    DMS_TRY(lazy_scratch(c, P.lz_small, 48, 64, nt_small));
+    int big_hash = 1024;
+    int32_t launch = 0;
+
+    auto args = [&](LazyScratch &s) {
+        LzArgs<T> a;
+        a.values = values; a.g = c.g; a.flags = P.flags.as<uint8_t>();
+        a.grad = P.grad.as<GradRec>(); a.vrank = P.vrank.as<int32_t>();
+        a.recs = P.recs.as<CritRec>(); a.base1 = P.base[1].as<int32_t>(); a.is_row = is_row;
+        a.v2 = P.c_vert[2].as<int32_t>(); a.l2 = P.c_loc[2].as<uint8_t>();
+        a.colmap = P.d1_colmap.as<int32_t>();
+        a.heap_all = lz_heap(s); a.hash_all = lz_hash(s); a.tgen = lz_tgen(s);
+        a.hcap = s.hcap; a.hashcap = s.hashcap;
+        return a;
+    };
+    // one thread per listed column, at most the scratch's threads (a
+    // multiple of 32), in blocks that divide that count exactly
+    auto advance = [&](LazyScratch &s, const int32_t *todo, int64_t ntodo, int32_t *retry) {
+        if (ntodo == 0) return cudaSuccess;
+        const int64_t nt = std::min<int64_t>(s.nt, (ntodo + 31) / 32 * 32);
+        const int threads = nt % 128 == 0 ? 128 : 32;
+        k_lz_advance<T><<<(unsigned)(nt / threads), threads, 0, c.s>>>(
+            args(s), todo, ntodo, P.d1_astamp.as<int32_t>(), launch++, pool, pool_cap,
+            P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), retry, c.st);
+        c.launches++;
+        return cudaGetLastError();
+    };
+
+    int64_t nactive = ncols, stamp = 0, overflowed = 0;
+    const int64_t list_cap = 4 * ncols;
+    const int64_t limit = P.max_iters > 0 ? P.max_iters : ((int64_t)1 << 22);
+    DMS_CUDA(cudaMemsetAsync(&c.st->misc[2], 0, sizeof(long long), c.s));
+    KEV(18);
+    KEV(19);
+    KEV(20);
+    const bool debug = getenv("DMS_DEBUG") != nullptr;
+    struct Events {
+        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Events() { for (auto x : e) if (x) cudaEventDestroy(x); }
+    } dbg;
+    cudaEvent_t *dev = dbg.e;
+    if (debug)
+        for (int i = 0; i < 4; i++) cudaEventCreate(&dev[i]);
+    for (int64_t r = 0; r < limit; r++, stamp++) {
+        DMS_CUDA(cudaMemsetAsync(&c.st->misc[0], 0, 2 * sizeof(long long), c.s));
+        DMS_CUDA(cudaMemsetAsync(&c.st->misc[3], 0, sizeof(long long), c.s));
+        if (debug) cudaEventRecord(dev[0], c.s);
+        if (advance(P.lz_small, P.d1_act.as<int32_t>(), nactive, P.d1_todo.as<int32_t>()) !=
+            cudaSuccess)
+            return DMS_ERR_CUDA;
+        if (debug) cudaEventRecord(dev[1], c.s);
+        DMS_LAUNCH(nactive, 256, k_lz_claim, P.d1_act.as<int32_t>(), nactive,
+                   P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), pool,
+                   P.vrank.as<int32_t>(), P.recs.as<CritRec>(), P.base[1].as<int32_t>(),
+                   P.d1_owner.as<int32_t>(), P.d1_re.as<int32_t>(), c.st);
+        if (debug) cudaEventRecord(dev[2], c.s);
+        {
+            // one warp per listed column, at most one per thread slot of the
+            // scratch: the larger one once it exists and has a slot per warp
+            const int64_t want = std::min<int64_t>(64 * nactive, (int64_t)152 * 64 * 256);
+            LazyScratch &sc = (P.lz_big.buf.p && P.lz_big.nt % 8 == 0 && want <= 32 * P.lz_big.nt)
+                                  ? P.lz_big : P.lz_small;
+            const int64_t th = std::min<int64_t>(want, 32 * sc.nt);
+            k_lz_add<T><<<(unsigned)((th + 255) / 256), 256, 0, c.s>>>(
+                args(sc), P.d1_act.as<int32_t>(), nactive, P.d1_re.as<int32_t>(),
+                P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), pool, P.d1_owner.as<int32_t>(),
+                P.d1_stamp.as<int32_t>(), (int32_t)stamp, P.d1_next.as<int32_t>(), pool_cap, c.st);
+            c.launches++;
+            DMS_CUDA(cudaGetLastError());
+        }
+        if (debug) cudaEventRecord(dev[3], c.s);
+        dms_status s = sync_status(c);
+        P.rounds_d1 = r + 1;
+        const int64_t nre = c.hst->misc[0], nnext = c.hst->misc[1];
+        int64_t nretry = c.hst->misc[3];
+        if (debug) {
+            float ta = 0, tc = 0, td = 0;
+            cudaEventElapsedTime(&ta, dev[0], dev[1]);
+            cudaEventElapsedTime(&tc, dev[1], dev[2]);
+            cudaEventElapsedTime(&td, dev[2], dev[3]);
+            fprintf(stderr, "d1 lazy round %lld: listed %lld retry %lld rechecked %lld next %lld "
+                    "adds %lld pool %llu | advance %.3f claim %.3f add %.3f ms\n", (long long)r,
+                    (long long)nactive, (long long)nretry, (long long)nre, (long long)nnext,
+                    c.hst->misc[2], c.hst->pool_top, ta, tc, td);
+        }
+        if (s != DMS_OK && s != DMS_ERR_CAPACITY) return s;
+        bool full = s == DMS_ERR_CAPACITY;
+        // the next round's list: the columns changed by additions, then those
+        // that were not advanced (or, after the pool filled up, every column
+        // this round listed)
+        int32_t *nx = P.d1_next.as<int32_t>();
+        int64_t nlist = nnext;
+        if (full) {
+            if (nlist + nactive + nre <= list_cap) {
+                DMS_CUDA(cudaMemcpyAsync(nx + nlist, P.d1_act.p, 4 * nactive,
+                                         cudaMemcpyDeviceToDevice, c.s));
+                DMS_CUDA(cudaMemcpyAsync(nx + nlist + nactive, P.d1_re.p, 4 * nre,
+                                         cudaMemcpyDeviceToDevice, c.s));
+                nlist += nactive + nre;
+            } else {
+                DMS_LAUNCH(ncols, 256, k_iota32, nx, ncols);   // listing every column is safe
+                nlist = ncols;
+            }
+        } else if (nretry > 0) {
+            // columns that outgrew the small scratch: advance them now with
+            // larger scratch (16x per level), then list them for their claims
+            overflowed += nretry;
+            int32_t *todo = P.d1_todo.as<int32_t>(), *retry = P.d1_re.as<int32_t>();
+            DMS_CUDA(cudaMemcpyAsync(nx + nlist, todo, 4 * nretry, cudaMemcpyDeviceToDevice,
+                                     c.s));
+            nlist += nretry;
+            while (nretry > 0 && !full) {
+                if (!P.lz_big.buf.p || P.lz_big.hashcap < big_hash) {
+                    const int bh = big_hash * 3 / 4;
+                    const size_t per = (size_t)bh * sizeof(HeapEnt) +
+                                       (size_t)big_hash * sizeof(HashEnt) + 4;
+                    int64_t nt = std::max<int64_t>(
+                        32, std::min<int64_t>(ncols, ((int64_t)4 << 30) / (int64_t)per));
+                    DMS_TRY(lazy_scratch(c, P.lz_big, bh, big_hash, (nt + 31) / 32 * 32));
+                }
+                DMS_CUDA(cudaMemsetAsync(&c.st->misc[3], 0, sizeof(long long), c.s));
+                if (advance(P.lz_big, todo, nretry, retry) != cudaSuccess) return DMS_ERR_CUDA;
+                s = sync_status(c);
+                if (s != DMS_OK && s != DMS_ERR_CAPACITY) return s;
+                full = s == DMS_ERR_CAPACITY;
+                const int64_t again = c.hst->misc[3];
+                if (again > 0 && !full) {
+                    big_hash *= 16;                     // still too large: next level
+                    if (big_hash > (1 << 24)) return DMS_ERR_CAPACITY;
+                }
+                std::swap(todo, retry);
+                nretry = again;
+            }
+        }
+        if (full) {
+            // compact the live lists into a pool twice as large
+            DMS_ALLOC(P.flag_a, 4 * ncols + 4);
+            DMS_ALLOC(P.flag_b, 4 * ncols + 4);
+            DMS_LAUNCH(ncols, 256, k_lz_live, ncols, P.d1_len.as<int32_t>(),
+                       P.flag_a.as<int32_t>());
+            DMS_TRY(scan(c, P.flag_a.as<int32_t>(), P.flag_b.as<int32_t>(), ncols,
+                         &c.st->total[3]));
+            DMS_CUDA(cudaMemcpyAsync(c.hst, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.s));
+            DMS_CUDA(cudaStreamSynchronize(c.s));
+            const int64_t live = c.hst->total[3];
+            // at least 3x the live entries stay free after the compaction
+            const int64_t cap2 = std::max<int64_t>(pool_cap, 4 * live + (1 << 20));
+            if (cap2 >= ((int64_t)1 << 31)) return DMS_ERR_CAPACITY;
+            DevBuf fresh;
+            if (!fresh.ensure(sizeof(Ent) * (size_t)cap2)) return DMS_ERR_OOM;
+            DMS_LAUNCH(ncols, 256, k_lz_compact, ncols, P.d1_start.as<int64_t>(),
+                       P.d1_len.as<int32_t>(), P.flag_b.as<int32_t>(), pool, fresh.as<Ent>());
+            DMS_CUDA(cudaStreamSynchronize(c.s));
+            P.d1_pool.release();
+            P.d1_pool = fresh;
+            pool = P.d1_pool.as<Ent>();
+            pool_cap = cap2;
+            c.hst->err = 0;
+            c.hst->pool_top = (unsigned long long)live;
+            DMS_CUDA(cudaMemcpyAsync(c.st, c.hst, sizeof(DevStatus), cudaMemcpyHostToDevice, c.s));
+            P.d1_pool_grows++;
+        }
+        nactive = nlist;
+        std::swap(P.d1_act, P.d1_next);
+        if (nactive == 0) {
+            P.d1_overflow = overflowed;
+            P.d1_io_read = c.hst->red_io[0];
+            P.d1_io_written = c.hst->red_io[1];
+            P.d1_additions = c.hst->misc[2];
+            P.d1_pool_used = (int64_t)c.hst->pool_top;
+            DMS_LAUNCH(ncols, 256, k_lz_result, ncols, P.d1_start.as<int64_t>(),
+                       P.d1_len.as<int32_t>(), pool, P.vrank.as<int32_t>(),
+                       P.recs.as<CritRec>(), P.base[1].as<int32_t>(), P.d1_row.as<int32_t>(),
+                       P.d1_rowpaired.as<uint8_t>(), c.st);
+            KEV(21);
+            return DMS_OK;
+        }
+    }
+    return DMS_ERR_ITER_LIMIT;
 }
 
 template <typename T> dms_status run(Ctx &c, const T *values) {
@@ -2316,14 +3046,22 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
     DMS_ALLOC(P.d1_ovf, ncols + 4);
     DMS_LAUNCH(n2, 256, k_compact_idx, is_col, P.flag_b.as<int32_t>(), n2, P.d1_colmap.as<int32_t>());
     DMS_CUDA(cudaMemsetAsync(P.d1_len.p, 0, 4 * ncols + 4, c.s));
-    int64_t pool_cap = std::max<int64_t>(1 << 24, 128 * ncols + 1024);
-    DMS_ALLOC(P.d1_pool, 4 * pool_cap);
     P.rounds_d1 = 0;
     DMS_ALLOC(P.d1_row, 4 * ncols + 4);
     DMS_ALLOC(P.d1_rowpaired, n1 + 4);
     DMS_CUDA(cudaMemsetAsync(P.d1_rowpaired.p, 0, n1 + 4, c.s));
     DMS_CUDA(cudaMemsetAsync(P.d1_row.p, 0xFF, 4 * ncols + 4, c.s));
-    if (ncols > 0) {
+    // mode 0 picks by the density of the columns: sparse 2-saddles (smooth
+    // fields) have long descending walls that the lazy columns expand only
+    // as far as their pivots; dense ones (noisy fields) have short traces and
+    // long chains of additions that the traced 4-byte columns serve better
+    const int mode = P.d1_mode != 0 ? P.d1_mode : (ncols * kLazyBelowDensity < n ? 3 : 1);
+    P.d1_mode_used = mode;
+    if (ncols > 0 && mode == 3) {
+        DMS_TRY(reduce_lazy<T>(c, values, ncols, n1, is_row));
+    } else if (ncols > 0) {
+        int64_t pool_cap = std::max<int64_t>(1 << 24, 128 * ncols + 1024);
+        DMS_ALLOC(P.d1_pool, 4 * pool_cap);
         uint8_t *ovf = P.d1_ovf.as<uint8_t>();
         DMS_CUDA(cudaMemsetAsync(ovf, 0, ncols, c.s));
         DMS_CUDA(cudaMemsetAsync(&c.st->pool_top, 0, sizeof(unsigned long long), c.s));
@@ -2555,10 +3293,10 @@ dms_status Pipeline::init(int64_t nx_, int64_t ny_, int64_t nz_, dms_dtype dt,
     if (dt != DMS_U16 && dt != DMS_F32 && dt != DMS_F64) return DMS_ERR_INVALID_ARG;
     if (o && o->virtual_max != 1) return DMS_ERR_INVALID_ARG;
     if (o && o->max_iters < 0) return DMS_ERR_INVALID_ARG;
-    if (o && (o->d1_mode < 0 || o->d1_mode > 2)) return DMS_ERR_INVALID_ARG;
+    if (o && (o->d1_mode < 0 || o->d1_mode > 3)) return DMS_ERR_INVALID_ARG;
     nx = nx_; ny = ny_; nz = nz_; n = nx * ny * nz; dtype = dt;
     max_iters = o ? o->max_iters : 0;
-    d1_mode = (o && o->d1_mode == 2) ? 2 : 1;
+    d1_mode = o ? o->d1_mode : 0;
     if (cudaGetDevice(&device) != cudaSuccess) return DMS_ERR_CUDA;
     dms_status s = ensure_tables(device);
     if (s != DMS_OK) return s;
@@ -2596,7 +3334,8 @@ void Pipeline::destroy() {
                      &vc_tmp,     &keys,     &keys_tmp,  &recs,      &arc_a,      &arc_b,
                      &dc_keys,    &dc_par,   &dc_lab,    &young,     &died,       &rowcol,
                      &flag_a,     &flag_b,   &d1_colmap, &d1_start,  &d1_len,     &d1_owner,
-                     &d1_ovf,     &d1_pool,  &d1_scratch, &d1_todo,  &scan_tmp,   &dstat};
+                     &d1_ovf,     &d1_pool,  &d1_scratch, &d1_todo,  &scan_tmp,   &dstat,
+                     &d1_astamp, &lz_small.buf, &lz_big.buf};
     for (DevBuf *b : all) b->release();
     for (int d = 0; d < 4; d++) {
         cnt[d].release(); base[d].release(); c_vert[d].release(); c_loc[d].release();

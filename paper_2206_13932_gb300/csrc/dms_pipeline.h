@@ -18,18 +18,29 @@ struct DevBuf {
     template <typename T> T *as() const { return static_cast<T *>(p); }
 };
 
+// Per-thread scratch of the lazy D1 advances: nt threads, each with a heap of
+// hcap entries, a hash of hashcap entries and a generation word.
+struct LazyScratch {
+    DevBuf buf;
+    int hcap = 0, hashcap = 0;
+    int64_t nt = 0;
+};
+
 struct Pipeline {
     int64_t nx = 0, ny = 0, nz = 0, n = 0;
     dms_dtype dtype = DMS_F32;
     int64_t max_iters = 0;
-    int d1_mode = 1;        // 1: reduce columns (homology), 2: anti-transpose (cohomology)
+    int d1_mode = 0;        // 0: by column density, 1: reduce columns (homology),
+                            // 2: anti-transpose (cohomology), 3: lazy columns
+                            // (propagation interleaved with the reduction)
+    int d1_mode_used = 1;   // the mode the last compute ran
     int device = 0;
 
     // grid-sized state
     DevBuf values_dev;      // copy of host values (values_on_host = 1)
     DevBuf flags;           // u8 per vertex: descent link | critical flag
     DevBuf vrank;           // i32 per vertex: position among sorted critical vertices
-    DevBuf grad;            // 40 B per vertex: memoised lower-star pairing
+    DevBuf grad;            // 48 B per vertex: memoised lower-star pairing
     DevBuf tile_cnt, tile_off;
     // critical-count-sized state
     DevBuf vc, vc_tmp, keys, keys_tmp, recs;
@@ -41,6 +52,8 @@ struct Pipeline {
     DevBuf d1_row, d1_rowpaired;               // D1 result per column / row
     DevBuf d1_rowpos, d1_rowmap, d1_cocnt, d1_costart, d1_cofill;   // transpose
     DevBuf d1_colmap, d1_start, d1_len, d1_owner, d1_ovf, d1_pool, d1_scratch, d1_todo;
+    DevBuf d1_astamp;                          // lazy D1: last advance per column
+    LazyScratch lz_small, lz_big;              // lazy D1: advance scratch
     DevBuf out_pairs[3];
     DevBuf scan_tmp;
     DevBuf dstat;           // device status words
