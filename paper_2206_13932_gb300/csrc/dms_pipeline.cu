@@ -1296,6 +1296,42 @@ __global__ void k_red_claim(const int32_t *__restrict__ active, int64_t nactive,
     warp_append(take, old, recheck, (unsigned long long *)&st->misc[0]);
 }
 
+// The owner of each row with the owner's current list, published after the
+// claims of a round so that an addition finds the column to add in one load
+// (the owner's list is stable until the owner loses the row).
+struct RowCol {
+    long long start;
+    int32_t len;
+    int32_t col;     // kNoOwner: unclaimed (the whole record is memset 0x7F)
+};
+
+// Listed columns that won their pivot publish it.
+__global__ void k_red_publish(const int32_t *__restrict__ active, int64_t nactive,
+                              const int64_t *__restrict__ start, const int32_t *__restrict__ len,
+                              const int32_t *__restrict__ pool, const int32_t *__restrict__ owner,
+                              RowCol *rowcol) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nactive) return;
+    const int32_t cj = active[q];
+    const int l = len[cj];
+    if (l <= 0) return;
+    const long long s0 = start[cj];
+    const int32_t r = pool[s0];
+    if (owner[r] == cj) rowcol[r] = RowCol{s0, l, cj};
+}
+
+// Every non-zero column that owns its pivot publishes it (after the pool moved).
+__global__ void k_red_publish_all(int64_t ncol, const int64_t *__restrict__ start,
+                                  const int32_t *__restrict__ len,
+                                  const int32_t *__restrict__ pool,
+                                  const int32_t *__restrict__ owner, RowCol *rowcol) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncol || len[c] <= 0) return;
+    const long long s0 = start[c];
+    const int32_t r = pool[s0];
+    if (owner[r] == (int32_t)c) rowcol[r] = RowCol{s0, len[c], (int32_t)c};
+}
+
 // Merge path split of two decreasing lists: how many of the first d
 // elements of their merge (ties: A first) come from A.  A tie that would
 // straddle the split is moved to the earlier side, so that equal entries of A
@@ -1355,7 +1391,7 @@ __device__ int warp_symdiff(const int32_t *A, int la, const int32_t *B, int lb, 
 // claim it in the next round).  A column listed twice is processed once.
 __global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
                           const int32_t *__restrict__ recheck, int64_t *start, int32_t *len,
-                          int32_t *pool, const int32_t *__restrict__ owner, int32_t *stamp,
+                          int32_t *pool, const RowCol *__restrict__ rowcol, int32_t *stamp,
                           int32_t round, int32_t *next, int64_t pool_cap, DevStatus *st) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1373,10 +1409,11 @@ __global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
         bool changed = false;
         unsigned chain = 0;
         for (int it = 0; la > 0 && it < (1 << 24); it++) {
-            int32_t k = owner[pool[sa]];
+            const RowCol rc = rowcol[pool[sa]];
+            const int32_t k = rc.col;
             if (k == cj || k == kNoOwner || k > cj) break;
-            int64_t sb = start[k];
-            int lb = len[k];
+            const int64_t sb = rc.start;
+            const int lb = rc.len;
             unsigned long long pos = 0;
             if (lane == 0) pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
             pos = __shfl_sync(0xffffffffu, pos, 0);
@@ -1468,13 +1505,14 @@ constexpr size_t kRedSmem = sizeof(int32_t) * (2 * kRedAcc + kRedStage);
 __global__ void __launch_bounds__(kRedBlock)
     k_red_add_block(const int32_t *__restrict__ active, int64_t nactive,
                     const int32_t *__restrict__ recheck, int64_t *start, int32_t *len,
-                    int32_t *pool, const int32_t *__restrict__ owner, int32_t *stamp,
+                    int32_t *pool, const RowCol *__restrict__ rowcol, int32_t *stamp,
                     int32_t round, int32_t *next, int64_t pool_cap, DevStatus *st) {
     extern __shared__ int32_t smem[];
     int32_t *acc[2] = {smem, smem + kRedAcc};
     int32_t *sB = smem + 2 * kRedAcc;
     __shared__ int sscan[kRedBlock / 32];
-    __shared__ int32_t s_cj, s_k, s_fresh;
+    __shared__ int32_t s_cj, s_fresh;
+    __shared__ RowCol s_rc;
     __shared__ unsigned long long s_pos;
     const int64_t nre = *(volatile long long *)&st->misc[0];
     const int64_t q = blockIdx.x;
@@ -1498,17 +1536,35 @@ __global__ void __launch_bounds__(kRedBlock)
     bool changed = false, failed = false;
     unsigned chain = 0;
     unsigned long long io_r = 0, io_w = 0;
+    // thread 0 keeps the owner record of the next pivot; it is loaded for the
+    // predicted pivot before each merge, so its latency overlaps the merge
+    RowCol pre{0, 0, kNoOwner};
+    if (threadIdx.x == 0 && la > 0) pre = rowcol[resident ? acc[0][0] : pool[sa]];
     for (int it = 0; la > 0 && it < (1 << 24); it++) {
-        if (threadIdx.x == 0) s_k = owner[resident ? acc[cur][0] : pool[sa]];
+        if (threadIdx.x == 0) s_rc = pre;
         __syncthreads();
-        const int32_t k = s_k;
+        const int32_t k = s_rc.col;
         if (k == cj || k == kNoOwner || k > cj) break;
-        const int64_t sb = start[k];
-        const int lb = len[k];
+        const int64_t sb = s_rc.start;
+        const int lb = s_rc.len;
         const int32_t *B = pool + sb;
         if (lb <= kRedStage) {
             for (int t = threadIdx.x; t < lb; t += kRedBlock) sB[t] = B[t];
             B = sB;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            // the pivot after this addition: the first entry past the two
+            // cancelling tops that the lists do not share
+            const int32_t *A = resident ? acc[cur] : pool + sa;
+            int i = 1, j = 1;
+            int32_t nt = -1;
+            while (i < la || j < lb) {
+                const int32_t x = i < la ? A[i] : -1, y = j < lb ? B[j] : -1;
+                if (x != y) { nt = x > y ? x : y; break; }
+                i++; j++;
+            }
+            pre = nt >= 0 ? rowcol[nt] : RowCol{0, 0, kNoOwner};
         }
         io_r += (unsigned long long)(la + lb);
         if (resident && la + lb <= kRedAcc) {
@@ -2516,11 +2572,14 @@ constexpr int64_t kBlockModeBelow = 8192;   // active columns below which a bloc
 dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used) {
     Pipeline &P = c.P;
     DMS_ALLOC(P.d1_owner, 4 * nent + 4);
+    DMS_ALLOC(P.d1_rowcol, sizeof(RowCol) * (nent + 1));
+    RowCol *rowcol = P.d1_rowcol.as<RowCol>();
     DMS_ALLOC(P.d1_act, 4 * 3 * ncol + 4);
     DMS_ALLOC(P.d1_next, 4 * 3 * ncol + 4);
     DMS_ALLOC(P.d1_re, 4 * ncol + 4);
     DMS_ALLOC(P.d1_stamp, 4 * ncol + 4);
     DMS_CUDA(cudaMemsetAsync(P.d1_owner.p, 0x7F, 4 * nent + 4, c.s));
+    DMS_CUDA(cudaMemsetAsync(rowcol, 0x7F, sizeof(RowCol) * (nent + 1), c.s));
     DMS_CUDA(cudaMemsetAsync(P.d1_stamp.p, 0xFF, 4 * ncol + 4, c.s));
     DMS_LAUNCH(ncol, 256, k_iota32, P.d1_act.as<int32_t>(), ncol);
     DMS_CUDA(cudaMemsetAsync(&c.st->misc[2], 0, 2 * sizeof(long long), c.s));
@@ -2535,17 +2594,20 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
         DMS_LAUNCH(nactive, 256, k_red_claim, P.d1_act.as<int32_t>(), nactive,
                    P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
                    P.d1_owner.as<int32_t>(), P.d1_re.as<int32_t>(), c.st);
+        DMS_LAUNCH(nactive, 256, k_red_publish, P.d1_act.as<int32_t>(), nactive,
+                   P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
+                   P.d1_owner.as<int32_t>(), rowcol);
         if (nactive > kBlockModeBelow) {
             DMS_LAUNCH(std::min<int64_t>(64 * nactive, (int64_t)152 * 64 * 256), 256, k_red_add,
                        P.d1_act.as<int32_t>(), nactive, P.d1_re.as<int32_t>(),
                        P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
-                       P.d1_owner.as<int32_t>(), P.d1_stamp.as<int32_t>(), (int32_t)stamp,
+                       rowcol, P.d1_stamp.as<int32_t>(), (int32_t)stamp,
                        P.d1_next.as<int32_t>(), pool_cap, c.st);
         } else {
             // one block per column (grid covers active + displaced, <= 2x active)
             k_red_add_block<<<(unsigned)(2 * nactive), kRedBlock, kRedSmem, c.s>>>(
                 P.d1_act.as<int32_t>(), nactive, P.d1_re.as<int32_t>(), P.d1_start.as<int64_t>(),
-                P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), P.d1_owner.as<int32_t>(),
+                P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), rowcol,
                 P.d1_stamp.as<int32_t>(), (int32_t)stamp, P.d1_next.as<int32_t>(), pool_cap, c.st);
             c.launches++;
             DMS_CUDA(cudaGetLastError());
@@ -2582,6 +2644,10 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
             P.d1_pool.release();
             P.d1_pool = fresh;
             pool_cap = cap2;
+            // the owners' lists moved: publish them again
+            DMS_LAUNCH(ncol, 256, k_red_publish_all, ncol, P.d1_start.as<int64_t>(),
+                       P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
+                       P.d1_owner.as<int32_t>(), rowcol);
             // every column the interrupted round listed or changed is listed again
             const int64_t nre = c.hst->misc[0], nnext = c.hst->misc[1];
             DMS_CUDA(cudaMemcpyAsync(P.d1_act.as<int32_t>() + nactive, P.d1_re.p, 4 * nre,
@@ -3335,7 +3401,7 @@ void Pipeline::destroy() {
                      &dc_keys,    &dc_par,   &dc_lab,    &young,     &died,       &rowcol,
                      &flag_a,     &flag_b,   &d1_colmap, &d1_start,  &d1_len,     &d1_owner,
                      &d1_ovf,     &d1_pool,  &d1_scratch, &d1_todo,  &scan_tmp,   &dstat,
-                     &d1_astamp, &lz_small.buf, &lz_big.buf};
+                     &d1_astamp, &lz_small.buf, &lz_big.buf, &d1_rowcol};
     for (DevBuf *b : all) b->release();
     for (int d = 0; d < 4; d++) {
         cnt[d].release(); base[d].release(); c_vert[d].release(); c_loc[d].release();

@@ -52,6 +52,7 @@ struct Pipeline {
     DevBuf d1_row, d1_rowpaired;               // D1 result per column / row
     DevBuf d1_rowpos, d1_rowmap, d1_cocnt, d1_costart, d1_cofill;   // transpose
     DevBuf d1_colmap, d1_start, d1_len, d1_owner, d1_ovf, d1_pool, d1_scratch, d1_todo;
+    DevBuf d1_rowcol;                          // D1: owner of each row with its list
     DevBuf d1_astamp;                          // lazy D1: last advance per column
     LazyScratch lz_small, lz_big;              // lazy D1: advance scratch
     DevBuf out_pairs[3];
