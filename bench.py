@@ -35,6 +35,7 @@ UNIT = "Mvertices/s"
 L2_BYTES = 129 * 2**20
 ORACLE_SAMPLE = 64          # edge of the cube cropped for the oracle (cpu_baseline)
 SERVE_REQUESTS = 128        # requests of the serving workload replayed per run
+SERVE_BATCH = 16            # most requests one batched pass takes
 REFERENCE_SAMPLE = 40       # edge of the crop per reference-arm step
 
 
@@ -152,16 +153,21 @@ def serving_section():
     r1, w1 = serve.run_stream(fields, zeros, slots=1)             # back to back, one at a time
     cap = len(fields) / w1
     r4, w4 = serve.run_stream(fields, zeros, slots=4)             # back to back, 4 slots
+    rB, wB = serve.run_stream(fields, zeros, slots=4, max_batch=SERVE_BATCH)   # batched
     arr = sf.poisson_arrivals(len(fields), 0.8 * cap)
     rb, wb = serve.run_stream(fields, arr, slots=4)
+    rbb, wbb = serve.run_stream(fields, arr, slots=4, max_batch=SERVE_BATCH)
     rs, ws = serve.run_stream(fields, arr, slots=1)
     return {
         "requests": len(fields), "mean_vertices": nvert / len(fields),
         "saturated": {"one_at_a_time_rps": cap, "one_at_a_time_Mvertices_s": nvert / w1 / 1e6,
                       "served_4_slots_rps": len(fields) / w4,
-                      "served_4_slots_Mvertices_s": nvert / w4 / 1e6},
+                      "served_4_slots_Mvertices_s": nvert / w4 / 1e6,
+                      f"batched_4_slots_x{SERVE_BATCH}_rps": len(fields) / wB,
+                      f"batched_4_slots_x{SERVE_BATCH}_Mvertices_s": nvert / wB / 1e6},
         "poisson_rho_0.8": {"rate_rps": 0.8 * cap,
                             "served_4_slots": serve.latency_stats(rb),
+                            f"batched_4_slots_x{SERVE_BATCH}": serve.latency_stats(rbb),
                             "one_at_a_time": serve.latency_stats(rs)},
     }
 

@@ -95,6 +95,38 @@ typedef struct dms_grid_s *dms_grid;
 dms_status dms_grid_create(int64_t nx, int64_t ny, int64_t nz, dms_dtype dtype,
                            const dms_options *opts, dms_grid *out);
 
+/* Creates a handle for a batch of nfields grids (1 <= nfields <= 65535) of
+ * their own shapes: shapes[3f..3f+2] = nx, ny, nz of field f (each >= 1,
+ * total vertex count < 2^31), one dtype.  The batch is computed in one pass
+ * of the pipeline -- one launch of each kernel for all fields -- over the
+ * disjoint union of the grids, whose persistence diagrams are those of the
+ * fields (a union of disjoint complexes has block-diagonal boundary
+ * matrices; the shared virtual maximum is older than every other node, so
+ * no field's merges change).
+ *   dms_compute_diagram: values = the fields one after another, each x
+ *     fastest (field f starts at element sum of the sizes of fields < f).
+ *   dms_fetch_pairs: the pairs of all fields grouped by field (field 0
+ *     first), each field's pairs in the order of a single-grid compute, with
+ *     simplex and vertex ids relative to the field; dms_batch_offsets gives
+ *     the ranges.  An infinite class dies at the maximum of its own field.
+ *   dms_get_counts: totals over the batch.
+ *   dms_backward_pairs: grad_field in the layout of values.
+ *   dms_grid_reshape: not available (DMS_ERR_INVALID_ARG). */
+dms_status dms_batch_create(int64_t nfields, const int64_t *shapes, dms_dtype dtype,
+                            const dms_options *opts, dms_grid *out);
+
+/* Re-targets a batch handle to another batch (same dtype and options): new
+ * field count and shapes as in dms_batch_create.  Device buffers are kept and
+ * grow only when needed, so one handle serves a stream of batches.  Drops the
+ * last result.  DMS_ERR_INVALID_ARG for a single-grid handle. */
+dms_status dms_batch_reshape(dms_grid grid, int64_t nfields, const int64_t *shapes);
+
+/* offsets[f] .. offsets[f+1] (nfields + 1 host int64) = the positions of
+ * field f's pairs of dimension dim in dms_fetch_pairs order, for the last
+ * successful compute of a batch (DMS_ERR_STATE for a single grid or without
+ * a result). */
+dms_status dms_batch_offsets(dms_grid grid, int dim, int64_t *offsets);
+
 /* Changes the grid dimensions of a handle (same dtype and options), keeping
  * its device buffers and growing them only when the new grid is larger, so
  * that one handle serves fields of many shapes.  Drops the last result. */

@@ -73,6 +73,13 @@ def load(build_if_missing: bool = False):
             lib.dms_backward_pairs.restype = ctypes.c_int
             lib.dms_grid_reshape.argtypes = [vp, i64, i64, i64]
             lib.dms_grid_reshape.restype = ctypes.c_int
+            lib.dms_batch_create.argtypes = [i64, p64, ctypes.c_int, ctypes.POINTER(_Options),
+                                             ctypes.POINTER(vp)]
+            lib.dms_batch_create.restype = ctypes.c_int
+            lib.dms_batch_reshape.argtypes = [vp, i64, p64]
+            lib.dms_batch_reshape.restype = ctypes.c_int
+            lib.dms_batch_offsets.argtypes = [vp, ctypes.c_int, p64]
+            lib.dms_batch_offsets.restype = ctypes.c_int
             lib.dms_grid_destroy.argtypes = [vp]
             lib.dms_status_string.argtypes = [ctypes.c_int]
             lib.dms_status_string.restype = ctypes.c_char_p
@@ -207,6 +214,84 @@ class Grid:
                  "levels_d2", "rounds_d1", "d1_columns", "d1_trace_overflow", "d1_additions",
                  "d1_pool_used", "d1_pool_grows", "d1_bytes_read", "d1_bytes_written")
         return dict(zip(names, [int(x) for x in s]))
+
+
+class Batch(Grid):
+    """A handle of ``dms_batch_create``: many fields of their own shapes, computed
+    in one pass of the pipeline.  ``compute`` takes the fields one after another
+    (a list of arrays/tensors indexed [z, y, x], or one packed array);
+    ``fetch_fields(dim)`` returns one PAIR_DTYPE array per field, with ids
+    relative to the field, equal to what a single-grid compute of that field
+    returns."""
+
+    def __init__(self, shapes_xyz, dtype, max_iters: int = 0, d1_mode: int = 0):
+        self._lib = load()
+        self.shapes_xyz = [tuple(int(s) for s in sh) for sh in shapes_xyz]
+        self.dtype = np.dtype(dtype)
+        if self.dtype not in _DTYPE_CODE:
+            raise TypeError(f"unsupported dtype {self.dtype}")
+        nf = len(self.shapes_xyz)
+        flat = (ctypes.c_int64 * (3 * nf))(*[v for sh in self.shapes_xyz for v in sh])
+        opts = _Options(1, int(max_iters), int(d1_mode))
+        h = ctypes.c_void_p()
+        _check(self._lib.dms_batch_create(nf, flat, _DTYPE_CODE[self.dtype], ctypes.byref(opts),
+                                          ctypes.byref(h)), "dms_batch_create")
+        self._h = h
+        self.sizes = [a * b * c for a, b, c in self.shapes_xyz]
+        self.n = int(sum(self.sizes))
+
+    def reshape(self, shapes_xyz):
+        """Re-targets this handle (and its device buffers) to another batch of
+        field shapes (a list of (nx, ny, nz))."""
+        if not shapes_xyz or not isinstance(shapes_xyz[0], (tuple, list)):
+            raise DmsError(1, "a batch is reshaped to a list of field shapes")
+        shapes = [tuple(int(s) for s in sh) for sh in shapes_xyz]
+        flat = (ctypes.c_int64 * (3 * len(shapes)))(*[v for sh in shapes for v in sh])
+        _check(self._lib.dms_batch_reshape(self._h, len(shapes), flat), "dms_batch_reshape")
+        self.shapes_xyz = shapes
+        self.sizes = [a * b * c for a, b, c in shapes]
+        self.n = int(sum(self.sizes))
+        return self
+
+    def _field_ptr(self, values):
+        if isinstance(values, (list, tuple)):
+            try:
+                import torch
+            except ImportError:  # pragma: no cover
+                torch = None
+            if torch is not None and all(isinstance(v, torch.Tensor) for v in values):
+                values = torch.cat([v.reshape(-1) for v in values])
+            else:
+                values = np.concatenate([np.asarray(v).reshape(-1) for v in values])
+        try:
+            import torch
+        except ImportError:  # pragma: no cover
+            torch = None
+        if torch is not None and isinstance(values, torch.Tensor):
+            if values.numel() != self.n or not values.is_contiguous():
+                raise ValueError("the packed fields must be contiguous with sum(sizes) elements")
+            if np.dtype(str(values.dtype).replace("torch.", "")) != self.dtype:
+                raise TypeError("dtype mismatch")
+            return values.data_ptr(), (0 if values.is_cuda else 1), values
+        arr = np.ascontiguousarray(values).reshape(-1)
+        if arr.size != self.n or arr.dtype != self.dtype:
+            raise ValueError("packed size or dtype mismatch")
+        return arr.ctypes.data, 1, arr
+
+    def offsets(self, dim: int) -> np.ndarray:
+        off = (ctypes.c_int64 * (len(self.shapes_xyz) + 1))()
+        _check(self._lib.dms_batch_offsets(self._h, dim, off), "dms_batch_offsets")
+        return np.array(off, dtype=np.int64)
+
+    def fetch_fields(self, dim: int):
+        allp = self.fetch(dim)
+        off = self.offsets(dim)
+        return [allp[off[f]:off[f + 1]] for f in range(len(self.shapes_xyz))]
+
+    def results(self):
+        """Per field: {dim: PAIR_DTYPE array}."""
+        per = [self.fetch_fields(d) for d in range(3)]
+        return [{d: per[d][f] for d in range(3)} for f in range(len(self.shapes_xyz))]
 
 
 def classify_static(values, flags_out, critical_out, stream=None) -> int:

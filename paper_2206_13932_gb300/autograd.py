@@ -86,12 +86,15 @@ def persistence_diagram(values: torch.Tensor, grid: Grid | None = None) -> list:
     """D0, D1, D2 of a CUDA field indexed [z, y, x] (float32 or float64), with
     births and deaths differentiable with respect to ``values``.  ``grid`` (a
     :class:`Grid` of the field's shape and dtype) may be reused across calls;
-    it must stay alive until the backward pass has run."""
+    it must stay alive until the backward pass has run.  With a :class:`Batch`
+    as ``grid``, ``values`` holds its fields packed one after another and the
+    diagrams hold every field's pairs, grouped by field (``grid.offsets(d)``
+    gives the ranges); the gradient comes back in the packed layout."""
     if not values.is_cuda:
         raise ValueError("values must be a CUDA tensor")
     values = values.contiguous()
-    nz, ny, nx = values.shape
     if grid is None:
+        nz, ny, nx = values.shape
         grid = Grid((nx, ny, nz), np.dtype(str(values.dtype).replace("torch.", "")))
     grid.compute(values.detach())
     pairs, ess = grid.counts()

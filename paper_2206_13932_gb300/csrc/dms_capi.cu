@@ -26,6 +26,34 @@ dms_status dms_grid_create(int64_t nx, int64_t ny, int64_t nz, dms_dtype dtype,
     return DMS_OK;
 }
 
+dms_status dms_batch_create(int64_t nfields, const int64_t *shapes, dms_dtype dtype,
+                            const dms_options *opts, dms_grid *out) {
+    if (!out || !shapes) return DMS_ERR_INVALID_ARG;
+    dms_grid g = new (std::nothrow) dms_grid_s;
+    if (!g) return DMS_ERR_OOM;
+    dms_status s = g->p.init_batch(nfields, shapes, dtype, opts);
+    if (s != DMS_OK) {
+        g->p.destroy();
+        delete g;
+        return s;
+    }
+    *out = g;
+    return DMS_OK;
+}
+
+dms_status dms_batch_reshape(dms_grid grid, int64_t nfields, const int64_t *shapes) {
+    if (!grid || !shapes) return DMS_ERR_INVALID_ARG;
+    return grid->p.set_batch(nfields, shapes);
+}
+
+dms_status dms_batch_offsets(dms_grid grid, int dim, int64_t *offsets) {
+    if (!grid || !offsets || dim < 0 || dim > 2) return DMS_ERR_INVALID_ARG;
+    const dms::Pipeline &p = grid->p;
+    if (!p.batch || !p.has_result) return DMS_ERR_STATE;
+    for (int64_t f = 0; f <= p.nf; f++) offsets[f] = p.batch_off[dim][f];
+    return DMS_OK;
+}
+
 dms_status dms_grid_reshape(dms_grid grid, int64_t nx, int64_t ny, int64_t nz) {
     if (!grid) return DMS_ERR_INVALID_ARG;
     return grid->p.reshape(nx, ny, nz);

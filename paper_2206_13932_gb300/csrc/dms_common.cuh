@@ -42,11 +42,30 @@ struct StarTables {
     uint16_t neg[3], pos[3];          // links with d = -1 / +1 along each axis
 };
 
-// Grid constants passed by value to kernels.
+// Grid constants passed by value to kernels.  A batch lays several grids
+// (fields) out one after another in one id space; `off` is the id of a
+// field's vertex (0,0,0) (0 for a single grid).
 struct GridParams {
     int32_t nx, ny, nz;
     int64_t n;                        // nx*ny*nz (< 2^31)
     int32_t dlin[kLinks];             // linear id offset of each link vertex
+    int64_t off;
+};
+
+// The grid of a vertex: the only one (B = false), or the field of a batch
+// that holds the vertex (B = true: a field index per vertex).
+template <bool B> struct Geo;
+template <> struct Geo<false> {
+    GridParams g0;
+    __device__ __forceinline__ const GridParams &at(int64_t) const { return g0; }
+};
+template <> struct Geo<true> {
+    const GridParams *fields;
+    const uint16_t *field_of;
+    __device__ __forceinline__ int field(int64_t v) const { return field_of[v]; }
+    __device__ __forceinline__ const GridParams &at(int64_t v) const {
+        return fields[field_of[v]];
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -103,7 +122,7 @@ __device__ __forceinline__ uint16_t present_links(const StarTables &S, const Gri
 
 __device__ __forceinline__ void coords(const GridParams &g, int64_t v, int &cx, int &cy,
                                        int &cz) {
-    int32_t vi = (int32_t)v;
+    int32_t vi = (int32_t)(v - g.off);
     int32_t row = vi / g.nx;
     cx = vi - row * g.nx;
     cz = row / g.ny;

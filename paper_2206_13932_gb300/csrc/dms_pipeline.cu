@@ -530,6 +530,83 @@ __global__ void __launch_bounds__(kClsThreads)
     }
 }
 
+// The tier-1 classification of a batch: blocks of kClsTile consecutive ids
+// (the tiles of k_compact2) over all fields, each vertex with the grid of
+// its field; also the largest key of each field (its infinite classes die
+// there).
+template <typename T>
+__global__ void __launch_bounds__(kClsThreads)
+    k_classify_batch(const T *__restrict__ values, Geo<true> geo, int64_t n,
+                     uint8_t *__restrict__ flags, int32_t *__restrict__ tile_cnt,
+                     unsigned long long *fmax_field, DevStatus *st) {
+    __shared__ uint32_t lut[(1 << kLinks) / 32];
+    __shared__ int scnt[kClsThreads / 32];
+    for (int i = threadIdx.x; i < (1 << kLinks) / 32; i += kClsThreads) lut[i] = g_regular[i];
+    __syncthreads();
+    const StarTables &S = g_star;
+    const int64_t base = (int64_t)blockIdx.x * kClsTile;
+    int cnt = 0, cur = -1;
+    unsigned long long cmax = 0;
+    bool bad = false;
+    for (int k = 0; k < kClsItems; k++) {
+        const int64_t v = base + (int64_t)k * kClsThreads + threadIdx.x;
+        if (v >= n) break;
+        const int f = geo.field(v);
+        const GridParams &g = geo.fields[f];
+        int cx, cy, cz;
+        coords(g, v, cx, cy, cz);
+        typename Key<T>::K kv;
+        const uint8_t fl = classify_vertex<T>(S, g, lut, values, v, cx, cy, cz, kv);
+        bad |= Key<T>::nan(values[v]);
+        flags[v] = fl;
+        cnt += (fl & kFlagCritical) != 0;
+        if (f != cur) {
+            if (cur >= 0) atomicMax(&fmax_field[cur], cmax);
+            cur = f;
+            cmax = 0;
+        }
+        cmax = (unsigned long long)kv > cmax ? (unsigned long long)kv : cmax;
+    }
+    if (cur >= 0) atomicMax(&fmax_field[cur], cmax);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if (lane == 0) scnt[w] = cnt;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->err, kErrNan);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int i = 0; i < kClsThreads / 32; i++) c += scnt[i];
+        tile_cnt[blockIdx.x] = c;
+    }
+}
+
+// field index of every vertex of a batch (offsets: nf + 1 ascending ids)
+__global__ void k_field_of(const int64_t *__restrict__ offsets, int nf, int64_t n,
+                           uint16_t *field_of) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int lo = 0, hi = nf - 1;
+    while (lo < hi) {            // the last field whose offset is <= v
+        const int mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    field_of[v] = (uint16_t)lo;
+}
+
+// pairs per field (batch output)
+__global__ void k_field_count(const int32_t *__restrict__ ofield, int64_t n, int32_t *cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[ofield[i]], 1);
+}
+
+// out[i] = in[perm[i]]
+__global__ void k_gather_pairs(const dms_pair *__restrict__ in, const int32_t *__restrict__ perm,
+                               int64_t n, dms_pair *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[perm[i]];
+}
+
 // ----------------------------------- stage 2: stable LSD radix sort by key
 
 constexpr int kRsThreads = 256, kRsWarps = kRsThreads / 32, kRsPerWarp = 512,
@@ -603,13 +680,14 @@ __global__ void __launch_bounds__(kRsThreads)
 
 // ProcessLowerStars of the vertices of an id-ordered list (or of every vertex
 // if list is null): the packed pairing of each lower star.
-template <typename T>
-__global__ void k_pls(const T *__restrict__ values, GridParams g, const int32_t *__restrict__ list,
+template <typename T, bool B>
+__global__ void k_pls(const T *__restrict__ values, Geo<B> geo, const int32_t *__restrict__ list,
                       int64_t count, uint8_t *flags, GradRec *grad) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const StarTables &S = g_star;
     int64_t x = list ? list[i] : i;
+    const GridParams &g = geo.at(x);
     StarView sv;
     load_star(S, g, values, x, sv);
     PLSResult R;
@@ -734,13 +812,15 @@ __device__ __forceinline__ int64_t descend(const GridParams &g, const uint8_t *_
 // Each critical edge links the two minima that its two descending v-paths
 // (vertex -> edge vectors: each regular vertex is paired with the edge to its
 // lowest neighbour) reach (Sec. 5.1 (a)-(b)).
-__global__ void k_d0_arcs(GridParams g, const uint8_t *__restrict__ flags,
+template <bool Bt>
+__global__ void k_d0_arcs(Geo<Bt> geo, const uint8_t *__restrict__ flags,
                           const int32_t *__restrict__ vrank, const int32_t *__restrict__ v1,
                           const uint8_t *__restrict__ l1, int64_t n1, int32_t *A, int32_t *B,
                           int32_t *young, int64_t max_steps, DevStatus *st) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n1) return;
     int64_t x = v1[j];
+    const GridParams &g = geo.at(x);
     int64_t u = x + g.dlin[l1[j]];
     int64_t ma = descend(g, flags, x, max_steps, st), mb = descend(g, flags, u, max_steps, st);
     // on failure both ends go to node 0: a self-loop, harmless until the
@@ -1003,8 +1083,8 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
     return vmax;
 }
 
-template <typename T>
-__global__ void k_d2_arcs(const T *__restrict__ values, GridParams g, uint8_t *flags,
+template <typename T, bool Bt>
+__global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *flags,
                           GradRec *grad, const int32_t *__restrict__ vrank,
                           const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
                           const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
@@ -1014,6 +1094,7 @@ __global__ void k_d2_arcs(const T *__restrict__ values, GridParams g, uint8_t *f
     if (j >= n2) return;
     const StarTables &S = g_star;
     int64_t x = v2[j];
+    const GridParams &g = geo.at(x);
     int s = l2[j];
     int cx, cy, cz;
     coords(g, x, cx, cy, cz);
@@ -1181,8 +1262,8 @@ __device__ __forceinline__ void trace_expand(TraceCtx &c, const StarTables &S, c
 // One thread per column: the Morse boundary of a critical triangle restricted
 // to the rows (1-saddles not paired in D0), as a descending list of C1
 // indices appended to the column pool.
-template <typename T>
-__global__ void k_d1_trace(const T *__restrict__ values, GridParams g, uint8_t *flags,
+template <typename T, bool B>
+__global__ void k_d1_trace(const T *__restrict__ values, Geo<B> geo, uint8_t *flags,
                            GradRec *grad, const int32_t *__restrict__ vrank,
                            const CritRec *__restrict__ recs, const int32_t *__restrict__ base1,
                            const uint8_t *__restrict__ is_row, const int32_t *__restrict__ v2,
@@ -1204,6 +1285,7 @@ __global__ void k_d1_trace(const T *__restrict__ values, GridParams g, uint8_t *
         int32_t cj = todo ? todo[q] : (int32_t)q;
         int32_t j2 = colmap[cj];
         int64_t x = v2[j2];
+        const GridParams &g = geo.at(x);
         int s = l2[j2];
         c.hn = 0; c.rn = 0; c.used = 0; c.overflow = false;
         c.gen = gen_base + cj;
@@ -1974,9 +2056,9 @@ __device__ int lz_advance_col(LazyCtx &c, const StarTables &S, const T *__restri
 }
 
 // The inputs every advance reads.
-template <typename T> struct LzArgs {
+template <typename T, bool B> struct LzArgs {
     const T *values;
-    GridParams g;
+    Geo<B> geo;
     uint8_t *flags;
     GradRec *grad;
     const int32_t *vrank;
@@ -1992,8 +2074,8 @@ template <typename T> struct LzArgs {
     int hcap, hashcap;
 };
 
-template <typename T>
-__device__ __forceinline__ LazyCtx lz_ctx(const LzArgs<T> &a, int64_t slot) {
+template <typename T, bool B>
+__device__ __forceinline__ LazyCtx lz_ctx(const LzArgs<T, B> &a, int64_t slot) {
     LazyCtx c;
     c.heap = a.heap_all + slot * a.hcap;
     c.hash = a.hash_all + slot * a.hashcap;
@@ -2006,9 +2088,9 @@ __device__ __forceinline__ LazyCtx lz_ctx(const LzArgs<T> &a, int64_t slot) {
 // Advances the listed columns (one thread each) whose top is regular or that
 // have no list yet.  A column that outgrows the scratch, or finds the pool
 // full, is left as it was and queued on `retry`.
-template <typename T>
+template <typename T, bool B>
 __global__ void __launch_bounds__(128)
-    k_lz_advance(LzArgs<T> a, const int32_t *__restrict__ todo, int64_t ntodo, int32_t *astamp,
+    k_lz_advance(LzArgs<T, B> a, const int32_t *__restrict__ todo, int64_t ntodo, int32_t *astamp,
                  int32_t launch, Ent *pool, int64_t pool_cap, int64_t *col_start,
                  int32_t *col_len, int32_t *retry, DevStatus *st) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2023,7 +2105,8 @@ __global__ void __launch_bounds__(128)
         if (la > 0 && (pool[sa].lo & 1)) continue;               // critical top
         if (atomicExch(&astamp[cj], launch) == launch) continue; // listed twice
         c.gen = ++gen;
-        const int r = lz_advance_col<T>(c, g_star, a.values, a.g, a.flags, a.grad, a.vrank,
+        const GridParams &g = a.geo.at(a.v2[a.colmap[cj]]);
+        const int r = lz_advance_col<T>(c, g_star, a.values, g, a.flags, a.grad, a.vrank,
                                         a.recs, a.base1, a.is_row, a.v2, a.l2, a.colmap, cj, la,
                                         sa, pool, pool_cap, col_start, col_len, st);
         if (r) retry[atomicAdd((unsigned long long *)&st->misc[3], 1ull)] = cj;
@@ -2109,8 +2192,8 @@ __device__ int ent_warp_symdiff(const Ent *A, int la, const Ent *B, int lb, Ent 
 // the scratch) and the additions go on, so a column's whole chain runs in one
 // round.  A changed column is listed for the next round (for its claim, or
 // for an advance with larger scratch when the inline one did not fit).
-template <typename T>
-__global__ void k_lz_add(LzArgs<T> a, const int32_t *__restrict__ active, int64_t nactive,
+template <typename T, bool B>
+__global__ void k_lz_add(LzArgs<T, B> a, const int32_t *__restrict__ active, int64_t nactive,
                          const int32_t *__restrict__ recheck, int64_t *start, int32_t *len,
                          Ent *pool, const int32_t *__restrict__ owner, int32_t *stamp,
                          int32_t round, int32_t *next, int64_t pool_cap, DevStatus *st) {
@@ -2138,7 +2221,8 @@ __global__ void k_lz_add(LzArgs<T> a, const int32_t *__restrict__ active, int64_
                 long long sa2 = 0;
                 if (lane == 0) {
                     c.gen = ++gen;
-                    r = lz_advance_col<T>(c, g_star, a.values, a.g, a.flags, a.grad, a.vrank,
+                    const GridParams &g = a.geo.at(a.v2[a.colmap[cj]]);
+                    r = lz_advance_col<T>(c, g_star, a.values, g, a.flags, a.grad, a.vrank,
                                           a.recs, a.base1, a.is_row, a.v2, a.l2, a.colmap, cj,
                                           la, sa, pool, pool_cap, start, len, st);
                     if (r == 0) { la2 = len[cj]; sa2 = start[cj]; }
@@ -2274,11 +2358,17 @@ __global__ void k_flag_min(const int32_t *v0, int64_t n0, const int32_t *vrank,
     if (i < n0) flag[i] = !died0[vrank[v0[i]]];
 }
 
-template <typename T>
-__global__ void k_write(int kind, OutArgs a, const T *__restrict__ values, GridParams g,
+// In a batch the ids are written relative to the pair's field (a simplex id
+// of dimension d is a multiple of the field offset: 1, 7, 12, 6 ids per
+// vertex), the field index goes to `ofield`, and an infinite class dies at
+// the maximum of its own field.
+template <typename T, bool B>
+__global__ void k_write(int kind, OutArgs a, const T *__restrict__ values, Geo<B> geo,
                         int64_t n, const int32_t *__restrict__ flag,
                         const int32_t *__restrict__ pos, int64_t offset, const int32_t *vrank,
-                        unsigned long long fmax_key, dms_pair *out) {
+                        unsigned long long fmax_key,
+                        const unsigned long long *__restrict__ fmax_field, int32_t *ofield,
+                        dms_pair *out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !flag[i]) return;
     const StarTables &S = g_star;
@@ -2289,7 +2379,7 @@ __global__ void k_write(int kind, OutArgs a, const T *__restrict__ values, GridP
     switch (kind) {
         case 0: {   // D0: (minimum, critical edge)
             bv = a.vc[a.young0[i]]; bs = bv;
-            dv = a.v1[i]; ds = edge_id(S, g, dv, a.l1[i]);
+            dv = a.v1[i]; ds = edge_id(S, geo.at(dv), dv, a.l1[i]);
             dim = 0; break;
         }
         case 1: {   // D0 infinite
@@ -2297,31 +2387,45 @@ __global__ void k_write(int kind, OutArgs a, const T *__restrict__ values, GridP
         }
         case 2: {   // D1: (critical edge = pivot row, critical triangle)
             int32_t row = a.d1_row[i];
-            bv = a.v1[row]; bs = edge_id(S, g, bv, a.l1[row]);
+            bv = a.v1[row]; bs = edge_id(S, geo.at(bv), bv, a.l1[row]);
             int32_t j2 = a.colmap[i];
-            dv = a.v2[j2]; ds = tri_id(S, g, dv, a.l2[j2]);
+            dv = a.v2[j2]; ds = tri_id(S, geo.at(dv), dv, a.l2[j2]);
             dim = 1; break;
         }
         case 3: {
-            bv = a.v1[i]; bs = edge_id(S, g, bv, a.l1[i]); dim = 1; ess = 1; break;
+            bv = a.v1[i]; bs = edge_id(S, geo.at(bv), bv, a.l1[i]); dim = 1; ess = 1; break;
         }
         case 4: {   // D2: (critical triangle, critical tet)
-            bv = a.v2[i]; bs = tri_id(S, g, bv, a.l2[i]);
+            bv = a.v2[i]; bs = tri_id(S, geo.at(bv), bv, a.l2[i]);
             int32_t t = a.young2[i];
-            dv = a.v3[t]; ds = tet_id(S, g, dv, a.l3[t]);
+            dv = a.v3[t]; ds = tet_id(S, geo.at(dv), dv, a.l3[t]);
             dim = 2; break;
         }
         case 5: {
             int32_t j2 = a.colmap[i];
-            bv = a.v2[j2]; bs = tri_id(S, g, bv, a.l2[j2]); dim = 2; ess = 1; break;
+            bv = a.v2[j2]; bs = tri_id(S, geo.at(bv), bv, a.l2[j2]); dim = 2; ess = 1; break;
         }
         case 6: {
-            bv = a.v3[i]; bs = tet_id(S, g, bv, a.l3[i]); dim = 3; ess = 1; break;
+            bv = a.v3[i]; bs = tet_id(S, geo.at(bv), bv, a.l3[i]); dim = 3; ess = 1; break;
         }
     }
-    p.birth_simplex = bs; p.death_simplex = ds; p.birth_vertex = bv; p.death_vertex = dv;
     p.birth_bits = Key<T>::bits(values[bv]);
-    p.death_bits = dv >= 0 ? Key<T>::bits(values[dv]) : fmax_bits<T>(fmax_key);
+    unsigned long long fkey = fmax_key;
+    if constexpr (B) {
+        const int f = geo.field(bv);
+        const int64_t off = geo.fields[f].off;
+        const int64_t per[4] = {1, 7, 12, 6};
+        bs -= per[dim] * off;
+        if (ds >= 0) ds -= per[dim + 1 > 3 ? 3 : dim + 1] * off;
+        fkey = fmax_field[f];
+        p.death_bits = dv >= 0 ? Key<T>::bits(values[dv]) : fmax_bits<T>(fkey);
+        bv -= off;
+        if (dv >= 0) dv -= off;
+        ofield[offset + pos[i]] = f;
+    } else {
+        p.death_bits = dv >= 0 ? Key<T>::bits(values[dv]) : fmax_bits<T>(fkey);
+    }
+    p.birth_simplex = bs; p.death_simplex = ds; p.birth_vertex = bv; p.death_vertex = dv;
     p.dim = (uint8_t)dim; p.essential = (uint8_t)ess;
     out[offset + pos[i]] = p;
 }
@@ -2349,14 +2453,29 @@ __global__ void k_compact_idx(const uint8_t *flag, const int32_t *pos, int64_t n
 // gradients of the births and deaths whose maximum vertex is v.  FP64
 // atomics accumulate them (a vertex is the maximum vertex of a few pairs at
 // most); the caller casts.
+// In a batch (pofs non-null) pair i belongs to the field f with
+// pofs[f] <= i < pofs[f+1], and its vertex ids are relative to vofs[f].
 __global__ void k_scatter_pair_grads(const dms_pair *__restrict__ pairs, int64_t n,
                                      const double *__restrict__ gbirth,
-                                     const double *__restrict__ gdeath, double *grad) {
+                                     const double *__restrict__ gdeath, double *grad,
+                                     const int64_t *__restrict__ pofs,
+                                     const int64_t *__restrict__ vofs, int nf) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const dms_pair p = pairs[i];
-    if (gbirth && gbirth[i] != 0.0) atomicAdd(&grad[p.birth_vertex], gbirth[i]);
-    if (gdeath && !p.essential && gdeath[i] != 0.0) atomicAdd(&grad[p.death_vertex], gdeath[i]);
+    int64_t base = 0;
+    if (pofs) {
+        int lo = 0, hi = nf - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pofs[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        base = vofs[lo];
+    }
+    if (gbirth && gbirth[i] != 0.0) atomicAdd(&grad[base + p.birth_vertex], gbirth[i]);
+    if (gdeath && !p.essential && gdeath[i] != 0.0)
+        atomicAdd(&grad[base + p.death_vertex], gdeath[i]);
 }
 
 // ------------------------------------------------------------- host side
@@ -2410,6 +2529,7 @@ struct Ctx {
     Pipeline &P;
     cudaStream_t s;
     GridParams g;
+    Geo<true> bgeo{};                        // a batch: per-field grids
     DevStatus *st;
     DevStatus *hst;
     cudaEvent_t *ev;    // stage boundaries
@@ -2417,6 +2537,14 @@ struct Ctx {
     int64_t launches = 0;
 };
 #define KEV(i) cudaEventRecord(c.kev[i], c.s)
+
+template <bool B> Geo<B> geo_of(const Ctx &c);
+template <> Geo<false> geo_of<false>(const Ctx &c) {
+    Geo<false> g;
+    g.g0 = c.g;
+    return g;
+}
+template <> Geo<true> geo_of<true>(const Ctx &c) { return c.bgeo; }
 
 uint32_t g_tables_ready = 0;   // one bit per device id (< 32)
 
@@ -2750,7 +2878,7 @@ dms_status lazy_scratch(Ctx &c, LazyScratch &s, int hcap, int hashcap, int64_t n
     return DMS_OK;
 }
 
-template <typename T>
+template <typename T, bool B>
 dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const uint8_t *is_row) {
     Pipeline &P = c.P;
     DMS_ALLOC(P.d1_owner, 4 * n1 + 4);
@@ -2779,8 +2907,8 @@ dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const
     int32_t launch = 0;
 
     auto args = [&](LazyScratch &s) {
-        LzArgs<T> a;
-        a.values = values; a.g = c.g; a.flags = P.flags.as<uint8_t>();
+        LzArgs<T, B> a;
+        a.values = values; a.geo = geo_of<B>(c); a.flags = P.flags.as<uint8_t>();
         a.grad = P.grad.as<GradRec>(); a.vrank = P.vrank.as<int32_t>();
         a.recs = P.recs.as<CritRec>(); a.base1 = P.base[1].as<int32_t>(); a.is_row = is_row;
         a.v2 = P.c_vert[2].as<int32_t>(); a.l2 = P.c_loc[2].as<uint8_t>();
@@ -2795,7 +2923,7 @@ dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const
         if (ntodo == 0) return cudaSuccess;
         const int64_t nt = std::min<int64_t>(s.nt, (ntodo + 31) / 32 * 32);
         const int threads = nt % 128 == 0 ? 128 : 32;
-        k_lz_advance<T><<<(unsigned)(nt / threads), threads, 0, c.s>>>(
+        k_lz_advance<T, B><<<(unsigned)(nt / threads), threads, 0, c.s>>>(
             args(s), todo, ntodo, P.d1_astamp.as<int32_t>(), launch++, pool, pool_cap,
             P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), retry, c.st);
         c.launches++;
@@ -2837,7 +2965,7 @@ dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const
             LazyScratch &sc = (P.lz_big.buf.p && P.lz_big.nt % 8 == 0 && want <= 32 * P.lz_big.nt)
                                   ? P.lz_big : P.lz_small;
             const int64_t th = std::min<int64_t>(want, 32 * sc.nt);
-            k_lz_add<T><<<(unsigned)((th + 255) / 256), 256, 0, c.s>>>(
+            k_lz_add<T, B><<<(unsigned)((th + 255) / 256), 256, 0, c.s>>>(
                 args(sc), P.d1_act.as<int32_t>(), nactive, P.d1_re.as<int32_t>(),
                 P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), pool, P.d1_owner.as<int32_t>(),
                 P.d1_stamp.as<int32_t>(), (int32_t)stamp, P.d1_next.as<int32_t>(), pool_cap, c.st);
@@ -2955,24 +3083,95 @@ dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const
     return DMS_ERR_ITER_LIMIT;
 }
 
-template <typename T> dms_status run(Ctx &c, const T *values) {
+// Batch output: the pairs of dimension d (all fields, in the order of the
+// single-grid output) regrouped field by field with a stable LSD radix sort
+// on the field index, so that each field's pairs keep their order; the
+// per-field ranges go to P.batch_off[d].
+dms_status group_by_field(Ctx &c, int d, int64_t rows) {
+    Pipeline &P = c.P;
+    const int nf = (int)P.nf;
+    P.batch_off[d].assign(nf + 1, 0);
+    if (rows == 0) {
+        DMS_ALLOC(P.batch_pofs[d], 8 * (nf + 1));
+        DMS_CUDA(cudaMemsetAsync(P.batch_pofs[d].p, 0, 8 * (nf + 1), c.s));
+        return DMS_OK;
+    }
+    for (int k = 0; k < 2; k++) {
+        DMS_ALLOC(P.bt_k[k], 4 * rows + 4);
+        DMS_ALLOC(P.bt_v[k], 4 * rows + 4);
+    }
+    const int rtiles = (int)((rows + kRsTile - 1) / kRsTile);
+    DMS_ALLOC(P.bt_h[0], 4 * (size_t)256 * rtiles);
+    DMS_ALLOC(P.bt_h[1], 4 * (size_t)256 * rtiles);
+    DMS_ALLOC(P.bt_cnt, 4 * (nf + 1));
+    DMS_ALLOC(P.out_tmp, sizeof(dms_pair) * (rows + 1));
+    DMS_CUDA(cudaMemcpyAsync(P.bt_k[0].p, P.out_field[d].p, 4 * rows, cudaMemcpyDeviceToDevice,
+                             c.s));
+    DMS_LAUNCH(rows, 256, k_iota32, P.bt_v[0].as<int32_t>(), rows);
+    uint32_t *kin = P.bt_k[0].as<uint32_t>(), *kout = P.bt_k[1].as<uint32_t>();
+    int32_t *vin = P.bt_v[0].as<int32_t>(), *vout = P.bt_v[1].as<int32_t>();
+    for (int shift = 0; shift < 16 && (shift == 0 || nf > (1 << shift)); shift += 8) {
+        k_rs_hist<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(kin, rows, shift,
+                                                           P.bt_h[0].as<int32_t>(), rtiles);
+        c.launches++;
+        DMS_TRY(scan(c, P.bt_h[0].as<int32_t>(), P.bt_h[1].as<int32_t>(), (int64_t)256 * rtiles,
+                     &c.st->total[1]));
+        k_rs_scatter<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(kin, vin, kout, vout, rows, shift,
+                                                              P.bt_h[1].as<int32_t>(), rtiles);
+        c.launches++;
+        DMS_CUDA(cudaGetLastError());
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    DMS_LAUNCH(rows, 256, k_gather_pairs, P.out_pairs[d].as<dms_pair>(), vin, rows,
+               P.out_tmp.as<dms_pair>());
+    std::swap(P.out_pairs[d], P.out_tmp);
+    DMS_CUDA(cudaMemsetAsync(P.bt_cnt.p, 0, 4 * (nf + 1), c.s));
+    DMS_LAUNCH(rows, 256, k_field_count, P.out_field[d].as<int32_t>(), rows,
+               P.bt_cnt.as<int32_t>());
+    std::vector<int32_t> cnt(nf);
+    DMS_CUDA(cudaMemcpyAsync(cnt.data(), P.bt_cnt.p, 4 * nf, cudaMemcpyDeviceToHost, c.s));
+    DMS_CUDA(cudaStreamSynchronize(c.s));
+    for (int f = 0; f < nf; f++) P.batch_off[d][f + 1] = P.batch_off[d][f] + cnt[f];
+    DMS_ALLOC(P.batch_pofs[d], 8 * (nf + 1));
+    DMS_CUDA(cudaMemcpyAsync(P.batch_pofs[d].p, P.batch_off[d].data(), 8 * (nf + 1),
+                             cudaMemcpyHostToDevice, c.s));
+    DMS_CUDA(cudaStreamSynchronize(c.s));
+    return DMS_OK;
+}
+
+template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     using K = typename Key<T>::K;
     Pipeline &P = c.P;
+    const Geo<B> geo = geo_of<B>(c);
     cudaEvent_t *ev = c.ev;
     const int64_t n = P.n;
     const int64_t max_steps = P.max_iters > 0 ? P.max_iters : n + 1;
     DMS_CUDA(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s));
 
     // ---- gradient: classification, compaction, sort, ProcessLowerStars
-    const ClsTiling ct = cls_tiling<T>(c.g, values);
+    ClsTiling ct;
+    if constexpr (B) {
+        ct.tile = kClsTile;
+        ct.ntiles = (n + kClsTile - 1) / kClsTile;
+    } else {
+        ct = cls_tiling<T>(c.g, values);
+    }
     const int64_t ntiles = ct.ntiles;
     DMS_ALLOC(P.tile_cnt, 4 * ntiles + 4);
     DMS_ALLOC(P.tile_off, 4 * ntiles + 4);
     for (int i = 0; i < 24; i++) KEV(i);   // families that do not run read 0 ms
     KEV(0);
-    k_classify2<T><<<(unsigned)ntiles, kClsThreads, 0, c.s>>>(
-        values, c.g, ct.rows_per_block, ct.runs_per_row, ct.aligned, P.flags.as<uint8_t>(),
-        P.tile_cnt.as<int32_t>(), c.st);
+    if constexpr (B) {
+        DMS_CUDA(cudaMemsetAsync(P.fmax_field.p, 0, 8 * P.nf, c.s));
+        k_classify_batch<T><<<(unsigned)ntiles, kClsThreads, 0, c.s>>>(
+            values, geo, n, P.flags.as<uint8_t>(), P.tile_cnt.as<int32_t>(),
+            P.fmax_field.as<unsigned long long>(), c.st);
+    } else {
+        k_classify2<T><<<(unsigned)ntiles, kClsThreads, 0, c.s>>>(
+            values, c.g, ct.rows_per_block, ct.runs_per_row, ct.aligned, P.flags.as<uint8_t>(),
+            P.tile_cnt.as<int32_t>(), c.st);
+    }
     c.launches++;
     DMS_CUDA(cudaGetLastError());
     KEV(1);
@@ -3002,10 +3201,10 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
         // most vertices), otherwise on the critical ones, the rest on demand
         KEV(6);
         if (nc * 4 > n || n <= kDenseGradientBelow)
-            DMS_LAUNCH(n, 128, k_pls<T>, values, c.g, (const int32_t *)nullptr, n,
+            DMS_LAUNCH(n, 128, (k_pls<T, B>), values, geo, (const int32_t *)nullptr, n,
                        P.flags.as<uint8_t>(), P.grad.as<GradRec>());
         else
-            DMS_LAUNCH(nc, 128, k_pls<T>, values, c.g, P.vc.as<int32_t>(), nc,
+            DMS_LAUNCH(nc, 128, (k_pls<T, B>), values, geo, P.vc.as<int32_t>(), nc,
                        P.flags.as<uint8_t>(), P.grad.as<GradRec>());
         KEV(7);
         // stable LSD radix sort of the critical vertices (in id order) by value
@@ -3071,7 +3270,7 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
 
     // ---- D0: arcs between minima, elder rule in increasing order
     KEV(10);
-    DMS_LAUNCH(n1, 256, k_d0_arcs, c.g, P.flags.as<uint8_t>(), P.vrank.as<int32_t>(),
+    DMS_LAUNCH(n1, 256, k_d0_arcs<B>, geo, P.flags.as<uint8_t>(), P.vrank.as<int32_t>(),
                P.c_vert[1].as<int32_t>(), P.c_loc[1].as<uint8_t>(), n1, P.arc_a.as<int32_t>(),
                P.arc_b.as<int32_t>(), young0, max_steps, c.st);
     KEV(11);
@@ -3083,7 +3282,7 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
     // ---- D2: arcs between maxima (node n3 = the virtual maximum), decreasing
     const int32_t vmax = (int32_t)n3;
     KEV(14);
-    DMS_LAUNCH(n2, 128, k_d2_arcs<T>, values, c.g, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
+    DMS_LAUNCH(n2, 128, (k_d2_arcs<T, B>), values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
                P.vrank.as<int32_t>(),
                P.recs.as<CritRec>(), P.base[3].as<int32_t>(), P.c_vert[2].as<int32_t>(),
                P.c_loc[2].as<uint8_t>(), n2, vmax, P.arc_a.as<int32_t>(), P.arc_b.as<int32_t>(),
@@ -3124,7 +3323,7 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
     const int mode = P.d1_mode != 0 ? P.d1_mode : (ncols * kLazyBelowDensity < n ? 3 : 1);
     P.d1_mode_used = mode;
     if (ncols > 0 && mode == 3) {
-        DMS_TRY(reduce_lazy<T>(c, values, ncols, n1, is_row));
+        DMS_TRY((reduce_lazy<T, B>(c, values, ncols, n1, is_row)));
     } else if (ncols > 0) {
         int64_t pool_cap = std::max<int64_t>(1 << 24, 128 * ncols + 1024);
         DMS_ALLOC(P.d1_pool, 4 * pool_cap);
@@ -3144,8 +3343,8 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
         DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nthreads * sizeof(HashEnt), c.s));
         KEV(18);
         auto dbg_p1 = std::chrono::steady_clock::now();
-        k_d1_trace<T><<<(unsigned)(nthreads / 128), 128, 0, c.s>>>(
-            values, c.g, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
+        k_d1_trace<T, B><<<(unsigned)(nthreads / 128), 128, 0, c.s>>>(
+            values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
             P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
             P.d1_colmap.as<int32_t>(), nullptr, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,
             P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
@@ -3183,8 +3382,8 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
             DMS_ALLOC(P.d1_todo, 4 * todo.size());
             DMS_CUDA(cudaMemcpyAsync(P.d1_todo.p, todo.data(), 4 * todo.size(),
                                      cudaMemcpyHostToDevice, c.s));
-            k_d1_trace<T><<<(unsigned)(nt / 32), 32, 0, c.s>>>(
-                values, c.g, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
+            k_d1_trace<T, B><<<(unsigned)(nt / 32), 32, 0, c.s>>>(
+                values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
                 P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(),
                 P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), P.d1_todo.as<int32_t>(),
                 (int64_t)todo.size(), heap, hash, rows, hcap, hashcap, rcap, gen,
@@ -3248,12 +3447,24 @@ template <typename T> dms_status run(Ctx &c, const T *values) {
         int64_t rows = cntp[2 * d] + cntp[2 * d + 1];
         DMS_ALLOC(P.out_pairs[d], sizeof(dms_pair) * (rows + 1));
     }
+    if constexpr (B) {
+        for (int d = 0; d < 3; d++) {
+            const int64_t rows = cntp[2 * d] + cntp[2 * d + 1];
+            DMS_ALLOC(P.out_field[d], 4 * (rows + 1));
+        }
+    }
     for (int q = 0; q < 6; q++) {
         int d = part_dim[q];
         int64_t off = (q & 1) ? cntp[q - 1] : 0;
-        DMS_LAUNCH(part_n[q], 128, k_write<T>, q, a, values, c.g, part_n[q], fl + foff[q],
+        DMS_LAUNCH(part_n[q], 128, (k_write<T, B>), q, a, values, geo, part_n[q], fl + foff[q],
                    ps + foff[q], off, P.vrank.as<int32_t>(), c.hst->maxkey,
+                   P.fmax_field.as<unsigned long long>(), P.out_field[d].as<int32_t>(),
                    P.out_pairs[d].as<dms_pair>());
+    }
+    if constexpr (B) {
+        // group each dimension's pairs by field, keeping their order inside a field
+        for (int d = 0; d < 3; d++)
+            DMS_TRY(group_by_field(c, d, cntp[2 * d] + cntp[2 * d + 1]));
     }
     P.n_pairs[0] = cntp[0]; P.n_pairs[1] = cntp[2]; P.n_pairs[2] = cntp[4];
     P.n_ess[0] = cntp[1]; P.n_ess[1] = cntp[3]; P.n_ess[2] = cntp[5]; P.n_ess[3] = cntp[6];
@@ -3361,6 +3572,74 @@ dms_status Pipeline::init(int64_t nx_, int64_t ny_, int64_t nz_, dms_dtype dt,
     if (o && o->max_iters < 0) return DMS_ERR_INVALID_ARG;
     if (o && (o->d1_mode < 0 || o->d1_mode > 3)) return DMS_ERR_INVALID_ARG;
     nx = nx_; ny = ny_; nz = nz_; n = nx * ny * nz; dtype = dt;
+    return init_common(o);
+}
+
+// The grid of one field of a batch (or of the single grid) at offset `off`.
+static GridParams grid_params(int64_t nx, int64_t ny, int64_t nz, int64_t off) {
+    GridParams g;
+    g.nx = (int32_t)nx; g.ny = (int32_t)ny; g.nz = (int32_t)nz; g.n = nx * ny * nz; g.off = off;
+    for (int l = 0; l < kLinks; l++) {
+        const int o = l % 7 + 1, sg = l < 7 ? 1 : -1;
+        g.dlin[l] = sg * ((o & 1) + (int32_t)nx * (((o >> 1) & 1) + (int32_t)ny * ((o >> 2) & 1)));
+    }
+    return g;
+}
+
+dms_status Pipeline::init_batch(int64_t nf_, const int64_t *shp, dms_dtype dt,
+                                const dms_options *o) {
+    if (dt != DMS_U16 && dt != DMS_F32 && dt != DMS_F64) return DMS_ERR_INVALID_ARG;
+    if (o && (o->virtual_max != 1 || o->max_iters < 0 || o->d1_mode < 0 || o->d1_mode > 3))
+        return DMS_ERR_INVALID_ARG;
+    batch = true;
+    dtype = dt;
+    dms_status s = init_common(o);
+    if (s != DMS_OK) return s;
+    return set_batch(nf_, shp);
+}
+
+// The layout of a batch: per-field grids and offsets, the field of every id.
+// Device buffers only grow, so a handle can be re-targeted to other batches.
+dms_status Pipeline::set_batch(int64_t nf_, const int64_t *shp) {
+    if (!batch) return DMS_ERR_INVALID_ARG;
+    if (nf_ < 1 || nf_ > 65535 || !shp) return DMS_ERR_INVALID_ARG;
+    std::vector<int64_t> off(nf_ + 1, 0);
+    std::vector<GridParams> gp(nf_);
+    for (int64_t f = 0; f < nf_; f++) {
+        const int64_t a = shp[3 * f], b = shp[3 * f + 1], c = shp[3 * f + 2];
+        if (a < 1 || b < 1 || c < 1 || a > (1 << 30) || b > (1 << 30) || c > (1 << 30) ||
+            a * b >= ((int64_t)1 << 31) || a * b * c >= ((int64_t)1 << 31))
+            return DMS_ERR_INVALID_ARG;
+        gp[f] = grid_params(a, b, c, off[f]);
+        off[f + 1] = off[f] + a * b * c;
+        if (off[f + 1] >= ((int64_t)1 << 31)) return DMS_ERR_INVALID_ARG;
+    }
+    const int64_t n2 = off[nf_];
+    const int64_t ntiles = (n2 + kClsTile - 1) / kClsTile;
+    if (!flags.ensure(n2) || !vrank.ensure(4 * n2) || !grad.ensure(sizeof(GradRec) * n2) ||
+        !tile_cnt.ensure(4 * ntiles) || !tile_off.ensure(4 * ntiles) ||
+        !fields_dev.ensure(sizeof(GridParams) * nf_) || !field_of.ensure(2 * n2 + 2) ||
+        !field_off_dev.ensure(8 * (nf_ + 1)) || !fmax_field.ensure(8 * nf_))
+        return DMS_ERR_OOM;
+    has_result = false;
+    nf = nf_;
+    shapes.assign(shp, shp + 3 * nf_);
+    field_off = off;
+    n = n2;
+    nx = n; ny = 1; nz = 1;   // the id space (the geometry comes from the fields)
+    if (cudaMemcpy(fields_dev.p, gp.data(), sizeof(GridParams) * nf_, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(field_off_dev.p, field_off.data(), 8 * (nf_ + 1), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return DMS_ERR_CUDA;
+    k_field_of<<<blocks_for(n, 256), 256>>>(field_off_dev.as<int64_t>(), (int)nf_, n,
+                                            field_of.as<uint16_t>());
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return DMS_ERR_CUDA;
+    return DMS_OK;
+}
+
+dms_status Pipeline::init_common(const dms_options *o) {
     max_iters = o ? o->max_iters : 0;
     d1_mode = o ? o->d1_mode : 0;
     if (cudaGetDevice(&device) != cudaSuccess) return DMS_ERR_CUDA;
@@ -3382,6 +3661,7 @@ dms_status Pipeline::init(int64_t nx_, int64_t ny_, int64_t nz_, dms_dtype dt,
 }
 
 dms_status Pipeline::reshape(int64_t nx_, int64_t ny_, int64_t nz_) {
+    if (batch) return DMS_ERR_INVALID_ARG;
     if (nx_ < 1 || ny_ < 1 || nz_ < 1 || nx_ > (1 << 30) || ny_ > (1 << 30) || nz_ > (1 << 30))
         return DMS_ERR_INVALID_ARG;
     if (nx_ * ny_ >= ((int64_t)1 << 31) || nx_ * ny_ * nz_ >= ((int64_t)1 << 31))
@@ -3401,12 +3681,16 @@ void Pipeline::destroy() {
                      &dc_keys,    &dc_par,   &dc_lab,    &young,     &died,       &rowcol,
                      &flag_a,     &flag_b,   &d1_colmap, &d1_start,  &d1_len,     &d1_owner,
                      &d1_ovf,     &d1_pool,  &d1_scratch, &d1_todo,  &scan_tmp,   &dstat,
-                     &d1_astamp, &lz_small.buf, &lz_big.buf, &d1_rowcol};
+                     &d1_astamp, &lz_small.buf, &lz_big.buf, &d1_rowcol,
+                     &fields_dev, &field_of, &field_off_dev, &fmax_field, &bt_k[0], &bt_k[1],
+                     &bt_v[0], &bt_v[1], &bt_h[0], &bt_h[1], &bt_cnt, &out_tmp};
     for (DevBuf *b : all) b->release();
     for (int d = 0; d < 4; d++) {
         cnt[d].release(); base[d].release(); c_vert[d].release(); c_loc[d].release();
     }
-    for (int d = 0; d < 3; d++) out_pairs[d].release();
+    for (int d = 0; d < 3; d++) {
+        out_pairs[d].release(); out_field[d].release(); batch_pofs[d].release();
+    }
     if (hstat) cudaFreeHost(hstat);
     hstat = nullptr;
     for (int i = 0; i < 24; i++) if (kev[i]) cudaEventDestroy((cudaEvent_t)kev[i]);
@@ -3427,10 +3711,10 @@ dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
     c.st = dstat.as<DevStatus>();
     c.hst = (DevStatus *)hstat;
     c.ev = ev;
-    c.g.nx = (int32_t)nx; c.g.ny = (int32_t)ny; c.g.nz = (int32_t)nz; c.g.n = n;
-    for (int l = 0; l < kLinks; l++) {
-        int o = l % 7 + 1, sg = l < 7 ? 1 : -1;
-        c.g.dlin[l] = sg * ((o & 1) + (int32_t)nx * (((o >> 1) & 1) + (int32_t)ny * ((o >> 2) & 1)));
+    c.g = grid_params(nx, ny, nz, 0);
+    if (batch) {
+        c.bgeo.fields = fields_dev.as<GridParams>();
+        c.bgeo.field_of = field_of.as<uint16_t>();
     }
     const size_t esz = dtype == DMS_U16 ? 2 : dtype == DMS_F32 ? 4 : 8;
     dms_status s = DMS_OK;
@@ -3445,9 +3729,15 @@ dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
     }
     cudaEventRecord(ev[1], c.s);
     if (s == DMS_OK) {
-        if (dtype == DMS_U16) s = run<uint16_t>(c, (const uint16_t *)dv);
-        else if (dtype == DMS_F32) s = run<float>(c, (const float *)dv);
-        else s = run<double>(c, (const double *)dv);
+        if (batch) {
+            if (dtype == DMS_U16) s = run<uint16_t, true>(c, (const uint16_t *)dv);
+            else if (dtype == DMS_F32) s = run<float, true>(c, (const float *)dv);
+            else s = run<double, true>(c, (const double *)dv);
+        } else {
+            if (dtype == DMS_U16) s = run<uint16_t, false>(c, (const uint16_t *)dv);
+            else if (dtype == DMS_F32) s = run<float, false>(c, (const float *)dv);
+            else s = run<double, false>(c, (const double *)dv);
+        }
     }
     launches = c.launches;
     if (s == DMS_OK) {
@@ -3478,8 +3768,13 @@ dms_status Pipeline::backward(int dim, const double *gbirth, const double *gdeat
     if (dim < 0 || dim > 2 || !grad) return DMS_ERR_INVALID_ARG;
     const int64_t total = n_pairs[dim] + n_ess[dim];
     if (total == 0) return DMS_OK;
+    const int64_t *pofs = nullptr, *vofs = nullptr;
+    if (batch) {   // per-field pair ranges of this dimension and field offsets
+        pofs = batch_pofs[dim].as<int64_t>();
+        vofs = field_off_dev.as<int64_t>();
+    }
     k_scatter_pair_grads<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
-        out_pairs[dim].as<dms_pair>(), total, gbirth, gdeath, grad);
+        out_pairs[dim].as<dms_pair>(), total, gbirth, gdeath, grad, pofs, vofs, (int)nf);
     return cudaGetLastError() == cudaSuccess ? DMS_OK : DMS_ERR_CUDA;
 }
 
@@ -3519,12 +3814,7 @@ extern "C" dms_status dms_classify_static(const void *values, dms_dtype dtype, i
     StaticScratch *scr = nullptr;
     dms_status st = static_setup(device, &scr);
     if (st != DMS_OK) return st;
-    GridParams g;
-    g.nx = (int32_t)nx; g.ny = (int32_t)ny; g.nz = (int32_t)nz; g.n = nx * ny * nz;
-    for (int l = 0; l < kLinks; l++) {
-        int o = l % 7 + 1, sg = l < 7 ? 1 : -1;
-        g.dlin[l] = sg * ((o & 1) + (int32_t)nx * (((o >> 1) & 1) + (int32_t)ny * ((o >> 2) & 1)));
-    }
+    const GridParams g = grid_params(nx, ny, nz, 0);
     *n_critical = 0;
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == DMS_U16)

@@ -56,6 +56,15 @@ struct Pipeline {
     DevBuf d1_astamp;                          // lazy D1: last advance per column
     LazyScratch lz_small, lz_big;              // lazy D1: advance scratch
     DevBuf out_pairs[3];
+    // a batch: nf fields laid out one after another (field f at ids
+    // field_off[f] ..), computed in one pass
+    bool batch = false;
+    int64_t nf = 1;
+    std::vector<int64_t> shapes;      // nx, ny, nz per field
+    std::vector<int64_t> field_off;   // nf + 1 offsets
+    DevBuf fields_dev, field_of, field_off_dev, fmax_field;
+    DevBuf out_field[3], bt_k[2], bt_v[2], bt_h[2], bt_cnt, out_tmp, batch_pofs[3];
+    std::vector<int64_t> batch_off[3];   // per dimension: nf + 1 pair offsets
     DevBuf scan_tmp;
     DevBuf dstat;           // device status words
     void *hstat = nullptr;  // pinned host mirror
@@ -72,6 +81,9 @@ struct Pipeline {
     bool has_result = false;
 
     dms_status init(int64_t nx, int64_t ny, int64_t nz, dms_dtype dt, const dms_options *o);
+    dms_status init_batch(int64_t nf, const int64_t *shapes, dms_dtype dt, const dms_options *o);
+    dms_status init_common(const dms_options *o);
+    dms_status set_batch(int64_t nf, const int64_t *shapes);
     dms_status compute(const void *values, int on_host, void *stream);
     dms_status reshape(int64_t nx, int64_t ny, int64_t nz);
     dms_status fetch(int dim, dms_pair *out, int64_t cap, int64_t *written, int out_is_device);

@@ -6,9 +6,12 @@ while others are on the GPU starts right away in a free slot, so the work of
 several requests overlaps on the device.  Each slot is a host thread that
 owns a CUDA stream and one reusable ``dms_grid`` per dtype (reshaped per
 request, so its device buffers are kept across requests); the C ABI calls
-release the GIL, so slots drive the GPU concurrently.  Each result is the
-same as the request's diagram computed alone (the pipeline is deterministic
-and handles share no state).
+release the GIL, so slots drive the GPU concurrently.  With max_batch > 1 a
+slot takes every waiting request it can (up to max_batch, within the budget)
+and runs them as one batch -- one pass of the pipeline over the disjoint union
+of their grids -- on a reusable batch handle.  Each result is the same as the
+request's diagram computed alone (the pipeline is deterministic, handles
+share no state, and a batch's per-field pairs equal the single-grid ones).
 """
 from __future__ import annotations
 
@@ -19,7 +22,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Grid
+from . import Batch, Grid
 
 
 def request_bytes(n_vertices: int, itemsize: int) -> int:
@@ -42,12 +45,16 @@ class Request:
 
 
 class DiagramServer:
-    """``slots`` concurrent requests at most, within ``mem_budget`` bytes."""
+    """``slots`` concurrent passes at most, within ``mem_budget`` bytes.  With
+    ``max_batch`` > 1 a free slot takes up to that many waiting requests (in
+    arrival order, one dtype, within the budget) and computes them as one
+    batch (``dms_batch_create``): one pass of the pipeline for all of them."""
 
-    def __init__(self, slots: int = 4, mem_budget: int = 16 << 30):
+    def __init__(self, slots: int = 4, mem_budget: int = 16 << 30, max_batch: int = 1):
         import torch
         self.slots = slots
         self.mem_budget = mem_budget
+        self.max_batch = max(1, int(max_batch))
         self._pending = []                 # FIFO of admitted-later requests
         self._cv = threading.Condition()
         self._in_flight_bytes = 0
@@ -76,19 +83,28 @@ class DiagramServer:
             t.join()
 
     def _take(self):
-        """The oldest pending request that fits the free budget (FIFO order;
-        a large head request waits until enough memory is free)."""
+        """The oldest pending requests that fit the free budget: up to
+        max_batch of them, in arrival order and of the head's dtype (a large
+        head request waits until enough memory is free)."""
         with self._cv:
             while True:
                 if self._stop and not self._pending:
                     return None
-                if self._pending:
-                    req = self._pending[0]
-                    need = request_bytes(req.values.size, req.values.dtype.itemsize)
-                    if self._in_flight_bytes + need <= self.mem_budget:
-                        self._pending.pop(0)
-                        self._in_flight_bytes += need
-                        return req, need
+                take, need = [], 0
+                for req in self._pending:
+                    if take and req.values.dtype != take[0].values.dtype:
+                        break
+                    r = request_bytes(req.values.size, req.values.dtype.itemsize)
+                    if self._in_flight_bytes + need + r > self.mem_budget:
+                        break
+                    take.append(req)
+                    need += r
+                    if len(take) == self.max_batch:
+                        break
+                if take:
+                    del self._pending[:len(take)]
+                    self._in_flight_bytes += need
+                    return take, need
                 self._cv.wait(0.05)
 
     def _release(self, need):
@@ -99,38 +115,53 @@ class DiagramServer:
     def _worker(self, k: int):
         torch = self._torch
         stream = torch.cuda.Stream()
-        grids = {}
+        grids, batches = {}, {}
         while True:
             got = self._take()
             if got is None:
                 break
-            req, need = got
-            req.admitted = time.perf_counter()
+            reqs, need = got
+            t = time.perf_counter()
+            for r in reqs:
+                r.admitted = t
             try:
-                v = req.values
-                nz, ny, nx = v.shape
-                g = grids.get(v.dtype)
-                if g is None:
-                    g = grids[v.dtype] = Grid((nx, ny, nz), v.dtype)
-                elif g.shape_xyz != (nx, ny, nz):
-                    g.reshape((nx, ny, nz))
+                dt = reqs[0].values.dtype
+                shapes = [(r.values.shape[2], r.values.shape[1], r.values.shape[0]) for r in reqs]
                 with torch.cuda.stream(stream):
-                    g.compute(v, stream=stream.cuda_stream)
-                    req.result = {d: g.fetch(d) for d in range(3)}
+                    if len(reqs) == 1:
+                        g = grids.get(dt)
+                        if g is None:
+                            g = grids[dt] = Grid(shapes[0], dt)
+                        elif g.shape_xyz != shapes[0]:
+                            g.reshape(shapes[0])
+                        g.compute(reqs[0].values, stream=stream.cuda_stream)
+                        reqs[0].result = {d: g.fetch(d) for d in range(3)}
+                    else:
+                        b = batches.get(dt)
+                        if b is None:
+                            b = batches[dt] = Batch(shapes, dt)
+                        else:
+                            b.reshape(shapes)
+                        b.compute([r.values for r in reqs], stream=stream.cuda_stream)
+                        for r, res in zip(reqs, b.results()):
+                            r.result = res
             except Exception as e:   # reported to the caller
-                req.error = e
-            req.finished = time.perf_counter()
+                for r in reqs:
+                    r.error = e
+            t = time.perf_counter()
             self._release(need)
-            req.done.set()
-        for g in grids.values():
+            for r in reqs:
+                r.finished = t
+                r.done.set()
+        for g in list(grids.values()) + list(batches.values()):
             g.close()
 
 
-def run_stream(fields, arrivals, slots: int, mem_budget: int = 16 << 30):
+def run_stream(fields, arrivals, slots: int, mem_budget: int = 16 << 30, max_batch: int = 1):
     """Replays requests arriving at ``arrivals`` (seconds from start) through
     a server; returns the requests (with timings and results) and the wall
     time."""
-    srv = DiagramServer(slots=slots, mem_budget=mem_budget)
+    srv = DiagramServer(slots=slots, mem_budget=mem_budget, max_batch=max_batch)
     reqs = []
     t0 = time.perf_counter()
     for i, (f, a) in enumerate(zip(fields, arrivals)):

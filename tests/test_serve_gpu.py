@@ -44,6 +44,21 @@ def test_results_identical_alone_and_in_the_mix(dms):
         assert stats["p99_ms"] >= stats["p50_ms"] > 0
 
 
+def test_batched_slots_identical_alone(dms):
+    from paper_2206_13932_gb300 import serve
+    fields = sf.serving_fields(40, seed0=4100, lo=8, hi=40)
+    fields += [sf.white_noise(sh, 190 + i) for i, sh in enumerate(sf.serving_shapes(8, 191, 8, 32))]
+    want = [_alone(dms, f) for f in fields]
+    for arrivals, budget in ((np.zeros(len(fields)), 1 << 34),
+                             (sf.poisson_arrivals(len(fields), 600.0),
+                              12 * serve.request_bytes(40 ** 3, 4))):
+        reqs, _ = serve.run_stream(fields, arrivals, slots=3, mem_budget=budget, max_batch=8)
+        for r, w in zip(reqs, want):
+            assert r.error is None
+            for d in range(3):
+                assert r.result[d].tobytes() == w[d].tobytes()
+
+
 def test_reshaped_handle_matches_fresh_handles(dms):
     fields = [sf.white_noise(sh, 7) for sh in ((9, 7, 5), (20, 11, 13), (6, 6, 6), (31, 2, 17))]
     with dms.Grid((4, 4, 4), np.float32) as g:
