@@ -225,6 +225,33 @@ dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, 
                                int64_t nz, uint8_t *flags_out, int32_t *critical_out,
                                int64_t cap, int64_t *n_critical, void *stream);
 
+/* Launch shapes and capacities of a handle, for an autotuner (values[k] in
+ * this order; none changes a result, only its speed):
+ *   DMS_TUNE_PLS_BLOCK        threads per block of ProcessLowerStars
+ *                             (32..512, a multiple of 32; default 128)
+ *   DMS_TUNE_TRACE_BLOCK      threads per block of the first D1 trace pass
+ *                             (32..512, a multiple of 32; default 128)
+ *   DMS_TUNE_TRACE_PER_SM     first-pass trace threads per SM (a multiple of
+ *                             the block, <= 8192; default 2048)
+ *   DMS_TUNE_TRACE_HEAP       first-pass trace heap entries per thread
+ *                             (8..1024; default 48; larger traces retry with
+ *                             16x more)
+ *   DMS_TUNE_RED_BLOCK_BELOW  active columns below which a whole block
+ *                             performs a column's additions (>= 0; 8192)
+ *   DMS_TUNE_LAZY_HEAP        first-pass heap entries of a lazy advance
+ *                             (8..1024; default 48)
+ *   DMS_TUNE_LAZY_DENSITY     d1_mode 0 reduces lazily when there are fewer
+ *                             2-saddle columns than vertices / this (1..4096;
+ *                             default 32)
+ * dms_set_tuning checks every value and changes nothing when one is out of
+ * range (DMS_ERR_INVALID_ARG); count must be DMS_TUNING_COUNT. */
+enum {
+    DMS_TUNE_PLS_BLOCK = 0, DMS_TUNE_TRACE_BLOCK, DMS_TUNE_TRACE_PER_SM, DMS_TUNE_TRACE_HEAP,
+    DMS_TUNE_RED_BLOCK_BELOW, DMS_TUNE_LAZY_HEAP, DMS_TUNE_LAZY_DENSITY, DMS_TUNING_COUNT
+};
+dms_status dms_set_tuning(dms_grid grid, const int32_t *values, int count);
+dms_status dms_get_tuning(dms_grid grid, int32_t *values, int count);
+
 /* Frees every device and host resource of the handle. */
 dms_status dms_grid_destroy(dms_grid grid);
 

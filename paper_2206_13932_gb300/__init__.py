@@ -80,6 +80,11 @@ def load(build_if_missing: bool = False):
             lib.dms_batch_reshape.restype = ctypes.c_int
             lib.dms_batch_offsets.argtypes = [vp, ctypes.c_int, p64]
             lib.dms_batch_offsets.restype = ctypes.c_int
+            p32 = ctypes.POINTER(ctypes.c_int32)
+            lib.dms_set_tuning.argtypes = [vp, p32, ctypes.c_int]
+            lib.dms_set_tuning.restype = ctypes.c_int
+            lib.dms_get_tuning.argtypes = [vp, p32, ctypes.c_int]
+            lib.dms_get_tuning.restype = ctypes.c_int
             lib.dms_grid_destroy.argtypes = [vp]
             lib.dms_status_string.argtypes = [ctypes.c_int]
             lib.dms_status_string.restype = ctypes.c_char_p

@@ -119,6 +119,27 @@ dms_status dms_get_kernel_ms(dms_grid grid, float ms[12]) {
     return DMS_OK;
 }
 
+dms_status dms_set_tuning(dms_grid grid, const int32_t *v, int count) {
+    if (!grid || !v || count != DMS_TUNING_COUNT) return DMS_ERR_INVALID_ARG;
+    auto block_ok = [](int32_t b) { return b >= 32 && b <= 512 && b % 32 == 0; };
+    if (!block_ok(v[DMS_TUNE_PLS_BLOCK]) || !block_ok(v[DMS_TUNE_TRACE_BLOCK])) return DMS_ERR_INVALID_ARG;
+    const int32_t per_sm = v[DMS_TUNE_TRACE_PER_SM];
+    if (per_sm < v[DMS_TUNE_TRACE_BLOCK] || per_sm > 8192 || per_sm % v[DMS_TUNE_TRACE_BLOCK])
+        return DMS_ERR_INVALID_ARG;
+    if (v[DMS_TUNE_TRACE_HEAP] < 8 || v[DMS_TUNE_TRACE_HEAP] > 1024) return DMS_ERR_INVALID_ARG;
+    if (v[DMS_TUNE_RED_BLOCK_BELOW] < 0) return DMS_ERR_INVALID_ARG;
+    if (v[DMS_TUNE_LAZY_HEAP] < 8 || v[DMS_TUNE_LAZY_HEAP] > 1024) return DMS_ERR_INVALID_ARG;
+    if (v[DMS_TUNE_LAZY_DENSITY] < 1 || v[DMS_TUNE_LAZY_DENSITY] > 4096) return DMS_ERR_INVALID_ARG;
+    for (int k = 0; k < DMS_TUNING_COUNT; k++) grid->p.tune[k] = v[k];
+    return DMS_OK;
+}
+
+dms_status dms_get_tuning(dms_grid grid, int32_t *v, int count) {
+    if (!grid || !v || count != DMS_TUNING_COUNT) return DMS_ERR_INVALID_ARG;
+    for (int k = 0; k < DMS_TUNING_COUNT; k++) v[k] = grid->p.tune[k];
+    return DMS_OK;
+}
+
 dms_status dms_grid_destroy(dms_grid grid) {
     if (!grid) return DMS_ERR_INVALID_ARG;
     grid->p.destroy();

@@ -2503,9 +2503,12 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // single-threaded lazy ProcessLowerStars).
 constexpr int64_t kDenseGradientBelow = (int64_t)1 << 25;
 
-// D1 mode 0 reduces lazily when there are fewer than one column per this
-// many vertices.
-constexpr int64_t kLazyBelowDensity = 32;
+// The smallest power of two holding `heap` entries at most 3/4 full.
+inline int hash_cap_for(int heap) {
+    int h = 16;
+    while (h * 3 < heap * 4) h *= 2;
+    return h;
+}
 
 // Tiling of the tier-1 stencil: R whole rows per block, at least 2048
 // vertices per tile.
@@ -2695,7 +2698,6 @@ int64_t d1_pool_entries(int64_t dflt) {
     return v >= 64 ? (int64_t)v : dflt;
 }
 
-constexpr int64_t kBlockModeBelow = 8192;   // active columns below which a block adds
 
 dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used) {
     Pipeline &P = c.P;
@@ -2725,7 +2727,7 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
         DMS_LAUNCH(nactive, 256, k_red_publish, P.d1_act.as<int32_t>(), nactive,
                    P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
                    P.d1_owner.as<int32_t>(), rowcol);
-        if (nactive > kBlockModeBelow) {
+        if (nactive > P.tune[DMS_TUNE_RED_BLOCK_BELOW]) {
             DMS_LAUNCH(std::min<int64_t>(64 * nactive, (int64_t)152 * 64 * 256), 256, k_red_add,
                        P.d1_act.as<int32_t>(), nactive, P.d1_re.as<int32_t>(),
                        P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
@@ -2902,7 +2904,8 @@ dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const
 
     // scratch: the first pass small (stays in L2), retries 16x larger per level
     const int64_t nt_small = std::min<int64_t>(152 * 16 * 128, (ncols + 127) / 128 * 128);
-    DMS_TRY(lazy_scratch(c, P.lz_small, 48, 64, nt_small));
+    const int heap0 = P.tune[DMS_TUNE_LAZY_HEAP];
+    DMS_TRY(lazy_scratch(c, P.lz_small, heap0, hash_cap_for(heap0), nt_small));
     int big_hash = 1024;
     int32_t launch = 0;
 
@@ -3201,10 +3204,10 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
         // most vertices), otherwise on the critical ones, the rest on demand
         KEV(6);
         if (nc * 4 > n || n <= kDenseGradientBelow)
-            DMS_LAUNCH(n, 128, (k_pls<T, B>), values, geo, (const int32_t *)nullptr, n,
+            DMS_LAUNCH(n, P.tune[DMS_TUNE_PLS_BLOCK], (k_pls<T, B>), values, geo, (const int32_t *)nullptr, n,
                        P.flags.as<uint8_t>(), P.grad.as<GradRec>());
         else
-            DMS_LAUNCH(nc, 128, (k_pls<T, B>), values, geo, P.vc.as<int32_t>(), nc,
+            DMS_LAUNCH(nc, P.tune[DMS_TUNE_PLS_BLOCK], (k_pls<T, B>), values, geo, P.vc.as<int32_t>(), nc,
                        P.flags.as<uint8_t>(), P.grad.as<GradRec>());
         KEV(7);
         // stable LSD radix sort of the critical vertices (in id order) by value
@@ -3320,7 +3323,8 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     // fields) have long descending walls that the lazy columns expand only
     // as far as their pivots; dense ones (noisy fields) have short traces and
     // long chains of additions that the traced 4-byte columns serve better
-    const int mode = P.d1_mode != 0 ? P.d1_mode : (ncols * kLazyBelowDensity < n ? 3 : 1);
+    const int mode = P.d1_mode != 0 ? P.d1_mode
+                                    : (ncols * P.tune[DMS_TUNE_LAZY_DENSITY] < n ? 3 : 1);
     P.d1_mode_used = mode;
     if (ncols > 0 && mode == 3) {
         DMS_TRY((reduce_lazy<T, B>(c, values, ncols, n1, is_row)));
@@ -3331,9 +3335,10 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
         DMS_CUDA(cudaMemsetAsync(ovf, 0, ncols, c.s));
         DMS_CUDA(cudaMemsetAsync(&c.st->pool_top, 0, sizeof(unsigned long long), c.s));
         // first pass: small per-thread scratch that stays in L2
-        int hcap = 48, hashcap = 64, rcap = 48;
-        int64_t nthreads = 152 * 16 * 128;
-        if (ncols < nthreads) nthreads = (ncols + 127) / 128 * 128;
+        int hcap = P.tune[DMS_TUNE_TRACE_HEAP], hashcap = hash_cap_for(hcap), rcap = hcap;
+        const int tb = P.tune[DMS_TUNE_TRACE_BLOCK];
+        int64_t nthreads = (int64_t)152 * P.tune[DMS_TUNE_TRACE_PER_SM];
+        if (ncols < nthreads) nthreads = (ncols + tb - 1) / tb * tb;
         size_t per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
                      (size_t)rcap * 8;
         DMS_ALLOC(P.d1_scratch, per * nthreads);
@@ -3343,7 +3348,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
         DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nthreads * sizeof(HashEnt), c.s));
         KEV(18);
         auto dbg_p1 = std::chrono::steady_clock::now();
-        k_d1_trace<T, B><<<(unsigned)(nthreads / 128), 128, 0, c.s>>>(
+        k_d1_trace<T, B><<<(unsigned)(nthreads / tb), tb, 0, c.s>>>(
             values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
             P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
             P.d1_colmap.as<int32_t>(), nullptr, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,

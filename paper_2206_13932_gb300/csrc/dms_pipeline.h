@@ -69,6 +69,9 @@ struct Pipeline {
     DevBuf dstat;           // device status words
     void *hstat = nullptr;  // pinned host mirror
 
+    // launch shapes and capacities (dms_set_tuning; order of DMS_TUNE_*)
+    int32_t tune[DMS_TUNING_COUNT] = {128, 128, 2048, 48, 8192, 48, 32};
+
     int64_t n_crit = 0, n_c[4] = {0, 0, 0, 0};
     int64_t n_pairs[3] = {0, 0, 0}, n_ess[4] = {0, 0, 0, 0};
     int64_t launches = 0, rounds_d0 = 0, rounds_d2 = 0, rounds_d1 = 0  /* D0/D2: halving levels */, d1_cols = 0;
