@@ -44,6 +44,7 @@ struct DevStatus {
     int changed;                   // D1: columns changed this round
     unsigned long long pool_top;   // D1 column pool bump pointer
     long long misc[4];
+    long long bx[4];               // block expansions: nodes, levels (discovery, order), columns
 };
 
 // Record of a critical vertex after ProcessLowerStars.
@@ -2114,6 +2115,365 @@ __global__ void __launch_bounds__(128)
     a.tgen[tid] = gen;
 }
 
+// ---- whole-column expansion by a block (columns with a large wall)
+//
+// A column whose advance outgrows the per-thread scratch usually sits on a
+// large descending wall, and a serial walk through it is long.  Here a block
+// expands such a column completely, in parallel, in two passes over the DAG
+// of the gradient flow restricted to the column (an edge -> the two edges its
+// expansion yields; acyclic since priorities strictly decrease):
+//   1. discovery, level by level from the column's entries: each new regular
+//      edge is expanded once, its products are inserted into a hash (one
+//      slot per edge) and their in-degrees counted;
+//   2. Kahn's order: an edge whose predecessors are all done adds its parity
+//      (mod 2) into its products; the multiplicity of a critical row is
+//      final when its in-degree is exhausted.
+// The column becomes the sorted list of its critical rows of odd
+// multiplicity: its Morse boundary, the limit of the advances.  A column
+// that does not fit the block's hash or lists is left unchanged and retried
+// by the serial advance in global memory.
+// Per block: a hash of the column's edges in three arrays (keys, states,
+// data), cleared before each column.
+struct BxData {
+    unsigned long long hi, lo;   // the edge's entry
+    int32_t p0, p1;              // product slots (-1: none)
+    int32_t spec;                // products of a regular edge: other star edge of its
+                                 // triangle | link of the higher triangle vertex << 4 |
+                                 // edge there << 8 (bit 12: invalid)
+    int32_t pad;
+};
+// state: bits 0-7 count the parity-1 contributions (mod 2 is the
+// multiplicity), bits 8-15 the in-edges not yet done
+constexpr uint32_t kBxIn = 256;
+constexpr int kBxThreads = 256;
+// block scratch sizes: hash slots (log2), frontier capacity, sink capacity,
+// blocks in flight
+struct BxLevel {
+    int hbits, fcap, scap, blocks;
+};
+constexpr BxLevel kBxLevels[2] = {{17, 65536, 16384, 152}, {21, 1 << 20, 1 << 16, 16}};
+constexpr size_t kBxSlotBytes = 8 + 4 + sizeof(BxData);
+
+struct BxCtx {
+    unsigned long long *keys;
+    uint32_t *state;
+    BxData *data;
+    uint32_t hmask;
+    int32_t *next;        // frontier being filled
+    int *nnext, fcap;
+    int32_t *sink;        // slots of critical rows
+    int *nsink, scap;
+    int *used, *fail;
+};
+
+// Inserts edge (y, m) (dropping heads of vertex->edge vectors and critical
+// edges paired in D0) or finds it; returns its slot or -1.  `initial`: an
+// entry of the column (parity 1, not counted as an in-edge); otherwise a
+// product (one more in-edge).  A new regular edge joins the next frontier
+// with its two products precomputed; a new critical row joins the sinks.
+// The vertex's flag, value and gradient record are loaded together up front.
+template <typename T>
+__device__ __noinline__ int32_t bx_insert(BxCtx &c, const StarTables &S, const GridParams &g,
+                                          const T *__restrict__ values, uint8_t *flags,
+                                          GradRec *grad, const int32_t *__restrict__ vrank,
+                                          const CritRec *__restrict__ recs,
+                                          const int32_t *__restrict__ base1,
+                                          const uint8_t *__restrict__ is_row, int64_t y, int m,
+                                          bool initial, DevStatus *st) {
+    if (m < 0 || m >= kLinks) { atomicOr(&st->err, kErrState); *c.fail = 1; return -1; }
+    const uint8_t fy = ((volatile const uint8_t *)flags)[y];
+    const T vy = values[y];
+    GradRec G;
+    {
+        const ulonglong2 *src = (const ulonglong2 *)&grad[y];
+        for (int k = 0; k < 3; k++) {
+            const ulonglong2 v = __ldcg(src + k);
+            G.w[2 * k] = v.x;
+            G.w[2 * k + 1] = v.y;
+        }
+    }
+    if ((fy & 0xF) == m) return -1;
+    bool crit = false;
+    if (fy & kFlagCritical) {
+        const int32_t i = vrank[y];
+        const CritRec rec = recs[i];
+        if (rec.crit_e >> m & 1) {
+            if (!is_row[base1[i] + local_index(S, rec, 1, m)]) return -1;
+            crit = true;
+        }
+    }
+    const unsigned long long key = lz_key(y, m);
+    uint32_t pos = hash64(key) & c.hmask;
+    int32_t slot = -1;
+    bool fresh = false;
+    for (uint32_t p = 0; p <= c.hmask; p++, pos = (pos + 1) & c.hmask) {
+        const unsigned long long prev = atomicCAS(&c.keys[pos], 0ull, key);
+        if (prev == 0ull) { slot = (int32_t)pos; fresh = true; break; }
+        if (prev == key) { slot = (int32_t)pos; break; }
+    }
+    if (slot < 0) { *c.fail = 1; return -1; }
+    if (fresh) {
+        if (atomicAdd(c.used, 1) * 4 >= (int)(c.hmask + 1) * 3) *c.fail = 1;
+        if (!(fy & kFlagGradient)) G = grad_fill(S, g, values, flags, grad, y);
+        int pair = 0, spec = 0;
+        if (!crit) {
+            pair = grad_edge_pair(G, m);
+            if (pair >= kTris) {                 // not a valid pairing: never expanded
+                atomicOr(&st->err, kErrState);
+                *c.fail = 1;
+                crit = true;
+                pair = 0;
+            } else {
+                const int ta = S.tri_v[pair][0], tb = S.tri_v[pair][1];
+                const bool aup = grad_rank(G, ta) > grad_rank(G, tb);
+                const int hi = aup ? ta : tb, lo = aup ? tb : ta;
+                const int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) +
+                                           3 * (S.dy[lo] - S.dy[hi] + 1) +
+                                           9 * (S.dz[lo] - S.dz[hi] + 1)];
+                spec = (ta == m ? tb : ta) | (hi << 4) | ((l & 15) << 8) | (l < 0 ? 1 << 12 : 0);
+            }
+        }
+        BxData &d = c.data[slot];
+        d.hi = (unsigned long long)Key<T>::of(vy);
+        d.lo = ((unsigned long long)y << 15) | ((unsigned long long)grad_edge_order(G, m) << 11) |
+               ((unsigned long long)m << 7) | ((unsigned long long)(pair & 63) << 1) |
+               (crit ? 1ull : 0ull);
+        d.p0 = -1;
+        d.p1 = -1;
+        d.spec = spec;
+        if (crit) {
+            const int k = atomicAdd(c.nsink, 1);
+            if (k < c.scap) c.sink[k] = slot; else *c.fail = 1;
+        } else {
+            const int k = atomicAdd(c.nnext, 1);
+            if (k < c.fcap) c.next[k] = slot; else *c.fail = 1;
+        }
+    }
+    atomicAdd(&c.state[slot], initial ? 1u : kBxIn);
+    return slot;
+}
+
+// descending order of (hi, lo) for a power-of-two count, by the block
+__device__ void bx_sort_desc(Ent *a, int n) {
+    for (int k = 2; k <= n; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool desc = (i & k) == 0;
+                    const Ent x = a[i], y = a[l];
+                    if (desc ? ent_gt(y, x) : ent_gt(x, y)) { a[i] = y; a[l] = x; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+template <typename T, bool B>
+__global__ void __launch_bounds__(kBxThreads)
+    k_lz_expand_block(LzArgs<T, B> a, const int32_t *__restrict__ todo, int64_t ntodo,
+                      int32_t *astamp, int32_t launch, Ent *pool, int64_t pool_cap,
+                      int64_t *col_start, int32_t *col_len, int32_t *retry, char *hash_all,
+                      int hbits, int32_t *list_all, int fcap, int32_t *sink_all, Ent *sort_all,
+                      int scap, DevStatus *st) {
+    // frontier counts rotate through three words so that a level needs one
+    // barrier: level i reads cnt[i%3], fills cnt[(i+1)%3] and clears
+    // cnt[(i+2)%3], which every thread finished reading before the last barrier
+    __shared__ int s_cnt[3];
+    __shared__ int s_take, s_nil, s_nsink, s_used, s_fail, s_nout;
+    __shared__ long long s_pos;
+    const StarTables &S = g_star;
+    const int t = threadIdx.x;
+    const size_t hn = (size_t)1 << hbits;
+    BxCtx c;
+    {
+        char *h = hash_all + (size_t)blockIdx.x * hn * kBxSlotBytes;
+        c.keys = (unsigned long long *)h;
+        c.data = (BxData *)(h + hn * 8);
+        c.state = (uint32_t *)(h + hn * (8 + sizeof(BxData)));
+    }
+    c.hmask = (uint32_t)hn - 1;
+    int32_t *F[2];
+    F[0] = list_all + (size_t)blockIdx.x * 3 * fcap;
+    F[1] = F[0] + fcap;
+    int32_t *IL = F[1] + fcap;
+    c.sink = sink_all + (size_t)blockIdx.x * scap;
+    Ent *SR = sort_all + (size_t)blockIdx.x * 2 * scap;
+    c.fcap = fcap; c.nsink = &s_nsink; c.scap = scap;
+    c.used = &s_used; c.fail = &s_fail;
+    for (int64_t q = blockIdx.x; q < ntodo; q += gridDim.x) {
+        const int32_t cj = todo[q];
+        const int la = col_len[cj];
+        const int64_t sa = col_start[cj];
+        if (la == 0) continue;
+        if (la > 0 && (pool[sa].lo & 1)) continue;
+        if (t == 0) s_take = atomicExch(&astamp[cj], launch) != launch;
+        __syncthreads();
+        if (!s_take) continue;
+        // clear the keys and states of the hash
+        {
+            uint4 *k4 = (uint4 *)c.keys;
+            for (size_t i = t; i < hn / 2; i += kBxThreads) k4[i] = make_uint4(0, 0, 0, 0);
+            uint4 *s4 = (uint4 *)c.state;
+            for (size_t i = t; i < hn / 4; i += kBxThreads) s4[i] = make_uint4(0, 0, 0, 0);
+        }
+        const int64_t x = a.v2[a.colmap[cj]];
+        const GridParams &g = a.geo.at(x);
+        if (t == 0) {
+            s_cnt[0] = 0; s_cnt[1] = 0; s_cnt[2] = 0;
+            s_nsink = 0; s_used = 0; s_fail = 0; s_nil = 0;
+        }
+        __syncthreads();
+        // the column's entries (parity 1 each), listed in IL; the regular ones
+        // form the first frontier
+        c.next = F[0];
+        c.nnext = &s_cnt[0];
+        if (la < 0) {
+            if (t == 0) {
+                const int s = a.l2[a.colmap[cj]];
+                const int ta = S.tri_v[s][0], tb = S.tri_v[s][1];
+                const GradRec Gx = grad_get(S, g, a.values, a.flags, a.grad, x);
+                const bool aup = grad_rank(Gx, ta) > grad_rank(Gx, tb);
+                const int hi = aup ? ta : tb, lo = aup ? tb : ta;
+                const int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
+                                           9 * (S.dz[lo] - S.dz[hi] + 1)];
+                IL[0] = bx_insert<T>(c, S, g, a.values, a.flags, a.grad, a.vrank, a.recs, a.base1,
+                                     a.is_row, x, ta, true, st);
+                IL[1] = bx_insert<T>(c, S, g, a.values, a.flags, a.grad, a.vrank, a.recs, a.base1,
+                                     a.is_row, x, tb, true, st);
+                IL[2] = bx_insert<T>(c, S, g, a.values, a.flags, a.grad, a.vrank, a.recs, a.base1,
+                                     a.is_row, x + g.dlin[hi], l, true, st);
+                s_nil = 3;
+            }
+        } else if (la > fcap) {
+            if (t == 0) s_fail = 1;
+        } else {
+            for (int k = t; k < la; k += kBxThreads) {
+                const Ent e = pool[sa + k];
+                IL[k] = bx_insert<T>(c, S, g, a.values, a.flags, a.grad, a.vrank, a.recs,
+                                     a.base1, a.is_row, ent_y(e), ent_m(e), true, st);
+            }
+            if (t == 0) s_nil = la;
+        }
+        __syncthreads();
+        // 1. discovery, level by level: expand each new regular edge once (a
+        //    thread per product), counting the in-edges of the products
+        int lv1 = 0;
+        for (int lv = 0;; lv++) {
+            const int ncur = s_cnt[lv % 3];
+            lv1 = lv;
+            if (ncur == 0 || s_fail) break;
+            if (t == 0) s_cnt[(lv + 2) % 3] = 0;
+            const int32_t *cur = F[lv & 1];
+            c.next = F[(lv + 1) & 1];
+            c.nnext = &s_cnt[(lv + 1) % 3];
+            for (int k = t; k < 2 * ncur; k += kBxThreads) {
+                const int32_t u = cur[k >> 1];
+                BxData &du = c.data[u];
+                const int64_t y = (int64_t)(du.lo >> 15);
+                const int spec = du.spec;
+                if (spec >> 12) { atomicOr(&st->err, kErrState); s_fail = 1; continue; }
+                if (k & 1)
+                    du.p1 = bx_insert<T>(c, S, g, a.values, a.flags, a.grad, a.vrank, a.recs,
+                                         a.base1, a.is_row, y + g.dlin[(spec >> 4) & 15],
+                                         (spec >> 8) & 15, false, st);
+                else
+                    du.p0 = bx_insert<T>(c, S, g, a.values, a.flags, a.grad, a.vrank, a.recs,
+                                         a.base1, a.is_row, y, spec & 15, false, st);
+            }
+            __syncthreads();
+        }
+        if (s_fail) {
+            if (t == 0) retry[atomicAdd((unsigned long long *)&st->misc[3], 1ull)] = cj;
+            __syncthreads();
+            continue;
+        }
+        // 2. Kahn's order from the entries without in-edges: an edge whose
+        //    in-edges are all done adds its parity into its products (a thread
+        //    per product)
+        if (t == 0) { s_cnt[0] = 0; s_cnt[1] = 0; s_cnt[2] = 0; }
+        __syncthreads();
+        const int nil = s_nil;
+        for (int k = t; k < nil; k += kBxThreads) {
+            const int32_t u = IL[k];
+            if (u >= 0 && (c.state[u] >> 8) == 0) F[0][atomicAdd(&s_cnt[0], 1)] = u;
+        }
+        __syncthreads();
+        int lv2 = 0;
+        for (int lv = 0;; lv++) {
+            const int ncur = s_cnt[lv % 3];
+            lv2 = lv;
+            if (ncur == 0 || s_fail) break;
+            if (t == 0) s_cnt[(lv + 2) % 3] = 0;
+            const int32_t *cur = F[lv & 1];
+            int32_t *nxt = F[(lv + 1) & 1];
+            int *nn = &s_cnt[(lv + 1) % 3];
+            for (int k = t; k < 2 * ncur; k += kBxThreads) {
+                const int32_t u = cur[k >> 1];
+                const BxData &du = c.data[u];
+                if (du.lo & 1) continue;                      // a critical row: a sink
+                const int32_t pr = (k & 1) ? du.p1 : du.p0;
+                if (pr < 0) continue;
+                const uint32_t par = c.state[u] & 1u;
+                const uint32_t old = atomicAdd(&c.state[pr], par - kBxIn);
+                if ((old >> 8) == 1) {
+                    const int w = atomicAdd(nn, 1);
+                    if (w < fcap) nxt[w] = pr; else s_fail = 1;
+                }
+            }
+            __syncthreads();
+        }
+        if (s_fail) {
+            if (t == 0) retry[atomicAdd((unsigned long long *)&st->misc[3], 1ull)] = cj;
+            __syncthreads();
+            continue;
+        }
+        if (t == 0) {
+            atomicAdd((unsigned long long *)&st->bx[0], (unsigned long long)s_used);
+            atomicAdd((unsigned long long *)&st->bx[1], (unsigned long long)lv1);
+            atomicAdd((unsigned long long *)&st->bx[2], (unsigned long long)lv2);
+            atomicAdd((unsigned long long *)&st->bx[3], 1ull);
+            s_nout = 0;
+        }
+        __syncthreads();
+        // the critical rows of odd multiplicity, sorted by decreasing priority
+        const int ns = s_nsink;
+        for (int k = t; k < ns; k += kBxThreads) {
+            const int32_t sk = c.sink[k];
+            if (c.state[sk] & 1u) SR[atomicAdd(&s_nout, 1)] = Ent{c.data[sk].hi, c.data[sk].lo};
+        }
+        __syncthreads();
+        const int nout = s_nout;
+        int np2 = 1;
+        while (np2 < nout) np2 <<= 1;
+        for (int k = nout + t; k < np2; k += kBxThreads) SR[k] = Ent{0, 0};
+        __syncthreads();
+        if (nout > 1) bx_sort_desc(SR, np2);
+        if (nout == 0) {
+            if (t == 0) { col_start[cj] = 0; col_len[cj] = 0; }
+            __syncthreads();
+            continue;
+        }
+        if (t == 0) {
+            const unsigned long long pos = atomicAdd(&st->pool_top, (unsigned long long)nout);
+            if ((int64_t)(pos + nout) > pool_cap) {
+                atomicOr(&st->err, kErrCap);
+                retry[atomicAdd((unsigned long long *)&st->misc[3], 1ull)] = cj;
+                s_take = -1;
+            } else {
+                s_take = 1;
+                s_pos = (long long)pos;
+                col_start[cj] = (int64_t)pos;
+                col_len[cj] = nout;
+            }
+        }
+        __syncthreads();
+        if (s_take == 1)
+            for (int k = t; k < nout; k += kBxThreads) pool[s_pos + k] = SR[k];
+        __syncthreads();
+    }
+}
+
 // Listed columns with a critical top claim it (atomic minimum of the column
 // index); a claim that displaces a later owner queues it on `recheck`.
 __global__ void k_lz_claim(const int32_t *__restrict__ active, int64_t nactive,
@@ -2906,7 +3266,7 @@ dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const
     const int64_t nt_small = std::min<int64_t>(152 * 16 * 128, (ncols + 127) / 128 * 128);
     const int heap0 = P.tune[DMS_TUNE_LAZY_HEAP];
     DMS_TRY(lazy_scratch(c, P.lz_small, heap0, hash_cap_for(heap0), nt_small));
-    int big_hash = 1024;
+    int big_hash = 1 << 22;   // the serial walks in global memory, after the block levels
     int32_t launch = 0;
 
     auto args = [&](LazyScratch &s) {
@@ -2963,10 +3323,10 @@ dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const
         if (debug) cudaEventRecord(dev[2], c.s);
         {
             // one warp per listed column, at most one per thread slot of the
-            // scratch: the larger one once it exists and has a slot per warp
+            // small scratch (a large wall fails fast here and is expanded by a
+            // block between rounds)
             const int64_t want = std::min<int64_t>(64 * nactive, (int64_t)152 * 64 * 256);
-            LazyScratch &sc = (P.lz_big.buf.p && P.lz_big.nt % 8 == 0 && want <= 32 * P.lz_big.nt)
-                                  ? P.lz_big : P.lz_small;
+            LazyScratch &sc = P.lz_small;
             const int64_t th = std::min<int64_t>(want, 32 * sc.nt);
             k_lz_add<T, B><<<(unsigned)((th + 255) / 256), 256, 0, c.s>>>(
                 args(sc), P.d1_act.as<int32_t>(), nactive, P.d1_re.as<int32_t>(),
@@ -3016,23 +3376,59 @@ dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const
             DMS_CUDA(cudaMemcpyAsync(nx + nlist, todo, 4 * nretry, cudaMemcpyDeviceToDevice,
                                      c.s));
             nlist += nretry;
+            // first expanded whole by blocks (two sizes of block scratch), then
+            // walked serially with per-thread scratch in global memory; the
+            // environment may set the first level (DMS_D1_LAZY_LEVEL = 0, 1, 2),
+            // which exercises the later ones
+            int level = 0;
+            if (const char *e = getenv("DMS_D1_LAZY_LEVEL")) level = std::min(2, std::max(0, atoi(e)));
             while (nretry > 0 && !full) {
-                if (!P.lz_big.buf.p || P.lz_big.hashcap < big_hash) {
-                    const int bh = big_hash * 3 / 4;
-                    const size_t per = (size_t)bh * sizeof(HeapEnt) +
-                                       (size_t)big_hash * sizeof(HashEnt) + 4;
-                    int64_t nt = std::max<int64_t>(
-                        32, std::min<int64_t>(ncols, ((int64_t)4 << 30) / (int64_t)per));
-                    DMS_TRY(lazy_scratch(c, P.lz_big, bh, big_hash, (nt + 31) / 32 * 32));
-                }
                 DMS_CUDA(cudaMemsetAsync(&c.st->misc[3], 0, sizeof(long long), c.s));
-                if (advance(P.lz_big, todo, nretry, retry) != cudaSuccess) return DMS_ERR_CUDA;
+                if (level < 2) {
+                    const BxLevel &L = kBxLevels[level];
+                    const size_t hash_b = (size_t)L.blocks * ((size_t)1 << L.hbits) * kBxSlotBytes;
+                    const size_t list_b = (size_t)L.blocks * 3 * L.fcap * 4;
+                    const size_t sink_b = (size_t)L.blocks * L.scap * 4;
+                    const size_t sort_b = (size_t)L.blocks * 2 * L.scap * sizeof(Ent);
+                    DevBuf &bx = P.bx_buf[level];
+                    DMS_ALLOC(bx, hash_b + list_b + sink_b + sort_b);
+                    char *base = bx.as<char>();
+                    k_lz_expand_block<T, B>
+                        <<<(unsigned)std::min<int64_t>(nretry, L.blocks), kBxThreads, 0, c.s>>>(
+                            args(P.lz_small), todo, nretry, P.d1_astamp.as<int32_t>(), launch++,
+                            pool, pool_cap, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+                            retry, base, L.hbits, (int32_t *)(base + hash_b), L.fcap,
+                            (int32_t *)(base + hash_b + list_b),
+                            (Ent *)(base + hash_b + list_b + sink_b), L.scap, c.st);
+                    c.launches++;
+                    DMS_CUDA(cudaGetLastError());
+                } else {
+                    if (!P.lz_big.buf.p || P.lz_big.hashcap < big_hash) {
+                        const int bh = big_hash * 3 / 4;
+                        const size_t per = (size_t)bh * sizeof(HeapEnt) +
+                                           (size_t)big_hash * sizeof(HashEnt) + 4;
+                        int64_t nt = std::max<int64_t>(
+                            32, std::min<int64_t>(ncols, ((int64_t)4 << 30) / (int64_t)per));
+                        DMS_TRY(lazy_scratch(c, P.lz_big, bh, big_hash, (nt + 31) / 32 * 32));
+                    }
+                    if (advance(P.lz_big, todo, nretry, retry) != cudaSuccess)
+                        return DMS_ERR_CUDA;
+                }
+                const auto t_retry = std::chrono::steady_clock::now();
                 s = sync_status(c);
+                if (debug)
+                    fprintf(stderr, "  retry %lld columns at level %d: %.3f ms (host); block "
+                            "expansions so far: %lld columns, %lld edges, %lld + %lld levels\n",
+                            (long long)nretry, level,
+                            std::chrono::duration<double, std::milli>(
+                                std::chrono::steady_clock::now() - t_retry).count(),
+                            c.hst->bx[3], c.hst->bx[0], c.hst->bx[1], c.hst->bx[2]);
                 if (s != DMS_OK && s != DMS_ERR_CAPACITY) return s;
                 full = s == DMS_ERR_CAPACITY;
                 const int64_t again = c.hst->misc[3];
                 if (again > 0 && !full) {
-                    big_hash *= 16;                     // still too large: next level
+                    if (level >= 2) big_hash *= 16;     // still too large: 16x more
+                    level++;
                     if (big_hash > (1 << 24)) return DMS_ERR_CAPACITY;
                 }
                 std::swap(todo, retry);
@@ -3688,7 +4084,8 @@ void Pipeline::destroy() {
                      &d1_ovf,     &d1_pool,  &d1_scratch, &d1_todo,  &scan_tmp,   &dstat,
                      &d1_astamp, &lz_small.buf, &lz_big.buf, &d1_rowcol,
                      &fields_dev, &field_of, &field_off_dev, &fmax_field, &bt_k[0], &bt_k[1],
-                     &bt_v[0], &bt_v[1], &bt_h[0], &bt_h[1], &bt_cnt, &out_tmp};
+                     &bt_v[0], &bt_v[1], &bt_h[0], &bt_h[1], &bt_cnt, &out_tmp, &bx_buf[0],
+                     &bx_buf[1]};
     for (DevBuf *b : all) b->release();
     for (int d = 0; d < 4; d++) {
         cnt[d].release(); base[d].release(); c_vert[d].release(); c_loc[d].release();

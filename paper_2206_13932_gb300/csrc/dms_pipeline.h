@@ -55,6 +55,7 @@ struct Pipeline {
     DevBuf d1_rowcol;                          // D1: owner of each row with its list
     DevBuf d1_astamp;                          // lazy D1: last advance per column
     LazyScratch lz_small, lz_big;              // lazy D1: advance scratch
+    DevBuf bx_buf[2];                          // lazy D1: block expansion scratch
     DevBuf out_pairs[3];
     // a batch: nf fields laid out one after another (field f at ids
     // field_off[f] ..), computed in one pass

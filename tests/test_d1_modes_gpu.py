@@ -99,3 +99,20 @@ def test_lazy_scratch_retries(dms):
     assert st["d1_trace_overflow"] > 0
     for d in range(3):
         assert got[d].tobytes() == want[d].tobytes()
+
+
+@pytest.mark.parametrize("level", ["1", "2"])
+def test_lazy_retry_levels(dms, level):
+    """The retried columns taken by the larger block scratch (level 1) or by
+    the serial walk in global memory (level 2) give the same pairs."""
+    v = sf.gaussian_mixture((64, 64, 64), 6, 31, noise=1e-4)
+    want, _ = _run(dms, v, 1)
+    os.environ["DMS_D1_LAZY_LEVEL"] = level
+    try:
+        got, st = _run(dms, v, 3)
+    finally:
+        del os.environ["DMS_D1_LAZY_LEVEL"]
+    assert st["d1_trace_overflow"] > 0
+    for d in range(3):
+        assert got[d].tobytes() == want[d].tobytes()
+
