@@ -254,7 +254,7 @@ def run_ours(args):
     src = "measured" if peaks else "fallback"
     cls_bytes = n * s_in + n + 4 * (n // 2048 + 1)      # values in, flag bytes out, tile counts
     cls_gbs = cls_bytes / (kavg["classify"] * 1e-3) / 1e9
-    roof_grad = {"bound": "hbm", "kernel": "k_classify", "achieved": cls_gbs, "peak": hbm,
+    roof_grad = {"bound": "hbm", "kernel": "k_classify2", "achieved": cls_gbs, "peak": hbm,
                  "unit": "GB/s", "frac": cls_gbs / hbm, "traffic": None,
                  "algorithmic_bytes_per_launch": cls_bytes, "peak_source": src}
     if dom == "d1_reduce":
