@@ -1264,7 +1264,7 @@ __device__ __forceinline__ void trace_expand(TraceCtx &c, const StarTables &S, c
 // to the rows (1-saddles not paired in D0), as a descending list of C1
 // indices appended to the column pool.
 template <typename T, bool B>
-__global__ void k_d1_trace(const T *__restrict__ values, Geo<B> geo, uint8_t *flags,
+__global__ void __launch_bounds__(256, 4) k_d1_trace(const T *__restrict__ values, Geo<B> geo, uint8_t *flags,
                            GradRec *grad, const int32_t *__restrict__ vrank,
                            const CritRec *__restrict__ recs, const int32_t *__restrict__ base1,
                            const uint8_t *__restrict__ is_row, const int32_t *__restrict__ v2,
