@@ -243,11 +243,17 @@ dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, 
  *   DMS_TUNE_LAZY_DENSITY     d1_mode 0 reduces lazily when there are fewer
  *                             2-saddle columns than vertices / this (1..4096;
  *                             default 32)
+ *   DMS_TUNE_RED_ASYNC        1: below DMS_TUNE_RED_BLOCK_BELOW active columns
+ *                             the traced reduction finishes in one
+ *                             asynchronous pass (compare-and-swap ownership
+ *                             and a device work queue); 0: in rounds
+ *                             (default 1)
  * dms_set_tuning checks every value and changes nothing when one is out of
  * range (DMS_ERR_INVALID_ARG); count must be DMS_TUNING_COUNT. */
 enum {
     DMS_TUNE_PLS_BLOCK = 0, DMS_TUNE_TRACE_BLOCK, DMS_TUNE_TRACE_PER_SM, DMS_TUNE_TRACE_HEAP,
-    DMS_TUNE_RED_BLOCK_BELOW, DMS_TUNE_LAZY_HEAP, DMS_TUNE_LAZY_DENSITY, DMS_TUNING_COUNT
+    DMS_TUNE_RED_BLOCK_BELOW, DMS_TUNE_LAZY_HEAP, DMS_TUNE_LAZY_DENSITY, DMS_TUNE_RED_ASYNC,
+    DMS_TUNING_COUNT
 };
 dms_status dms_set_tuning(dms_grid grid, const int32_t *values, int count);
 dms_status dms_get_tuning(dms_grid grid, int32_t *values, int count);

@@ -4,8 +4,10 @@ The tunables (``dms_set_tuning``, in ``TUNABLES`` order) change only how fast
 a diagram is computed, never the diagram: thread-block sizes of
 ProcessLowerStars and of the first D1 trace pass, the number of trace
 threads per SM and their heap size, the number of active columns below which
-a whole block performs a column's additions, the heap size of a lazy
-advance, and the column density below which D1 mode 0 reduces lazily.
+a whole block performs a column's additions (and the asynchronous tail
+starts), the heap size of a lazy advance, the column density below which D1
+mode 0 reduces lazily, and whether the tail of the traced reduction runs as
+one asynchronous pass.
 
 ``tune`` runs a coordinate descent: starting from the handle's current
 values, it tries each candidate of one tunable with the others fixed, keeps
@@ -25,8 +27,8 @@ import numpy as np
 from . import _check
 
 TUNABLES = ("pls_block", "trace_block", "trace_per_sm", "trace_heap", "red_block_below",
-            "lazy_heap", "lazy_density")
-DEFAULT = (128, 128, 2048, 48, 8192, 48, 32)
+            "lazy_heap", "lazy_density", "red_async")
+DEFAULT = (128, 128, 2048, 48, 8192, 48, 32, 1)
 CANDIDATES = {
     "pls_block": (64, 128, 256),
     "trace_block": (64, 128, 256),
@@ -35,6 +37,7 @@ CANDIDATES = {
     "red_block_below": (2048, 8192, 32768),
     "lazy_heap": (32, 48, 96),
     "lazy_density": (16, 32, 64),
+    "red_async": (0, 1),
 }
 
 

@@ -1701,6 +1701,287 @@ __global__ void __launch_bounds__(kRedBlock)
     }
 }
 
+// ---- the tail of the reduction, asynchronous
+//
+// Once few columns remain active, the rounds are dominated by their longest
+// chain of additions while displaced columns wait for the round to end.  This
+// persistent kernel runs the same reduction without rounds (the lock-free
+// form of Sec. 7.2's temporary pairs): blocks take columns from a device
+// queue; a column adds the current list of the owner of its pivot while that
+// owner is an earlier column, and takes the pivot by compare-and-swap when it
+// is unowned or owned by a later column, which then goes back to the queue.
+// Any list a column o has held is a sum of columns <= o whose top is o's
+// pivot at that time, so adding a snapshot of an earlier column's list is a
+// valid step of the reduction even if that column is being displaced
+// meanwhile; the pivots reached are those of the standard reduction.  A
+// column's list is published (start << 32 | length, one 64-bit word) before
+// the compare-and-swap that makes it an owner.
+struct AsyncQ {
+    unsigned int head, tail;
+    int pending;       // columns queued or in progress
+    int abort;         // the pool or the queue filled up: stop taking columns
+};
+
+// A list written by another block in this kernel is read from L2 (ld.cg): an
+// L1 line cached while reading a neighbouring list could hold stale entries.
+template <bool G>
+__device__ __forceinline__ int32_t ld_list(const int32_t *p) {
+    if constexpr (G) return __ldcg(p);
+    else return *p;
+}
+
+template <bool AG, bool BG>
+__device__ __forceinline__ void merge_split_g(const int32_t *A, int la, const int32_t *B, int lb,
+                                              int d, int &i, int &j) {
+    int lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (ld_list<AG>(A + mid) >= ld_list<BG>(B + d - 1 - mid)) lo = mid + 1;
+        else hi = mid;
+    }
+    i = lo;
+    j = d - lo;
+    if (i > 0 && j < lb && ld_list<AG>(A + i - 1) == ld_list<BG>(B + j)) j++;
+}
+
+// block_symdiff with global operands read from L2 (AG / BG: A / B in global memory)
+template <int NT, bool AG, bool BG>
+__device__ int block_symdiff_g(const int32_t *A, int la, const int32_t *B, int lb, int32_t *out,
+                               int *sscan) {
+    const int t = threadIdx.x;
+    const int L = la + lb, per = (L + NT - 1) / NT;
+    int i0, j0, i1, j1;
+    merge_split_g<AG, BG>(A, la, B, lb, min(t * per, L), i0, j0);
+    merge_split_g<AG, BG>(A, la, B, lb, min(t * per + per, L), i1, j1);
+    int cnt = 0;
+    {
+        int i = i0, j = j0;
+        while (i < i1 || j < j1) {
+            int32_t x = i < i1 ? ld_list<AG>(A + i) : -1, y = j < j1 ? ld_list<BG>(B + j) : -1;
+            if (x > y) { cnt++; i++; }
+            else if (y > x) { cnt++; j++; }
+            else { i++; j++; }
+        }
+    }
+    const int lane = t & 31, w = t >> 5;
+    int inc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) sscan[w] = inc;
+    __syncthreads();
+    int pre = 0, total = 0;
+    for (int q = 0; q < NT / 32; q++) { if (q < w) pre += sscan[q]; total += sscan[q]; }
+    int o = pre + inc - cnt;
+    int i = i0, j = j0;
+    while (i < i1 || j < j1) {
+        int32_t x = i < i1 ? ld_list<AG>(A + i) : -1, y = j < j1 ? ld_list<BG>(B + j) : -1;
+        if (x > y) { out[o++] = x; i++; }
+        else if (y > x) { out[o++] = y; j++; }
+        else { i++; j++; }
+    }
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ unsigned long long pack_list(int64_t start, int32_t len) {
+    return ((unsigned long long)start << 32) | (uint32_t)len;
+}
+
+__device__ __forceinline__ void aq_push(AsyncQ *q, int32_t *queue, unsigned int qcap, int32_t c,
+                                        bool count, DevStatus *st) {
+    if (count) atomicAdd(&q->pending, 1);
+    const unsigned int i = atomicAdd(&q->tail, 1u);
+    if (i >= qcap) {                     // cannot happen with the capacity reserved
+        atomicOr(&st->err, kErrCap);
+        atomicExch(&q->abort, 1);
+        return;
+    }
+    ((volatile int32_t *)queue)[i] = c;
+    __threadfence();
+}
+
+__global__ void __launch_bounds__(kRedBlock)
+    k_red_async(AsyncQ *q, int32_t *queue, unsigned int qcap, int32_t *owner,
+                unsigned long long *info, int64_t *start, int32_t *len, int32_t *pool,
+                int64_t pool_cap, DevStatus *st) {
+    extern __shared__ int32_t smem[];
+    int32_t *acc[2] = {smem, smem + kRedAcc};
+    int32_t *sB = smem + 2 * kRedAcc;
+    __shared__ int sscan[kRedBlock / 32];
+    __shared__ int32_t s_cj, s_o, s_state;
+    __shared__ unsigned long long s_rec, s_pos;
+    const int t = threadIdx.x;
+    unsigned adds = 0;
+    unsigned long long io_r = 0, io_w = 0;
+    for (;;) {
+        // take a column (thread 0), or leave once nothing is queued or in progress
+        if (t == 0) {
+            s_cj = -1;
+            for (int spin = 0; spin < (1 << 22); spin++) {
+                if (*(volatile int *)&q->abort) break;
+                const unsigned int h = *(volatile unsigned int *)&q->head;
+                const unsigned int tl = *(volatile unsigned int *)&q->tail;
+                if (h < tl && h < qcap) {
+                    if (atomicCAS(&q->head, h, h + 1) != h) continue;
+                    int32_t c = -1;
+                    for (int w = 0; w < (1 << 20) && c < 0; w++) {
+                        c = ((volatile int32_t *)queue)[h];
+                        if (c < 0) __nanosleep(64);
+                    }
+                    if (c < 0) { atomicOr(&st->err, kErrIter); atomicExch(&q->abort, 1); }
+                    s_cj = c;
+                    break;
+                }
+                if (*(volatile int *)&q->pending == 0) break;
+                __nanosleep(256);
+                if (spin == (1 << 22) - 1) { atomicOr(&st->err, kErrIter); atomicExch(&q->abort, 1); }
+            }
+        }
+        __syncthreads();
+        const int32_t cj = s_cj;
+        if (cj < 0) break;
+        if (t == 0) s_rec = *(volatile unsigned long long *)&info[cj];
+        __syncthreads();
+        int la = (int)(uint32_t)(s_rec & 0xffffffffull);
+        int64_t sa = (int64_t)(s_rec >> 32);
+        bool resident = la <= kRedAcc;
+        int cur = 0;
+        if (resident) {
+            for (int k = t; k < la; k += kRedBlock) acc[0][k] = __ldcg(pool + sa + k);
+            __syncthreads();
+        }
+        // state: 0 working, 1 done, 2 stopped (pool full: requeued)
+        int state = 0;
+        for (int it = 0; state == 0 && it < (1 << 24); it++) {
+            if (la == 0) {
+                if (t == 0) {
+                    *(volatile unsigned long long *)&info[cj] = pack_list(0, 0);
+                    start[cj] = 0;
+                    len[cj] = 0;
+                }
+                state = 1;
+                break;
+            }
+            if (t == 0) s_o = *(volatile int32_t *)&owner[resident ? acc[cur][0] : __ldcg(pool + sa)];
+            __syncthreads();
+            const int32_t o = s_o;
+            if (o == cj) { state = 1; break; }             // already the owner
+            if (o != kNoOwner && o < cj) {
+                // add the earlier owner's current list
+                if (t == 0) s_rec = *(volatile unsigned long long *)&info[o];
+                __syncthreads();
+                const int lb = (int)(uint32_t)(s_rec & 0xffffffffull);
+                const int32_t *B = pool + (int64_t)(s_rec >> 32);
+                const bool staged = lb <= kRedStage;
+                if (staged) {
+                    for (int k = t; k < lb; k += kRedBlock) sB[k] = __ldcg(B + k);
+                    B = sB;
+                }
+                io_r += (unsigned long long)(la + lb);
+                if (resident && la + lb <= kRedAcc) {
+                    __syncthreads();
+                    la = staged ? block_symdiff_g<kRedBlock, false, false>(acc[cur], la, B, lb,
+                                                                           acc[cur ^ 1], sscan)
+                                : block_symdiff_g<kRedBlock, false, true>(acc[cur], la, B, lb,
+                                                                          acc[cur ^ 1], sscan);
+                    cur ^= 1;
+                } else {
+                    if (t == 0) s_pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
+                    __syncthreads();
+                    const unsigned long long pos = s_pos;
+                    if ((int64_t)(pos + la + lb) > pool_cap) {
+                        if (t == 0) { atomicOr(&st->err, kErrCap); atomicExch(&q->abort, 1); }
+                        state = 2;
+                        break;
+                    }
+                    __syncthreads();
+                    if (resident)
+                        la = staged ? block_symdiff_g<kRedBlock, false, false>(acc[cur], la, B, lb,
+                                                                               pool + pos, sscan)
+                                    : block_symdiff_g<kRedBlock, false, true>(acc[cur], la, B, lb,
+                                                                              pool + pos, sscan);
+                    else
+                        la = staged ? block_symdiff_g<kRedBlock, true, false>(pool + sa, la, B, lb,
+                                                                              pool + pos, sscan)
+                                    : block_symdiff_g<kRedBlock, true, true>(pool + sa, la, B, lb,
+                                                                             pool + pos, sscan);
+                    sa = (int64_t)pos;
+                    resident = false;
+                }
+                io_w += (unsigned long long)la;
+                adds++;
+                continue;
+            }
+            // unowned, or owned by a later column: publish the list and take the pivot
+            __threadfence();
+            __syncthreads();
+            if (resident) {
+                if (t == 0) s_pos = atomicAdd(&st->pool_top, (unsigned long long)la);
+                __syncthreads();
+                const unsigned long long pos = s_pos;
+                if ((int64_t)(pos + la) > pool_cap) {
+                    if (t == 0) { atomicOr(&st->err, kErrCap); atomicExch(&q->abort, 1); }
+                    state = 2;
+                    break;
+                }
+                for (int k = t; k < la; k += kRedBlock) pool[pos + k] = acc[cur][k];
+                sa = (int64_t)pos;
+                resident = false;
+                __threadfence();
+                __syncthreads();
+            }
+            if (t == 0) {
+                start[cj] = sa;
+                len[cj] = la;
+                *(volatile unsigned long long *)&info[cj] = pack_list(sa, la);
+                __threadfence();
+                const int32_t prev = atomicCAS(&owner[__ldcg(pool + sa)], o, cj);
+                s_state = prev == o ? 1 : 0;
+                if (prev == o && o != kNoOwner) aq_push(q, queue, qcap, o, true, st);
+            }
+            __syncthreads();
+            state = s_state;
+            // on a lost race the owner is read again; the list stays in the pool
+            if (state == 0) {
+                resident = la <= kRedAcc;
+                if (resident) {
+                    cur = 0;
+                    for (int k = t; k < la; k += kRedBlock) acc[0][k] = __ldcg(pool + sa + k);
+                    __syncthreads();
+                }
+            }
+        }
+        __syncthreads();
+        if (state == 0 && t == 0) {        // the chain bound ran out
+            atomicOr(&st->err, kErrIter);
+            atomicExch(&q->abort, 1);
+        }
+        if (t == 0) {
+            if (state == 2) {
+                // the column keeps its last published list; it goes back to the queue
+                aq_push(q, queue, qcap, cj, false, st);
+            } else {
+                atomicSub(&q->pending, 1);
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0 && adds) {
+        atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)adds);
+        atomicAdd((unsigned long long *)&st->red_io[0], io_r * 4ull);
+        atomicAdd((unsigned long long *)&st->red_io[1], io_w * 4ull);
+    }
+}
+
+// info[c] = start << 32 | length of every column
+__global__ void k_pack_info(int64_t ncol, const int64_t *__restrict__ start,
+                            const int32_t *__restrict__ len, unsigned long long *info) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncol) info[c] = pack_list(start[c], len[c]);
+}
+
 __global__ void k_iota32(int32_t *p, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = (int32_t)i;
@@ -2951,6 +3232,8 @@ dms_status ensure_tables(int device) {
     build_regular_lut(S, lut);
     DMS_CUDA(cudaMemcpyToSymbol(g_star, &S, sizeof S));
     DMS_CUDA(cudaMemcpyToSymbol(g_regular, lut.data(), lut.size() * sizeof(uint32_t)));
+    DMS_CUDA(cudaFuncSetAttribute(k_red_async, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kRedSmem));
     DMS_CUDA(cudaFuncSetAttribute(k_red_add_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kRedSmem));
     if (device < 32) g_tables_ready |= 1u << device;
@@ -3059,6 +3342,74 @@ int64_t d1_pool_entries(int64_t dflt) {
 }
 
 
+// Compacts the live columns (int32 entries) into a fresh pool at least twice
+// as large (and 4x the live entries), clears the status error and resets the
+// bump pointer.  The host status mirror keeps the other words of the last sync.
+dms_status grow_pool(Ctx &c, int64_t ncol, int64_t *pool_cap) {
+    Pipeline &P = c.P;
+    DMS_ALLOC(P.flag_a, 4 * ncol + 4);
+    DMS_ALLOC(P.flag_b, 4 * ncol + 4);
+    DMS_CUDA(cudaMemcpyAsync(P.flag_a.p, P.d1_len.p, 4 * ncol, cudaMemcpyDeviceToDevice, c.s));
+    DMS_TRY(scan(c, P.flag_a.as<int32_t>(), P.flag_b.as<int32_t>(), ncol, &c.st->total[3]));
+    DMS_CUDA(cudaMemcpyAsync(c.hst, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.s));
+    DMS_CUDA(cudaStreamSynchronize(c.s));
+    const int64_t live = c.hst->total[3];
+    const int64_t cap2 = std::max<int64_t>(2 * *pool_cap, 4 * live + (1 << 20));
+    if (cap2 >= ((int64_t)1 << 31)) return DMS_ERR_CAPACITY;
+    DevBuf fresh;
+    if (!fresh.ensure(4 * (size_t)cap2)) return DMS_ERR_OOM;
+    DMS_LAUNCH(ncol, 256, k_pool_compact, ncol, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+               P.flag_b.as<int32_t>(), P.d1_pool.as<int32_t>(), fresh.as<int32_t>());
+    DMS_CUDA(cudaStreamSynchronize(c.s));
+    P.d1_pool.release();
+    P.d1_pool = fresh;
+    *pool_cap = cap2;
+    c.hst->err = 0;
+    c.hst->pool_top = (unsigned long long)live;
+    DMS_CUDA(cudaMemcpyAsync(c.st, c.hst, sizeof(DevStatus), cudaMemcpyHostToDevice, c.s));
+    P.d1_pool_grows++;
+    return DMS_OK;
+}
+
+// The tail of the reduction in one asynchronous pass (k_red_async) over the
+// `nactive` columns listed in P.d1_act.  Returns DMS_OK when every column is
+// reduced, or DMS_ERR_CAPACITY with the unfinished columns back in P.d1_act
+// (*nactive) when the pool filled up.
+dms_status reduce_tail_async(Ctx &c, int64_t ncol, int64_t *nactive, int64_t pool_cap) {
+    Pipeline &P = c.P;
+    const int64_t n0 = *nactive;
+    const int64_t qcap = std::max<int64_t>(4 * ncol, n0 + (1 << 20));
+    if (qcap >= ((int64_t)1 << 31)) return DMS_ERR_CAPACITY;
+    DMS_ALLOC(P.d1_info, 8 * ncol + 8);
+    DMS_ALLOC(P.d1_queue, 4 * qcap);
+    DMS_ALLOC(P.d1_aq, sizeof(AsyncQ));
+    DMS_LAUNCH(ncol, 256, k_pack_info, ncol, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+               P.d1_info.as<unsigned long long>());
+    DMS_CUDA(cudaMemsetAsync(P.d1_queue.p, 0xFF, 4 * qcap, c.s));
+    DMS_CUDA(cudaMemcpyAsync(P.d1_queue.p, P.d1_act.p, 4 * n0, cudaMemcpyDeviceToDevice, c.s));
+    AsyncQ q0{0u, (unsigned int)n0, (int)n0, 0};
+    DMS_CUDA(cudaMemcpyAsync(P.d1_aq.p, &q0, sizeof q0, cudaMemcpyHostToDevice, c.s));
+    k_red_async<<<152, kRedBlock, kRedSmem, c.s>>>(
+        P.d1_aq.as<AsyncQ>(), P.d1_queue.as<int32_t>(), (unsigned int)qcap,
+        P.d1_owner.as<int32_t>(), P.d1_info.as<unsigned long long>(), P.d1_start.as<int64_t>(),
+        P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), pool_cap, c.st);
+    c.launches++;
+    DMS_CUDA(cudaGetLastError());
+    AsyncQ q1;
+    DMS_CUDA(cudaMemcpyAsync(&q1, P.d1_aq.p, sizeof q1, cudaMemcpyDeviceToHost, c.s));
+    dms_status s = sync_status(c);
+    if (s != DMS_OK && s != DMS_ERR_CAPACITY) return s;
+    if (s == DMS_OK && !q1.abort && q1.pending == 0) return DMS_OK;
+    if (s == DMS_OK) return DMS_ERR_STATE;
+    // the pool filled up: the queued columns go back to the rounds
+    const int64_t h = q1.head, tl = std::min<int64_t>(q1.tail, qcap);
+    if (tl < h || tl - h > 4 * ncol) return DMS_ERR_STATE;
+    DMS_CUDA(cudaMemcpyAsync(P.d1_act.p, P.d1_queue.as<int32_t>() + h, 4 * (tl - h),
+                             cudaMemcpyDeviceToDevice, c.s));
+    *nactive = tl - h;
+    return DMS_ERR_CAPACITY;
+}
+
 dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used) {
     Pipeline &P = c.P;
     DMS_ALLOC(P.d1_owner, 4 * nent + 4);
@@ -3080,6 +3431,25 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
     int64_t nactive = ncol, stamp = 0;
     const int64_t limit = P.max_iters > 0 ? P.max_iters : ((int64_t)1 << 22);
     for (int64_t r = 0; r < limit; r++, stamp++) {
+        if (nactive <= P.tune[DMS_TUNE_RED_BLOCK_BELOW] && P.tune[DMS_TUNE_RED_ASYNC]) {
+            // the tail: one asynchronous pass instead of rounds
+            dms_status s = reduce_tail_async(c, ncol, &nactive, pool_cap);
+            P.rounds_d1 = r + 1;
+            if (s == DMS_OK) {
+                P.d1_io_read = c.hst->red_io[0];
+                P.d1_io_written = c.hst->red_io[1];
+                P.d1_additions = c.hst->misc[2];
+                P.d1_pool_used = (int64_t)c.hst->pool_top;
+                return DMS_OK;
+            }
+            if (s != DMS_ERR_CAPACITY) return s;
+            // compact into a larger pool, publish the owners again, go on in rounds
+            DMS_TRY(grow_pool(c, ncol, &pool_cap));
+            DMS_LAUNCH(ncol, 256, k_red_publish_all, ncol, P.d1_start.as<int64_t>(),
+                       P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
+                       P.d1_owner.as<int32_t>(), rowcol);
+            continue;
+        }
         DMS_CUDA(cudaMemsetAsync(&c.st->misc[0], 0, 2 * sizeof(long long), c.s));
         DMS_LAUNCH(nactive, 256, k_red_claim, P.d1_act.as<int32_t>(), nactive,
                    P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
@@ -3116,24 +3486,7 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
         }
         if (s == DMS_ERR_CAPACITY) {
             // compact the live columns into a pool twice as large, then sweep all columns
-            DMS_ALLOC(P.flag_a, 4 * ncol + 4);
-            DMS_ALLOC(P.flag_b, 4 * ncol + 4);
-            DMS_CUDA(cudaMemcpyAsync(P.flag_a.p, P.d1_len.p, 4 * ncol, cudaMemcpyDeviceToDevice, c.s));
-            DMS_TRY(scan(c, P.flag_a.as<int32_t>(), P.flag_b.as<int32_t>(), ncol, &c.st->total[3]));
-            DMS_CUDA(cudaMemcpyAsync(c.hst, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.s));
-            DMS_CUDA(cudaStreamSynchronize(c.s));
-            int64_t live = c.hst->total[3];
-            int64_t cap2 = std::max<int64_t>(2 * pool_cap, 4 * live + (1 << 20));
-            if (cap2 >= ((int64_t)1 << 31)) return DMS_ERR_CAPACITY;
-            DevBuf fresh;
-            if (!fresh.ensure(4 * (size_t)cap2)) return DMS_ERR_OOM;
-            DMS_LAUNCH(ncol, 256, k_pool_compact, ncol, P.d1_start.as<int64_t>(),
-                       P.d1_len.as<int32_t>(), P.flag_b.as<int32_t>(), P.d1_pool.as<int32_t>(),
-                       fresh.as<int32_t>());
-            DMS_CUDA(cudaStreamSynchronize(c.s));
-            P.d1_pool.release();
-            P.d1_pool = fresh;
-            pool_cap = cap2;
+            DMS_TRY(grow_pool(c, ncol, &pool_cap));
             // the owners' lists moved: publish them again
             DMS_LAUNCH(ncol, 256, k_red_publish_all, ncol, P.d1_start.as<int64_t>(),
                        P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
@@ -3145,10 +3498,6 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
             DMS_CUDA(cudaMemcpyAsync(P.d1_act.as<int32_t>() + nactive + nre, P.d1_next.p,
                                      4 * nnext, cudaMemcpyDeviceToDevice, c.s));
             nactive += nre + nnext;
-            c.hst->err = 0;
-            c.hst->pool_top = (unsigned long long)live;
-            DMS_CUDA(cudaMemcpyAsync(c.st, c.hst, sizeof(DevStatus), cudaMemcpyHostToDevice, c.s));
-            P.d1_pool_grows++;
             continue;
         }
         if (s != DMS_OK) return s;
@@ -4085,7 +4434,7 @@ void Pipeline::destroy() {
                      &d1_astamp, &lz_small.buf, &lz_big.buf, &d1_rowcol,
                      &fields_dev, &field_of, &field_off_dev, &fmax_field, &bt_k[0], &bt_k[1],
                      &bt_v[0], &bt_v[1], &bt_h[0], &bt_h[1], &bt_cnt, &out_tmp, &bx_buf[0],
-                     &bx_buf[1]};
+                     &bx_buf[1], &d1_info, &d1_queue, &d1_aq};
     for (DevBuf *b : all) b->release();
     for (int d = 0; d < 4; d++) {
         cnt[d].release(); base[d].release(); c_vert[d].release(); c_loc[d].release();

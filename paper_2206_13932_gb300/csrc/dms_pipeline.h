@@ -53,6 +53,7 @@ struct Pipeline {
     DevBuf d1_rowpos, d1_rowmap, d1_cocnt, d1_costart, d1_cofill;   // transpose
     DevBuf d1_colmap, d1_start, d1_len, d1_owner, d1_ovf, d1_pool, d1_scratch, d1_todo;
     DevBuf d1_rowcol;                          // D1: owner of each row with its list
+    DevBuf d1_info, d1_queue, d1_aq;           // D1: asynchronous tail (lists, queue)
     DevBuf d1_astamp;                          // lazy D1: last advance per column
     LazyScratch lz_small, lz_big;              // lazy D1: advance scratch
     DevBuf bx_buf[2];                          // lazy D1: block expansion scratch
@@ -71,7 +72,7 @@ struct Pipeline {
     void *hstat = nullptr;  // pinned host mirror
 
     // launch shapes and capacities (dms_set_tuning; order of DMS_TUNE_*)
-    int32_t tune[DMS_TUNING_COUNT] = {128, 128, 2048, 48, 8192, 48, 32};
+    int32_t tune[DMS_TUNING_COUNT] = {128, 128, 2048, 48, 8192, 48, 32, 1};
 
     int64_t n_crit = 0, n_c[4] = {0, 0, 0, 0};
     int64_t n_pairs[3] = {0, 0, 0}, n_ess[4] = {0, 0, 0, 0};
