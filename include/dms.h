@@ -237,7 +237,7 @@ dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, 
  *                             (8..1024; default 48; larger traces retry with
  *                             16x more)
  *   DMS_TUNE_RED_BLOCK_BELOW  active columns below which a whole block
- *                             performs a column's additions (>= 0; 8192)
+ *                             performs a column's additions (>= 0; 4096)
  *   DMS_TUNE_LAZY_HEAP        first-pass heap entries of a lazy advance
  *                             (8..1024; default 48)
  *   DMS_TUNE_LAZY_DENSITY     d1_mode 0 reduces lazily when there are fewer
