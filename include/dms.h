@@ -248,12 +248,16 @@ dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, 
  *                             asynchronous pass (compare-and-swap ownership
  *                             and a device work queue); 0: in rounds
  *                             (default 1)
+ *   DMS_TUNE_PLS_SORT         ProcessLowerStars on blocks of 512 stars sorted
+ *                             by shape: 0 never, 1 when more than a quarter
+ *                             of the vertices are critical (default), 2
+ *                             always
  * dms_set_tuning checks every value and changes nothing when one is out of
  * range (DMS_ERR_INVALID_ARG); count must be DMS_TUNING_COUNT. */
 enum {
     DMS_TUNE_PLS_BLOCK = 0, DMS_TUNE_TRACE_BLOCK, DMS_TUNE_TRACE_PER_SM, DMS_TUNE_TRACE_HEAP,
     DMS_TUNE_RED_BLOCK_BELOW, DMS_TUNE_LAZY_HEAP, DMS_TUNE_LAZY_DENSITY, DMS_TUNE_RED_ASYNC,
-    DMS_TUNING_COUNT
+    DMS_TUNE_PLS_SORT, DMS_TUNING_COUNT
 };
 dms_status dms_set_tuning(dms_grid grid, const int32_t *values, int count);
 dms_status dms_get_tuning(dms_grid grid, int32_t *values, int count);

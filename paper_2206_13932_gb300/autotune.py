@@ -7,7 +7,7 @@ threads per SM and their heap size, the number of active columns below which
 a whole block performs a column's additions (and the asynchronous tail
 starts), the heap size of a lazy advance, the column density below which D1
 mode 0 reduces lazily, and whether the tail of the traced reduction runs as
-one asynchronous pass.
+one asynchronous pass, and when ProcessLowerStars sorts its stars by shape.
 
 ``tune`` runs a coordinate descent: starting from the handle's current
 values, it tries each candidate of one tunable with the others fixed, keeps
@@ -27,8 +27,8 @@ import numpy as np
 from . import _check
 
 TUNABLES = ("pls_block", "trace_block", "trace_per_sm", "trace_heap", "red_block_below",
-            "lazy_heap", "lazy_density", "red_async")
-DEFAULT = (128, 128, 2048, 48, 4096, 48, 32, 1)
+            "lazy_heap", "lazy_density", "red_async", "pls_sort")
+DEFAULT = (128, 128, 2048, 48, 4096, 48, 32, 1, 1)
 CANDIDATES = {
     "pls_block": (64, 128, 256),
     "trace_block": (64, 128, 256),
@@ -38,6 +38,7 @@ CANDIDATES = {
     "lazy_heap": (32, 48, 96),
     "lazy_density": (16, 32, 64),
     "red_async": (0, 1),
+    "pls_sort": (0, 1, 2),
 }
 
 

@@ -698,6 +698,64 @@ __global__ void k_pls(const T *__restrict__ values, Geo<B> geo, const int32_t *_
     flags[x] = (uint8_t)(flags[x] | kFlagGradient);
 }
 
+// The same, for fields whose stars vary widely (noise): the work of a lower
+// star grows with its size and shape, so a block first loads the stars of its
+// NT vertices (coalesced), sorts them in shared memory by (number of lower
+// links, lower mask), and each thread then runs ProcessLowerStars on the star
+// at its sorted position, so that the threads of a warp follow similar paths.
+template <typename T, bool B, int NT>
+__global__ void __launch_bounds__(NT)
+    k_pls_sorted(const T *__restrict__ values, Geo<B> geo, const int32_t *__restrict__ list,
+                 int64_t count, uint8_t *flags, GradRec *grad) {
+    __shared__ uint32_t skey[NT];
+    __shared__ uint16_t sidx[NT];
+    __shared__ unsigned long long srank[NT];
+    const int t = threadIdx.x;
+    const StarTables &S = g_star;
+    const int64_t i = (int64_t)blockIdx.x * NT + t;
+    uint32_t key = 0xFFFFFFFFu;
+    if (i < count) {
+        const int64_t x = list ? list[i] : i;
+        const GridParams &g = geo.at(x);
+        StarView sv;
+        load_star(S, g, values, x, sv);
+        unsigned long long rk = 0;
+        for (int n = 0; n < kLinks; n++) rk |= (unsigned long long)(sv.rank[n] & 15) << (4 * n);
+        srank[t] = rk;
+        key = ((uint32_t)__popc(sv.lower) << 14) | sv.lower;
+    }
+    skey[t] = key;
+    sidx[t] = (uint16_t)t;
+    __syncthreads();
+    // bitonic sort of (key, index), ascending
+    for (int k = 2; k <= NT; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int l = t ^ j;
+            if (l > t) {
+                const bool up = (t & k) == 0;
+                const uint32_t a = skey[t], b = skey[l];
+                if (up ? a > b : a < b) {
+                    skey[t] = b; skey[l] = a;
+                    const uint16_t u = sidx[t]; sidx[t] = sidx[l]; sidx[l] = u;
+                }
+            }
+            __syncthreads();
+        }
+    const uint32_t mykey = skey[t];
+    if (mykey == 0xFFFFFFFFu) return;
+    const int src = sidx[t];
+    const int64_t si = (int64_t)blockIdx.x * NT + src;
+    const int64_t x = list ? list[si] : si;
+    uint8_t rank[kLinks];
+    const unsigned long long rk = srank[src];
+    for (int n = 0; n < kLinks; n++) rank[n] = (uint8_t)((rk >> (4 * n)) & 15);
+    PLSResult R;
+    GradRec G;
+    pls(S, (uint16_t)(mykey & kAllLinks), rank, R, &G);
+    grad[x] = G;
+    flags[x] = (uint8_t)(flags[x] | kFlagGradient);
+}
+
 // The critical cells of the lower star of each sorted critical vertex, read
 // off its packed pairing: the critical edges and tets are the lower ones left
 // unpaired, the critical triangles those paired with neither an edge nor a
@@ -3888,6 +3946,27 @@ dms_status group_by_field(Ctx &c, int d, int64_t rows) {
     return DMS_OK;
 }
 
+// ProcessLowerStars: sorted by star shape in blocks of 512 when `sorted`,
+// else plain with the tuned block size.
+template <typename T, bool B>
+dms_status launch_pls(Ctx &c, const T *values, const Geo<B> &geo, const int32_t *list,
+                      int64_t count, bool sorted) {
+    Pipeline &P = c.P;
+    if (count <= 0) return DMS_OK;
+    uint8_t *fl = P.flags.as<uint8_t>();
+    GradRec *gr = P.grad.as<GradRec>();
+    if (sorted) {
+        k_pls_sorted<T, B, 512><<<blocks_for(count, 512), 512, 0, c.s>>>(values, geo, list, count,
+                                                                        fl, gr);
+    } else {
+        const int nt = P.tune[DMS_TUNE_PLS_BLOCK];
+        k_pls<T, B><<<blocks_for(count, nt), nt, 0, c.s>>>(values, geo, list, count, fl, gr);
+    }
+    c.launches++;
+    DMS_CUDA(cudaGetLastError());
+    return DMS_OK;
+}
+
 template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     using K = typename Key<T>::K;
     Pipeline &P = c.P;
@@ -3948,12 +4027,12 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
         // when critical vertices are dense (the walks of D2 and D1 then visit
         // most vertices), otherwise on the critical ones, the rest on demand
         KEV(6);
+        const int ps = P.tune[DMS_TUNE_PLS_SORT];
+        const bool sort_stars = ps == 2 || (ps == 1 && nc * 4 > n);
         if (nc * 4 > n || n <= kDenseGradientBelow)
-            DMS_LAUNCH(n, P.tune[DMS_TUNE_PLS_BLOCK], (k_pls<T, B>), values, geo, (const int32_t *)nullptr, n,
-                       P.flags.as<uint8_t>(), P.grad.as<GradRec>());
+            DMS_TRY((launch_pls<T, B>(c, values, geo, nullptr, n, sort_stars)));
         else
-            DMS_LAUNCH(nc, P.tune[DMS_TUNE_PLS_BLOCK], (k_pls<T, B>), values, geo, P.vc.as<int32_t>(), nc,
-                       P.flags.as<uint8_t>(), P.grad.as<GradRec>());
+            DMS_TRY((launch_pls<T, B>(c, values, geo, P.vc.as<int32_t>(), nc, sort_stars)));
         KEV(7);
         // stable LSD radix sort of the critical vertices (in id order) by value
         KEV(4);
