@@ -45,6 +45,7 @@ struct DevStatus {
     unsigned long long pool_top;   // D1 column pool bump pointer
     long long misc[4];
     long long bx[4];               // block expansions: nodes, levels (discovery, order), columns
+    unsigned long long trace_next; // D1 trace: next column to take
 };
 
 // Record of a critical vertex after ProcessLowerStars.
@@ -1320,54 +1321,94 @@ __device__ __forceinline__ void trace_expand(TraceCtx &c, const StarTables &S, c
 
 // One thread per column: the Morse boundary of a critical triangle restricted
 // to the rows (1-saddles not paired in D0), as a descending list of C1
-// indices appended to the column pool.
+// indices appended to the column pool.  The walks differ widely in length,
+// so the loop is flat: in every iteration each lane takes one step of its
+// current column -- start it, expand one edge, or write it out -- and lanes
+// that finish fetch the next column at once (one atomic per warp), instead of
+// the warp waiting for its longest walk before the next batch of columns.
 template <typename T, bool B>
-__global__ void __launch_bounds__(256, 4) k_d1_trace(const T *__restrict__ values, Geo<B> geo, uint8_t *flags,
-                           GradRec *grad, const int32_t *__restrict__ vrank,
-                           const CritRec *__restrict__ recs, const int32_t *__restrict__ base1,
-                           const uint8_t *__restrict__ is_row, const int32_t *__restrict__ v2,
-                           const uint8_t *__restrict__ l2, const int32_t *__restrict__ colmap,
-                           const int32_t *__restrict__ todo, int64_t ntodo, HeapEnt *heap_all,
-                           HashEnt *hash_all, int32_t *rows_all, int hcap, int hashcap, int rcap,
-                           int32_t gen_base, int32_t *pool, int64_t pool_cap, int64_t *col_start,
-                           int32_t *col_len, uint8_t *overflow, DevStatus *st) {
+__global__ void __launch_bounds__(256, 4)
+    k_d1_trace(const T *__restrict__ values, Geo<B> geo, uint8_t *flags, GradRec *grad,
+               const int32_t *__restrict__ vrank, const CritRec *__restrict__ recs,
+               const int32_t *__restrict__ base1, const uint8_t *__restrict__ is_row,
+               const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
+               const int32_t *__restrict__ colmap, const int32_t *__restrict__ todo,
+               int64_t ntodo, HeapEnt *heap_all, HashEnt *hash_all, int32_t *rows_all, int hcap,
+               int hashcap, int rcap, int32_t gen_base, int32_t *pool, int64_t pool_cap,
+               int64_t *col_start, int32_t *col_len, uint8_t *overflow,
+               unsigned long long *next_col, DevStatus *st) {
     const StarTables &S = g_star;
-    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     TraceCtx c;
     c.heap = heap_all + tid * hcap;
     c.hash = hash_all + tid * hashcap;
     c.rows = rows_all + tid * 2 * rcap;
     c.rslot = c.rows + rcap;
     c.hcap = hcap; c.hashmask = hashcap - 1; c.rcap = rcap;
-    for (int64_t q = tid; q < ntodo; q += nth) {
-        int32_t cj = todo ? todo[q] : (int32_t)q;
-        int32_t j2 = colmap[cj];
-        int64_t x = v2[j2];
-        const GridParams &g = geo.at(x);
-        int s = l2[j2];
-        c.hn = 0; c.rn = 0; c.used = 0; c.overflow = false;
-        c.gen = gen_base + cj;
-        // boundary: (x,a), (x,b) and the edge between x+a and x+b
-        GradRec Gx = grad_get(S, g, values, flags, grad, x);
-        trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, x,
-                        S.tri_v[s][0], st);
-        trace_expand<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, x, s,
-                        S.tri_v[s][0], Gx, st);
-        while (c.hn > 0 && !c.overflow) {
-            HeapEnt top = heap_pop(c);
-            int64_t y = (int64_t)(top.lo >> 12);
-            int m = (int)(top.lo & 0xF);
+    int32_t cj = -1;
+    bool done = false;
+    const GridParams *gp = nullptr;
+    // every iteration runs the same two warp collectives on all lanes (the
+    // ballot and the vote); the per-lane work after them has none.  A column
+    // takes at most hashcap + 8 steps, which bounds the loop.
+    const int64_t max_iter = ntodo * (int64_t)(hashcap + 8) + 64;
+    for (int64_t iter = 0;; iter++) {
+        // lanes without a column take the next ones
+        const bool need = cj < 0 && !done;
+        const unsigned want = __ballot_sync(0xffffffffu, need);
+        unsigned long long base = 0;
+        if (want) {
+            const int leader = __ffs(want) - 1;
+            if (lane == leader) base = atomicAdd(next_col, (unsigned long long)__popc(want));
+            base = __shfl_sync(0xffffffffu, base, leader);
+        }
+        bool started = false;
+        if (need) {
+            const int64_t q = (int64_t)base + __popc(want & lanemask_lt());
+            if (q >= ntodo) done = true;
+            else { cj = todo ? todo[q] : (int32_t)q; started = true; }
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+        if (iter >= max_iter) {                  // cannot happen: every step makes progress
+            atomicOr(&st->err, kErrIter);
+            break;
+        }
+        if (cj < 0) continue;
+        if (started) {
+            const int32_t j2 = colmap[cj];
+            const int64_t x = v2[j2];
+            gp = &geo.at(x);
+            const int s = l2[j2];
+            c.hn = 0; c.rn = 0; c.used = 0; c.overflow = false;
+            c.gen = gen_base + cj;
+            // boundary: (x,a), (x,b) and the edge between x+a and x+b
+            const GradRec Gx = grad_get(S, *gp, values, flags, grad, x);
+            trace_toggle<T>(c, S, *gp, values, flags, grad, vrank, recs, base1, is_row, x,
+                            S.tri_v[s][0], st);
+            trace_expand<T>(c, S, *gp, values, flags, grad, vrank, recs, base1, is_row, x, s,
+                            S.tri_v[s][0], Gx, st);
+            continue;
+        }
+        if (c.hn > 0 && !c.overflow) {
+            // one expansion
+            const HeapEnt top = heap_pop(c);
+            const int64_t y = (int64_t)(top.lo >> 12);
+            const int m = (int)(top.lo & 0xF);
             HashEnt *e = trace_find(c, y, m);
             if (!e || !hinfo_parity(e->info)) continue;
             e->info &= ~(1u << 31);
-            GradRec G = grad_get(S, g, values, flags, grad, y);
-            trace_expand<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, y,
+            const GradRec G = grad_get(S, *gp, values, flags, grad, y);
+            trace_expand<T>(c, S, *gp, values, flags, grad, vrank, recs, base1, is_row, y,
                             hinfo_pair(e->info), m, G, st);
+            continue;
         }
+        // the column is complete (or outgrew the scratch): write it out
+        const int32_t col = cj;
+        cj = -1;
         if (c.overflow) {
-            overflow[cj] = 1;
-            col_len[cj] = 0;
+            overflow[col] = 1;
+            col_len[col] = 0;
             continue;
         }
         // the rows with odd multiplicity, sorted decreasingly
@@ -1375,22 +1416,22 @@ __global__ void __launch_bounds__(256, 4) k_d1_trace(const T *__restrict__ value
         for (int k = 0; k < c.rn; k++)
             if (hinfo_parity(c.hash[c.rslot[k]].info)) c.rows[len++] = c.rows[k];
         for (int k = 1; k < len; k++) {
-            int32_t v = c.rows[k];
+            const int32_t v = c.rows[k];
             int p = k;
             while (p > 0 && c.rows[p - 1] < v) { c.rows[p] = c.rows[p - 1]; p--; }
             c.rows[p] = v;
         }
-        overflow[cj] = 0;
-        if (len == 0) { col_len[cj] = 0; col_start[cj] = 0; continue; }
-        unsigned long long pos = atomicAdd(&st->pool_top, (unsigned long long)len);
+        overflow[col] = 0;
+        if (len == 0) { col_len[col] = 0; col_start[col] = 0; continue; }
+        const unsigned long long pos = atomicAdd(&st->pool_top, (unsigned long long)len);
         if ((int64_t)(pos + len) > pool_cap) {
             atomicOr(&st->err, kErrCap);
-            col_len[cj] = 0;
+            col_len[col] = 0;
             continue;
         }
         for (int k = 0; k < len; k++) pool[pos + k] = c.rows[k];
-        col_start[cj] = (int64_t)pos;
-        col_len[cj] = len;
+        col_start[col] = (int64_t)pos;
+        col_len[col] = len;
     }
 }
 
@@ -4172,12 +4213,13 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
         DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nthreads * sizeof(HashEnt), c.s));
         KEV(18);
         auto dbg_p1 = std::chrono::steady_clock::now();
+        DMS_CUDA(cudaMemsetAsync(&c.st->trace_next, 0, sizeof(unsigned long long), c.s));
         k_d1_trace<T, B><<<(unsigned)(nthreads / tb), tb, 0, c.s>>>(
             values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
             P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
             P.d1_colmap.as<int32_t>(), nullptr, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,
             P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
-            ovf, c.st);
+            ovf, &c.st->trace_next, c.st);
         c.launches++;
         DMS_CUDA(cudaGetLastError());
         // columns whose trace outgrew the scratch run again with 16x more
@@ -4211,13 +4253,14 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
             DMS_ALLOC(P.d1_todo, 4 * todo.size());
             DMS_CUDA(cudaMemcpyAsync(P.d1_todo.p, todo.data(), 4 * todo.size(),
                                      cudaMemcpyHostToDevice, c.s));
+            DMS_CUDA(cudaMemsetAsync(&c.st->trace_next, 0, sizeof(unsigned long long), c.s));
             k_d1_trace<T, B><<<(unsigned)(nt / 32), 32, 0, c.s>>>(
                 values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
                 P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(),
                 P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), P.d1_todo.as<int32_t>(),
                 (int64_t)todo.size(), heap, hash, rows, hcap, hashcap, rcap, gen,
                 P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(),
-                P.d1_len.as<int32_t>(), ovf, c.st);
+                P.d1_len.as<int32_t>(), ovf, &c.st->trace_next, c.st);
             c.launches++;
             DMS_CUDA(cudaGetLastError());
             gen += (int32_t)ncols;
