@@ -621,6 +621,16 @@ __global__ void k_gather_keys(const T *__restrict__ values, const int32_t *__res
     if (i < nc) keys[i] = Key<T>::of(values[vc[i]]);
 }
 
+// keys[i] = vertex of item i (vert[idx[i]], or vert[i]), vals[i] = i: the
+// input of a radix sort that puts items in vertex-id order
+__global__ void k_gather_vid(const int32_t *__restrict__ vert, const int32_t *__restrict__ idx,
+                             int64_t n, uint32_t *keys, int32_t *vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = (uint32_t)vert[idx ? idx[i] : i];
+    vals[i] = (int32_t)i;
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads)
     k_rs_hist(const K *__restrict__ keys, int64_t n, int shift, int32_t *hist, int ntiles) {
@@ -1148,10 +1158,13 @@ __global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *fl
                           GradRec *grad, const int32_t *__restrict__ vrank,
                           const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
                           const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
-                          int64_t n2, int32_t vmax, int32_t *A, int32_t *B,
-                          int32_t *young, int64_t max_steps, DevStatus *st) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n2) return;
+                          int64_t n2, const int32_t *__restrict__ order, int32_t vmax, int32_t *A,
+                          int32_t *B, int32_t *young, int64_t max_steps, DevStatus *st) {
+    // arcs in vertex-id order (`order`), so that the walks of a warp start
+    // close together and share the records they read
+    const int64_t jj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (jj >= n2) return;
+    const int64_t j = order ? order[jj] : jj;
     const StarTables &S = g_star;
     int64_t x = v2[j];
     const GridParams &g = geo.at(x);
@@ -3987,6 +4000,44 @@ dms_status group_by_field(Ctx &c, int d, int64_t rows) {
     return DMS_OK;
 }
 
+// A permutation of n items (item i at vertex vert[idx[i]], or vert[i]) into
+// vertex-id order, by a stable LSD radix sort; *perm points into scratch
+// buffer `slot` (0 or 1) and stays valid until the next call with that slot.
+dms_status order_by_vertex(Ctx &c, const int32_t *vert, const int32_t *idx, int64_t n, int slot,
+                           const int32_t **perm) {
+    Pipeline &P = c.P;
+    *perm = nullptr;
+    if (n <= 0) return DMS_OK;
+    DevBuf *kb = &P.ord_k[2 * slot], *vb = &P.ord_v[2 * slot];
+    for (int k = 0; k < 2; k++) {
+        DMS_ALLOC(kb[k], 4 * n + 4);
+        DMS_ALLOC(vb[k], 4 * n + 4);
+    }
+    const int rtiles = (int)((n + kRsTile - 1) / kRsTile);
+    DMS_ALLOC(P.ord_h[0], 4 * (size_t)256 * rtiles);
+    DMS_ALLOC(P.ord_h[1], 4 * (size_t)256 * rtiles);
+    uint32_t *kin = kb[0].as<uint32_t>(), *kout = kb[1].as<uint32_t>();
+    int32_t *vin = vb[0].as<int32_t>(), *vout = vb[1].as<int32_t>();
+    DMS_LAUNCH(n, 256, k_gather_vid, vert, idx, n, kin, vin);
+    int bits = 0;
+    while (bits < 32 && (((int64_t)1 << bits) < P.n)) bits++;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_rs_hist<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(kin, n, shift, P.ord_h[0].as<int32_t>(),
+                                                           rtiles);
+        c.launches++;
+        DMS_TRY(scan(c, P.ord_h[0].as<int32_t>(), P.ord_h[1].as<int32_t>(), (int64_t)256 * rtiles,
+                     &c.st->total[1]));
+        k_rs_scatter<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(kin, vin, kout, vout, n, shift,
+                                                              P.ord_h[1].as<int32_t>(), rtiles);
+        c.launches++;
+        DMS_CUDA(cudaGetLastError());
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    *perm = vin;
+    return DMS_OK;
+}
+
 // ProcessLowerStars: sorted by star shape in blocks of 512 when `sorted`,
 // else plain with the tuned block size.
 template <typename T, bool B>
@@ -4150,11 +4201,13 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     // ---- D2: arcs between maxima (node n3 = the virtual maximum), decreasing
     const int32_t vmax = (int32_t)n3;
     KEV(14);
+    const int32_t *order2 = nullptr;
+    DMS_TRY(order_by_vertex(c, P.c_vert[2].as<int32_t>(), nullptr, n2, 0, &order2));
     DMS_LAUNCH(n2, 128, (k_d2_arcs<T, B>), values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
                P.vrank.as<int32_t>(),
                P.recs.as<CritRec>(), P.base[3].as<int32_t>(), P.c_vert[2].as<int32_t>(),
-               P.c_loc[2].as<uint8_t>(), n2, vmax, P.arc_a.as<int32_t>(), P.arc_b.as<int32_t>(),
-               young2, max_steps, c.st);
+               P.c_loc[2].as<uint8_t>(), n2, order2, vmax, P.arc_a.as<int32_t>(),
+               P.arc_b.as<int32_t>(), young2, max_steps, c.st);
     KEV(15);
     KEV(16);
     DMS_TRY(elder_rule(c, n2, 1, 1, young2, died3, &P.rounds_d2));
@@ -4213,11 +4266,15 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
         DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nthreads * sizeof(HashEnt), c.s));
         KEV(18);
         auto dbg_p1 = std::chrono::steady_clock::now();
+        // columns in vertex-id order: the walks of a warp share the records they read
+        const int32_t *corder = nullptr;
+        DMS_TRY(order_by_vertex(c, P.c_vert[2].as<int32_t>(), P.d1_colmap.as<int32_t>(), ncols, 1,
+                                &corder));
         DMS_CUDA(cudaMemsetAsync(&c.st->trace_next, 0, sizeof(unsigned long long), c.s));
         k_d1_trace<T, B><<<(unsigned)(nthreads / tb), tb, 0, c.s>>>(
             values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
             P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
-            P.d1_colmap.as<int32_t>(), nullptr, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,
+            P.d1_colmap.as<int32_t>(), corder, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,
             P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
             ovf, &c.st->trace_next, c.st);
         c.launches++;
@@ -4556,7 +4613,8 @@ void Pipeline::destroy() {
                      &d1_astamp, &lz_small.buf, &lz_big.buf, &d1_rowcol,
                      &fields_dev, &field_of, &field_off_dev, &fmax_field, &bt_k[0], &bt_k[1],
                      &bt_v[0], &bt_v[1], &bt_h[0], &bt_h[1], &bt_cnt, &out_tmp, &bx_buf[0],
-                     &bx_buf[1], &d1_info, &d1_queue, &d1_aq};
+                     &bx_buf[1], &d1_info, &d1_queue, &d1_aq, &ord_k[0], &ord_k[1], &ord_k[2],
+                     &ord_k[3], &ord_v[0], &ord_v[1], &ord_v[2], &ord_v[3], &ord_h[0], &ord_h[1]};
     for (DevBuf *b : all) b->release();
     for (int d = 0; d < 4; d++) {
         cnt[d].release(); base[d].release(); c_vert[d].release(); c_loc[d].release();
