@@ -3701,6 +3701,9 @@ dms_status lazy_scratch(Ctx &c, LazyScratch &s, int hcap, int hashcap, int64_t n
     return DMS_OK;
 }
 
+dms_status order_by_vertex(Ctx &c, const int32_t *vert, const int32_t *idx, int64_t n, int slot,
+                           const int32_t **perm);
+
 template <typename T, bool B>
 dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const uint8_t *is_row) {
     Pipeline &P = c.P;
@@ -3715,7 +3718,13 @@ dms_status reduce_lazy(Ctx &c, const T *values, int64_t ncols, int64_t n1, const
     DMS_CUDA(cudaMemsetAsync(P.d1_stamp.p, 0xFF, 4 * ncols + 4, c.s));
     DMS_CUDA(cudaMemsetAsync(P.d1_astamp.p, 0xFF, 4 * ncols + 4, c.s));
     DMS_CUDA(cudaMemsetAsync(P.d1_len.p, 0xFF, 4 * ncols + 4, c.s));   // -1: not yet listed
-    DMS_LAUNCH(ncols, 256, k_iota32, P.d1_act.as<int32_t>(), ncols);
+    {
+        // the first advances in vertex-id order (nearby walks share their records)
+        const int32_t *corder = nullptr;
+        DMS_TRY(order_by_vertex(c, P.c_vert[2].as<int32_t>(), P.d1_colmap.as<int32_t>(), ncols, 1,
+                                &corder));
+        DMS_CUDA(cudaMemcpyAsync(P.d1_act.p, corder, 4 * ncols, cudaMemcpyDeviceToDevice, c.s));
+    }
     DMS_CUDA(cudaMemsetAsync(&c.st->misc[0], 0, 4 * sizeof(long long), c.s));
     DMS_CUDA(cudaMemsetAsync(&c.st->red_io[0], 0, 2 * sizeof(long long), c.s));
     DMS_CUDA(cudaMemsetAsync(&c.st->pool_top, 0, sizeof(unsigned long long), c.s));
