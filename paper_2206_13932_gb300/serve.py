@@ -32,6 +32,26 @@ def request_bytes(n_vertices: int, itemsize: int) -> int:
     return int(n_vertices) * (itemsize + 1 + 4 + 48 + 96)
 
 
+def select_batch(pending, in_flight: int, budget: int, max_batch: int):
+    """Admission: how many of the pending requests (a list of (vertices,
+    dtype) in arrival order) start now, and their bytes.  The oldest ones that
+    fit the free budget, up to max_batch, all of the head's dtype; nothing
+    overtakes a head request that does not fit, so it is never starved."""
+    k, need = 0, 0
+    for size, dtype in pending:
+        dt = np.dtype(dtype)
+        if k and dt != np.dtype(pending[0][1]):
+            break
+        r = request_bytes(size, dt.itemsize)
+        if in_flight + need + r > budget:
+            break
+        k += 1
+        need += r
+        if k == max_batch:
+            break
+    return k, need
+
+
 @dataclass(order=True)
 class Request:
     arrival: float
@@ -83,26 +103,16 @@ class DiagramServer:
             t.join()
 
     def _take(self):
-        """The oldest pending requests that fit the free budget: up to
-        max_batch of them, in arrival order and of the head's dtype (a large
-        head request waits until enough memory is free)."""
+        """The next batch to run (see select_batch), waiting until one fits."""
         with self._cv:
             while True:
                 if self._stop and not self._pending:
                     return None
-                take, need = [], 0
-                for req in self._pending:
-                    if take and req.values.dtype != take[0].values.dtype:
-                        break
-                    r = request_bytes(req.values.size, req.values.dtype.itemsize)
-                    if self._in_flight_bytes + need + r > self.mem_budget:
-                        break
-                    take.append(req)
-                    need += r
-                    if len(take) == self.max_batch:
-                        break
-                if take:
-                    del self._pending[:len(take)]
+                k, need = select_batch([(r.values.size, r.values.dtype) for r in self._pending],
+                                       self._in_flight_bytes, self.mem_budget, self.max_batch)
+                if k:
+                    take = self._pending[:k]
+                    del self._pending[:k]
                     self._in_flight_bytes += need
                     return take, need
                 self._cv.wait(0.05)

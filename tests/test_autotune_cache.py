@@ -1,0 +1,34 @@
+"""Host side of the autotuner (no GPU): candidate validity, cache keys and
+the JSON cache."""
+import numpy as np
+
+from paper_2206_13932_gb300 import autotune as at
+
+
+def test_defaults_and_candidates_are_valid_settings():
+    assert len(at.DEFAULT) == len(at.TUNABLES)
+    assert at.valid(at.DEFAULT)
+    for k, name in enumerate(at.TUNABLES):
+        assert at.DEFAULT[k] in at.CANDIDATES[name]
+        for cand in at.CANDIDATES[name]:
+            vals = tuple(cand if i == k else x for i, x in enumerate(at.DEFAULT))
+            assert at.valid(vals), (name, cand)
+
+
+def test_trace_threads_must_be_whole_blocks():
+    vals = list(at.DEFAULT)
+    vals[at.TUNABLES.index("trace_block")] = 256
+    vals[at.TUNABLES.index("trace_per_sm")] = 128
+    assert not at.valid(vals)
+
+
+def test_cache_round_trip(tmp_path):
+    path = str(tmp_path / "tune.json")
+    k1 = at.cache_key(np.float32, 256 ** 3, 0)
+    k2 = at.cache_key(np.uint16, 512 ** 3, 3)
+    assert k1 != k2 and at.cache_key(np.float32, 256 ** 3 + 5, 0) == k1
+    assert at.load(path, k1) is None
+    at.save(path, k1, at.DEFAULT)
+    at.save(path, k2, tuple(reversed(at.DEFAULT)))
+    assert at.load(path, k1) == at.DEFAULT
+    assert at.load(path, k2) == tuple(reversed(at.DEFAULT))

@@ -1,0 +1,38 @@
+"""Admission of the diagram server (host logic, no GPU): arrival order, the
+memory budget, the batch cap and one dtype per batch."""
+import numpy as np
+
+from paper_2206_13932_gb300.serve import request_bytes, select_batch
+
+
+def _req(n, dt=np.float32):
+    return (n, np.dtype(dt))
+
+
+def test_oldest_requests_within_budget_and_cap():
+    pend = [_req(1000), _req(2000), _req(3000), _req(4000)]
+    b = request_bytes(1000, 4) + request_bytes(2000, 4) + request_bytes(3000, 4)
+    assert select_batch(pend, 0, b, 8) == (3, b)
+    assert select_batch(pend, 0, 10 ** 12, 2) == (2, request_bytes(1000, 4) + request_bytes(2000, 4))
+    assert select_batch(pend, 0, 10 ** 12, 1) == (1, request_bytes(1000, 4))
+
+
+def test_head_that_does_not_fit_blocks_the_queue():
+    pend = [_req(10 ** 6), _req(10)]
+    small = request_bytes(10, 4)
+    # the small request behind a large head waits: no overtaking
+    assert select_batch(pend, 0, request_bytes(10 ** 6, 4) - 1, 8) == (0, 0)
+    # memory in flight counts against the budget
+    assert select_batch([_req(10)], 10 ** 9, 10 ** 9 + small - 1, 8) == (0, 0)
+    assert select_batch([_req(10)], 10 ** 9, 10 ** 9 + small, 8) == (1, small)
+
+
+def test_one_dtype_per_batch():
+    pend = [_req(100), _req(100), _req(100, np.uint16), _req(100)]
+    assert select_batch(pend, 0, 10 ** 12, 8)[0] == 2
+    assert select_batch(pend[2:], 0, 10 ** 12, 8)[0] == 1
+
+
+def test_request_bytes_grows_with_size_and_itemsize():
+    assert request_bytes(100, 4) > request_bytes(100, 2)
+    assert request_bytes(200, 4) == 2 * request_bytes(100, 4)
