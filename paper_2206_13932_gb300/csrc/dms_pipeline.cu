@@ -1697,6 +1697,8 @@ __device__ int block_symdiff(const int32_t *A, int la, const int32_t *B, int lb,
 // with merges through the global pool.
 constexpr int kRedBlock = 512, kRedAcc = 24576, kRedStage = 4096;
 constexpr size_t kRedSmem = sizeof(int32_t) * (2 * kRedAcc + kRedStage);
+constexpr int kAsyncBlock = 256, kAsyncAcc = 12288, kAsyncStage = 2048;
+constexpr size_t kAsyncSmem = sizeof(int32_t) * (2 * kAsyncAcc + kAsyncStage);
 __global__ void __launch_bounds__(kRedBlock)
     k_red_add_block(const int32_t *__restrict__ active, int64_t nactive,
                     const int32_t *__restrict__ recheck, int64_t *start, int32_t *len,
@@ -1914,14 +1916,15 @@ __device__ __forceinline__ void aq_push(AsyncQ *q, int32_t *queue, unsigned int 
     __threadfence();
 }
 
-__global__ void __launch_bounds__(kRedBlock)
+template <int NT, int ACC, int STAGE>
+__global__ void __launch_bounds__(NT)
     k_red_async(AsyncQ *q, int32_t *queue, unsigned int qcap, int32_t *owner,
                 unsigned long long *info, int64_t *start, int32_t *len, int32_t *pool,
                 int64_t pool_cap, DevStatus *st) {
     extern __shared__ int32_t smem[];
-    int32_t *acc[2] = {smem, smem + kRedAcc};
-    int32_t *sB = smem + 2 * kRedAcc;
-    __shared__ int sscan[kRedBlock / 32];
+    int32_t *acc[2] = {smem, smem + ACC};
+    int32_t *sB = smem + 2 * ACC;
+    __shared__ int sscan[NT / 32];
     __shared__ int32_t s_cj, s_o, s_state;
     __shared__ unsigned long long s_rec, s_pos;
     const int t = threadIdx.x;
@@ -1958,10 +1961,10 @@ __global__ void __launch_bounds__(kRedBlock)
         __syncthreads();
         int la = (int)(uint32_t)(s_rec & 0xffffffffull);
         int64_t sa = (int64_t)(s_rec >> 32);
-        bool resident = la <= kRedAcc;
+        bool resident = la <= ACC;
         int cur = 0;
         if (resident) {
-            for (int k = t; k < la; k += kRedBlock) acc[0][k] = __ldcg(pool + sa + k);
+            for (int k = t; k < la; k += NT) acc[0][k] = __ldcg(pool + sa + k);
             __syncthreads();
         }
         // state: 0 working, 1 done, 2 stopped (pool full: requeued)
@@ -1986,17 +1989,17 @@ __global__ void __launch_bounds__(kRedBlock)
                 __syncthreads();
                 const int lb = (int)(uint32_t)(s_rec & 0xffffffffull);
                 const int32_t *B = pool + (int64_t)(s_rec >> 32);
-                const bool staged = lb <= kRedStage;
+                const bool staged = lb <= STAGE;
                 if (staged) {
-                    for (int k = t; k < lb; k += kRedBlock) sB[k] = __ldcg(B + k);
+                    for (int k = t; k < lb; k += NT) sB[k] = __ldcg(B + k);
                     B = sB;
                 }
                 io_r += (unsigned long long)(la + lb);
-                if (resident && la + lb <= kRedAcc) {
+                if (resident && la + lb <= ACC) {
                     __syncthreads();
-                    la = staged ? block_symdiff_g<kRedBlock, false, false>(acc[cur], la, B, lb,
+                    la = staged ? block_symdiff_g<NT, false, false>(acc[cur], la, B, lb,
                                                                            acc[cur ^ 1], sscan)
-                                : block_symdiff_g<kRedBlock, false, true>(acc[cur], la, B, lb,
+                                : block_symdiff_g<NT, false, true>(acc[cur], la, B, lb,
                                                                           acc[cur ^ 1], sscan);
                     cur ^= 1;
                 } else {
@@ -2010,14 +2013,14 @@ __global__ void __launch_bounds__(kRedBlock)
                     }
                     __syncthreads();
                     if (resident)
-                        la = staged ? block_symdiff_g<kRedBlock, false, false>(acc[cur], la, B, lb,
+                        la = staged ? block_symdiff_g<NT, false, false>(acc[cur], la, B, lb,
                                                                                pool + pos, sscan)
-                                    : block_symdiff_g<kRedBlock, false, true>(acc[cur], la, B, lb,
+                                    : block_symdiff_g<NT, false, true>(acc[cur], la, B, lb,
                                                                               pool + pos, sscan);
                     else
-                        la = staged ? block_symdiff_g<kRedBlock, true, false>(pool + sa, la, B, lb,
+                        la = staged ? block_symdiff_g<NT, true, false>(pool + sa, la, B, lb,
                                                                               pool + pos, sscan)
-                                    : block_symdiff_g<kRedBlock, true, true>(pool + sa, la, B, lb,
+                                    : block_symdiff_g<NT, true, true>(pool + sa, la, B, lb,
                                                                              pool + pos, sscan);
                     sa = (int64_t)pos;
                     resident = false;
@@ -2038,7 +2041,7 @@ __global__ void __launch_bounds__(kRedBlock)
                     state = 2;
                     break;
                 }
-                for (int k = t; k < la; k += kRedBlock) pool[pos + k] = acc[cur][k];
+                for (int k = t; k < la; k += NT) pool[pos + k] = acc[cur][k];
                 sa = (int64_t)pos;
                 resident = false;
                 __threadfence();
@@ -2057,10 +2060,10 @@ __global__ void __launch_bounds__(kRedBlock)
             state = s_state;
             // on a lost race the owner is read again; the list stays in the pool
             if (state == 0) {
-                resident = la <= kRedAcc;
+                resident = la <= ACC;
                 if (resident) {
                     cur = 0;
-                    for (int k = t; k < la; k += kRedBlock) acc[0][k] = __ldcg(pool + sa + k);
+                    for (int k = t; k < la; k += NT) acc[0][k] = __ldcg(pool + sa + k);
                     __syncthreads();
                 }
             }
@@ -3344,8 +3347,8 @@ dms_status ensure_tables(int device) {
     build_regular_lut(S, lut);
     DMS_CUDA(cudaMemcpyToSymbol(g_star, &S, sizeof S));
     DMS_CUDA(cudaMemcpyToSymbol(g_regular, lut.data(), lut.size() * sizeof(uint32_t)));
-    DMS_CUDA(cudaFuncSetAttribute(k_red_async, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kRedSmem));
+    DMS_CUDA(cudaFuncSetAttribute(k_red_async<kAsyncBlock, kAsyncAcc, kAsyncStage>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAsyncSmem));
     DMS_CUDA(cudaFuncSetAttribute(k_red_add_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kRedSmem));
     if (device < 32) g_tables_ready |= 1u << device;
@@ -3501,7 +3504,9 @@ dms_status reduce_tail_async(Ctx &c, int64_t ncol, int64_t *nactive, int64_t poo
     DMS_CUDA(cudaMemcpyAsync(P.d1_queue.p, P.d1_act.p, 4 * n0, cudaMemcpyDeviceToDevice, c.s));
     AsyncQ q0{0u, (unsigned int)n0, (int)n0, 0};
     DMS_CUDA(cudaMemcpyAsync(P.d1_aq.p, &q0, sizeof q0, cudaMemcpyHostToDevice, c.s));
-    k_red_async<<<152, kRedBlock, kRedSmem, c.s>>>(
+    // 2 blocks of 256 threads per SM, each holding up to 12 K-entry columns in
+    // shared memory (larger ones merge through the pool)
+    k_red_async<kAsyncBlock, kAsyncAcc, kAsyncStage><<<2 * 152, kAsyncBlock, kAsyncSmem, c.s>>>(
         P.d1_aq.as<AsyncQ>(), P.d1_queue.as<int32_t>(), (unsigned int)qcap,
         P.d1_owner.as<int32_t>(), P.d1_info.as<unsigned long long>(), P.d1_start.as<int64_t>(),
         P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), pool_cap, c.st);
