@@ -922,20 +922,28 @@ __device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
     return (uint32_t)k;
 }
 
+// One slot of the (segment, label) table: the key, the union-find parent (a
+// slot index) and the label the slot stands for, in one 16-byte line so that
+// a probe, a find step and a label read touch one sector.
+struct DcSlot {
+    unsigned long long key;   // ~0: empty
+    int32_t par, lab;
+};
+
 __device__ __forceinline__ int64_t dc_time(int64_t j, int64_t narcs, int descending) {
     return descending ? narcs - 1 - j : j;
 }
 
 // slot of key (inserting it if absent); -1 if the table is full
-__device__ __forceinline__ int32_t dc_insert(unsigned long long *keys, uint32_t mask,
-                                             unsigned long long key, bool *fresh) {
+__device__ __forceinline__ int32_t dc_insert(DcSlot *tab, uint32_t mask, unsigned long long key,
+                                             bool *fresh) {
     uint32_t h = hash_key(key) & mask;
     for (uint32_t p = 0; p <= mask; p++) {
         uint32_t s = (h + p) & mask;
-        unsigned long long k = keys[s];
+        unsigned long long k = tab[s].key;
         if (k == key) { *fresh = false; return (int32_t)s; }
         if (k == ~0ull) {
-            unsigned long long old = atomicCAS(&keys[s], ~0ull, key);
+            unsigned long long old = atomicCAS(&tab[s].key, ~0ull, key);
             if (old == ~0ull) { *fresh = true; return (int32_t)s; }
             if (old == key) { *fresh = false; return (int32_t)s; }
         }
@@ -943,52 +951,55 @@ __device__ __forceinline__ int32_t dc_insert(unsigned long long *keys, uint32_t 
     return -1;
 }
 
-__device__ __forceinline__ int32_t dc_lookup(const unsigned long long *keys, uint32_t mask,
+__device__ __forceinline__ int32_t dc_lookup(const DcSlot *tab, uint32_t mask,
                                              unsigned long long key) {
     uint32_t h = hash_key(key) & mask;
     for (uint32_t p = 0; p <= mask; p++) {
         uint32_t s = (h + p) & mask;
-        unsigned long long k = keys[s];
+        unsigned long long k = tab[s].key;
         if (k == key) return (int32_t)s;
         if (k == ~0ull) return -1;
     }
     return -1;
 }
 
-__device__ __forceinline__ int32_t dc_find(int32_t *par, int32_t a) {
+__device__ __forceinline__ int32_t dc_find(DcSlot *tab, int32_t a) {
     while (true) {
-        int32_t p = par[a];
+        int32_t p = tab[a].par;
         if (p == a) return a;
-        int32_t gp = par[p];
-        if (gp != p) par[a] = gp;
+        int32_t gp = tab[p].par;
+        if (gp != p) tab[a].par = gp;
         a = gp;
     }
 }
 
-// light arcs of each segment: register both endpoint labels
+// light arcs of each segment: register both endpoint labels.  An arc whose
+// two ends already carry the same label joins nothing: its label is left out
+// (a heavy arc looking it up keeps it, as its component in the light half
+// is then itself or is registered by another arc).
 __global__ void k_dc_insert(int64_t narcs, int shift, int descending, const int32_t *A,
-                            const int32_t *B, unsigned long long *keys, int32_t *par,
-                            int32_t *lab, uint32_t mask, DevStatus *st) {
+                            const int32_t *B, DcSlot *tab, uint32_t mask, DevStatus *st) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= narcs) return;
     int64_t t = dc_time(j, narcs, descending);
     int64_t seg = t >> shift;
     if ((t >> (shift - 1)) & 1) return;                  // heavy half
     int32_t ab[2] = {A[j], B[j]};
+    if (ab[0] == ab[1]) return;
     for (int e = 0; e < 2; e++) {
         unsigned long long key = ((unsigned long long)seg << 32) | (uint32_t)ab[e];
         bool fresh;
-        int32_t s = dc_insert(keys, mask, key, &fresh);
+        int32_t s = dc_insert(tab, mask, key, &fresh);
         if (s < 0) { atomicOr(&st->err, kErrCap); return; }
-        if (fresh) { par[s] = s; lab[s] = ab[e]; }
+        if (fresh) { tab[s].par = s; tab[s].lab = ab[e]; }
     }
 }
 
 // light arcs: union their endpoints; a root is hooked under the root holding
 // the older label (smaller for D0, larger for D2)
 __global__ void k_dc_union(int64_t narcs, int shift, int descending, int older_is_larger,
-                           const int32_t *A, const int32_t *B, const unsigned long long *keys,
-                           int32_t *par, const int32_t *lab, uint32_t mask, DevStatus *st) {
+                           const int32_t *A, const int32_t *B, DcSlot *tab, uint32_t mask,
+                           DevStatus *st) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= narcs) return;
     int64_t t = dc_time(j, narcs, descending);
@@ -996,23 +1007,23 @@ __global__ void k_dc_union(int64_t narcs, int shift, int descending, int older_i
     if ((t >> (shift - 1)) & 1) return;
     int32_t a = A[j], b = B[j];
     if (a == b) return;
-    int32_t sa = dc_lookup(keys, mask, ((unsigned long long)seg << 32) | (uint32_t)a);
-    int32_t sb = dc_lookup(keys, mask, ((unsigned long long)seg << 32) | (uint32_t)b);
+    int32_t sa = dc_lookup(tab, mask, ((unsigned long long)seg << 32) | (uint32_t)a);
+    int32_t sb = dc_lookup(tab, mask, ((unsigned long long)seg << 32) | (uint32_t)b);
     if (sa < 0 || sb < 0) { atomicOr(&st->err, kErrState); return; }
     for (int it = 0; it < (1 << 20); it++) {
-        int32_t ra = dc_find(par, sa), rb = dc_find(par, sb);
+        int32_t ra = dc_find(tab, sa), rb = dc_find(tab, sb);
         if (ra == rb) return;
-        bool a_older = older_is_larger ? lab[ra] > lab[rb] : lab[ra] < lab[rb];
+        const int32_t la = tab[ra].lab, lb = tab[rb].lab;
+        bool a_older = older_is_larger ? la > lb : la < lb;
         int32_t young = a_older ? rb : ra, old = a_older ? ra : rb;
-        if (atomicCAS(&par[young], young, old) == young) return;
+        if (atomicCAS(&tab[young].par, young, old) == young) return;
     }
     atomicOr(&st->err, kErrIter);
 }
 
 // heavy arcs: relabel endpoints by the light half's components
 __global__ void k_dc_relabel(int64_t narcs, int shift, int descending, int32_t *A, int32_t *B,
-                             const unsigned long long *keys, int32_t *par, const int32_t *lab,
-                             uint32_t mask) {
+                             DcSlot *tab, uint32_t mask) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= narcs) return;
     int64_t t = dc_time(j, narcs, descending);
@@ -1020,8 +1031,8 @@ __global__ void k_dc_relabel(int64_t narcs, int shift, int descending, int32_t *
     if (!((t >> (shift - 1)) & 1)) return;               // light half
     int32_t *ends[2] = {&A[j], &B[j]};
     for (int e = 0; e < 2; e++) {
-        int32_t s = dc_lookup(keys, mask, ((unsigned long long)seg << 32) | (uint32_t)*ends[e]);
-        if (s >= 0) *ends[e] = lab[dc_find(par, s)];
+        int32_t s = dc_lookup(tab, mask, ((unsigned long long)seg << 32) | (uint32_t)*ends[e]);
+        if (s >= 0) *ends[e] = tab[dc_find(tab, s)].lab;
     }
 }
 
@@ -3421,21 +3432,17 @@ dms_status elder_rule(Ctx &c, int64_t narcs, int descending, int older_is_larger
     if (narcs == 0) return DMS_OK;
     int L = 0;
     while (((int64_t)1 << L) < narcs) L++;
+    // at most one key per light-arc endpoint per level: a table at most 2/3 full
     uint32_t cap = 1024;
-    while ((int64_t)cap < 2 * narcs + 2) cap <<= 1;
-    DMS_ALLOC(P.dc_keys, 8 * (size_t)cap);
-    DMS_ALLOC(P.dc_par, 4 * (size_t)cap);
-    DMS_ALLOC(P.dc_lab, 4 * (size_t)cap);
-    auto *keys = P.dc_keys.as<unsigned long long>();
-    int32_t *par = P.dc_par.as<int32_t>(), *lab = P.dc_lab.as<int32_t>();
+    while ((int64_t)cap * 2 < 3 * narcs + 2) cap <<= 1;
+    DMS_ALLOC(P.dc_keys, sizeof(DcSlot) * (size_t)cap);
+    DcSlot *tab = P.dc_keys.as<DcSlot>();
     for (int shift = L; shift >= 1; shift--) {
-        DMS_CUDA(cudaMemsetAsync(keys, 0xFF, 8 * (size_t)cap, c.s));
-        DMS_LAUNCH(narcs, 256, k_dc_insert, narcs, shift, descending, A, B, keys, par, lab,
+        DMS_CUDA(cudaMemsetAsync(tab, 0xFF, sizeof(DcSlot) * (size_t)cap, c.s));
+        DMS_LAUNCH(narcs, 256, k_dc_insert, narcs, shift, descending, A, B, tab, cap - 1, c.st);
+        DMS_LAUNCH(narcs, 256, k_dc_union, narcs, shift, descending, older_is_larger, A, B, tab,
                    cap - 1, c.st);
-        DMS_LAUNCH(narcs, 256, k_dc_union, narcs, shift, descending, older_is_larger, A, B, keys,
-                   par, lab, cap - 1, c.st);
-        DMS_LAUNCH(narcs, 256, k_dc_relabel, narcs, shift, descending, A, B, keys, par, lab,
-                   cap - 1);
+        DMS_LAUNCH(narcs, 256, k_dc_relabel, narcs, shift, descending, A, B, tab, cap - 1);
     }
     DMS_LAUNCH(narcs, 256, k_dc_decide, narcs, older_is_larger, A, B, young, died);
     *levels_out = L;
