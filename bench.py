@@ -36,6 +36,19 @@ L2_BYTES = 129 * 2**20
 ORACLE_SAMPLE = 64          # edge of the cube cropped for the oracle (cpu_baseline)
 SERVE_REQUESTS = 128        # requests of the serving workload replayed per run
 SERVE_BATCH = 16            # most requests one batched pass takes
+# DRAM bytes per launch of the classification stencil on this workload, from
+# one ncu capture (profiles/classify_dram_noise256_f32.md), valid only for the
+# kernel sources it was taken on (their sha256); otherwise reported as null.
+CLASSIFY_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+
+
+def _kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("dms_pipeline.cu", "dms_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2206_13932_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 REFERENCE_SAMPLE = 40       # edge of the crop per reference-arm step
 
 
@@ -251,8 +264,10 @@ def run_ours(args):
     src = "measured" if peaks else "fallback"
     cls_bytes = n * s_in + n + 4 * (n // 2048 + 1)      # values in, flag bytes out, tile counts
     cls_gbs = cls_bytes / (kavg["classify"] * 1e-3) / 1e9
+    cls_traffic = (CLASSIFY_TRAFFIC["bytes_per_launch"]
+                   if CLASSIFY_TRAFFIC["sources_sha256"] == _kernel_sources_sha256() else None)
     roof_grad = {"bound": "hbm", "kernel": "k_classify2", "achieved": cls_gbs, "peak": hbm,
-                 "unit": "GB/s", "frac": cls_gbs / hbm, "traffic": None,
+                 "unit": "GB/s", "frac": cls_gbs / hbm, "traffic": cls_traffic,
                  "algorithmic_bytes_per_launch": cls_bytes, "peak_source": src}
     if dom == "d1_reduce":
         red_bytes = stats["d1_bytes_read"] + stats["d1_bytes_written"]
