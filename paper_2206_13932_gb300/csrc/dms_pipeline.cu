@@ -1595,11 +1595,19 @@ __device__ int warp_symdiff(const int32_t *A, int la, const int32_t *B, int lb, 
 // claims happen in k_red_claim), so every column added is stable.  Stops at
 // its own pivot, an unclaimed pivot or one claimed by a later column (those
 // claim it in the next round).  A column listed twice is processed once.
-__global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
-                          const int32_t *__restrict__ recheck, int64_t *start, int32_t *len,
-                          int32_t *pool, const RowCol *__restrict__ rowcol, int32_t *stamp,
-                          int32_t round, int32_t *next, int64_t pool_cap, DevStatus *st) {
+// Short columns stay in the warp's shared memory through their chain (the
+// merge-path searches then probe shared memory, not the pool), and the
+// added column is staged there too; the result is written to the pool once.
+constexpr int kWarpAcc = 256;
+__global__ void __launch_bounds__(256)
+    k_red_add(const int32_t *__restrict__ active, int64_t nactive,
+              const int32_t *__restrict__ recheck, int64_t *start, int32_t *len, int32_t *pool,
+              const RowCol *__restrict__ rowcol, int32_t *stamp, int32_t round, int32_t *next,
+              int64_t pool_cap, DevStatus *st) {
+    __shared__ int32_t wsm[8][3 * kWarpAcc];
     const int lane = threadIdx.x & 31;
+    int32_t *acc[2] = {wsm[threadIdx.x >> 5], wsm[threadIdx.x >> 5] + kWarpAcc};
+    int32_t *stg = wsm[threadIdx.x >> 5] + 2 * kWarpAcc;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nre = *(volatile long long *)&st->misc[0];
@@ -1612,27 +1620,58 @@ __global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
         if (!__shfl_sync(0xffffffffu, fresh, 0)) continue;
         int la = len[cj];
         int64_t sa = start[cj];
+        bool resident = la <= kWarpAcc;
+        int cur = 0;
+        if (resident) {
+            for (int k = lane; k < la; k += 32) acc[0][k] = pool[sa + k];
+            __syncwarp();
+        }
         bool changed = false;
         unsigned chain = 0;
         for (int it = 0; la > 0 && it < (1 << 24); it++) {
-            const RowCol rc = rowcol[pool[sa]];
+            const RowCol rc = rowcol[resident ? acc[cur][0] : pool[sa]];
             const int32_t k = rc.col;
             if (k == cj || k == kNoOwner || k > cj) break;
-            const int64_t sb = rc.start;
             const int lb = rc.len;
-            unsigned long long pos = 0;
-            if (lane == 0) pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
-            pos = __shfl_sync(0xffffffffu, pos, 0);
-            if ((int64_t)(pos + la + lb) > pool_cap) {
-                if (lane == 0) atomicOr(&st->err, kErrCap);
-                break;
+            const int32_t *B = pool + rc.start;
+            if (lb <= kWarpAcc) {
+                for (int t = lane; t < lb; t += 32) stg[t] = B[t];
+                __syncwarp();
+                B = stg;
             }
             io_r += (unsigned long long)(la + lb);
-            la = warp_symdiff(pool + sa, la, pool + sb, lb, pool + pos);
+            if (resident && la + lb <= kWarpAcc) {
+                la = warp_symdiff(acc[cur], la, B, lb, acc[cur ^ 1]);
+                cur ^= 1;
+            } else {
+                unsigned long long pos = 0;
+                if (lane == 0) pos = atomicAdd(&st->pool_top, (unsigned long long)(la + lb));
+                pos = __shfl_sync(0xffffffffu, pos, 0);
+                if ((int64_t)(pos + la + lb) > pool_cap) {
+                    if (lane == 0) atomicOr(&st->err, kErrCap);
+                    break;
+                }
+                la = warp_symdiff(resident ? acc[cur] : pool + sa, la, B, lb, pool + pos);
+                sa = (int64_t)pos;
+                resident = false;
+            }
+            __syncwarp();
             io_w += (unsigned long long)la;
-            sa = (int64_t)pos;
             changed = true;
             chain++;
+        }
+        if (changed && resident) {
+            // the chain ended in shared memory: one write to the pool
+            unsigned long long pos = 0;
+            if (lane == 0 && la > 0) pos = atomicAdd(&st->pool_top, (unsigned long long)la);
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (la > 0 && (int64_t)(pos + la) > pool_cap) {
+                if (lane == 0) atomicOr(&st->err, kErrCap);
+                changed = false;                 // the column keeps its previous state
+            } else {
+                for (int t = lane; t < la; t += 32) pool[pos + t] = acc[cur][t];
+                sa = (int64_t)pos;
+            }
         }
         adds += chain;
         longest = max(longest, chain);
@@ -1641,6 +1680,7 @@ __global__ void k_red_add(const int32_t *__restrict__ active, int64_t nactive,
             len[cj] = la;
             if (la > 0) next[atomicAdd((unsigned long long *)&st->misc[1], 1ull)] = cj;
         }
+        __syncwarp();
     }
     if (lane == 0 && adds) {
         atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)adds);
