@@ -1256,7 +1256,9 @@ __device__ HeapEnt heap_pop(TraceCtx &c) {
 // regular edge is pushed on the max-heap keyed by (vertex order of its
 // maximum vertex y, classification order inside the lower star of y), which is
 // a topological order of the gradient paths, so that every regular edge is
-// expanded at most once.
+// expanded at most once; the two edges its expansion yields are precomputed
+// (the spec in the hash entry), so the expansion reads no record.  The
+// vertex's flag, value and record are loaded together up front.
 template <typename T>
 __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams &g,
                              const T *__restrict__ values, uint8_t *flags, GradRec *grad,
@@ -1264,7 +1266,17 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
                              const int32_t *__restrict__ base1, const uint8_t *__restrict__ is_row,
                              int64_t y, int m, DevStatus *st) {
     if (m < 0 || m >= kLinks) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
-    uint8_t fy = flags[y];
+    const uint8_t fy = ((volatile const uint8_t *)flags)[y];
+    const T vy = values[y];
+    GradRec G;
+    {
+        const ulonglong2 *src = (const ulonglong2 *)&grad[y];
+        for (int k = 0; k < 3; k++) {
+            const ulonglong2 v = __ldcg(src + k);
+            G.w[2 * k] = v.x;
+            G.w[2 * k + 1] = v.y;
+        }
+    }
     if ((fy & 0xF) == m) return;
     unsigned long long key = (((unsigned long long)y << 4) | (unsigned)m) + 1;
     uint32_t hpos = hash64(key) & c.hashmask;
@@ -1294,18 +1306,27 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
             return;
         }
     }
-    GradRec G = grad_get(S, g, values, flags, grad, y);
+    if (!(fy & kFlagGradient)) G = grad_fill(S, g, values, flags, grad, y);
     int sp = grad_edge_pair(G, m);
     if (sp >= kTris) { atomicOr(&st->err, kErrState); return; }
+    // the expansion through triangle sp: the other star edge of y, and the
+    // edge between the triangle's link vertices in the star of the higher one
+    const int ta = S.tri_v[sp][0], tb = S.tri_v[sp][1];
+    const bool aup = grad_rank(G, ta) > grad_rank(G, tb);
+    const int hi = aup ? ta : tb, lo = aup ? tb : ta;
+    const int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
+                               9 * (S.dz[lo] - S.dz[hi] + 1)];
+    if (l < 0) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
+    const uint32_t spec = (uint32_t)(ta == m ? tb : ta) | ((uint32_t)hi << 4) | ((uint32_t)l << 8);
     HeapEnt he;
-    he.hi = (unsigned long long)Key<T>::of(values[y]);
+    he.hi = (unsigned long long)Key<T>::of(vy);
     he.lo = ((unsigned long long)y << 12) | ((unsigned long long)grad_edge_order(G, m) << 4) |
             (unsigned)m;
     heap_push(c, he);
     if (c.overflow) return;
     slot->key = key;
     slot->gen = c.gen;
-    slot->info = hinfo(0, sp, kKindReg, 1);
+    slot->info = hinfo(spec, sp, kKindReg, 1);
     c.used++;
 }
 
@@ -1422,9 +1443,11 @@ __global__ void __launch_bounds__(256, 4)
             HashEnt *e = trace_find(c, y, m);
             if (!e || !hinfo_parity(e->info)) continue;
             e->info &= ~(1u << 31);
-            const GradRec G = grad_get(S, *gp, values, flags, grad, y);
-            trace_expand<T>(c, S, *gp, values, flags, grad, vrank, recs, base1, is_row, y,
-                            hinfo_pair(e->info), m, G, st);
+            const uint32_t spec = hinfo_aux(e->info);
+            trace_toggle<T>(c, S, *gp, values, flags, grad, vrank, recs, base1, is_row, y,
+                            (int)(spec & 15), st);
+            trace_toggle<T>(c, S, *gp, values, flags, grad, vrank, recs, base1, is_row,
+                            y + gp->dlin[(spec >> 4) & 15], (int)((spec >> 8) & 15), st);
             continue;
         }
         // the column is complete (or outgrew the scratch): write it out
