@@ -4132,7 +4132,7 @@ dms_status launch_pls(Ctx &c, const T *values, const Geo<B> &geo, const int32_t 
     uint8_t *fl = P.flags.as<uint8_t>();
     GradRec *gr = P.grad.as<GradRec>();
     if (sorted) {
-        k_pls_sorted<T, B, 512><<<blocks_for(count, 512), 512, 0, c.s>>>(values, geo, list, count,
+        k_pls_sorted<T, B, 1024><<<blocks_for(count, 1024), 1024, 0, c.s>>>(values, geo, list, count,
                                                                         fl, gr);
     } else {
         const int nt = P.tune[DMS_TUNE_PLS_BLOCK];
