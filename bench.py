@@ -39,8 +39,8 @@ SERVE_BATCH = 16            # most requests one batched pass takes
 # DRAM bytes per launch of the classification stencil on this workload, from
 # one ncu capture (profiles/classify_dram_noise256_f32.md), valid only for the
 # kernel sources it was taken on (their sha256); otherwise reported as null.
-CLASSIFY_TRAFFIC = {"sources_sha256": "fbd26d6788beb12a711be01383c305f238a61a2938f5892f3b9788e937ad67a6",
-                    "bytes_per_launch": 67180288 + 7354624}
+CLASSIFY_TRAFFIC = {"sources_sha256": "9a7648ef420e25420decd7acc1df81148d7e7b1d5ee343242f97fc54f9d3c646",
+                    "bytes_per_launch": 67167232 + 6994176}
 
 
 def _kernel_sources_sha256():
