@@ -34,7 +34,7 @@ METRIC = "full-diagram Mvertices/s"
 UNIT = "Mvertices/s"
 L2_BYTES = 129 * 2**20
 ORACLE_SAMPLE = 64          # edge of the cube cropped for the oracle (cpu_baseline)
-SERVE_REQUESTS = 128        # requests of the serving workload replayed per run
+SERVE_REQUESTS = 1024       # requests of the serving workload replayed per run
 SERVE_BATCH = 16            # most requests one batched pass takes
 # DRAM bytes per launch of the classification stencil on this workload, from
 # one ncu capture (profiles/classify_dram_noise256_f32.md), valid only for the
