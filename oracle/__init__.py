@@ -15,11 +15,20 @@ Functions (all CPU, all exact):
   Edelsbrunner sub-level-set method), elder rule.
 - :func:`kruskal_d2` -- D2 by union-find on the dual graph with a virtual
   maximum on the outer boundary (Sec. 5.2).
+- :func:`sandwich` -- the method's own steps (``sandwich.c``): discrete
+  gradient (Alg. 2), D0 and D2 by v-paths and union-find (Sec. 5), D1 by
+  Alg. 3 with homologous propagation, with or without the virtual maximum
+  (Sec. 5.2, App. A), and the 1-cycle generators of the D1 pairs (Sec. 8).
+- :func:`gradient` -- the discrete gradient of that first step.
 - :func:`simplex_counts`, :func:`simplex_vertices` -- the id scheme.
 
 Parity of every function here is pinned by tests in ``tests/test_oracle_*.py``
 (brute-force rank formulas, persistent Betti numbers, invariants, worked
-fields); none is unpinned.
+fields).  :func:`sandwich` with the virtual maximum must equal
+:func:`pairsimplices`; its generators are checked against the definition of a
+cycle homologous to the boundary of the death triangle.  Without the virtual
+maximum it is pinned only in part (invariants and the cases where it must
+agree with the default); that part is marked "parity partly pinned".
 """
 from __future__ import annotations
 
@@ -31,14 +40,15 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "pairsimplices.c")
+_SRCS = [os.path.join(_HERE, f) for f in ("pairsimplices.c", "sandwich.c", "complex.h")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 DTYPES = {np.dtype(np.uint16): 0, np.dtype(np.float32): 1, np.dtype(np.float64): 2}
-ERRORS = {1: "invalid argument", 2: "NaN in input", 3: "out of memory"}
+ERRORS = {1: "invalid argument", 2: "NaN in input", 3: "out of memory",
+          4: "internal inconsistency"}
 # result columns
 COLS = ("dim", "birth", "death", "birth_vertex", "death_vertex", "essential",
         "birth_pos", "death_pos")
@@ -47,10 +57,11 @@ COLS = ("dim", "birth", "death", "birth_vertex", "death_vertex", "essential",
 def build(force: bool = False) -> str:
     """Compiles the oracle with gcc into ``oracle/_build/liboracle.so``."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-Wall",
-                               "-o", tmp, _SRC])
+                               "-o", tmp] + [f for f in _SRCS if f.endswith(".c")])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -70,6 +81,13 @@ def _load():
                                                  [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                                   pp64, p64])
             lib.oracle_pairsimplices.restype = ctypes.c_int
+            lib.oracle_sandwich.argtypes = ([ctypes.c_int64] * 3 +
+                                            [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                             pp64, p64, pp64, p64])
+            lib.oracle_sandwich.restype = ctypes.c_int
+            lib.oracle_gradient.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_int,
+                                                                   ctypes.c_void_p, pp64, p64]
+            lib.oracle_gradient.restype = ctypes.c_int
             lib.oracle_simplex_counts.argtypes = [ctypes.c_int64] * 3 + [p64]
             lib.oracle_simplex_counts.restype = ctypes.c_int
             lib.oracle_simplex_vertices.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_int,
@@ -126,6 +144,63 @@ def kruskal_d0(values: np.ndarray) -> np.ndarray:
 def kruskal_d2(values: np.ndarray) -> np.ndarray:
     """D2 by union-find on the dual graph with a virtual maximum."""
     return _call(_load().oracle_kruskal_d2, values)
+
+
+def _take(ptr, n, width):
+    try:
+        if n == 0:
+            return np.zeros((0, width) if width else 0, np.int64)
+        shape = (n, width) if width else (n,)
+        return np.ctypeslib.as_array(ptr, shape=shape).copy()
+    finally:
+        _load().oracle_free(ptr)
+
+
+def sandwich(values: np.ndarray, virtual_max: bool = True):
+    """The diagrams by the method's own steps (``sandwich.c``).
+
+    Returns ``(rows, generators)``: ``rows`` as :func:`pairsimplices` (columns
+    :data:`COLS`, infinite classes flagged), and ``generators`` a dict
+    ``{(birth_edge_id, death_triangle_id): [edge ids]}`` holding, for every D1
+    pair, the cycle on which the homologous propagation of Alg. 3 stopped,
+    in increasing filtration order.
+    """
+    lib = _load()
+    nx, ny, nz, code, arr = _field(values)
+    rows_p = ctypes.POINTER(ctypes.c_int64)()
+    gen_p = ctypes.POINTER(ctypes.c_int64)()
+    n_rows, n_gen = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = lib.oracle_sandwich(nx, ny, nz, code, arr.ctypes.data_as(ctypes.c_void_p),
+                             int(bool(virtual_max)), ctypes.byref(rows_p),
+                             ctypes.byref(n_rows), ctypes.byref(gen_p), ctypes.byref(n_gen))
+    if st:
+        raise ValueError(f"oracle: {ERRORS.get(st, st)}")
+    rows = _take(rows_p, n_rows.value, 8)
+    flat = _take(gen_p, n_gen.value, 0)
+    gens, i = {}, 0
+    while i < len(flat):
+        k = int(flat[i + 2])
+        gens[(int(flat[i]), int(flat[i + 1]))] = [int(e) for e in flat[i + 3:i + 3 + k]]
+        i += 3 + k
+    return rows, gens
+
+
+def gradient(values: np.ndarray) -> np.ndarray:
+    """The discrete gradient of Alg. 2: one ``(dim, id, partner_dim,
+    partner_id)`` row per simplex in lexicographic order (``-1, -1`` for a
+    critical simplex)."""
+    return _call4(_load().oracle_gradient, values)
+
+
+def _call4(fn, values):
+    nx, ny, nz, code, arr = _field(values)
+    out = ctypes.POINTER(ctypes.c_int64)()
+    n = ctypes.c_int64(0)
+    st = fn(nx, ny, nz, code, arr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out),
+            ctypes.byref(n))
+    if st:
+        raise ValueError(f"oracle: {ERRORS.get(st, st)}")
+    return _take(out, n.value, 4)
 
 
 def simplex_counts(nx: int, ny: int, nz: int) -> tuple:

@@ -1,7 +1,7 @@
 """Seeded synthetic scalar fields shaped like the paper's 3D volumes.
 
 The paper benchmarks public volumes resampled to 192^3 plus an elevation and a
-random field (Sec. 8.1).  Those volumes are not available here, so seeded
+random field (Sec. 9.1).  Those volumes are not available here, so seeded
 synthetic fields with the same structure stand in for them: smooth Gaussian
 mixtures (few critical points, long integral lines), white noise (the paper's
 "random" stress case, the largest diagrams) and quantised fields with heavy

@@ -1,7 +1,7 @@
 """Pins of the oracle against what the paper and the mathematics fix.
 
 Every function of ``oracle/`` is checked here against something other than
-itself: closed forms, the paper's worked elevation case (Sec. 8.1), a
+itself: closed forms, the paper's worked elevation case (Sec. 9.1), a
 brute-force rank formula for the pairing, brute-force persistent Betti
 numbers, two textbook union-find special cases, invariants at any size and
 white-noise statistics.
@@ -54,7 +54,7 @@ def test_simplex_ids_match_chain_definition():
         assert got == want
 
 
-# ------------------------------------------ Sec. 8.1: the elevation field
+# ------------------------------------------ Sec. 9.1: the elevation field
 
 def test_elevation_single_bar():
     cases = json.load(open(os.path.join(GOLDEN, "elevation.json")))["cases"]
