@@ -230,7 +230,7 @@ dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, 
  *   DMS_TUNE_PLS_BLOCK        threads per block of ProcessLowerStars
  *                             (32..512, a multiple of 32; default 128)
  *   DMS_TUNE_TRACE_BLOCK      threads per block of the first D1 trace pass
- *                             (32..512, a multiple of 32; default 128)
+ *                             (32..256, a multiple of 32; default 128)
  *   DMS_TUNE_TRACE_PER_SM     first-pass trace threads per SM (a multiple of
  *                             the block, <= 8192; default 2048)
  *   DMS_TUNE_TRACE_HEAP       first-pass trace heap entries per thread
@@ -248,7 +248,7 @@ dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, 
  *                             asynchronous pass (compare-and-swap ownership
  *                             and a device work queue); 0: in rounds
  *                             (default 1)
- *   DMS_TUNE_PLS_SORT         ProcessLowerStars on blocks of 512 stars sorted
+ *   DMS_TUNE_PLS_SORT         ProcessLowerStars on blocks of 1024 stars sorted
  *                             by shape: 0 never, 1 when more than a quarter
  *                             of the vertices are critical (default), 2
  *                             always

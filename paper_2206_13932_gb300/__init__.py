@@ -17,7 +17,7 @@ import numpy as np
 from ._build_lib import LIB as _LIB_PATH
 from ._build_lib import build
 
-__all__ = ["build", "load", "Grid", "diagram", "classify_static", "PAIR_DTYPE", "DmsError",
+__all__ = ["build", "load", "Grid", "Batch", "diagram", "classify_static", "PAIR_DTYPE", "DmsError",
            "STATUS"]
 
 PAIR_DTYPE = np.dtype([("birth_simplex", "<i8"), ("death_simplex", "<i8"),

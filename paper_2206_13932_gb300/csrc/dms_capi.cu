@@ -121,8 +121,10 @@ dms_status dms_get_kernel_ms(dms_grid grid, float ms[12]) {
 
 dms_status dms_set_tuning(dms_grid grid, const int32_t *v, int count) {
     if (!grid || !v || count != DMS_TUNING_COUNT) return DMS_ERR_INVALID_ARG;
-    auto block_ok = [](int32_t b) { return b >= 32 && b <= 512 && b % 32 == 0; };
-    if (!block_ok(v[DMS_TUNE_PLS_BLOCK]) || !block_ok(v[DMS_TUNE_TRACE_BLOCK])) return DMS_ERR_INVALID_ARG;
+    // the trace kernel is compiled for at most 256 threads per block
+    auto block_ok = [](int32_t b, int32_t most) { return b >= 32 && b <= most && b % 32 == 0; };
+    if (!block_ok(v[DMS_TUNE_PLS_BLOCK], 512) || !block_ok(v[DMS_TUNE_TRACE_BLOCK], 256))
+        return DMS_ERR_INVALID_ARG;
     if (v[DMS_TUNE_PLS_SORT] < 0 || v[DMS_TUNE_PLS_SORT] > 2) return DMS_ERR_INVALID_ARG;
     const int32_t per_sm = v[DMS_TUNE_TRACE_PER_SM];
     if (per_sm < v[DMS_TUNE_TRACE_BLOCK] || per_sm > 8192 || per_sm % v[DMS_TUNE_TRACE_BLOCK])

@@ -4122,7 +4122,7 @@ dms_status order_by_vertex(Ctx &c, const int32_t *vert, const int32_t *idx, int6
     return DMS_OK;
 }
 
-// ProcessLowerStars: sorted by star shape in blocks of 512 when `sorted`,
+// ProcessLowerStars: sorted by star shape in blocks of 1024 when `sorted`,
 // else plain with the tuned block size.
 template <typename T, bool B>
 dms_status launch_pls(Ctx &c, const T *values, const Geo<B> &geo, const int32_t *list,

@@ -32,3 +32,15 @@ def test_rank0_prints_one_line_with_the_contract_keys():
 
 def test_other_ranks_exit_quietly():
     assert _run({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_traffic_hash_ignores_comments_only():
+    """The stored DRAM traffic stays valid across comment edits, not code edits."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = 'int f(int a) { // one\n  return a + 1; /* two\n */ }\nconst char *s = "a // b";\n'
+    same = 'int f(int a) {\n  return a + 1; /* changed */ }\n// new line\nconst char *s = "a // b";\n'
+    other = 'int f(int a) { // one\n  return a + 2; }\nconst char *s = "a // b";\n'
+    assert bench._code_only(src) == bench._code_only(same)
+    assert bench._code_only(src) != bench._code_only(other)
+    assert '"a // b"' in bench._code_only(src)
