@@ -21,6 +21,7 @@ Every check compares it with something other than itself:
   interior simplices changes; the highest maximum becomes an infinite class;
   every critical simplex is paired or infinite exactly once.
 """
+import itertools
 import zlib
 
 import numpy as np
@@ -87,6 +88,19 @@ def test_sandwich_equals_standard_reduction_larger(name):
     rows, gens = oracle.sandwich(v)
     assert _pairs(rows) == _pairs(oracle.pairsimplices(v))
     assert set(gens) == {(int(r[1]), int(r[2])) for r in rows if r[0] == 1 and not r[5]}
+
+
+def test_sandwich_equals_standard_reduction_on_every_order_of_a_cube():
+    """All 8! vertex orders of the 2x2x2 grid: the two oracles agree on every
+    one, and without the virtual maximum D0 stays and the infinite classes
+    still add up to the Euler characteristic."""
+    for perm in itertools.permutations(range(8)):
+        v = np.array(perm, dtype=np.float32).reshape(2, 2, 2)
+        rows, _ = oracle.sandwich(v)
+        assert _pairs(rows) == _pairs(oracle.pairsimplices(v)), perm
+        off, _ = oracle.sandwich(v, virtual_max=False)
+        assert {p for p in _pairs(off) if p[0] == 0} == {p for p in _pairs(rows) if p[0] == 0}
+        assert sum((-1) ** int(r[0]) for r in off if r[5]) == 1
 
 
 def test_sandwich_equals_rank_formula():
