@@ -38,9 +38,9 @@ SERVE_REQUESTS = 1024       # requests of the serving workload replayed per run
 SERVE_BATCH = 16            # most requests one batched pass takes
 # DRAM bytes per launch of the classification stencil on this workload, from
 # one ncu capture (profiles/classify_dram_noise256_f32.md), valid only for the
-# kernel code it was taken on (sha256 of the sources without their comments);
-# otherwise reported as null.
-CLASSIFY_TRAFFIC = {"sources_sha256": "348cbabc2e5003b2bb3cacf1b77dff1575b6a87146b9805c46845233dc4fe5c7",
+# code it was taken on (sha256 of the code behind that kernel, comments
+# excluded: _CLASSIFY_SPANS); otherwise reported as null.
+CLASSIFY_TRAFFIC = {"sources_sha256": "eb26737328563b5ce987eccc9b9472e26eb7afd8df787c6404174cb78de85218",
                     "bytes_per_launch": 67167232 + 6994176}
 
 
@@ -69,16 +69,38 @@ def _code_only(src: str) -> str:
     return " ".join("".join(out).split())
 
 
+# The code that decides the classification kernel's DRAM traffic, as
+# (start, end) markers in dms_pipeline.cu: everything up to the end of the
+# classification stage (tables, scan, the kernels), the tiling of its launch,
+# and the launch itself.  dms_common.cuh counts whole.
+_CLASSIFY_SPANS = (("", "stage 2: stable LSD radix sort"), ("struct ClsTiling", "struct Ctx"),
+                   ("k_classify2<T><<<", ");"))
+
+
+def _classify_code_of(pipeline_src: str, common_src: str):
+    """Comment-free text of the code behind the classification kernel, or None
+    when a marker is missing."""
+    parts = [common_src]
+    for a, b in _CLASSIFY_SPANS:
+        i = pipeline_src.find(a) if a else 0
+        j = pipeline_src.find(b, i + len(a)) if i >= 0 else -1
+        if i < 0 or j < 0:
+            return None
+        parts.append(pipeline_src[i:j + len(b)])
+    return "\0".join(_code_only(p) for p in parts)
+
+
 def _kernel_sources_sha256():
-    """Hash of the code (comments excluded) of the kernel sources: the stored
-    DRAM traffic is reported only while it matches."""
+    """Hash of the code (comments excluded) behind the classification kernel:
+    the stored DRAM traffic is reported only while it matches."""
     import hashlib
-    h = hashlib.sha256()
-    for f in ("dms_pipeline.cu", "dms_common.cuh"):
-        with open(os.path.join(ROOT, "paper_2206_13932_gb300", "csrc", f)) as fh:
-            h.update(_code_only(fh.read()).encode())
-        h.update(b"\0")
-    return h.hexdigest()
+    csrc = os.path.join(ROOT, "paper_2206_13932_gb300", "csrc")
+    with open(os.path.join(csrc, "dms_pipeline.cu")) as f:
+        pipeline_src = f.read()
+    with open(os.path.join(csrc, "dms_common.cuh")) as f:
+        common_src = f.read()
+    code = _classify_code_of(pipeline_src, common_src)
+    return None if code is None else hashlib.sha256(code.encode()).hexdigest()
 
 
 REFERENCE_SAMPLE = 40       # edge of the crop per reference-arm step

@@ -46,7 +46,7 @@ typedef enum {
     DMS_ERR_CUDA = 4,          /* a CUDA runtime call failed                 */
     DMS_ERR_ITER_LIMIT = 5,    /* a bounded device loop hit its limit        */
     DMS_ERR_STATE = 6,         /* no result available / inconsistent result  */
-    DMS_ERR_CAPACITY = 7       /* a per-item scratch limit was exceeded      */
+    DMS_ERR_CAPACITY = 7       /* a scratch or index limit was exceeded      */
 } dms_status;
 
 typedef enum { DMS_U16 = 0, DMS_F32 = 1, DMS_F64 = 2 } dms_dtype;
@@ -137,7 +137,10 @@ dms_status dms_grid_reshape(dms_grid grid, int64_t nx, int64_t ny, int64_t nz);
  * must stay valid until `stream` (a cudaStream_t, NULL = legacy default)
  * reaches the end of the call; = 1: a host pointer, copied in on `stream`.
  * The call returns after the result is resident on the device (it
- * synchronises `stream`).  NaN in the field -> DMS_ERR_NAN. */
+ * synchronises `stream`).  NaN in the field -> DMS_ERR_NAN.  Critical
+ * simplices are indexed in int32: a field (or batch) with more than
+ * (2^31 - 1) / 12 = 178956970 PL-critical vertices -> DMS_ERR_CAPACITY (a
+ * lower star holds at most 12 critical cells). */
 dms_status dms_compute_diagram(dms_grid grid, const void *values, int values_on_host,
                                void *stream);
 

@@ -3340,6 +3340,10 @@ inline int hash_cap_for(int heap) {
     return h;
 }
 
+// Most PL-critical vertices of one compute: 12 critical cells at most per
+// lower star must keep every critical-simplex index below 2^31.
+constexpr int64_t kMaxCriticalVertices = (((int64_t)1 << 31) - 1) / 12;
+
 // Tiling of the tier-1 stencil: R whole rows per block, at least 2048
 // vertices per tile.
 struct ClsTiling {
@@ -4182,6 +4186,11 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     DMS_TRY(sync_status(c));
     const int64_t nc = c.hst->total[0];
     P.n_crit = nc;
+    // Critical simplices are indexed and scanned in int32.  A lower star
+    // holds at most 1 + 5 + 5 + 1 critical cells (the largest reduced Betti
+    // numbers of a lower link), so up to (2^31 - 1) / 12 PL-critical
+    // vertices every index, per dimension and over all of them, fits.
+    if (nc > kMaxCriticalVertices) return DMS_ERR_CAPACITY;
     DMS_ALLOC(P.vc, 4 * nc + 4);
     DMS_ALLOC(P.vc_tmp, 4 * nc + 4);
     DMS_ALLOC(P.keys, sizeof(K) * nc + 8);

@@ -44,3 +44,22 @@ def test_traffic_hash_ignores_comments_only():
     assert bench._code_only(src) == bench._code_only(same)
     assert bench._code_only(src) != bench._code_only(other)
     assert '"a // b"' in bench._code_only(src)
+
+
+def test_traffic_hash_covers_the_classification_code_only():
+    """A change outside the classification code keeps the stored traffic; a
+    change inside it, or a lost marker, drops it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(os.path.join(ROOT, "paper_2206_13932_gb300", "csrc", "dms_pipeline.cu")) as f:
+        src = f.read()
+    base = bench._classify_code_of(src, "x")
+    assert base is not None
+    outside = src.replace("const int64_t nc = c.hst->total[0];",
+                          "const int64_t nc = c.hst->total[0]; (void)0;")
+    assert outside != src and bench._classify_code_of(outside, "x") == base
+    inside = src.replace("struct ClsTiling {", "struct ClsTiling { int unused;", 1)
+    assert inside != src and bench._classify_code_of(inside, "x") != base
+    assert bench._classify_code_of(src, "y") != base
+    lost = src.replace("stage 2: stable LSD radix sort", "stage 2")
+    assert bench._classify_code_of(lost, "x") is None
