@@ -3340,6 +3340,22 @@ inline int hash_cap_for(int heap) {
     return h;
 }
 
+// Host-side NVTX ranges named after the stages ("dms/gradient", ..., one at
+// a time), so that a profiler can pick out one stage's kernels, e.g.
+// ncu --nvtx --nvtx-include "dms/d1/".  With no tool attached the calls do
+// nothing.
+struct StageRanges {
+    bool open = false;
+    void next(const char *name) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~StageRanges() {
+        if (open) nvtxRangePop();
+    }
+};
+
 // Most PL-critical vertices of one compute: 12 critical cells at most per
 // lower star must keep every critical-simplex index below 2^31.
 constexpr int64_t kMaxCriticalVertices = (((int64_t)1 << 31) - 1) / 12;
@@ -3372,6 +3388,7 @@ struct Ctx {
     cudaEvent_t *ev;    // stage boundaries
     cudaEvent_t *kev;   // kernel family start/end pairs
     int64_t launches = 0;
+    StageRanges nv;     // NVTX range of the current stage
 };
 #define KEV(i) cudaEventRecord(c.kev[i], c.s)
 
@@ -4250,6 +4267,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
                    P.cnt[2].as<int32_t>(), P.cnt[3].as<int32_t>(), P.vrank.as<int32_t>());
     }
     cudaEventRecord(ev[2], c.s);
+    c.nv.next("dms/sort");
 
     // ---- critical simplices C0..C3 in lexicographic order
     for (int d = 0; d < 4; d++)
@@ -4269,6 +4287,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
                P.c_vert[3].as<int32_t>(), P.c_loc[3].as<uint8_t>());
     KEV(9);
     cudaEventRecord(ev[3], c.s);
+    c.nv.next("dms/d0");
 
     // union-find state shared by D0 and D2; results kept for the output
     const int64_t narc_max = std::max(n1, n2);
@@ -4290,6 +4309,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     DMS_TRY(elder_rule(c, n1, 0, 0, young0, died0, &P.rounds_d0));
     KEV(13);
     cudaEventRecord(ev[4], c.s);
+    c.nv.next("dms/d2");
 
     // ---- D2: arcs between maxima (node n3 = the virtual maximum), decreasing
     const int32_t vmax = (int32_t)n3;
@@ -4307,6 +4327,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     KEV(17);
     DMS_TRY(sync_status(c));
     cudaEventRecord(ev[5], c.s);
+    c.nv.next("dms/d1");
 
     // ---- D1: rows = C1 not paired in D0, columns = C2 not paired in D2
     DMS_ALLOC(P.rowcol, n1 + n2 + 16);
@@ -4431,6 +4452,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
         KEV(21);
     }
     cudaEventRecord(ev[6], c.s);
+    c.nv.next("dms/output");
     KEV(22);
 
     // ---- output: per dimension, finite pairs (ordered by the simplex that
@@ -4743,6 +4765,7 @@ dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
     const size_t esz = dtype == DMS_U16 ? 2 : dtype == DMS_F32 ? 4 : 8;
     dms_status s = DMS_OK;
     cudaEventRecord(ev[0], c.s);
+    c.nv.next("dms/h2d");
     const void *dv = values;
     if (on_host) {
         if (!values_dev.ensure(n * esz)) s = DMS_ERR_OOM;
@@ -4752,6 +4775,7 @@ dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
         dv = values_dev.p;
     }
     cudaEventRecord(ev[1], c.s);
+    c.nv.next("dms/gradient");
     if (s == DMS_OK) {
         if (batch) {
             if (dtype == DMS_U16) s = run<uint16_t, true>(c, (const uint16_t *)dv);

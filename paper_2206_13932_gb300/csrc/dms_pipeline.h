@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dms.h"
 
 namespace dms {
