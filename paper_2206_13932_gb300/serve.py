@@ -12,10 +12,15 @@ and runs them as one batch -- one pass of the pipeline over the disjoint union
 of their grids -- on a reusable batch handle.  Each result is the same as the
 request's diagram computed alone (the pipeline is deterministic, handles
 share no state, and a batch's per-field pairs equal the single-grid ones).
+
+Device memory: the requests in flight stay within ``mem_budget``.  A handle's
+buffers only grow, so after a request a slot keeps the handle only while that
+request fit the slot's share of the budget (``keeps_buffers``); a larger one
+is freed at once.  Idle handles therefore hold at most ``mem_budget / slots``
+each.
 """
 from __future__ import annotations
 
-import queue
 import threading
 import time
 from dataclasses import dataclass, field
@@ -30,6 +35,12 @@ def request_bytes(n_vertices: int, itemsize: int) -> int:
     (flags, ranks, 48-byte gradient records) and a bound for the critical
     simplices, arcs and D1 columns."""
     return int(n_vertices) * (itemsize + 1 + 4 + 48 + 96)
+
+
+def keeps_buffers(need: int, budget: int, slots: int) -> bool:
+    """Whether a slot keeps a handle (and its device buffers) after running a
+    request of ``need`` bytes: only within the slot's share of the budget."""
+    return need <= budget // max(1, int(slots))
 
 
 def select_batch(pending, in_flight: int, budget: int, max_batch: int):
@@ -158,6 +169,11 @@ class DiagramServer:
             except Exception as e:   # reported to the caller
                 for r in reqs:
                     r.error = e
+            if not keeps_buffers(need, self.mem_budget, self.slots):
+                handles = grids if len(reqs) == 1 else batches
+                h = handles.pop(reqs[0].values.dtype, None)
+                if h is not None:
+                    h.close()
             t = time.perf_counter()
             self._release(need)
             for r in reqs:

@@ -2,7 +2,7 @@
 memory budget, the batch cap and one dtype per batch."""
 import numpy as np
 
-from paper_2206_13932_gb300.serve import request_bytes, select_batch
+from paper_2206_13932_gb300.serve import keeps_buffers, request_bytes, select_batch
 
 
 def _req(n, dt=np.float32):
@@ -36,3 +36,10 @@ def test_one_dtype_per_batch():
 def test_request_bytes_grows_with_size_and_itemsize():
     assert request_bytes(100, 4) > request_bytes(100, 2)
     assert request_bytes(200, 4) == 2 * request_bytes(100, 4)
+
+
+def test_idle_handles_stay_within_a_share_of_the_budget():
+    assert keeps_buffers(100, 400, 4) and keeps_buffers(100, 400, 1)
+    assert not keeps_buffers(101, 400, 4)
+    assert keeps_buffers(400, 400, 1) and not keeps_buffers(401, 400, 1)
+    assert keeps_buffers(0, 0, 0)
