@@ -54,3 +54,56 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(dms, "_lib", None)
     with pytest.raises(RuntimeError):
         dms.load()
+
+
+def test_argument_checks_without_gpu():
+    """Invalid arguments are refused before any CUDA call, so these run on a
+    machine without a GPU: every entry point rejects a null handle, and
+    dms_grid_create rejects bad sizes, dtypes and options."""
+    import paper_2206_13932_gb300 as dms
+    lib = dms.load(build_if_missing=True)
+    bad = 1   # DMS_ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+
+    def create(nx, ny, nz, dtype=1, opts=None):
+        return lib.dms_grid_create(nx, ny, nz, dtype, ctypes.byref(opts) if opts else None,
+                                   ctypes.byref(h))
+
+    assert create(0, 4, 4) == bad and create(4, -1, 4) == bad
+    assert create(1 << 16, 1 << 16, 1) == bad            # nx*ny >= 2^31
+    assert create(1 << 11, 1 << 10, 1 << 10) == bad      # N >= 2^31
+    assert create(4, 4, 4, dtype=3) == bad
+    assert create(4, 4, 4, opts=dms._Options(0, 0, 0)) == bad    # no virtual maximum
+    assert create(4, 4, 4, opts=dms._Options(1, -1, 0)) == bad    # negative iteration cap
+    assert create(4, 4, 4, opts=dms._Options(1, 0, 4)) == bad    # unknown D1 mode
+    assert lib.dms_grid_create(4, 4, 4, 1, None, None) == bad     # no output handle
+    assert not h.value
+    null = ctypes.c_void_p(0)
+    p3, p4 = (ctypes.c_int64 * 3)(), (ctypes.c_int64 * 4)()
+    w = ctypes.c_int64(0)
+    assert lib.dms_compute_diagram(null, null, 1, null) == bad
+    assert lib.dms_get_counts(null, p3, p4) == bad
+    assert lib.dms_fetch_pairs(null, 0, null, 0, ctypes.byref(w), 0) == bad
+    assert lib.dms_grid_reshape(null, 4, 4, 4) == bad
+    assert lib.dms_batch_reshape(null, 1, p3) == bad
+    assert lib.dms_batch_offsets(null, 0, p4) == bad
+    assert lib.dms_backward_pairs(null, 0, null, null, null, null) == bad
+    assert lib.dms_get_stage_ms(null, (ctypes.c_float * 8)()) == bad
+    assert lib.dms_get_kernel_ms(null, (ctypes.c_float * 12)()) == bad
+    assert lib.dms_get_stats(null, (ctypes.c_int64 * 16)()) == bad
+    assert lib.dms_set_tuning(null, (ctypes.c_int32 * 9)(), 9) == bad
+    assert lib.dms_get_tuning(null, (ctypes.c_int32 * 9)(), 9) == bad
+    assert lib.dms_grid_destroy(null) == bad
+    assert lib.dms_batch_create(1, None, 1, None, ctypes.byref(h)) == bad
+    # the allocation-free classification checks its arguments first too
+    n = ctypes.c_int64(0)
+    buf = (ctypes.c_uint8 * 64)()
+    crit = (ctypes.c_int32 * 64)()
+    cls = lib.dms_classify_static
+    assert cls(None, 1, 4, 4, 4, buf, crit, 64, ctypes.byref(n), None) == bad
+    assert cls(buf, 1, 4, 4, 4, None, crit, 64, ctypes.byref(n), None) == bad
+    assert cls(buf, 1, 4, 4, 4, buf, None, 64, ctypes.byref(n), None) == bad
+    assert cls(buf, 1, 4, 4, 4, buf, crit, -1, ctypes.byref(n), None) == bad
+    assert cls(buf, 1, 0, 4, 4, buf, crit, 64, ctypes.byref(n), None) == bad
+    assert cls(buf, 1, 1 << 10, 1 << 10, 1 << 9, buf, crit, 64, ctypes.byref(n), None) == bad
+    assert cls(buf, 7, 4, 4, 4, buf, crit, 64, ctypes.byref(n), None) == bad
