@@ -271,6 +271,14 @@ dms_status dms_grid_destroy(dms_grid grid);
 /* Static description of a status code. */
 const char *dms_status_string(dms_status status);
 
+/* Test hook, host only (no GPU involved): copies the tables of the 14-vertex
+ * Freudenthal star that the kernels use (link offsets, the star's triangles
+ * and tetrahedra and their incidences; the layout of StarTables in
+ * csrc/dms_common.cuh) into `out` when `bytes` is at least their size.
+ * Returns that size, or -1 if the tables cannot be built.  Lets tests run the
+ * lower-star code on the host against the oracle. */
+int64_t dms_star_tables(void *out, int64_t bytes);
+
 #ifdef __cplusplus
 }
 #endif

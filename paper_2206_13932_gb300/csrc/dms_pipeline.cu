@@ -4875,3 +4875,12 @@ extern "C" dms_status dms_classify_static(const void *values, dms_dtype dtype, i
                                    n_critical, s, scr);
 }
 
+
+// The star tables of the kernels, copied to the host (no GPU involved), for
+// tests that run the lower-star code on the host.
+extern "C" int64_t dms_star_tables(void *out, int64_t bytes) {
+    dms::StarTables S;
+    if (!dms::build_star_tables(S)) return -1;
+    if (out && bytes >= (int64_t)sizeof S) memcpy(out, &S, sizeof S);
+    return (int64_t)sizeof S;
+}
