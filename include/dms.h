@@ -279,6 +279,13 @@ const char *dms_status_string(dms_status status);
  * lower-star code on the host against the oracle. */
 int64_t dms_star_tables(void *out, int64_t bytes);
 
+/* Test hook, host only (no GPU involved): copies the classification's table
+ * of PL-regular lower links (bit m of word m / 32 set: a vertex whose lower
+ * link vertices form mask m, in the link order of dms_star_tables, has no
+ * critical cell) into `out` when `words` is at least its length (2^14 / 32).
+ * Returns that length, or -1 if the tables cannot be built. */
+int64_t dms_regular_table(uint32_t *out, int64_t words);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4884,3 +4884,14 @@ extern "C" int64_t dms_star_tables(void *out, int64_t bytes) {
     if (out && bytes >= (int64_t)sizeof S) memcpy(out, &S, sizeof S);
     return (int64_t)sizeof S;
 }
+
+// The regular-vertex table of the classification (bit m set: lower link mask
+// m is PL-regular), copied to the host (no GPU involved), for tests.
+extern "C" int64_t dms_regular_table(uint32_t *out, int64_t words) {
+    dms::StarTables S;
+    if (!dms::build_star_tables(S)) return -1;
+    std::vector<uint32_t> lut;
+    dms::build_regular_lut(S, lut);
+    if (out && words >= (int64_t)lut.size()) memcpy(out, lut.data(), 4 * lut.size());
+    return (int64_t)lut.size();
+}

@@ -142,11 +142,14 @@ def _oracle_stars(values, vertices=None):
 
 
 def _check_field(star_layout, values, vertices=None):
+    """Compares every lower star (or those of ``vertices``); returns the
+    oracle's critical cells per vertex."""
     shape, keys, crit, pairs = _oracle_stars(values, vertices)
     for v in (range(len(keys)) if vertices is None else vertices):
         got_crit, got_pairs = _library_star(star_layout, shape, v, keys)
         assert got_crit == crit.get(v, set()), v
         assert got_pairs == pairs.get(v, set()), v
+    return crit
 
 
 @pytest.mark.parametrize("kind", ["float", "ties", "perm"])
@@ -166,15 +169,32 @@ def test_every_lower_star_of_random_fields(star, kind):
 
 def test_every_lower_link_mask_of_an_interior_vertex(star):
     """All 2^14 lower masks of the centre of a 3x3x3 grid, each with random
-    values (so random ranks) on its lower and upper neighbours."""
+    values (so random ranks) on its lower and upper neighbours.  The
+    classification's table of PL-regular masks (``dms_regular_table``) must
+    mark exactly the masks whose lower star has no critical cell in the
+    oracle's gradient (Sec. 2.6: critical cells lie only in lower stars of PL
+    critical points)."""
+    import paper_2206_13932_gb300 as dms
+    lib = dms.load()
+    lib.dms_regular_table.restype = ctypes.c_int64
+    lib.dms_regular_table.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    words = lib.dms_regular_table(None, 0)
+    assert words == (1 << 14) // 32
+    table = (ctypes.c_uint32 * words)()
+    assert lib.dms_regular_table(table, words) == words
     rng = np.random.default_rng(7)
     _, _, offs, _, _ = star
     centre = 13
     link_ids = [(1 + dx) + 3 * ((1 + dy) + 3 * (1 + dz)) for dx, dy, dz in offs]
+    regular = 0
     for m in range(1 << 14):
         v = rng.random(27) + 2.0                     # everything above the centre
         v[centre] = 1.5
         for n in range(14):
             if m >> n & 1:
                 v[link_ids[n]] = rng.random()        # below the centre
-        _check_field(star, v.reshape(3, 3, 3), vertices=[centre])
+        crit = _check_field(star, v.reshape(3, 3, 3), vertices=[centre])
+        is_regular = not crit.get(centre)
+        assert bool(table[m >> 5] >> (m & 31) & 1) == is_regular, m
+        regular += is_regular
+    assert 0 < regular < 1 << 14
