@@ -55,3 +55,31 @@ extern "C" void harness_layout(const void *tables, int64_t *out) {
     for (int h = 0; h < dms::kTets; h++)
         for (int i = 0; i < 3; i++) out[k++] = S.tet_v[h][i];
 }
+
+// The star view the gradient kernels load for vertex v of an nx*ny*nz grid
+// (load_star): out[0] present links, out[1] lower links, out[2] the descent
+// link, out[3..16] the rank of each lower link.  dtype 0 uint16, 1 float32,
+// 2 float64.  The grid's linear link offsets come from the star's offsets.
+extern "C" void harness_load_star(const void *tables, int dtype, const void *values, int nx,
+                                  int ny, int nz, int64_t v, int64_t *out) {
+    dms::StarTables S;
+    memcpy(&S, tables, sizeof S);
+    dms::GridParams g;
+    memset(&g, 0, sizeof g);
+    g.nx = nx; g.ny = ny; g.nz = nz; g.n = (int64_t)nx * ny * nz; g.off = 0;
+    for (int n = 0; n < dms::kLinks; n++) g.dlin[n] = S.dx[n] + nx * (S.dy[n] + ny * S.dz[n]);
+    dms::StarView sv;
+    if (dtype == 0) dms::load_star(S, g, (const uint16_t *)values, v, sv);
+    else if (dtype == 1) dms::load_star(S, g, (const float *)values, v, sv);
+    else dms::load_star(S, g, (const double *)values, v, sv);
+    out[0] = sv.present;
+    out[1] = sv.lower;
+    out[2] = sv.descent;
+    for (int n = 0; n < dms::kLinks; n++) out[3 + n] = sv.rank[n];
+}
+
+// The order keys (Key<T>::of) and NaN tests of the vertex values.
+extern "C" uint64_t harness_key_f32(float f) { return dms::Key<float>::of(f); }
+extern "C" uint64_t harness_key_f64(double d) { return dms::Key<double>::of(d); }
+extern "C" int harness_nan_f32(float f) { return dms::Key<float>::nan(f); }
+extern "C" int harness_nan_f64(double d) { return dms::Key<double>::nan(d); }

@@ -198,3 +198,75 @@ def test_every_lower_link_mask_of_an_interior_vertex(star):
         assert bool(table[m >> 5] >> (m & 31) & 1) == is_regular, m
         regular += is_regular
     assert 0 < regular < 1 << 14
+
+
+def _harness_extra(star):
+    h = star[0]
+    h.harness_load_star.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
+    h.harness_key_f32.argtypes = [ctypes.c_float]
+    h.harness_key_f32.restype = ctypes.c_uint64
+    h.harness_key_f64.argtypes = [ctypes.c_double]
+    h.harness_key_f64.restype = ctypes.c_uint64
+    h.harness_nan_f32.argtypes = [ctypes.c_float]
+    h.harness_nan_f64.argtypes = [ctypes.c_double]
+    return h
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.float32, np.float64])
+def test_star_view_follows_the_vertex_order(star, dtype):
+    """load_star (lower links, their ranks, the descent link) against the
+    order by (value, vertex id) of Sec. 2.1, with heavy ties and signed zeros."""
+    h = _harness_extra(star)
+    _, tables, offs, _, _ = star
+    rng = np.random.default_rng(11)
+    code = {np.uint16: 0, np.float32: 1, np.float64: 2}[dtype]
+    for shape in [(3, 3, 3), (5, 4, 3), (4, 1, 6), (1, 1, 5)]:
+        nx, ny, nz = shape
+        for _ in range(4):
+            if dtype == np.uint16:
+                v = rng.integers(0, 3, (nz, ny, nx)).astype(np.uint16)
+            else:
+                pool = np.array([-0.0, 0.0, -1.5, 1.5, np.inf, -np.inf, 2.0], dtype=dtype)
+                v = pool[rng.integers(0, len(pool), (nz, ny, nx))]
+            keys = bf.vertex_keys(v)
+            flat = np.ascontiguousarray(v).reshape(-1)
+            out = (ctypes.c_int64 * 17)()
+            for vid in range(flat.size):
+                h.harness_load_star(tables, code, flat.ctypes.data, nx, ny, nz, vid, out)
+                L, rank, edge, _, _ = _star_cells(star, shape, vid, keys)
+                present = 0
+                x, y, z = vid % nx, (vid // nx) % ny, vid // (nx * ny)
+                for n, (dx, dy, dz) in enumerate(offs):
+                    if 0 <= x + dx < nx and 0 <= y + dy < ny and 0 <= z + dz < nz:
+                        present |= 1 << n
+                assert out[0] == present and out[1] == L, vid
+                assert [out[3 + n] for n in range(14) if L >> n & 1] == \
+                    [rank[n] for n in range(14) if L >> n & 1]
+                lowest = [n for n in range(14) if L >> n & 1 and rank[n] == 0]
+                assert out[2] == (lowest[0] if lowest else 0xF)
+
+
+def test_order_keys_and_nan(star):
+    """Key<T>::of orders like the numbers (-0.0 = +0.0, infinities at the
+    ends) and Key<T>::nan finds every NaN, in float32 and float64."""
+    h = _harness_extra(star)
+    rng = np.random.default_rng(12)
+    for dt, key, isnan, ubits in ((np.float32, h.harness_key_f32, h.harness_nan_f32, np.uint32),
+                                  (np.float64, h.harness_key_f64, h.harness_nan_f64, np.uint64)):
+        special = np.array([0.0, -0.0, np.inf, -np.inf, np.finfo(dt).max, -np.finfo(dt).max,
+                            np.finfo(dt).tiny, -np.finfo(dt).tiny, np.finfo(dt).smallest_subnormal,
+                            -np.finfo(dt).smallest_subnormal, 1.0, -1.0], dtype=dt)
+        vals = np.concatenate([special, (rng.standard_normal(400) * 1e3).astype(dt),
+                               rng.standard_normal(100).astype(dt) * np.finfo(dt).tiny])
+        ks = [key(float(x)) for x in vals]
+        for i in range(len(vals)):
+            for j in range(0, len(vals), 7):
+                a, b = vals[i], vals[j]
+                assert (ks[i] < ks[j]) == (a < b) and (ks[i] == ks[j]) == (a == b), (a, b)
+        nan_bits = [0x7FC00000, 0xFFC00000, 0x7F800001, 0xFFFFFFFF] if dt == np.float32 else \
+            [0x7FF8000000000000, 0xFFF8000000000000, 0x7FF0000000000001, 0xFFFFFFFFFFFFFFFF]
+        for b in nan_bits:
+            x = np.array([b], dtype=ubits).view(dt)[0]
+            assert isnan(float(x))
+        assert not any(isnan(float(x)) for x in vals)
