@@ -12,7 +12,6 @@ import json
 import os
 import sys
 
-import numpy as np
 
 
 def main():
