@@ -13,7 +13,6 @@ import os
 import sys
 
 
-
 def main():
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
