@@ -31,9 +31,24 @@ def _rand_field(rng, shape_xyz, kind):
 
 # ----------------------------------------------------------- closed forms
 
+def _closed_form_counts(nx, ny, nz):
+    """V, E, T, Tet of the Freudenthal triangulation by counting anchors: a
+    chain simplex with largest offset o fits at prod_k (n_k - o_k) anchors."""
+    n = (nx, ny, nz)
+
+    def fits(o):
+        return int(np.prod([n[k] - ((o >> k) & 1) for k in range(3)]))
+    edges = sum(fits(o) for o in range(1, 8))
+    # triangles: chains a < b of non-empty offsets (a a proper subset of b)
+    tris = sum(fits(b) for b in range(1, 8) for a in range(1, 8) if a != b and a & b == a)
+    tets = 6 * fits(7)
+    return [nx * ny * nz, edges, tris, tets]
+
+
 def test_simplex_counts_closed_form():
     cases = json.load(open(os.path.join(GOLDEN, "simplex_counts.json")))["cases"]
     for c in cases:
+        assert c["counts"] == _closed_form_counts(*c["shape_xyz"])
         counts = oracle.simplex_counts(*c["shape_xyz"])
         assert list(counts) == c["counts"]
         assert counts[0] - counts[1] + counts[2] - counts[3] == 1   # chi of a cube
