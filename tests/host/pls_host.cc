@@ -20,7 +20,7 @@ static inline long long __double_as_longlong(double d) {
     return u;
 }
 
-#include "../../paper_2206_13932_gb300/csrc/dms_common.cuh"
+#include "dms_common.cuh"   // -I the kernels' csrc/ (or a copy of it)
 
 extern "C" int64_t harness_tables_size() { return (int64_t)sizeof(dms::StarTables); }
 
