@@ -54,8 +54,19 @@ def set_tuning(grid, values) -> None:
 
 
 def valid(values) -> bool:
-    d = dict(zip(TUNABLES, values))
-    return d["trace_per_sm"] % d["trace_block"] == 0 and d["trace_per_sm"] >= d["trace_block"]
+    """The ranges ``dms_set_tuning`` accepts (it refuses anything else)."""
+    if len(values) != len(TUNABLES):
+        return False
+    d = dict(zip(TUNABLES, (int(x) for x in values)))
+
+    def block(b, most):
+        return 32 <= b <= most and b % 32 == 0
+    return (block(d["pls_block"], 512) and block(d["trace_block"], 256) and
+            d["trace_block"] <= d["trace_per_sm"] <= 8192 and
+            d["trace_per_sm"] % d["trace_block"] == 0 and
+            8 <= d["trace_heap"] <= 1024 and d["red_block_below"] >= 0 and
+            8 <= d["lazy_heap"] <= 1024 and 1 <= d["lazy_density"] <= 4096 and
+            d["red_async"] in (0, 1) and d["pls_sort"] in (0, 1, 2))
 
 
 def measure(grid, field, repeats: int = 3) -> float:
