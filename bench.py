@@ -336,7 +336,12 @@ def run_ours(args):
         roofline = dict(roof_grad) if dom == "classify" else {
             "bound": "latency", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s",
             "frac": None, "traffic": None, "peak_source": src}
-    serving = serving_section() if not args.no_serve else None
+    serving = None
+    if not args.no_serve:
+        try:
+            serving = serving_section()
+        except Exception as e:   # the headline line is printed even if serving fails
+            serving = {"error": f"{type(e).__name__}: {e}"}
     # oracle on a bounded crop of the same field
     nv, dt, _ = _oracle_sample(field, ORACLE_SAMPLE)
     line = {
