@@ -63,6 +63,26 @@ def select_batch(pending, in_flight: int, budget: int, max_batch: int):
     return k, need
 
 
+class CudaBackend:
+    """What a slot needs from the device: a stream of its own, the context
+    that makes it current, its handle for the C ABI, and the handle types."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.Grid, self.Batch = Grid, Batch
+
+    def stream(self):
+        return self.torch.cuda.Stream()
+
+    def current(self, stream):
+        return self.torch.cuda.stream(stream)
+
+    @staticmethod
+    def handle(stream):
+        return stream.cuda_stream
+
+
 @dataclass(order=True)
 class Request:
     arrival: float
@@ -81,8 +101,9 @@ class DiagramServer:
     arrival order, one dtype, within the budget) and computes them as one
     batch (``dms_batch_create``): one pass of the pipeline for all of them."""
 
-    def __init__(self, slots: int = 4, mem_budget: int = 16 << 30, max_batch: int = 1):
-        import torch
+    def __init__(self, slots: int = 4, mem_budget: int = 16 << 30, max_batch: int = 1,
+                 backend=None):
+        self._be = backend if backend is not None else CudaBackend()
         self.slots = slots
         self.mem_budget = mem_budget
         self.max_batch = max(1, int(max_batch))
@@ -91,7 +112,6 @@ class DiagramServer:
         self._in_flight_bytes = 0
         self._stop = False
         self._workers = []
-        self._torch = torch
         for k in range(slots):
             t = threading.Thread(target=self._worker, args=(k,), daemon=True)
             t.start()
@@ -134,8 +154,11 @@ class DiagramServer:
             self._cv.notify_all()
 
     def _worker(self, k: int):
-        torch = self._torch
-        stream = torch.cuda.Stream()
+        be = self._be
+        try:
+            stream, setup_error = be.stream(), None
+        except Exception as e:   # every request this slot takes then reports it
+            stream, setup_error = None, e
         grids, batches = {}, {}
         while True:
             got = self._take()
@@ -146,24 +169,26 @@ class DiagramServer:
             for r in reqs:
                 r.admitted = t
             try:
+                if setup_error is not None:
+                    raise setup_error
                 dt = reqs[0].values.dtype
                 shapes = [(r.values.shape[2], r.values.shape[1], r.values.shape[0]) for r in reqs]
-                with torch.cuda.stream(stream):
+                with be.current(stream):
                     if len(reqs) == 1:
                         g = grids.get(dt)
                         if g is None:
-                            g = grids[dt] = Grid(shapes[0], dt)
+                            g = grids[dt] = be.Grid(shapes[0], dt)
                         elif g.shape_xyz != shapes[0]:
                             g.reshape(shapes[0])
-                        g.compute(reqs[0].values, stream=stream.cuda_stream)
+                        g.compute(reqs[0].values, stream=be.handle(stream))
                         reqs[0].result = {d: g.fetch(d) for d in range(3)}
                     else:
                         b = batches.get(dt)
                         if b is None:
-                            b = batches[dt] = Batch(shapes, dt)
+                            b = batches[dt] = be.Batch(shapes, dt)
                         else:
                             b.reshape(shapes)
-                        b.compute([r.values for r in reqs], stream=stream.cuda_stream)
+                        b.compute([r.values for r in reqs], stream=be.handle(stream))
                         for r, res in zip(reqs, b.results()):
                             r.result = res
             except Exception as e:   # reported to the caller
@@ -183,11 +208,13 @@ class DiagramServer:
             g.close()
 
 
-def run_stream(fields, arrivals, slots: int, mem_budget: int = 16 << 30, max_batch: int = 1):
+def run_stream(fields, arrivals, slots: int, mem_budget: int = 16 << 30, max_batch: int = 1,
+               backend=None):
     """Replays requests arriving at ``arrivals`` (seconds from start) through
     a server; returns the requests (with timings and results) and the wall
     time."""
-    srv = DiagramServer(slots=slots, mem_budget=mem_budget, max_batch=max_batch)
+    srv = DiagramServer(slots=slots, mem_budget=mem_budget, max_batch=max_batch,
+                        backend=backend)
     reqs = []
     t0 = time.perf_counter()
     for i, (f, a) in enumerate(zip(fields, arrivals)):
