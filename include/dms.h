@@ -186,6 +186,12 @@ dms_status dms_get_stage_ms(dms_grid grid, float ms[8]);
  * by D1 column additions, [15] bytes written by D1 column additions. */
 dms_status dms_get_stats(dms_grid grid, int64_t stats[16]);
 
+/* Device memory the handle holds now, in bytes: the sum of its device
+ * arenas (grid-sized state, critical lists, union-find tables, D1 pools and
+ * output), which only grow and are kept across computes and reshapes.  Host
+ * pinned memory and the library's fixed tables are not counted. */
+dms_status dms_get_device_bytes(dms_grid grid, int64_t *bytes);
+
 /* Device milliseconds of the last compute per kernel family, from CUDA event
  * pairs recorded on the compute stream around the launches (host round trips
  * between launches of one family are included): [0] classify (the per-vertex

@@ -66,6 +66,8 @@ def load(build_if_missing: bool = False):
             lib.dms_get_stage_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
             lib.dms_get_stats.argtypes = [vp, p64]
             lib.dms_get_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+            lib.dms_get_device_bytes.argtypes = [vp, p64]
+            lib.dms_get_device_bytes.restype = ctypes.c_int
             lib.dms_classify_static.argtypes = [vp, ctypes.c_int, i64, i64, i64, vp, vp, i64,
                                                 p64, vp]
             lib.dms_classify_static.restype = ctypes.c_int
@@ -211,6 +213,12 @@ class Grid:
         ms = (ctypes.c_float * 12)()
         _check(self._lib.dms_get_kernel_ms(self._h, ms), "dms_get_kernel_ms")
         return dict(zip(self.KERNELS, [float(x) for x in ms]))
+
+    def device_bytes(self) -> int:
+        """Device memory this handle holds now (its arenas only grow)."""
+        b = ctypes.c_int64(0)
+        _check(self._lib.dms_get_device_bytes(self._h, ctypes.byref(b)), "dms_get_device_bytes")
+        return int(b.value)
 
     def stats(self):
         s = (ctypes.c_int64 * 16)()

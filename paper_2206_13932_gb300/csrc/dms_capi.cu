@@ -112,6 +112,12 @@ dms_status dms_get_stats(dms_grid grid, int64_t stats[16]) {
     return DMS_OK;
 }
 
+dms_status dms_get_device_bytes(dms_grid grid, int64_t *bytes) {
+    if (!grid || !bytes) return DMS_ERR_INVALID_ARG;
+    *bytes = grid->p.device_bytes();
+    return DMS_OK;
+}
+
 dms_status dms_get_kernel_ms(dms_grid grid, float ms[12]) {
     if (!grid || !ms) return DMS_ERR_INVALID_ARG;
     if (!grid->p.has_result) return DMS_ERR_STATE;

@@ -4718,8 +4718,9 @@ dms_status Pipeline::reshape(int64_t nx_, int64_t ny_, int64_t nz_) {
     return DMS_OK;
 }
 
-void Pipeline::destroy() {
-    DevBuf *all[] = {&d1_row, &d1_rowpaired, &d1_rowpos, &d1_rowmap, &d1_cocnt, &d1_costart,
+// Every device buffer of the handle.
+std::vector<DevBuf *> Pipeline::buffers() {
+    std::vector<DevBuf *> all = {&d1_row, &d1_rowpaired, &d1_rowpos, &d1_rowmap, &d1_cocnt, &d1_costart,
                      &d1_cofill, &d1_act, &d1_next, &d1_re, &d1_stamp, &grad, &values_dev, &flags,    &vrank,     &tile_cnt,  &tile_off,   &vc,
                      &vc_tmp,     &keys,     &keys_tmp,  &recs,      &arc_a,      &arc_b,
                      &dc_keys,    &dc_par,   &dc_lab,    &young,     &died,       &rowcol,
@@ -4730,13 +4731,21 @@ void Pipeline::destroy() {
                      &bt_v[0], &bt_v[1], &bt_h[0], &bt_h[1], &bt_cnt, &out_tmp, &bx_buf[0],
                      &bx_buf[1], &d1_info, &d1_queue, &d1_aq, &ord_k[0], &ord_k[1], &ord_k[2],
                      &ord_k[3], &ord_v[0], &ord_v[1], &ord_v[2], &ord_v[3], &ord_h[0], &ord_h[1]};
-    for (DevBuf *b : all) b->release();
-    for (int d = 0; d < 4; d++) {
-        cnt[d].release(); base[d].release(); c_vert[d].release(); c_loc[d].release();
-    }
-    for (int d = 0; d < 3; d++) {
-        out_pairs[d].release(); out_field[d].release(); batch_pofs[d].release();
-    }
+    for (int d = 0; d < 4; d++)
+        for (DevBuf *b : {&cnt[d], &base[d], &c_vert[d], &c_loc[d]}) all.push_back(b);
+    for (int d = 0; d < 3; d++)
+        for (DevBuf *b : {&out_pairs[d], &out_field[d], &batch_pofs[d]}) all.push_back(b);
+    return all;
+}
+
+int64_t Pipeline::device_bytes() {
+    int64_t total = 0;
+    for (DevBuf *b : buffers()) total += (int64_t)b->bytes;
+    return total;
+}
+
+void Pipeline::destroy() {
+    for (DevBuf *b : buffers()) b->release();
     if (hstat) cudaFreeHost(hstat);
     hstat = nullptr;
     for (int i = 0; i < 24; i++) if (kev[i]) cudaEventDestroy((cudaEvent_t)kev[i]);

@@ -98,6 +98,8 @@ struct Pipeline {
     dms_status backward(int dim, const double *gbirth, const double *gdeath, double *grad,
                         void *stream);
     void destroy();
+    std::vector<DevBuf *> buffers();   // every device buffer of the handle
+    int64_t device_bytes();            // bytes they hold now
 };
 
 }  // namespace dms

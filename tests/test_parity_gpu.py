@@ -151,3 +151,15 @@ def test_deterministic_and_reusable(dms):
             g.compute(t)
             outs.append([g.fetch(d).tobytes() for d in range(3)])
     assert outs[0] == outs[1] == outs[2]
+
+
+def test_device_bytes_hold_the_grid_state_and_only_grow(dms):
+    v = sf.white_noise((20, 18, 16), 4)
+    with dms.Grid((20, 18, 16), np.float32) as g:
+        before = g.device_bytes()
+        g.compute(v)
+        after = g.device_bytes()
+        assert after >= before and after >= v.size * (1 + 4 + 48)   # flags, ranks, records
+        w = sf.white_noise((40, 30, 20), 5)
+        g.reshape((40, 30, 20)).compute(w)
+        assert g.device_bytes() > after
