@@ -5,6 +5,15 @@ This module is a thin binding of the C ABI in ``include/dms.h`` (library
 ``_build/libdms.so``): argument marshalling only, every step of the method runs
 in the CUDA kernels of ``csrc/``.  PyTorch is used for device memory and
 streams.  There is no CPU fallback: if the library is missing the calls raise.
+
+- :class:`Grid` -- one grid shape and dtype; ``compute``, ``fetch``,
+  ``reshape``, timings, statistics and ``device_bytes``.
+- :class:`Batch` -- many fields of their own shapes in one pass.
+- :func:`diagram` -- one field's D0, D1, D2 in one call.
+- :func:`classify_static` -- the allocation-free classification step.
+- Submodules: ``autograd`` (differentiable births and deaths), ``serve``
+  (continuous-batching server), ``autotune`` (launch shapes), ``replicas``
+  (timing of independent replicas), ``run_case`` (one workload, for profiling).
 """
 from __future__ import annotations
 
