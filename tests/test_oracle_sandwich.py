@@ -90,6 +90,19 @@ def test_sandwich_equals_standard_reduction_larger(name):
     assert set(gens) == {(int(r[1]), int(r[2])) for r in rows if r[0] == 1 and not r[5]}
 
 
+@pytest.mark.parametrize("name", ["noise40", "recipe48_u16"])
+def test_sandwich_equals_standard_reduction_medium(name):
+    """At the larger sizes where the GPU tests use the sandwich in place of the
+    slower reduction, the two still agree pair for pair."""
+    if name == "noise40":
+        v = sf.white_noise((40, 40, 40), 13)
+    else:
+        v = sf.quantize_u16(sf.gaussian_mixture((48, 48, 48), 24, 14, noise=0.05, dtype=None,
+                                                noise_rel=True))
+    rows, _ = oracle.sandwich(v)
+    assert _pairs(rows) == _pairs(oracle.pairsimplices(v))
+
+
 def test_sandwich_equals_standard_reduction_on_every_order_of_a_cube():
     """All 8! vertex orders of the 2x2x2 grid: the two oracles agree on every
     one, and without the virtual maximum D0 stays and the infinite classes
