@@ -32,13 +32,17 @@ def _gpu(dms, values, mode):
         return {d: g.fetch(d) for d in range(3)}
 
 
-@pytest.mark.parametrize("name", ["mixture112_f32", "recipe96_u16"])
+@pytest.mark.parametrize("name", ["mixture112_f32", "recipe96_u16", "noise96_f32"])
 def test_medium_fields_against_the_sandwich_oracle(dms, name):
+    modes = (0, 1)
     if name == "mixture112_f32":        # smooth: few 2-saddles, long walls (lazy mode)
         v = sf.gaussian_mixture((112, 112, 112), 16, 1, noise=1e-3)
-    else:                                # the 512^3 uint16 recipe at 96^3: heavy ties
+    elif name == "recipe96_u16":         # the 512^3 uint16 recipe at 96^3: heavy ties
         v = sf.quantize_u16(sf.gaussian_mixture((96, 96, 96), 64, 3, noise=0.05, dtype=None,
                                                 noise_rel=True))
+    else:                                # noise: many columns, long addition chains, the
+        v = sf.white_noise((96, 96, 96), 2)     # asynchronous tail; every D1 mode
+        modes = (0, 1, 2, 3)
     rows, _ = oracle.sandwich(v)
-    for mode in (0, 1):
+    for mode in modes:
         compare(v, _gpu(dms, v, mode), rows)
