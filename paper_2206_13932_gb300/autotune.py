@@ -80,8 +80,8 @@ def measure(grid, field, repeats: int = 3) -> float:
 
 def tune(grid, field, repeats: int = 3, min_gain: float = 0.02, budget_s: float | None = None):
     """Coordinate descent over CANDIDATES on ``grid`` computing ``field``.
-    Returns (best values, {"default_ms", "best_ms", "trials": [(values, ms)]}).
-    The handle is left set to the best values."""
+    Returns (best values, {"start_ms", "best_ms", "trials": [(values, ms)],
+    "seconds"}).  The handle is left set to the best values."""
     t0 = time.perf_counter()
     grid.compute(field)                         # warm-up: buffers sized, tables loaded
     cur = get_tuning(grid)
