@@ -63,3 +63,17 @@ def test_traffic_hash_covers_the_classification_code_only():
     assert bench._classify_code_of(src, "y") != base
     lost = src.replace("stage 2: stable LSD radix sort", "stage 2")
     assert bench._classify_code_of(lost, "x") is None
+
+
+def test_clock_summary_parses_the_sampled_lines():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = ["1965, 2070, 1100.5, Not Active, Not Active, Not Active, Active",
+               "1980, 2070, 1180.2, Not Active, Not Active, Not Active, Not Active",
+               "2010, 2070, 1200.0, Active, Not Active, Not Active, Not Active",
+               "[N/A], 2070, 0, x, x, x, x", "garbage"]
+    s = c.summary()
+    assert s["sm_mhz"] == 1980 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler(0).summary()["sm_mhz"] is None
