@@ -153,7 +153,8 @@ dms_status dms_get_counts(dms_grid grid, int64_t pairs[3], int64_t essential[4])
  * edge for D0, the death triangle for D1, the birth triangle for D2), then the
  * infinite classes of that dimension -- into out[0..cap).  *written = number copied; if cap is smaller
  * than the count, DMS_ERR_CAPACITY is returned and nothing is copied.
- * out_is_device = 1: out is a device pointer (copy on the compute stream). */
+ * out_is_device = 1: out is a device pointer (a synchronous device-to-device
+ * copy; the result is already complete when dms_compute_diagram returns). */
 dms_status dms_fetch_pairs(dms_grid grid, int dim, dms_pair *out, int64_t cap,
                            int64_t *written, int out_is_device);
 
