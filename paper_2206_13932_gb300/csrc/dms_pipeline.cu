@@ -4630,9 +4630,26 @@ static GridParams grid_params(int64_t nx, int64_t ny, int64_t nz, int64_t off) {
     return g;
 }
 
+// The shapes of a batch are valid: 1..65535 fields (the field index is 16
+// bits), each 1 <= n <= 2^30 per axis, every count below 2^31.
+static bool batch_shapes_ok(int64_t nf_, const int64_t *shp) {
+    if (nf_ < 1 || nf_ > 65535 || !shp) return false;
+    int64_t total = 0;
+    for (int64_t f = 0; f < nf_; f++) {
+        const int64_t a = shp[3 * f], b = shp[3 * f + 1], c = shp[3 * f + 2];
+        if (a < 1 || b < 1 || c < 1 || a > (1 << 30) || b > (1 << 30) || c > (1 << 30) ||
+            a * b >= ((int64_t)1 << 31) || a * b * c >= ((int64_t)1 << 31))
+            return false;
+        total += a * b * c;
+        if (total >= ((int64_t)1 << 31)) return false;
+    }
+    return true;
+}
+
 dms_status Pipeline::init_batch(int64_t nf_, const int64_t *shp, dms_dtype dt,
                                 const dms_options *o) {
     if (dt != DMS_U16 && dt != DMS_F32 && dt != DMS_F64) return DMS_ERR_INVALID_ARG;
+    if (!batch_shapes_ok(nf_, shp)) return DMS_ERR_INVALID_ARG;   // before any CUDA call
     if (o && (o->virtual_max != 1 || o->max_iters < 0 || o->d1_mode < 0 || o->d1_mode > 3))
         return DMS_ERR_INVALID_ARG;
     batch = true;
@@ -4646,7 +4663,7 @@ dms_status Pipeline::init_batch(int64_t nf_, const int64_t *shp, dms_dtype dt,
 // Device buffers only grow, so a handle can be re-targeted to other batches.
 dms_status Pipeline::set_batch(int64_t nf_, const int64_t *shp) {
     if (!batch) return DMS_ERR_INVALID_ARG;
-    if (nf_ < 1 || nf_ > 65535 || !shp) return DMS_ERR_INVALID_ARG;
+    if (!batch_shapes_ok(nf_, shp)) return DMS_ERR_INVALID_ARG;
     std::vector<int64_t> off(nf_ + 1, 0);
     std::vector<GridParams> gp(nf_);
     for (int64_t f = 0; f < nf_; f++) {

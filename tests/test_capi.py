@@ -108,3 +108,21 @@ def test_argument_checks_without_gpu():
     assert cls(buf, 1, 0, 4, 4, buf, crit, 64, ctypes.byref(n), None) == bad
     assert cls(buf, 1, 1 << 10, 1 << 10, 1 << 9, buf, crit, 64, ctypes.byref(n), None) == bad
     assert cls(buf, 7, 4, 4, 4, buf, crit, 64, ctypes.byref(n), None) == bad
+
+
+def test_batch_shapes_are_checked_without_gpu():
+    """dms_batch_create refuses bad field lists before any CUDA call."""
+    import paper_2206_13932_gb300 as dms
+    lib = dms.load(build_if_missing=True)
+    h = ctypes.c_void_p()
+
+    def create(shapes):
+        flat = (ctypes.c_int64 * max(1, len(shapes) * 3))(*[v for s in shapes for v in s])
+        return lib.dms_batch_create(len(shapes), flat, 1, None, ctypes.byref(h))
+
+    assert create([]) == 1                                   # no field
+    assert create([(4, 4, 4), (0, 4, 4)]) == 1               # an empty axis
+    assert create([(1 << 16, 1 << 16, 1)]) == 1              # nx*ny >= 2^31
+    assert create([(1 << 10, 1 << 10, 1 << 10)] * 2) == 1    # total >= 2^31
+    assert create([(2, 2, 2)] * 65536) == 1                  # more fields than the index holds
+    assert not h.value
