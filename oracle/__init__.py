@@ -11,6 +11,12 @@ Functions (all CPU, all exact):
   boundary-matrix reduction of the lexicographic filtration (Sec. 2.2,
   Sec. 2.4-2.5), keeping the pairs whose simplices have different maximum
   vertices plus the infinite-persistence classes (Sec. 4.1 (c), Sec. 6).
+- :func:`fastpairs` -- the same standard reduction with result-preserving
+  shortcuts (``fastpairs.c``): one dimension at a time from tets down to
+  edges with clearing (Sec. 4, observation (a)), columns that need no
+  addition regenerated from their ids instead of stored, and the filtration
+  streamed lower star by lower star instead of sorted globally.  It reaches
+  128^3 grids and more; the tests pin it equal to :func:`pairsimplices`.
 - :func:`kruskal_d0` -- D0 by union-find over all edges (Sec. 1.1, the
   Edelsbrunner sub-level-set method), elder rule.
 - :func:`kruskal_d2` -- D2 by union-find on the dual graph with a virtual
@@ -40,7 +46,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, f) for f in ("pairsimplices.c", "sandwich.c", "complex.h")]
+_SRCS = [os.path.join(_HERE, f) for f in ("pairsimplices.c", "sandwich.c", "fastpairs.c",
+                                          "complex.h")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -81,6 +88,10 @@ def _load():
                                                  [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                                   pp64, p64])
             lib.oracle_pairsimplices.restype = ctypes.c_int
+            lib.oracle_fastpairs.argtypes = ([ctypes.c_int64] * 3 +
+                                             [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                              pp64, p64, p64])
+            lib.oracle_fastpairs.restype = ctypes.c_int
             lib.oracle_sandwich.argtypes = ([ctypes.c_int64] * 3 +
                                             [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                              pp64, p64, pp64, p64])
@@ -109,12 +120,12 @@ def _field(values: np.ndarray):
     return nx, ny, nz, DTYPES[values.dtype], values
 
 
-def _call(fn, values, *extra):
+def _call(fn, values, *extra, tail=()):
     nx, ny, nz, code, arr = _field(values)
     out = ctypes.POINTER(ctypes.c_int64)()
     n = ctypes.c_int64(0)
     st = fn(nx, ny, nz, code, arr.ctypes.data_as(ctypes.c_void_p), *extra,
-            ctypes.byref(out), ctypes.byref(n))
+            ctypes.byref(out), ctypes.byref(n), *tail)
     if st:
         raise ValueError(f"oracle: {ERRORS.get(st, st)}")
     try:
@@ -134,6 +145,18 @@ def pairsimplices(values: np.ndarray, keep_zero: bool = False) -> np.ndarray:
     """
     lib = _load()
     return _call(lib.oracle_pairsimplices, values, int(bool(keep_zero)))
+
+
+def fastpairs(values: np.ndarray, keep_zero: bool = False, stats: dict | None = None) -> np.ndarray:
+    """The pairs of :func:`pairsimplices`, computed by the fast-mode standard
+    reduction (``fastpairs.c``).  The two filtration-position columns are -1.
+    ``stats``: if given, receives ``additions`` (column additions made)."""
+    lib = _load()
+    adds = ctypes.c_int64(0)
+    rows = _call(lib.oracle_fastpairs, values, int(bool(keep_zero)), tail=(ctypes.byref(adds),))
+    if stats is not None:
+        stats["additions"] = int(adds.value)
+    return rows
 
 
 def kruskal_d0(values: np.ndarray) -> np.ndarray:

@@ -1,0 +1,340 @@
+/*
+ * oracle/fastpairs.c -- the oracle's standard reduction in "fast mode":
+ * the same persistence pairing as oracle_pairsimplices (pairsimplices.c),
+ * computed with result-preserving shortcuts so that it reaches grids of
+ * 128^3 vertices and more on one CPU core.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load or call this code.  It
+ * shares no code, header, table or helper with the CUDA path of the package.
+ *
+ * What is computed is unchanged (Sec. 2.2, Sec. 2.4-2.5, Alg. 1): the
+ * standard reduction of the boundary matrix of the lexicographic filtration
+ * of every simplex -- for each column j in filtration order, while the
+ * lowest non-zero row of column j is the pivot of an earlier column k, add
+ * column k to column j (mod 2) -- keeping the pairs whose two simplices have
+ * different maximum vertices (Sec. 4.1 (c)) and the unpaired simplices as
+ * infinite classes (Sec. 6).  The shortcuts, each of which leaves every
+ * pivot of the reduction unchanged:
+ *
+ *  1. Dimension separability.  A column of dimension d only ever receives
+ *     columns of dimension d (a column is added only to a column with the
+ *     same lowest row, and rows of a d-column are (d-1)-simplices), so the
+ *     reduction runs one dimension at a time, each in filtration order.
+ *  2. Clearing (the twist; Sec. 4, observation (a)).  Dimensions are reduced
+ *     from 3 down to 1.  A d-simplex that is the pivot of a (d+1)-column is
+ *     a birth, so its own column reduces to zero: it is skipped.
+ *  3. Apparent pairs.  A column that needs no addition keeps its boundary as
+ *     its reduced form; it is not stored, and is regenerated from the
+ *     simplex id whenever a later column adds it.
+ *  4. Implicit boundaries and streamed filtration.  No global list of
+ *     simplices is built or sorted.  The key of a simplex (its vertex ranks
+ *     in decreasing order, Sec. 2.2) is computed from its id; the d-simplices
+ *     of the filtration are visited vertex by vertex in increasing rank,
+ *     and within the lower star of a vertex in increasing key.  Every
+ *     simplex lies in the lower star of its maximum vertex, and the key of a
+ *     simplex starts with the rank of that vertex, so this is exactly the
+ *     filtration order restricted to dimension d.
+ *
+ * Result rows as pairsimplices.c (8 int64: dim, birth_id, death_id,
+ * birth_vertex, death_vertex, essential, birth_pos, death_pos), except that
+ * the two filtration positions are -1 (no global list is formed).
+ */
+#include "complex.h"
+
+/* A filtration key: the vertex ranks r0 > r1 > r2 > r3 of a simplex, missing
+ * ranks as -1, packed so that unsigned (hi, lo) order is the lexicographic
+ * order with a face (a prefix) before its cofaces. */
+typedef struct { uint64_t hi, lo; } fkey_t;
+
+static inline int key_lt(fkey_t a, fkey_t b)
+{
+    return a.hi != b.hi ? a.hi < b.hi : a.lo < b.lo;
+}
+
+static inline int key_eq(fkey_t a, fkey_t b) { return a.hi == b.hi && a.lo == b.lo; }
+
+typedef struct {
+    grid_t g;
+    int64_t n;
+    int64_t *rank;          /* rank of each vertex in the (value, id) order */
+    int64_t *vert_of_rank;
+} fctx_t;
+
+static fkey_t key_of_vertices(const fctx_t *c, int dim, const int64_t *vs)
+{
+    int64_t r[4] = {-1, -1, -1, -1};
+    for (int i = 0; i <= dim; i++) r[i] = c->rank[vs[i]];
+    sort_desc(r, dim + 1);
+    fkey_t k;
+    k.hi = ((uint64_t)(r[0] + 1) << 32) | (uint64_t)(r[1] + 1);
+    k.lo = ((uint64_t)(r[2] + 1) << 32) | (uint64_t)(r[3] + 1);
+    return k;
+}
+
+/* The simplex of dimension dim with key k (its vertices are the vertices of
+ * the ranks in k). */
+static int64_t id_of_key(const fctx_t *c, int dim, fkey_t k)
+{
+    int64_t r[4] = {(int64_t)(k.hi >> 32) - 1, (int64_t)(k.hi & 0xffffffffu) - 1,
+                    (int64_t)(k.lo >> 32) - 1, (int64_t)(k.lo & 0xffffffffu) - 1};
+    int64_t vs[4];
+    for (int i = 0; i <= dim; i++) vs[i] = c->vert_of_rank[r[i]];
+    return simplex_id(&c->g, dim, vs);
+}
+
+static int64_t max_vertex_of_key(const fctx_t *c, fkey_t k)
+{
+    return c->vert_of_rank[(int64_t)(k.hi >> 32) - 1];
+}
+
+/* The boundary of (dim, id): keys of its dim+1 facets, in increasing order. */
+static int boundary_keys(const fctx_t *c, int dim, int64_t id, fkey_t *out)
+{
+    int64_t vs[4], fv[3];
+    simplex_vertices(&c->g, dim, id, vs);
+    for (int drop = 0; drop <= dim; drop++) {
+        int m = 0;
+        for (int i = 0; i <= dim; i++) if (i != drop) fv[m++] = vs[i];
+        out[drop] = key_of_vertices(c, dim - 1, fv);
+    }
+    for (int i = 1; i <= dim; i++)
+        for (int j = i; j > 0 && key_lt(out[j], out[j - 1]); j--) {
+            fkey_t t = out[j]; out[j] = out[j - 1]; out[j - 1] = t;
+        }
+    return dim + 1;
+}
+
+/* The d-simplices of the lower star of v (those containing v whose other
+ * vertices all have lower rank), with their keys, in increasing key order.
+ * A simplex containing v is anchored at v - o for an offset o of its chain. */
+static int lower_star(const fctx_t *c, int64_t v, int dim, int64_t *ids, fkey_t *keys)
+{
+    static const int EDGE_CHAIN[7][2] = {{0, 1}, {0, 2}, {0, 3}, {0, 4}, {0, 5}, {0, 6}, {0, 7}};
+    const grid_t *g = &c->g;
+    int64_t x = v % g->nx, y = (v / g->nx) % g->ny, z = v / (g->nx * g->ny);
+    int cnt = 0;
+    for (int o = 0; o < 8; o++) {
+        int64_t ax = x - (o & 1), ay = y - ((o >> 1) & 1), az = z - ((o >> 2) & 1);
+        if (ax < 0 || ay < 0 || az < 0) continue;
+        int64_t a = vid(g, ax, ay, az);
+        int nk = ID_MULT[dim];
+        for (int k = 0; k < nk; k++) {
+            int chain[4], m = 0;
+            if (dim == 1) { chain[m++] = EDGE_CHAIN[k][0]; chain[m++] = EDGE_CHAIN[k][1]; }
+            else if (dim == 2) { chain[m++] = 0; chain[m++] = TRI_A[k]; chain[m++] = TRI_B[k]; }
+            else { chain[m++] = 0; chain[m++] = TET_A[k]; chain[m++] = TET_B[k]; chain[m++] = 7; }
+            int has = 0;
+            for (int i = 0; i < m; i++) has |= chain[i] == o;
+            if (!has) continue;
+            int64_t id = ID_MULT[dim] * a + k, vs[4];
+            if (!simplex_vertices(g, dim, id, vs)) continue;
+            int lower = 1;
+            for (int i = 0; i <= dim; i++)
+                if (vs[i] != v && c->rank[vs[i]] > c->rank[v]) lower = 0;
+            if (!lower) continue;
+            ids[cnt] = id;
+            keys[cnt] = key_of_vertices(c, dim, vs);
+            cnt++;
+        }
+    }
+    for (int i = 1; i < cnt; i++)
+        for (int j = i; j > 0 && key_lt(keys[j], keys[j - 1]); j--) {
+            fkey_t tk = keys[j]; keys[j] = keys[j - 1]; keys[j - 1] = tk;
+            int64_t ti = ids[j]; ids[j] = ids[j - 1]; ids[j - 1] = ti;
+        }
+    return cnt;
+}
+
+/* Reduced columns kept in one append-only arena (standard reduction: a
+ * column is final once processed). */
+typedef struct {
+    fkey_t *e;
+    int64_t n, cap;
+} arena_t;
+
+static int arena_push(arena_t *a, const fkey_t *src, int64_t len, int64_t *start)
+{
+    if (a->n + len > a->cap) {
+        int64_t nc = a->cap ? a->cap : 1 << 16;
+        while (nc < a->n + len) nc *= 2;
+        fkey_t *ne = realloc(a->e, sizeof(fkey_t) * (size_t)nc);
+        if (!ne) return OR_ERR_MEM;
+        a->e = ne; a->cap = nc;
+    }
+    memcpy(a->e + a->n, src, sizeof(fkey_t) * (size_t)len);
+    *start = a->n;
+    a->n += len;
+    return OR_OK;
+}
+
+/* dst <- dst + src (mod 2), both sorted increasingly. */
+static int xor_into(fkey_t **dst, int64_t *dn, int64_t *dcap, const fkey_t *src, int64_t sn,
+                    fkey_t **tmp, int64_t *tcap)
+{
+    int64_t need = *dn + sn;
+    if (need > *tcap) {
+        fkey_t *nt = realloc(*tmp, sizeof(fkey_t) * (size_t)need);
+        if (!nt) return OR_ERR_MEM;
+        *tmp = nt; *tcap = need;
+    }
+    int64_t i = 0, j = 0, k = 0;
+    fkey_t *d = *dst, *t = *tmp;
+    while (i < *dn || j < sn) {
+        if (j >= sn || (i < *dn && key_lt(d[i], src[j]))) t[k++] = d[i++];
+        else if (i >= *dn || key_lt(src[j], d[i])) t[k++] = src[j++];
+        else { i++; j++; }      /* 1 + 1 = 0 (mod 2) */
+    }
+    if (k > *dcap) {
+        fkey_t *nd = realloc(*dst, sizeof(fkey_t) * (size_t)k);
+        if (!nd) return OR_ERR_MEM;
+        *dst = nd; *dcap = k;
+    }
+    memcpy(*dst, t, sizeof(fkey_t) * (size_t)k);
+    *dn = k;
+    return OR_OK;
+}
+
+/* Reduction of the columns of dimension dim (1..3).
+ *   cleared: (dim)-simplex ids to skip (pivots of dimension dim+1), or NULL.
+ *   owner:   out, per (dim-1)-simplex id: the dim-simplex whose reduced
+ *            column has it as pivot, or -1.
+ *   zero:    out, per dim-simplex id: 1 when its column reduced to zero (or
+ *            was cleared), else 0. */
+static int reduce_dim(const fctx_t *c, int dim, const int64_t *cleared, int64_t *owner,
+                      uint8_t *zero, int64_t *additions)
+{
+    const int64_t n = c->n, nrow = n * ID_MULT[dim - 1], ncol = n * ID_MULT[dim];
+    for (int64_t i = 0; i < nrow; i++) owner[i] = -1;
+    for (int64_t i = 0; i < ncol; i++) zero[i] = 1;
+    /* where each stored (non-apparent) column sits in the arena */
+    int64_t *cstart = malloc(sizeof(int64_t) * (size_t)(ncol ? ncol : 1));
+    int32_t *clen = malloc(sizeof(int32_t) * (size_t)(ncol ? ncol : 1));
+    if (!cstart || !clen) { free(cstart); free(clen); return OR_ERR_MEM; }
+    for (int64_t i = 0; i < ncol; i++) clen[i] = -1;      /* -1: not stored (apparent) */
+    arena_t arena = {0};
+    fkey_t *col = NULL, *tmp = NULL, bnd[4];
+    int64_t cn = 0, ccap = 0, tcap = 0;
+    int64_t ids[36];
+    fkey_t keys[36];
+    int st = OR_OK;
+    for (int64_t r = 0; r < n && !st; r++) {
+        int64_t v = c->vert_of_rank[r];
+        int cnt = lower_star(c, v, dim, ids, keys);
+        for (int s = 0; s < cnt && !st; s++) {
+            int64_t tau = ids[s];
+            if (cleared && cleared[tau] >= 0) continue;    /* a birth: its column is zero */
+            int nb = boundary_keys(c, dim, tau, bnd);
+            if (nb > ccap) {
+                fkey_t *ncol2 = realloc(col, sizeof(fkey_t) * (size_t)nb);
+                if (!ncol2) { st = OR_ERR_MEM; break; }
+                col = ncol2; ccap = nb;
+            }
+            memcpy(col, bnd, sizeof(fkey_t) * (size_t)nb);
+            cn = nb;
+            int added = 0;
+            while (cn > 0) {
+                int64_t low = id_of_key(c, dim - 1, col[cn - 1]);
+                int64_t k = owner[low];
+                if (k < 0) break;
+                if (clen[k] >= 0) {
+                    st = xor_into(&col, &cn, &ccap, arena.e + cstart[k], clen[k], &tmp, &tcap);
+                } else {
+                    fkey_t kb[4];
+                    int kn = boundary_keys(c, dim, k, kb);
+                    st = xor_into(&col, &cn, &ccap, kb, kn, &tmp, &tcap);
+                }
+                if (st) break;
+                added = 1;
+                (*additions)++;
+            }
+            if (st || cn == 0) continue;
+            int64_t low = id_of_key(c, dim - 1, col[cn - 1]);
+            owner[low] = tau;
+            zero[tau] = 0;
+            if (added) {
+                if (cn > INT32_MAX) { st = OR_ERR_MEM; break; }
+                st = arena_push(&arena, col, cn, &cstart[tau]);
+                clen[tau] = (int32_t)cn;
+            }
+        }
+    }
+    free(col); free(tmp); free(arena.e); free(cstart); free(clen);
+    return st;
+}
+
+static int emit_pairs(const fctx_t *c, int dim, const int64_t *owner, int keep_zero,
+                      result_t *res)
+{
+    /* owner indexes (dim-1)-simplices; each pivot gives the pair
+     * (birth = that (dim-1)-simplex, death = its owner). */
+    const int64_t nrow = c->n * ID_MULT[dim - 1];
+    for (int64_t b = 0; b < nrow; b++) {
+        int64_t d = owner[b];
+        if (d < 0) continue;
+        int64_t vb[4], vd[4];
+        simplex_vertices(&c->g, dim - 1, b, vb);
+        simplex_vertices(&c->g, dim, d, vd);
+        int64_t bmax = max_vertex_of_key(c, key_of_vertices(c, dim - 1, vb));
+        int64_t dmax = max_vertex_of_key(c, key_of_vertices(c, dim, vd));
+        if (bmax == dmax && !keep_zero) continue;
+        int64_t row[8] = {dim - 1, b, d, bmax, dmax, 0, -1, -1};
+        int st = push_row(res, row);
+        if (st) return st;
+    }
+    return OR_OK;
+}
+
+int oracle_fastpairs(int64_t nx, int64_t ny, int64_t nz, int dtype, const void *values,
+                     int keep_zero, int64_t **out_rows, int64_t *out_n, int64_t *additions)
+{
+    if (!grid_ok(nx, ny, nz) || !values || !out_rows || !out_n) return OR_ERR_ARG;
+    fctx_t c = {{nx, ny, nz}, nx * ny * nz, NULL, NULL};
+    const int64_t n = c.n;
+    int st;
+    int64_t adds = 0;
+    c.rank = malloc(sizeof(int64_t) * (size_t)n);
+    c.vert_of_rank = malloc(sizeof(int64_t) * (size_t)n);
+    if (!c.rank || !c.vert_of_rank) { free(c.rank); free(c.vert_of_rank); return OR_ERR_MEM; }
+    if ((st = vertex_ranks(dtype, values, n, c.rank))) {
+        free(c.rank); free(c.vert_of_rank); return st;
+    }
+    for (int64_t v = 0; v < n; v++) c.vert_of_rank[c.rank[v]] = v;
+
+    /* owner[d]: per (d-1)-simplex, the d-simplex whose column it is the
+     * pivot of; zero[d]: per d-simplex, column reduced to zero */
+    int64_t *owner[4] = {NULL, NULL, NULL, NULL};
+    uint8_t *zero[4] = {NULL, NULL, NULL, NULL};
+    for (int d = 1; d <= 3 && !st; d++) {
+        owner[d] = malloc(sizeof(int64_t) * (size_t)(n * ID_MULT[d - 1]));
+        zero[d] = malloc((size_t)(n * ID_MULT[d]));
+        if (!owner[d] || !zero[d]) st = OR_ERR_MEM;
+    }
+    /* tets first, then triangles cleared by the tets' pivots, then edges
+     * cleared by the triangles' pivots */
+    for (int d = 3; d >= 1 && !st; d--)
+        st = reduce_dim(&c, d, d < 3 ? owner[d + 1] : NULL, owner[d], zero[d], &adds);
+
+    result_t res = {0};
+    for (int d = 1; d <= 3 && !st; d++) st = emit_pairs(&c, d, owner[d], keep_zero, &res);
+    /* infinite classes: simplices that are neither a pivot of the next
+     * dimension nor the owner of a pivot */
+    for (int dim = 0; dim <= 3 && !st; dim++) {
+        for (int64_t id = 0; id < n * ID_MULT[dim] && !st; id++) {
+            int birth = dim < 3 && owner[dim + 1][id] >= 0;
+            int death = dim > 0 && !zero[dim][id];
+            int64_t vs[4];
+            if (birth || death || !simplex_vertices(&c.g, dim, id, vs)) continue;
+            int64_t v = max_vertex_of_key(&c, key_of_vertices(&c, dim, vs));
+            int64_t row[8] = {dim, id, -1, v, -1, 1, -1, -1};
+            st = push_row(&res, row);
+        }
+    }
+    for (int d = 1; d <= 3; d++) { free(owner[d]); free(zero[d]); }
+    free(c.rank); free(c.vert_of_rank);
+    if (st) { free(res.rows); return st; }
+    *out_rows = res.rows;
+    *out_n = res.n;
+    if (additions) *additions = adds;
+    return OR_OK;
+}

@@ -9,8 +9,9 @@ are the independent ones of ``test_oracle_pins.py`` and
 ``test_oracle_sandwich.py``, on small cases: the id scheme against the chain
 definition, the pairing against the rank formula, persistent Betti numbers,
 the union-find special cases, the elevation bar, the sandwich's steps against
-the standard reduction, generator cycles, and the invariants of the option
-without the virtual maximum.
+the standard reduction, generator cycles, the invariants of the option
+without the virtual maximum, and the fast-mode reduction against the rank
+formula and the textbook mode.
 """
 import importlib.util
 import os
@@ -160,8 +161,33 @@ def check_without_virtual_max(orc):
             "highest maximum"
 
 
+def check_fast(orc):
+    """The fast-mode reduction against the rank formula and the textbook mode."""
+    rng = np.random.default_rng(11)
+    for shape, kind, trials in [((2, 2, 2), "perm", 8), ((3, 2, 2), "ties", 4)]:
+        for _ in range(trials):
+            v = _field(rng, shape, kind)
+            order = bf.lex_order(bf.freudenthal_simplices(shape), bf.vertex_keys(v))
+            want, paired = set(), set()
+            for i, j in bf.pairing_by_ranks(order):
+                want.add((len(order[i]) - 1, bf.simplex_id(shape, order[i]),
+                          bf.simplex_id(shape, order[j])))
+                paired |= {i, j}
+            rows = orc.fastpairs(v, keep_zero=True)
+            assert {(int(r[0]), int(r[1]), int(r[2])) for r in rows if not r[5]} == want, \
+                "fast mode: rank formula"
+            assert {(int(r[0]), int(r[1])) for r in rows if r[5]} == \
+                {(len(order[i]) - 1, bf.simplex_id(shape, order[i]))
+                 for i in range(len(order)) if i not in paired}, "fast mode: infinite"
+    for shape, kind in [((6, 5, 4), "float"), ((5, 5, 4), "ties")]:
+        v = _field(rng, shape, kind)
+        full = {tuple(int(x) for x in r[:6]) for r in orc.pairsimplices(v)}
+        assert {tuple(int(x) for x in r[:6]) for r in orc.fastpairs(v)} == full, \
+            "fast mode = textbook"
+
+
 CHECKS = [check_ids, check_rank_formula, check_betti, check_union_find, check_elevation,
-          check_sandwich, check_generators, check_without_virtual_max]
+          check_sandwich, check_generators, check_without_virtual_max, check_fast]
 
 
 def main(directory):

@@ -6,7 +6,8 @@ mistake in its C source, builds the copy and runs the compact pin set of
 fail (or the copy must crash).  The unmodified copy must pass them all.  The
 mistakes cover the vertex order, the filtration order, the id tables, the
 boundary, the pivot, the zero-persistence filter, both union-find special
-cases and the sandwich's steps.
+cases, the sandwich's steps and the fast-mode reduction (clearing, the
+streamed order, implicit boundaries, the key packing, infinite classes).
 """
 import os
 import shutil
@@ -61,6 +62,27 @@ MUTANTS = [
     ("sandwich: infinite maxima dropped", "sandwich.c",
      "if (w->grad[p] >= 0 || partner[p] >= 0) continue;",
      "if (w->grad[p] >= 0 || partner[p] >= 0 || w->s[p].dim == 3) continue;"),
+    ("fast mode: clearing inverted", "fastpairs.c",
+     "if (cleared && cleared[tau] >= 0) continue;",
+     "if (cleared && cleared[tau] < 0) continue;"),
+    ("fast mode: a lower star visited in decreasing order", "fastpairs.c",
+     "for (int j = i; j > 0 && key_lt(keys[j], keys[j - 1]); j--) {",
+     "for (int j = i; j > 0 && key_lt(keys[j - 1], keys[j]); j--) {"),
+    ("fast mode: a boundary without its last facet", "fastpairs.c",
+     "for (int drop = 0; drop <= dim; drop++) {",
+     "for (int drop = 0; drop < dim; drop++) {"),
+    ("fast mode: a coface before its face", "fastpairs.c",
+     "k.lo = ((uint64_t)(r[2] + 1) << 32) | (uint64_t)(r[3] + 1);",
+     "k.lo = ((uint64_t)(r[2]) << 32) | (uint64_t)(r[3]);"),
+    ("fast mode: zero-persistence filter inverted", "fastpairs.c",
+     "if (bmax == dmax && !keep_zero) continue;",
+     "if (bmax != dmax && !keep_zero) continue;"),
+    ("fast mode: births reported as infinite", "fastpairs.c",
+     "int birth = dim < 3 && owner[dim + 1][id] >= 0;",
+     "int birth = 0;"),
+    ("fast mode: dimensions reduced upward, clearing from pivots not yet found", "fastpairs.c",
+     "for (int d = 3; d >= 1 && !st; d--)",
+     "for (int d = 1; d <= 3 && !st; d++)"),
 ]
 
 
