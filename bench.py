@@ -1,15 +1,22 @@
 """Benchmark of the full D0/D1/D2 pipeline on one GPU (or N independent
 replicas under torchrun), printing one JSON line.
 
-Workload: 256^3 float32 white noise (seed 2) -- the paper's "random" stress
-case (largest diagrams, densest critical cells), one field per step.  A step
-is one pass of the whole pipeline (gradient, critical simplices, D0, D2, D1,
-output) over that field.
+Workload: the 512^3 uint16 field (64 Gaussians + uniform noise of half-width
+5 % of the range, quantised: heavy ties broken by vertex id, seed 3), one
+field per step -- the largest single-GPU configuration.  A step is one pass
+of the whole pipeline (gradient, critical simplices, D0, D2, D1, output) over
+that field.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (the standard reduction of Alg. 1) on
 bounded sub-volumes of the same field, on this machine's host cores.
+
+Rooflines in the line: ``roofline`` for the kernel family that takes the most
+device time, ``roofline_gradient`` for the gradient stage (classification,
+compaction and ProcessLowerStars) against its algorithmic bytes N*s_in +
+8*|C| (every value read once, every critical simplex written once), and
+``roofline_classify`` for the per-vertex stencil alone.
 """
 from __future__ import annotations
 
@@ -29,7 +36,11 @@ sys.path.insert(0, ROOT)
 
 import synthfields as sf  # noqa: E402
 
-WORKLOAD = "noise256_f32"
+WORKLOAD = "mixture512_u16"
+WORKLOAD_TEXT = ("512^3 uint16: 64 Gaussians + uniform noise of half-width 0.05*(max-min), "
+                 "quantised to uint16 (heavy ties), seed 3 (one field per step)")
+DTYPE_NAME = "u16"
+SMS, SMSPS, SM_MAX_MHZ = 152, 4, 2070.0    # GB300: issue peak = SMs x schedulers x clock
 METRIC = "full-diagram Mvertices/s"
 UNIT = "Mvertices/s"
 L2_BYTES = 129 * 2**20
@@ -37,11 +48,11 @@ ORACLE_SAMPLE = 64          # edge of the cube cropped for the oracle (cpu_basel
 SERVE_REQUESTS = 1024       # requests of the serving workload replayed per run
 SERVE_BATCH = 16            # most requests one batched pass takes
 # DRAM bytes per launch of the classification stencil on this workload, from
-# one ncu capture (profiles/classify_dram_noise256_f32.md), valid only for the
-# code it was taken on (sha256 of the code behind that kernel, comments
-# excluded: _CLASSIFY_SPANS); otherwise reported as null.
+# one ncu capture (profiles/classify_u16_512.md), valid only for the code it
+# was taken on (sha256 of the code behind that kernel, comments excluded:
+# _CLASSIFY_SPANS); otherwise reported as null.
 CLASSIFY_TRAFFIC = {"sources_sha256": "eb26737328563b5ce987eccc9b9472e26eb7afd8df787c6404174cb78de85218",
-                    "bytes_per_launch": 67167232 + 6994176}
+                    "bytes_per_launch": 268718336 + 117972992}
 
 
 def _code_only(src: str) -> str:
@@ -170,6 +181,40 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_info():
+    """The host the oracle runs on: CPU model, logical CPUs, RAM."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    ram = None
+    try:
+        with open("/proc/meminfo") as f:
+            ram = round(int(f.readline().split()[1]) / 2**20, 1)
+    except (OSError, ValueError, IndexError):
+        pass
+    import platform
+    return {"cpu_model": model, "machine": platform.machine(), "os_cpu_count": os.cpu_count(),
+            "host_ram_gib": ram}
+
+
+def workload_field():
+    """The bench field, generated with torch on the GPU when there is one (the
+    Gaussians only; the same formula and seeds as on the CPU)."""
+    dev = None
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else None
+    except ImportError:
+        pass
+    return sf.config_field(WORKLOAD, device=dev)
+
+
 def _oracle_sample(field, edge):
     """Times the oracle on an edge^3 crop of the field (CPU, single thread)."""
     import oracle
@@ -185,7 +230,7 @@ def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
         return
-    field = sf.config_field(WORKLOAD)
+    field = workload_field()
     for _ in range(args.warmup):
         _oracle_sample(field, 16)
     tot_v, tot_t = 0, 0.0
@@ -194,15 +239,15 @@ def run_reference(args):
         tot_v += nv
         tot_t += dt
     value = tot_v / tot_t / 1e6
-    sample = f"{REFERENCE_SAMPLE}^3 crop of the 256^3 white-noise field per step"
+    sample = (f"{REFERENCE_SAMPLE}^3 corner crop of the {WORKLOAD_TEXT.split(':')[0]} field per "
+              "step, textbook standard reduction, one thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": {"workload": "256^3 float32 white noise U[0,1), seed 2",
-                                        "oracle_sample": sample},
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME,
+        "data": "synthetic", "config": {"workload": WORKLOAD_TEXT, "oracle_sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, **host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -239,6 +284,48 @@ def serving_section():
     }
 
 
+def roofline_gradient(n, s_in, stats, kavg, hbm, src):
+    """The gradient stage against its algorithmic bytes: every value read once
+    (N*s_in) and every critical simplex written once (8*|C|), over the device
+    time of classification + compaction + ProcessLowerStars."""
+    ncrit = sum(stats[f"c{d}"] for d in range(4))
+    nbytes = n * s_in + 8 * ncrit
+    ms = kavg["classify"] + kavg["compact"] + kavg["process_lower_stars"]
+    gbs = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else None
+    return {"bound": "hbm", "kernel": "gradient stage (k_classify2, k_compact2, k_pls_sorted)",
+            "achieved": gbs, "peak": hbm, "unit": "GB/s",
+            "frac": gbs / hbm if gbs is not None else None, "traffic": None,
+            "algorithmic_bytes_per_launch": nbytes, "ms": ms, "peak_source": src,
+            "critical_simplices": ncrit,
+            "note": "bound by ProcessLowerStars' integer work on the PL-critical vertices, "
+                    "not by HBM"}
+
+
+def roofline_classify(n, s_in, kavg, hbm, src):
+    """The per-vertex stencil (k_classify2): values in, one flag byte out."""
+    nbytes = n * s_in + n + 4 * (n // 2048 + 1)      # values in, flag bytes out, tile counts
+    gbs = nbytes / (kavg["classify"] * 1e-3) / 1e9
+    traffic = (CLASSIFY_TRAFFIC["bytes_per_launch"]
+               if CLASSIFY_TRAFFIC["sources_sha256"] == _kernel_sources_sha256() else None)
+    return {"bound": "hbm", "kernel": "k_classify2", "achieved": gbs, "peak": hbm,
+            "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
+            "algorithmic_bytes_per_launch": nbytes, "peak_source": src}
+
+
+def roofline_dominant(dom, kavg, rgrad, rcls, hbm, src):
+    """The family with the most device time.  The stencil and the gradient
+    stage are measured against HBM; the walks, union-find levels and the D1
+    reduction have no algorithmic byte count that bounds them (dependent
+    gathers, atomics and addition chains) and are reported with their time."""
+    if dom == "classify":
+        return dict(rcls)
+    if dom in ("process_lower_stars", "compact"):
+        return dict(rgrad)
+    return {"bound": "hbm", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s",
+            "frac": None, "traffic": None, "ms": kavg[dom], "peak_source": src,
+            "note": "latency-bound (dependent loads, atomics); no algorithmic byte count"}
+
+
 def run_ours(args):
     import torch
     import paper_2206_13932_gb300 as dms
@@ -254,7 +341,7 @@ def run_ours(args):
     shape, dtype, recipe = sf.CONFIGS[WORKLOAD]
     nx, ny, nz = shape
     n = nx * ny * nz
-    field = sf.config_field(WORKLOAD)
+    field = workload_field()
     dev = torch.from_numpy(field).cuda()
     host = torch.from_numpy(field).pin_memory()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -269,6 +356,13 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         g.compute(dev)
+    # pinned host buffers for the pairs of the end-to-end runs (sized once)
+    pcount, ecount = g.counts()
+    outs = []
+    for d in range(3):
+        k = pcount[d] + ecount[d]
+        buf = torch.empty(max(k, 1) * dms.PAIR_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+        outs.append(buf.numpy().view(dms.PAIR_DTYPE))
     # ---- device-resident timing (inputs in HBM, L2 flushed before each step)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -290,7 +384,8 @@ def run_ours(args):
     value = replicas.job_throughput(n, ms) / 1e6
     stats = g.stats()
     counts = g.counts()
-    # ---- end to end through the C ABI: host field in, host pairs out
+    stage = g.stage_ms()
+    # ---- end to end through the C ABI: pinned host field in, host pairs out
     e2e_ms = []
     d2h = 0
     for k in range(args.steps):
@@ -298,14 +393,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.compute(host)
-        pairs = [g.fetch(d) for d in range(3)]
+        pairs = [g.fetch(d, out=outs[d]) for d in range(3)]
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
         d2h = sum(p.nbytes for p in pairs)
     e2e_val = replicas.job_throughput(
         n, replicas.max_over_ranks(statistics.mean(e2e_ms), device="cuda")) / 1e6
     if rank != 0:
         return
-    # ---- rooflines: the dominant kernel family, and the per-vertex stencil
+    # ---- rooflines
     kavg = {k: v / args.steps for k, v in kern.items()}
     dom = max(kavg, key=kavg.get)
     s_in = np.dtype(dtype).itemsize
@@ -316,26 +411,9 @@ def run_ours(args):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     src = "measured" if peaks else "fallback"
-    cls_bytes = n * s_in + n + 4 * (n // 2048 + 1)      # values in, flag bytes out, tile counts
-    cls_gbs = cls_bytes / (kavg["classify"] * 1e-3) / 1e9
-    cls_traffic = (CLASSIFY_TRAFFIC["bytes_per_launch"]
-                   if CLASSIFY_TRAFFIC["sources_sha256"] == _kernel_sources_sha256() else None)
-    roof_grad = {"bound": "hbm", "kernel": "k_classify2", "achieved": cls_gbs, "peak": hbm,
-                 "unit": "GB/s", "frac": cls_gbs / hbm, "traffic": cls_traffic,
-                 "algorithmic_bytes_per_launch": cls_bytes, "peak_source": src}
-    if dom == "d1_reduce":
-        red_bytes = stats["d1_bytes_read"] + stats["d1_bytes_written"]
-        gbs = red_bytes / (kavg[dom] * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "D1 reduction (k_red_claim, k_red_publish, "
-                    "k_red_add, k_red_add_block, k_red_async)", "achieved": gbs, "peak": hbm,
-                    "unit": "GB/s",
-                    "frac": gbs / hbm, "traffic": None,
-                    "algorithmic_bytes_per_step": red_bytes, "peak_source": src,
-                    "note": "latency-bound on long addition chains"}
-    else:
-        roofline = dict(roof_grad) if dom == "classify" else {
-            "bound": "latency", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s",
-            "frac": None, "traffic": None, "peak_source": src}
+    rgrad = roofline_gradient(n, s_in, stats, kavg, hbm, src)
+    rcls = roofline_classify(n, s_in, kavg, hbm, src)
+    roofline = roofline_dominant(dom, kavg, rgrad, rcls, hbm, src)
     serving = None
     if not args.no_serve:
         try:
@@ -347,24 +425,26 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "256^3 float32 white noise U[0,1), seed 2 (one field per step)",
+        "vs_baseline": None, "dtype": DTYPE_NAME, "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT,
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": n * s_in,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roofline,
-        "roofline_gradient": roof_grad,
+        "roofline_gradient": rgrad,
+        "roofline_classify": rcls,
         "dominant_kernel": {"name": dom, "ms": kavg[dom]},
         "kernel_ms": kavg,
-        "stage_ms": g.stage_ms(),
+        "stage_ms": stage,
         "stats": stats,
         "pairs": {"d0": counts[0][0], "d1": counts[0][1], "d2": counts[0][2],
                   "essential": list(counts[1])},
         "cpu_baseline": {"value": nv / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{ORACLE_SAMPLE}^3 crop of the same field, standard reduction",
-                         "seconds": dt},
+                         "sample": f"{ORACLE_SAMPLE}^3 corner crop of the same field, textbook "
+                                   "standard reduction, one thread",
+                         "seconds": dt, **host_info()},
         "clocks": clk.summary(),
         "serving": serving,
     }

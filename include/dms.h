@@ -158,19 +158,28 @@ dms_status dms_get_counts(dms_grid grid, int64_t pairs[3], int64_t essential[4])
 dms_status dms_fetch_pairs(dms_grid grid, int dim, dms_pair *out, int64_t cap,
                            int64_t *written, int out_is_device);
 
+/* Identifier of the last successful compute of the handle: every
+ * successful dms_compute_diagram gives a new value (a counter of the
+ * handle).  DMS_ERR_STATE without a result. */
+dms_status dms_get_result_id(dms_grid grid, uint64_t *result_id);
+
 /* Backward pass of a loss of the diagram (differentiation).  The value of a
  * pair is the value of its maximum vertices (Sec. 2.4: persistence =
  * f(max vertex of death) - f(max vertex of birth)), so the gradient of a
  * loss with respect to the field is the sum, at each vertex, of the
  * gradients of the births and deaths whose maximum vertex it is.
+ * result_id: the dms_get_result_id of the compute whose pairs the gradients
+ * belong to; if the handle has computed another field since (or holds no
+ * result), the call returns DMS_ERR_STATE and launches nothing, since the
+ * gradient arrays would not match the current pairs.
  * grad_birth / grad_death: device arrays of doubles, one per pair of
  * dimension dim in dms_fetch_pairs order (either may be NULL; the death
  * gradient of an infinite class is ignored).  grad_field: device array of
  * nx*ny*nz doubles that the call adds into (atomically; the caller zeroes
- * it first).  Runs on `stream`, asynchronously; needs the result of the last
- * successful dms_compute_diagram. */
-dms_status dms_backward_pairs(dms_grid grid, int dim, const double *grad_birth,
-                              const double *grad_death, double *grad_field, void *stream);
+ * it first).  Runs on `stream`, asynchronously. */
+dms_status dms_backward_pairs(dms_grid grid, int dim, uint64_t result_id,
+                              const double *grad_birth, const double *grad_death,
+                              double *grad_field, void *stream);
 
 /* Per-stage device milliseconds of the last compute (CUDA events):
  * [0] gradient (classification + ProcessLowerStars + compaction),

@@ -13,7 +13,7 @@ streams.  There is no CPU fallback: if the library is missing the calls raise.
 - :func:`classify_static` -- the allocation-free classification step.
 - Submodules: ``autograd`` (differentiable births and deaths), ``serve``
   (continuous-batching server), ``autotune`` (launch shapes), ``replicas``
-  (timing of independent replicas), ``run_case`` (one workload, for profiling).
+  (timing of independent replicas).
 """
 from __future__ import annotations
 
@@ -80,8 +80,10 @@ def load(build_if_missing: bool = False):
             lib.dms_classify_static.argtypes = [vp, ctypes.c_int, i64, i64, i64, vp, vp, i64,
                                                 p64, vp]
             lib.dms_classify_static.restype = ctypes.c_int
-            lib.dms_backward_pairs.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
+            lib.dms_backward_pairs.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, vp, vp, vp, vp]
             lib.dms_backward_pairs.restype = ctypes.c_int
+            lib.dms_get_result_id.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+            lib.dms_get_result_id.restype = ctypes.c_int
             lib.dms_grid_reshape.argtypes = [vp, i64, i64, i64]
             lib.dms_grid_reshape.restype = ctypes.c_int
             lib.dms_batch_create.argtypes = [i64, p64, ctypes.c_int, ctypes.POINTER(_Options),
@@ -193,14 +195,19 @@ class Grid:
         _check(self._lib.dms_get_counts(self._h, p, e), "dms_get_counts")
         return tuple(p), tuple(e)
 
-    def fetch(self, dim: int) -> np.ndarray:
-        """Pairs of dimension ``dim`` as a structured array of PAIR_DTYPE."""
+    def fetch(self, dim: int, out: np.ndarray | None = None) -> np.ndarray:
+        """Pairs of dimension ``dim`` as a structured array of PAIR_DTYPE.
+        ``out``: a host array of PAIR_DTYPE to copy into (e.g. a view of
+        pinned memory, reused across calls); the result is its first part."""
         p, e = self.counts()
         n = p[dim] + e[dim]
-        out = np.zeros(n, PAIR_DTYPE)
+        if out is None:
+            out = np.empty(n, PAIR_DTYPE)
+        elif out.dtype != PAIR_DTYPE or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous PAIR_DTYPE array")
         w = ctypes.c_int64(0)
-        _check(self._lib.dms_fetch_pairs(self._h, dim, out.ctypes.data if n else None, n,
-                                         ctypes.byref(w), 0), "dms_fetch_pairs")
+        _check(self._lib.dms_fetch_pairs(self._h, dim, out.ctypes.data if n else None,
+                                         len(out), ctypes.byref(w), 0), "dms_fetch_pairs")
         return out[: w.value]
 
     def fetch_device(self, dim: int, out_ptr: int, cap: int) -> int:
@@ -228,6 +235,12 @@ class Grid:
         b = ctypes.c_int64(0)
         _check(self._lib.dms_get_device_bytes(self._h, ctypes.byref(b)), "dms_get_device_bytes")
         return int(b.value)
+
+    def result_id(self) -> int:
+        """Identifier of the last successful compute (new for every compute)."""
+        r = ctypes.c_uint64(0)
+        _check(self._lib.dms_get_result_id(self._h, ctypes.byref(r)), "dms_get_result_id")
+        return int(r.value)
 
     def stats(self):
         s = (ctypes.c_int64 * 16)()

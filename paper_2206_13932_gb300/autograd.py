@@ -55,8 +55,9 @@ class _DiagramFn(torch.autograd.Function):
     field; backward scatters their gradients with dms_backward_pairs."""
 
     @staticmethod
-    def forward(ctx, values, grid, counts, *bd):
+    def forward(ctx, values, grid, counts, result_id, *bd):
         ctx.grid = grid
+        ctx.result_id = result_id
         ctx.shape = values.shape
         ctx.dtype = values.dtype
         ctx.counts = counts
@@ -75,18 +76,20 @@ class _DiagramFn(torch.autograd.Function):
             gb = gb.to(torch.float64).contiguous() if gb is not None else None
             gd = gd.to(torch.float64).contiguous() if gd is not None else None
             _check(grid._lib.dms_backward_pairs(
-                grid._h, d, ctypes.c_void_p(gb.data_ptr() if gb is not None else 0),
+                grid._h, d, ctx.result_id, ctypes.c_void_p(gb.data_ptr() if gb is not None else 0),
                 ctypes.c_void_p(gd.data_ptr() if gd is not None else 0),
                 ctypes.c_void_p(gfield.data_ptr()), ctypes.c_void_p(int(stream))),
                 "dms_backward_pairs")
-        return (gfield.to(ctx.dtype).view(ctx.shape), None, None) + (None,) * len(grads)
+        return (gfield.to(ctx.dtype).view(ctx.shape), None, None, None) + (None,) * len(grads)
 
 
 def persistence_diagram(values: torch.Tensor, grid: Grid | None = None) -> list:
     """D0, D1, D2 of a CUDA field indexed [z, y, x] (float32 or float64), with
     births and deaths differentiable with respect to ``values``.  ``grid`` (a
     :class:`Grid` of the field's shape and dtype) may be reused across calls;
-    it must stay alive until the backward pass has run.  With a :class:`Batch`
+    it must stay alive until the backward pass has run, and the backward pass
+    refuses (DMS_ERR_STATE) once the grid has computed another field since,
+    because its pairs are no longer the ones these diagrams hold.  With a :class:`Batch`
     as ``grid``, ``values`` holds its fields packed one after another and the
     diagrams hold every field's pairs, grouped by field (``grid.offsets(d)``
     gives the ranges); the gradient comes back in the packed layout."""
@@ -108,7 +111,7 @@ def persistence_diagram(values: torch.Tensor, grid: Grid | None = None) -> list:
                _bits_to_values(i64[:, 5].contiguous(), values.dtype)]
         meta.append((rec[:, 49].to(torch.bool), i64[:, 2].clone(), i64[:, 3].clone(),
                      i64[:, 0].clone(), i64[:, 1].clone()))
-    outs = _DiagramFn.apply(values, grid, counts, *bd)
+    outs = _DiagramFn.apply(values, grid, counts, grid.result_id(), *bd)
     return [Diagram(outs[2 * d], outs[2 * d + 1], *meta[d]) for d in range(3)]
 
 

@@ -79,10 +79,18 @@ dms_status dms_fetch_pairs(dms_grid grid, int dim, dms_pair *out, int64_t cap, i
     return grid->p.fetch(dim, out, cap, written, out_is_device);
 }
 
-dms_status dms_backward_pairs(dms_grid grid, int dim, const double *grad_birth,
-                              const double *grad_death, double *grad_field, void *stream) {
+dms_status dms_get_result_id(dms_grid grid, uint64_t *result_id) {
+    if (!grid || !result_id) return DMS_ERR_INVALID_ARG;
+    if (!grid->p.has_result) return DMS_ERR_STATE;
+    *result_id = grid->p.result_id;
+    return DMS_OK;
+}
+
+dms_status dms_backward_pairs(dms_grid grid, int dim, uint64_t result_id,
+                              const double *grad_birth, const double *grad_death,
+                              double *grad_field, void *stream) {
     if (!grid) return DMS_ERR_INVALID_ARG;
-    return grid->p.backward(dim, grad_birth, grad_death, grad_field, stream);
+    return grid->p.backward(dim, result_id, grad_birth, grad_death, grad_field, stream);
 }
 
 dms_status dms_get_stage_ms(dms_grid grid, float ms[8]) {

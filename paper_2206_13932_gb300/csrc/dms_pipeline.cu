@@ -3400,7 +3400,11 @@ template <> Geo<false> geo_of<false>(const Ctx &c) {
 }
 template <> Geo<true> geo_of<true>(const Ctx &c) { return c.bgeo; }
 
-uint32_t g_tables_ready = 0;   // one bit per device id (< 32)
+// Devices whose constant tables are uploaded, guarded by g_tables_mutex: handles are
+// created from several host threads (one per serving slot), and the upload must
+// happen once per device, before any kernel there reads the tables.
+std::mutex g_tables_mutex;
+std::vector<char> g_tables_ready;   // indexed by device id
 
 #define DMS_CUDA(call)                                                                 \
     do {                                                                               \
@@ -3435,7 +3439,9 @@ uint32_t g_tables_ready = 0;   // one bit per device id (< 32)
     } while (0)
 
 dms_status ensure_tables(int device) {
-    if (device < 32 && (g_tables_ready >> device & 1)) return DMS_OK;
+    if (device < 0) return DMS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_tables_mutex);
+    if ((size_t)device < g_tables_ready.size() && g_tables_ready[device]) return DMS_OK;
     StarTables S;
     if (!build_star_tables(S)) return DMS_ERR_STATE;
     std::vector<uint32_t> lut;
@@ -3446,7 +3452,8 @@ dms_status ensure_tables(int device) {
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAsyncSmem));
     DMS_CUDA(cudaFuncSetAttribute(k_red_add_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kRedSmem));
-    if (device < 32) g_tables_ready |= 1u << device;
+    if ((size_t)device >= g_tables_ready.size()) g_tables_ready.resize(device + 1, 0);
+    g_tables_ready[device] = 1;
     return DMS_OK;
 }
 
@@ -4829,6 +4836,7 @@ dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
             kernel_ms[k] = t;
         }
         has_result = true;
+        result_id++;
     } else {
         cudaStreamSynchronize(c.s);
         cudaGetLastError();
@@ -4836,9 +4844,9 @@ dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
     return s;
 }
 
-dms_status Pipeline::backward(int dim, const double *gbirth, const double *gdeath, double *grad,
-                              void *stream) {
-    if (!has_result) return DMS_ERR_STATE;
+dms_status Pipeline::backward(int dim, uint64_t rid, const double *gbirth, const double *gdeath,
+                              double *grad, void *stream) {
+    if (!has_result || rid != result_id) return DMS_ERR_STATE;   // not the caller's pairing
     if (dim < 0 || dim > 2 || !grad) return DMS_ERR_INVALID_ARG;
     const int64_t total = n_pairs[dim] + n_ess[dim];
     if (total == 0) return DMS_OK;

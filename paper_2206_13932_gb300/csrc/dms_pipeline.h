@@ -87,6 +87,7 @@ struct Pipeline {
     void *kev[24] = {nullptr};   // cudaEvent_t pairs per kernel family
     void *sev[8] = {nullptr};    // cudaEvent_t stage boundaries
     bool has_result = false;
+    uint64_t result_id = 0;   // bumped by every successful compute
 
     dms_status init(int64_t nx, int64_t ny, int64_t nz, dms_dtype dt, const dms_options *o);
     dms_status init_batch(int64_t nf, const int64_t *shapes, dms_dtype dt, const dms_options *o);
@@ -95,8 +96,8 @@ struct Pipeline {
     dms_status compute(const void *values, int on_host, void *stream);
     dms_status reshape(int64_t nx, int64_t ny, int64_t nz);
     dms_status fetch(int dim, dms_pair *out, int64_t cap, int64_t *written, int out_is_device);
-    dms_status backward(int dim, const double *gbirth, const double *gdeath, double *grad,
-                        void *stream);
+    dms_status backward(int dim, uint64_t rid, const double *gbirth, const double *gdeath,
+                        double *grad, void *stream);
     void destroy();
     std::vector<DevBuf *> buffers();   // every device buffer of the handle
     int64_t device_bytes();            // bytes they hold now

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = ["gaussian_mixture", "white_noise", "quantize_u16", "ramp", "constant",
            "config_field", "sha256", "CONFIGS", "blob_params", "serving_shapes", "serving_fields",
-           "poisson_arrivals"]
+           "serving_field", "poisson_arrivals"]
 
 
 def blob_params(n_blobs: int, rng: np.random.Generator):
@@ -150,6 +150,12 @@ def serving_fields(count: int, seed0: int = 4000, lo: int = 16, hi: int = 128):
     shapes = serving_shapes(count, seed0, lo, hi)
     return [gaussian_mixture(sh, 16, seed0 + i, noise=1e-3, dtype=np.float32)
             for i, sh in enumerate(shapes)]
+
+
+def serving_field(i: int, seed0: int = 4000, lo: int = 16, hi: int = 128):
+    """Field i of :func:`serving_fields` alone (the same shape and bytes)."""
+    shape = serving_shapes(i + 1, seed0, lo, hi)[i]
+    return gaussian_mixture(shape, 16, seed0 + i, noise=1e-3, dtype=np.float32)
 
 
 def poisson_arrivals(count: int, rate_per_s: float, seed: int = 4100):

@@ -1,6 +1,7 @@
-"""Runs the pipeline on one synthetic field (for profiling and timing).
+"""Runs the pipeline on one synthetic field (for profiling and timing): the
+driver of the ncu captures summarised under profiles/.
 
-    python -m paper_2206_13932_gb300.run_case --workload noise --edge 128 [--repeat 1]
+    python -m tests.run_case --workload noise --edge 128 [--repeat 1]
 
 Workloads: noise (iid U[0,1) float32, seed 2), mixture_u16 (the 512^3 uint16 recipe at
 the given edge), mixture32 (16 Gaussians + 1e-3 noise float32, seed 1).

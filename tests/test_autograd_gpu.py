@@ -124,6 +124,27 @@ def test_gradient_scatter_sums_shared_vertices(ad):
     assert np.allclose(t.grad.cpu().numpy().reshape(-1), want, rtol=1e-12, atol=1e-12)
 
 
+def test_backward_refuses_a_newer_result(ad):
+    """A grid that computed another field after the forward pass no longer
+    holds the pairs the saved gradients index: the backward pass is refused
+    (DMS_ERR_STATE) instead of scattering onto the new field's vertices, and
+    a forward on the current result still differentiates."""
+    import torch
+    import paper_2206_13932_gb300 as dms
+    a = sf.white_noise((10, 9, 8), 3, np.float64)
+    b = sf.white_noise((10, 9, 8), 4, np.float64)      # more pairs than a's D1 for some dims
+    with dms.Grid((10, 9, 8), np.float64) as g:
+        ta = torch.from_numpy(a).cuda().requires_grad_(True)
+        tb = torch.from_numpy(b).cuda().requires_grad_(True)
+        la = sum(ad.persistence_diagram(ta, g)[d].birth.sum() for d in range(3))
+        lb = sum(ad.persistence_diagram(tb, g)[d].birth.sum() for d in range(3))
+        with pytest.raises(dms.DmsError) as e:
+            la.backward()
+        assert e.value.status == 6
+        lb.backward()
+        assert tb.grad is not None and float(tb.grad.abs().sum()) > 0
+
+
 def test_batch_of_eight_128_fields(ad):
     """The differentiation workload: 8 float32 128^3 mixtures (16 blobs, no
     noise, seeds 5000+i), loss summed over the batch, backward in float32,

@@ -46,14 +46,22 @@ class _FakeGrid:
         return {k: 1.0 for k in ("gradient", "sort", "d0", "d2", "d1", "output", "total", "h2d")}
 
     def stats(self):
-        return {"launches": 50, "d1_bytes_read": 10 ** 8, "d1_bytes_written": 5 * 10 ** 7}
+        return {"launches": 50, "d1_bytes_read": 10 ** 8, "d1_bytes_written": 5 * 10 ** 7,
+                "c0": 10, "c1": 20, "c2": 30, "c3": 40}
 
     def counts(self):
         return (3, 2, 1), (1, 0, 0, 0)
 
-    def fetch(self, d):
+    def fetch(self, d, out=None):
         import paper_2206_13932_gb300 as dms
-        return np.zeros(2, dms.PAIR_DTYPE)
+        p, e = self.counts()
+        k = p[d] + e[d]
+        res = np.zeros(k, dms.PAIR_DTYPE)
+        if out is not None:
+            assert out.dtype == dms.PAIR_DTYPE and len(out) >= k
+            out[:k] = res
+            return out[:k]
+        return res
 
     def close(self):
         pass
@@ -83,7 +91,7 @@ def fake_device(monkeypatch):
     monkeypatch.setattr(serve, "CudaBackend", _FakeBackend)
     monkeypatch.setattr(bench, "L2_BYTES", 4096)
     monkeypatch.setattr(bench, "ORACLE_SAMPLE", 8)
-    monkeypatch.setitem(sf.CONFIGS, "noise256_f32", ((16, 16, 16), np.float32, "small"))
+    monkeypatch.setitem(sf.CONFIGS, "mixture512_u16", ((16, 16, 16), np.uint16, "small"))
     small = [np.random.default_rng(i).random((4 + i % 3, 5, 6)).astype(np.float32)
              for i in range(12)]
     monkeypatch.setattr(sf, "serving_fields", lambda count, *a, **k: small)
@@ -115,13 +123,20 @@ def test_one_line_with_every_contract_key(fake_device):
     assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
     assert d["gpu_launches"] == 100
     assert set(d["e2e"]) == {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
-    assert d["e2e"]["h2d_bytes_per_step"] == 16 ** 3 * 4
-    r = d["roofline"]
-    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["frac"] == pytest.approx(
-        r["achieved"] / r["peak"])
-    assert r["achieved"] == pytest.approx(1.5e8 / 4e-3 / 1e9)      # d1 bytes / d1_reduce time
+    assert d["e2e"]["h2d_bytes_per_step"] == 16 ** 3 * 2 and d["dtype"] == "u16"
+    assert d["e2e"]["d2h_bytes_per_step"] == (4 + 2 + 1) * 56
+    assert "512^3 uint16" in d["config"]["workload"]
+    r = d["roofline"]                      # d1_reduce dominates the fake timings
+    assert r["kernel"] == "d1_reduce" and r["achieved"] is None and r["frac"] is None
+    rg = d["roofline_gradient"]            # N*s_in + 8*|C| over classify+compact+PLS
+    assert rg["algorithmic_bytes_per_launch"] == 16 ** 3 * 2 + 8 * 100
+    assert rg["achieved"] == pytest.approx((16 ** 3 * 2 + 800) / 3e-3 / 1e9)
+    assert rg["frac"] == pytest.approx(rg["achieved"] / rg["peak"])
+    rc = d["roofline_classify"]
+    assert rc["bound"] == "hbm" and rc["frac"] == pytest.approx(rc["achieved"] / rc["peak"])
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0 and "sample" in cb
+    assert cb["os_cpu_count"] == os.cpu_count() and "cpu_model" in cb and "host_ram_gib" in cb
     s = d["serving"]
     assert s["requests"] == 12 and s["saturated"]["one_at_a_time_rps"] > 0
 
@@ -138,3 +153,15 @@ def test_a_failing_serving_section_keeps_the_line(fake_device, monkeypatch):
 
 def test_no_serve_skips_the_section(fake_device):
     assert _run(fake_device, {"no_serve": True})["serving"] is None
+
+
+def test_dominant_gradient_reports_the_stage(fake_device, monkeypatch):
+    """When ProcessLowerStars takes the most time, the headline roofline is
+    the gradient stage's."""
+    def kms(self):
+        return {k: (9.0 if k == "process_lower_stars" else 1.0) for k in self.KERNELS}
+    import paper_2206_13932_gb300 as dms
+    monkeypatch.setattr(dms.Grid, "kernel_ms", kms)
+    d = _run(fake_device, {"no_serve": True})
+    assert d["roofline"]["kernel"].startswith("gradient stage")
+    assert d["roofline"] == d["roofline_gradient"]

@@ -17,16 +17,34 @@ def _run(env_extra):
     return [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
 
 
-def test_rank0_prints_one_line_with_the_contract_keys():
-    lines = _run({"RANK": "0", "WORLD_SIZE": "1"})
+def test_rank0_prints_one_line_with_the_contract_keys(monkeypatch):
+    """In-process on a 24^3 stand-in of the workload (the 512^3 field takes a
+    minute to generate on a CPU)."""
+    import contextlib
+    import io
+
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import synthfields as sf
+    monkeypatch.setitem(sf.CONFIGS, "mixture512_u16", ((24, 24, 24), np.uint16, "small"))
+    monkeypatch.setattr(bench, "REFERENCE_SAMPLE", 12)
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    args = bench.argparse.Namespace(gpus=1, steps=1, warmup=0, impl="reference", no_serve=True)
+    out = io.StringIO()
+    with contextlib.redirect_stdout(out):
+        bench.run_reference(args)
+    lines = [ln for ln in out.getvalue().splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
               "cpu_baseline", "e2e"):
         assert k in d, k
-    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["impl"] == "reference" and d["value"] > 0 and d["dtype"] == "u16"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["os_cpu_count"] == os.cpu_count()
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
 
 

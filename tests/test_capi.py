@@ -87,7 +87,9 @@ def test_argument_checks_without_gpu():
     assert lib.dms_grid_reshape(null, 4, 4, 4) == bad
     assert lib.dms_batch_reshape(null, 1, p3) == bad
     assert lib.dms_batch_offsets(null, 0, p4) == bad
-    assert lib.dms_backward_pairs(null, 0, null, null, null, null) == bad
+    assert lib.dms_backward_pairs(null, 0, 0, null, null, null, null) == bad
+    r = ctypes.c_uint64(0)
+    assert lib.dms_get_result_id(null, ctypes.byref(r)) == bad
     assert lib.dms_get_stage_ms(null, (ctypes.c_float * 8)()) == bad
     assert lib.dms_get_kernel_ms(null, (ctypes.c_float * 12)()) == bad
     assert lib.dms_get_stats(null, (ctypes.c_int64 * 16)()) == bad
