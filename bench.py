@@ -253,10 +253,15 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+SERVE_LOADS = (0.5, 0.8, 0.95)   # Poisson arrival rates, fractions of one-at-a-time capacity
+
+
 def serving_section():
     """Continuous batching vs one request at a time on the serving workload:
     fields of log-uniform shapes in [16,128]^3 (16 Gaussians + 1e-3 noise,
-    float32), Poisson arrivals at 80 % of the one-at-a-time capacity."""
+    float32); back to back (throughput), then Poisson arrivals at 50, 80 and
+    95 % of the one-at-a-time capacity (latency, split into the wait for a
+    slot and the service)."""
     from paper_2206_13932_gb300 import serve
     fields = sf.serving_fields(SERVE_REQUESTS)
     nvert = sum(f.size for f in fields)
@@ -266,22 +271,24 @@ def serving_section():
     cap = len(fields) / w1
     r4, w4 = serve.run_stream(fields, zeros, slots=4)             # back to back, 4 slots
     rB, wB = serve.run_stream(fields, zeros, slots=4, max_batch=SERVE_BATCH)   # batched
-    arr = sf.poisson_arrivals(len(fields), 0.8 * cap)
-    rb, wb = serve.run_stream(fields, arr, slots=4)
-    rbb, wbb = serve.run_stream(fields, arr, slots=4, max_batch=SERVE_BATCH)
-    rs, ws = serve.run_stream(fields, arr, slots=1)
-    return {
+    out = {
         "requests": len(fields), "mean_vertices": nvert / len(fields),
         "saturated": {"one_at_a_time_rps": cap, "one_at_a_time_Mvertices_s": nvert / w1 / 1e6,
                       "served_4_slots_rps": len(fields) / w4,
                       "served_4_slots_Mvertices_s": nvert / w4 / 1e6,
                       f"batched_4_slots_x{SERVE_BATCH}_rps": len(fields) / wB,
                       f"batched_4_slots_x{SERVE_BATCH}_Mvertices_s": nvert / wB / 1e6},
-        "poisson_rho_0.8": {"rate_rps": 0.8 * cap,
-                            "served_4_slots": serve.latency_stats(rb),
-                            f"batched_4_slots_x{SERVE_BATCH}": serve.latency_stats(rbb),
-                            "one_at_a_time": serve.latency_stats(rs)},
     }
+    for rho in SERVE_LOADS:
+        arr = sf.poisson_arrivals(len(fields), rho * cap)
+        rb, _ = serve.run_stream(fields, arr, slots=4)
+        rbb, _ = serve.run_stream(fields, arr, slots=4, max_batch=SERVE_BATCH)
+        rs, _ = serve.run_stream(fields, arr, slots=1)
+        out[f"poisson_rho_{rho}"] = {"rate_rps": rho * cap,
+                                     "served_4_slots": serve.latency_stats(rb),
+                                     f"batched_4_slots_x{SERVE_BATCH}": serve.latency_stats(rbb),
+                                     "one_at_a_time": serve.latency_stats(rs)}
+    return out
 
 
 def roofline_gradient(n, s_in, stats, kavg, hbm, src):

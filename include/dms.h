@@ -52,8 +52,16 @@ typedef enum {
 typedef enum { DMS_U16 = 0, DMS_F32 = 1, DMS_F64 = 2 } dms_dtype;
 
 typedef struct {
-    int virtual_max;      /* 1 (the only supported value): Sec. 5.2 virtual
-                             maximum on the outer boundary                   */
+    int virtual_max;      /* 1: the outer boundary is one virtual maximum,
+                             older than every tet (Sec. 5.2, "Domains with
+                             boundary"); D2 then equals the standard
+                             reduction of the cube.  0: no virtual maximum
+                             (App. A): a 2-saddle whose ascending path
+                             leaves the domain on either side merges nothing
+                             in D2 and goes to D1; maxima left unpaired are
+                             infinite classes of dimension 3, and 2-saddles
+                             whose D1 column reduces to zero infinite classes
+                             of dimension 2.                                 */
     int64_t max_iters;    /* cap on device loops and path lengths; 0 = default */
     int d1_mode;          /* D1 reduction: 0 = by density (3 when there are
                              fewer 2-saddle columns than 1 per 32 vertices,
@@ -151,7 +159,9 @@ dms_status dms_get_counts(dms_grid grid, int64_t pairs[3], int64_t essential[4])
 /* Copies the pairs of dimension dim (0..2) -- the finite pairs in increasing
  * lexicographic order of the critical simplex that indexes them (the death
  * edge for D0, the death triangle for D1, the birth triangle for D2), then the
- * infinite classes of that dimension -- into out[0..cap).  *written = number copied; if cap is smaller
+ * infinite classes of that dimension; for dim 2, last, the infinite classes
+ * of dimension 3 (dim field 3; only with virtual_max = 0) -- into
+ * out[0..cap): pairs[dim] + essential[dim] rows (+ essential[3] for dim 2).  *written = number copied; if cap is smaller
  * than the count, DMS_ERR_CAPACITY is returned and nothing is copied.
  * out_is_device = 1: out is a device pointer (a synchronous device-to-device
  * copy; the result is already complete when dms_compute_diagram returns). */

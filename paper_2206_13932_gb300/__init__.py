@@ -115,15 +115,19 @@ def _check(st: int, where: str):
 
 
 class Grid:
-    """A handle of ``dms_grid``: one grid shape and dtype, reusable across fields."""
+    """A handle of ``dms_grid``: one grid shape and dtype, reusable across fields.
+    ``virtual_max=False`` drops the virtual maximum on the outer boundary
+    (App. A): unpaired maxima are then infinite classes of dimension 3,
+    listed at the end of ``fetch(2)``."""
 
-    def __init__(self, shape_xyz, dtype, max_iters: int = 0, d1_mode: int = 0):
+    def __init__(self, shape_xyz, dtype, max_iters: int = 0, d1_mode: int = 0,
+                 virtual_max: bool = True):
         self._lib = load()
         self.shape_xyz = tuple(int(s) for s in shape_xyz)
         self.dtype = np.dtype(dtype)
         if self.dtype not in _DTYPE_CODE:
             raise TypeError(f"unsupported dtype {self.dtype}")
-        opts = _Options(1, int(max_iters), int(d1_mode))
+        opts = _Options(int(bool(virtual_max)), int(max_iters), int(d1_mode))
         h = ctypes.c_void_p()
         nx, ny, nz = self.shape_xyz
         _check(self._lib.dms_grid_create(nx, ny, nz, _DTYPE_CODE[self.dtype],
@@ -195,12 +199,18 @@ class Grid:
         _check(self._lib.dms_get_counts(self._h, p, e), "dms_get_counts")
         return tuple(p), tuple(e)
 
+    def list_rows(self, dim: int) -> int:
+        """Rows that ``fetch(dim)`` returns: the finite pairs and infinite
+        classes of dimension ``dim``; the list of dimension 2 also holds the
+        infinite classes of dimension 3 (only without the virtual maximum)."""
+        p, e = self.counts()
+        return p[dim] + e[dim] + (e[3] if dim == 2 else 0)
+
     def fetch(self, dim: int, out: np.ndarray | None = None) -> np.ndarray:
         """Pairs of dimension ``dim`` as a structured array of PAIR_DTYPE.
         ``out``: a host array of PAIR_DTYPE to copy into (e.g. a view of
         pinned memory, reused across calls); the result is its first part."""
-        p, e = self.counts()
-        n = p[dim] + e[dim]
+        n = self.list_rows(dim)
         if out is None:
             out = np.empty(n, PAIR_DTYPE)
         elif out.dtype != PAIR_DTYPE or not out.flags.c_contiguous:
@@ -259,7 +269,8 @@ class Batch(Grid):
     relative to the field, equal to what a single-grid compute of that field
     returns."""
 
-    def __init__(self, shapes_xyz, dtype, max_iters: int = 0, d1_mode: int = 0):
+    def __init__(self, shapes_xyz, dtype, max_iters: int = 0, d1_mode: int = 0,
+                 virtual_max: bool = True):
         self._lib = load()
         self.shapes_xyz = [tuple(int(s) for s in sh) for sh in shapes_xyz]
         self.dtype = np.dtype(dtype)
@@ -267,7 +278,7 @@ class Batch(Grid):
             raise TypeError(f"unsupported dtype {self.dtype}")
         nf = len(self.shapes_xyz)
         flat = (ctypes.c_int64 * (3 * nf))(*[v for sh in self.shapes_xyz for v in sh])
-        opts = _Options(1, int(max_iters), int(d1_mode))
+        opts = _Options(int(bool(virtual_max)), int(max_iters), int(d1_mode))
         h = ctypes.c_void_p()
         _check(self._lib.dms_batch_create(nf, flat, _DTYPE_CODE[self.dtype], ctypes.byref(opts),
                                           ctypes.byref(h)), "dms_batch_create")

@@ -101,7 +101,7 @@ def persistence_diagram(values: torch.Tensor, grid: Grid | None = None) -> list:
         grid = Grid((nx, ny, nz), np.dtype(str(values.dtype).replace("torch.", "")))
     grid.compute(values.detach())
     pairs, ess = grid.counts()
-    counts = tuple(pairs[d] + ess[d] for d in range(3))
+    counts = tuple(grid.list_rows(d) for d in range(3))
     bd, meta = [], []
     for d in range(3):
         n = counts[d]

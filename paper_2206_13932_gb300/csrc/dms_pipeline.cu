@@ -973,14 +973,18 @@ __device__ __forceinline__ int32_t dc_find(DcSlot *tab, int32_t a) {
     }
 }
 
-// light arcs of each segment: register both endpoint labels.  An arc whose
-// two ends already carry the same label joins nothing: its label is left out
-// (a heavy arc looking it up keeps it, as its component in the light half
-// is then itself or is registered by another arc).
-__global__ void k_dc_insert(int64_t narcs, int shift, int descending, const int32_t *A,
-                            const int32_t *B, DcSlot *tab, uint32_t mask, DevStatus *st) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= narcs) return;
+// The kernels of one level run over the arcs still open (act[0..nact)): an
+// arc whose two ends carry one label has both ends in one component at its
+// segment's start, and components only merge, so it closes a cycle and is
+// dropped from the later levels (its young stays -1).
+//
+// light arcs of each segment: register both endpoint labels.
+__global__ void k_dc_insert(const int32_t *__restrict__ act, int64_t nact, int64_t narcs,
+                            int shift, int descending, const int32_t *A, const int32_t *B,
+                            DcSlot *tab, uint32_t mask, DevStatus *st) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nact) return;
+    const int64_t j = act[k];
     int64_t t = dc_time(j, narcs, descending);
     int64_t seg = t >> shift;
     if ((t >> (shift - 1)) & 1) return;                  // heavy half
@@ -997,11 +1001,12 @@ __global__ void k_dc_insert(int64_t narcs, int shift, int descending, const int3
 
 // light arcs: union their endpoints; a root is hooked under the root holding
 // the older label (smaller for D0, larger for D2)
-__global__ void k_dc_union(int64_t narcs, int shift, int descending, int older_is_larger,
-                           const int32_t *A, const int32_t *B, DcSlot *tab, uint32_t mask,
-                           DevStatus *st) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= narcs) return;
+__global__ void k_dc_union(const int32_t *__restrict__ act, int64_t nact, int64_t narcs,
+                           int shift, int descending, int older_is_larger, const int32_t *A,
+                           const int32_t *B, DcSlot *tab, uint32_t mask, DevStatus *st) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nact) return;
+    const int64_t j = act[k];
     int64_t t = dc_time(j, narcs, descending);
     int64_t seg = t >> shift;
     if ((t >> (shift - 1)) & 1) return;
@@ -1021,26 +1026,38 @@ __global__ void k_dc_union(int64_t narcs, int shift, int descending, int older_i
     atomicOr(&st->err, kErrIter);
 }
 
-// heavy arcs: relabel endpoints by the light half's components
-__global__ void k_dc_relabel(int64_t narcs, int shift, int descending, int32_t *A, int32_t *B,
-                             DcSlot *tab, uint32_t mask) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= narcs) return;
+// heavy arcs: relabel endpoints by the light half's components; then every
+// open arc flags whether it is still open
+__global__ void k_dc_relabel(const int32_t *__restrict__ act, int64_t nact, int64_t narcs,
+                             int shift, int descending, int32_t *A, int32_t *B, DcSlot *tab,
+                             uint32_t mask, int32_t *open) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nact) return;
+    const int64_t j = act[k];
     int64_t t = dc_time(j, narcs, descending);
     int64_t seg = t >> shift;
-    if (!((t >> (shift - 1)) & 1)) return;               // light half
-    int32_t *ends[2] = {&A[j], &B[j]};
-    for (int e = 0; e < 2; e++) {
-        int32_t s = dc_lookup(tab, mask, ((unsigned long long)seg << 32) | (uint32_t)*ends[e]);
-        if (s >= 0) *ends[e] = tab[dc_find(tab, s)].lab;
+    int32_t a = A[j], b = B[j];
+    if ((t >> (shift - 1)) & 1) {                        // heavy half
+        int32_t s = dc_lookup(tab, mask, ((unsigned long long)seg << 32) | (uint32_t)a);
+        if (s >= 0) a = A[j] = tab[dc_find(tab, s)].lab;
+        s = dc_lookup(tab, mask, ((unsigned long long)seg << 32) | (uint32_t)b);
+        if (s >= 0) b = B[j] = tab[dc_find(tab, s)].lab;
     }
+    open[k] = a != b;
+}
+
+// the arcs open at the start: ends in different minima (maxima)
+__global__ void k_dc_open(const int32_t *A, const int32_t *B, int64_t narcs, int32_t *open) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < narcs) open[j] = A[j] != B[j];
 }
 
 // every arc now sees the components at its turn: the elder rule
-__global__ void k_dc_decide(int64_t narcs, int older_is_larger, const int32_t *A,
-                            const int32_t *B, int32_t *young, uint8_t *died) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= narcs) return;
+__global__ void k_dc_decide(const int32_t *__restrict__ act, int64_t nact, int older_is_larger,
+                            const int32_t *A, const int32_t *B, int32_t *young, uint8_t *died) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nact) return;
+    const int64_t j = act[k];
     int32_t a = A[j], b = B[j];
     if (a == b) { young[j] = -1; return; }
     int32_t y = older_is_larger ? (a < b ? a : b) : (a > b ? a : b);
@@ -1169,10 +1186,13 @@ __global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *fl
                           GradRec *grad, const int32_t *__restrict__ vrank,
                           const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
                           const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
-                          int64_t n2, const int32_t *__restrict__ order, int32_t vmax, int32_t *A,
-                          int32_t *B, int32_t *young, int64_t max_steps, DevStatus *st) {
+                          int64_t n2, const int32_t *__restrict__ order, int32_t vmax,
+                          int vmax_on, int32_t *A, int32_t *B, int32_t *young, int64_t max_steps,
+                          DevStatus *st) {
     // arcs in vertex-id order (`order`), so that the walks of a warp start
-    // close together and share the records they read
+    // close together and share the records they read.  Without the virtual
+    // maximum (App. A) a 2-saddle whose ascent leaves the domain on either
+    // side merges nothing: its arc becomes a loop at the outside node.
     const int64_t jj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (jj >= n2) return;
     const int64_t j = order ? order[jj] : jj;
@@ -1193,6 +1213,7 @@ __global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *fl
                                            vmax, max_steps, st)
                                   : vmax;
     }
+    if (!vmax_on && (ends[0] == vmax || ends[1] == vmax)) ends[0] = ends[1] = vmax;
     A[j] = ends[0];
     B[j] = ends[1];
     young[j] = -1;
@@ -3274,6 +3295,17 @@ __global__ void k_compact_idx(const uint8_t *flag, const int32_t *pos, int64_t n
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && flag[i]) out[pos[i]] = (int32_t)i;
 }
+// flag32[k] = flag[list[k]] (list null: flag[k])
+__global__ void k_flags_of(const int32_t *list, int64_t m, const uint8_t *flag, int32_t *flag32) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) flag32[k] = flag[list ? list[k] : k];
+}
+// out[pos[k]] = list[k] (list null: k) for the flagged entries
+__global__ void k_compact_list(const int32_t *list, const int32_t *flag32, const int32_t *pos,
+                               int64_t m, int32_t *out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m && flag32[k]) out[pos[k]] = list ? list[k] : (int32_t)k;
+}
 
 // ------------------------------------------------ backward (differentiation)
 //
@@ -3523,19 +3555,41 @@ dms_status elder_rule(Ctx &c, int64_t narcs, int descending, int older_is_larger
     if (narcs == 0) return DMS_OK;
     int L = 0;
     while (((int64_t)1 << L) < narcs) L++;
-    // at most one key per light-arc endpoint per level: a table at most 2/3 full
+    // the open arcs (two lists, this level's and the next's), their flags and scan
+    DMS_ALLOC(P.dc_par, 8 * narcs + 8);
+    DMS_ALLOC(P.dc_lab, 8 * narcs + 8);
+    int32_t *act = P.dc_par.as<int32_t>(), *act2 = act + narcs;
+    int32_t *open = P.dc_lab.as<int32_t>(), *pos = open + narcs;
+    DMS_LAUNCH(narcs, 256, k_dc_open, A, B, narcs, open);
+    DMS_TRY(scan(c, open, pos, narcs, &c.st->total[3]));
+    DMS_TRY(sync_status(c));
+    int64_t nact = c.hst->total[3];
+    DMS_LAUNCH(narcs, 256, k_compact_list, (const int32_t *)nullptr, open, pos, narcs, act);
+    // at most two keys per open arc: a table at most 2/3 full
     uint32_t cap = 1024;
-    while ((int64_t)cap * 2 < 3 * narcs + 2) cap <<= 1;
+    while ((int64_t)cap < 3 * nact + 2) cap <<= 1;
     DMS_ALLOC(P.dc_keys, sizeof(DcSlot) * (size_t)cap);
     DcSlot *tab = P.dc_keys.as<DcSlot>();
-    for (int shift = L; shift >= 1; shift--) {
-        DMS_CUDA(cudaMemsetAsync(tab, 0xFF, sizeof(DcSlot) * (size_t)cap, c.s));
-        DMS_LAUNCH(narcs, 256, k_dc_insert, narcs, shift, descending, A, B, tab, cap - 1, c.st);
-        DMS_LAUNCH(narcs, 256, k_dc_union, narcs, shift, descending, older_is_larger, A, B, tab,
-                   cap - 1, c.st);
-        DMS_LAUNCH(narcs, 256, k_dc_relabel, narcs, shift, descending, A, B, tab, cap - 1);
+    for (int shift = L; shift >= 1 && nact > 0; shift--) {
+        uint32_t lcap = 1024;
+        while ((int64_t)lcap < 3 * nact + 2) lcap <<= 1;
+        DMS_CUDA(cudaMemsetAsync(tab, 0xFF, sizeof(DcSlot) * (size_t)lcap, c.s));
+        DMS_LAUNCH(nact, 256, k_dc_insert, act, nact, narcs, shift, descending, A, B, tab,
+                   lcap - 1, c.st);
+        DMS_LAUNCH(nact, 256, k_dc_union, act, nact, narcs, shift, descending, older_is_larger, A,
+                   B, tab, lcap - 1, c.st);
+        DMS_LAUNCH(nact, 256, k_dc_relabel, act, nact, narcs, shift, descending, A, B, tab,
+                   lcap - 1, open);
+        if (shift > 1) {   // keep the arcs still open
+            DMS_TRY(scan(c, open, pos, nact, &c.st->total[3]));
+            DMS_TRY(sync_status(c));
+            const int64_t nnext = c.hst->total[3];
+            DMS_LAUNCH(nact, 256, k_compact_list, act, open, pos, nact, act2);
+            std::swap(act, act2);
+            nact = nnext;
+        }
     }
-    DMS_LAUNCH(narcs, 256, k_dc_decide, narcs, older_is_larger, A, B, young, died);
+    DMS_LAUNCH(nact, 256, k_dc_decide, act, nact, older_is_larger, A, B, young, died);
     *levels_out = L;
     return DMS_OK;
 }
@@ -4326,7 +4380,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     DMS_LAUNCH(n2, 128, (k_d2_arcs<T, B>), values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
                P.vrank.as<int32_t>(),
                P.recs.as<CritRec>(), P.base[3].as<int32_t>(), P.c_vert[2].as<int32_t>(),
-               P.c_loc[2].as<uint8_t>(), n2, order2, vmax, P.arc_a.as<int32_t>(),
+               P.c_loc[2].as<uint8_t>(), n2, order2, vmax, P.virtual_max, P.arc_a.as<int32_t>(),
                P.arc_b.as<int32_t>(), young2, max_steps, c.st);
     KEV(15);
     KEV(16);
@@ -4400,27 +4454,33 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
             ovf, &c.st->trace_next, c.st);
         c.launches++;
         DMS_CUDA(cudaGetLastError());
-        // columns whose trace outgrew the scratch run again with 16x more
-        std::vector<uint8_t> hovf(ncols);
-        DMS_CUDA(cudaMemcpyAsync(hovf.data(), ovf, ncols, cudaMemcpyDeviceToHost, c.s));
+        // columns whose trace outgrew the scratch run again with 16x more; the
+        // list of them is compacted on the device (flag, scan, scatter), the
+        // host reads only its length
+        DMS_ALLOC(P.flag_a, 4 * ncols + 4);
+        DMS_ALLOC(P.flag_b, 4 * ncols + 4);
+        int32_t *f32 = P.flag_a.as<int32_t>(), *fpos = P.flag_b.as<int32_t>();
+        DMS_LAUNCH(ncols, 256, k_flags_of, (const int32_t *)nullptr, ncols, ovf, f32);
+        DMS_TRY(scan(c, f32, fpos, ncols, &c.st->total[3]));
         DMS_TRY(sync_status(c));
-        std::vector<int32_t> todo;
-        for (int64_t q = 0; q < ncols; q++)
-            if (hovf[q]) todo.push_back((int32_t)q);
-        P.d1_overflow = (int64_t)todo.size();
+        int64_t ntodo = c.hst->total[3];
+        P.d1_overflow = ntodo;
+        DMS_ALLOC(P.d1_todo, 8 * ntodo + 8);   // two lists: this pass's and the next's
+        int32_t *todo = P.d1_todo.as<int32_t>(), *todo_next = todo + ntodo;
+        DMS_LAUNCH(ncols, 256, k_compact_list, (const int32_t *)nullptr, f32, fpos, ncols, todo);
         auto dbg_t0 = std::chrono::steady_clock::now();
         if (getenv("DMS_DEBUG")) {
-            fprintf(stderr, "d1 trace pass 1: %lld columns, %zu overflow, pool %llu, %.3f ms\n",
-                    (long long)ncols, todo.size(), c.hst->pool_top,
+            fprintf(stderr, "d1 trace pass 1: %lld columns, %lld overflow, pool %llu, %.3f ms\n",
+                    (long long)ncols, (long long)ntodo, c.hst->pool_top,
                     std::chrono::duration<double, std::milli>(dbg_t0 - dbg_p1).count());
         }
         int32_t gen = (int32_t)ncols;
-        while (!todo.empty()) {
+        while (ntodo > 0) {
             hcap *= 16; hashcap *= 16; rcap *= 16;
             if (hashcap > (1 << 24)) return DMS_ERR_CAPACITY;
             per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
                   (size_t)rcap * 8;
-            int64_t nt = std::min<int64_t>((int64_t)todo.size(),
+            int64_t nt = std::min<int64_t>(ntodo,
                                            std::max<int64_t>(32, ((int64_t)4 << 30) / (int64_t)per));
             nt = (nt + 31) / 32 * 32;
             DMS_ALLOC(P.d1_scratch, per * nt);
@@ -4428,26 +4488,23 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
             hash = (HashEnt *)(heap + (size_t)hcap * nt);
             rows = (int32_t *)(hash + (size_t)hashcap * nt);
             DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nt * sizeof(HashEnt), c.s));
-            DMS_ALLOC(P.d1_todo, 4 * todo.size());
-            DMS_CUDA(cudaMemcpyAsync(P.d1_todo.p, todo.data(), 4 * todo.size(),
-                                     cudaMemcpyHostToDevice, c.s));
             DMS_CUDA(cudaMemsetAsync(&c.st->trace_next, 0, sizeof(unsigned long long), c.s));
             k_d1_trace<T, B><<<(unsigned)(nt / 32), 32, 0, c.s>>>(
                 values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
                 P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(),
-                P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), P.d1_todo.as<int32_t>(),
-                (int64_t)todo.size(), heap, hash, rows, hcap, hashcap, rcap, gen,
-                P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(),
-                P.d1_len.as<int32_t>(), ovf, &c.st->trace_next, c.st);
+                P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), todo, ntodo, heap, hash,
+                rows, hcap, hashcap, rcap, gen, P.d1_pool.as<int32_t>(), pool_cap,
+                P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), ovf, &c.st->trace_next, c.st);
             c.launches++;
             DMS_CUDA(cudaGetLastError());
             gen += (int32_t)ncols;
-            DMS_CUDA(cudaMemcpyAsync(hovf.data(), ovf, ncols, cudaMemcpyDeviceToHost, c.s));
+            DMS_LAUNCH(ntodo, 256, k_flags_of, todo, ntodo, ovf, f32);
+            DMS_TRY(scan(c, f32, fpos, ntodo, &c.st->total[3]));
             DMS_TRY(sync_status(c));
-            std::vector<int32_t> next;
-            for (int32_t q : todo)
-                if (hovf[q]) next.push_back(q);
-            todo.swap(next);
+            const int64_t nnext = c.hst->total[3];
+            DMS_LAUNCH(ntodo, 256, k_compact_list, todo, f32, fpos, ntodo, todo_next);
+            std::swap(todo, todo_next);
+            ntodo = nnext;
         }
         if (getenv("DMS_DEBUG"))
             fprintf(stderr, "d1 trace retries: %.3f ms\n",
@@ -4494,19 +4551,17 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     DMS_TRY(sync_status(c));
     int64_t cntp[7];
     for (int q = 0; q < 7; q++) cntp[q] = c.hst->parts[q];
-    for (int d = 0; d < 3; d++) {
-        int64_t rows = cntp[2 * d] + cntp[2 * d + 1];
-        DMS_ALLOC(P.out_pairs[d], sizeof(dms_pair) * (rows + 1));
-    }
+    // rows per output list: the D2 list ends with the infinite classes of
+    // dimension 3 (maxima left unpaired, only without the virtual maximum)
+    const int64_t list_rows[3] = {cntp[0] + cntp[1], cntp[2] + cntp[3],
+                                  cntp[4] + cntp[5] + cntp[6]};
+    for (int d = 0; d < 3; d++) DMS_ALLOC(P.out_pairs[d], sizeof(dms_pair) * (list_rows[d] + 1));
     if constexpr (B) {
-        for (int d = 0; d < 3; d++) {
-            const int64_t rows = cntp[2 * d] + cntp[2 * d + 1];
-            DMS_ALLOC(P.out_field[d], 4 * (rows + 1));
-        }
+        for (int d = 0; d < 3; d++) DMS_ALLOC(P.out_field[d], 4 * (list_rows[d] + 1));
     }
-    for (int q = 0; q < 6; q++) {
-        int d = part_dim[q];
-        int64_t off = (q & 1) ? cntp[q - 1] : 0;
+    for (int q = 0; q < 7; q++) {
+        const int d = part_dim[q] < 3 ? part_dim[q] : 2;
+        const int64_t off = q == 6 ? cntp[4] + cntp[5] : (q & 1) ? cntp[q - 1] : 0;
         DMS_LAUNCH(part_n[q], 128, (k_write<T, B>), q, a, values, geo, part_n[q], fl + foff[q],
                    ps + foff[q], off, P.vrank.as<int32_t>(), c.hst->maxkey,
                    P.fmax_field.as<unsigned long long>(), P.out_field[d].as<int32_t>(),
@@ -4514,8 +4569,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     }
     if constexpr (B) {
         // group each dimension's pairs by field, keeping their order inside a field
-        for (int d = 0; d < 3; d++)
-            DMS_TRY(group_by_field(c, d, cntp[2 * d] + cntp[2 * d + 1]));
+        for (int d = 0; d < 3; d++) DMS_TRY(group_by_field(c, d, list_rows[d]));
     }
     P.n_pairs[0] = cntp[0]; P.n_pairs[1] = cntp[2]; P.n_pairs[2] = cntp[4];
     P.n_ess[0] = cntp[1]; P.n_ess[1] = cntp[3]; P.n_ess[2] = cntp[5]; P.n_ess[3] = cntp[6];
@@ -4619,7 +4673,7 @@ dms_status Pipeline::init(int64_t nx_, int64_t ny_, int64_t nz_, dms_dtype dt,
     if (nx_ * ny_ >= ((int64_t)1 << 31) || nx_ * ny_ * nz_ >= ((int64_t)1 << 31))
         return DMS_ERR_INVALID_ARG;
     if (dt != DMS_U16 && dt != DMS_F32 && dt != DMS_F64) return DMS_ERR_INVALID_ARG;
-    if (o && o->virtual_max != 1) return DMS_ERR_INVALID_ARG;
+    if (o && o->virtual_max != 0 && o->virtual_max != 1) return DMS_ERR_INVALID_ARG;
     if (o && o->max_iters < 0) return DMS_ERR_INVALID_ARG;
     if (o && (o->d1_mode < 0 || o->d1_mode > 3)) return DMS_ERR_INVALID_ARG;
     nx = nx_; ny = ny_; nz = nz_; n = nx * ny * nz; dtype = dt;
@@ -4657,7 +4711,8 @@ dms_status Pipeline::init_batch(int64_t nf_, const int64_t *shp, dms_dtype dt,
                                 const dms_options *o) {
     if (dt != DMS_U16 && dt != DMS_F32 && dt != DMS_F64) return DMS_ERR_INVALID_ARG;
     if (!batch_shapes_ok(nf_, shp)) return DMS_ERR_INVALID_ARG;   // before any CUDA call
-    if (o && (o->virtual_max != 1 || o->max_iters < 0 || o->d1_mode < 0 || o->d1_mode > 3))
+    if (o && ((o->virtual_max != 0 && o->virtual_max != 1) || o->max_iters < 0 ||
+              o->d1_mode < 0 || o->d1_mode > 3))
         return DMS_ERR_INVALID_ARG;
     batch = true;
     dtype = dt;
@@ -4708,6 +4763,7 @@ dms_status Pipeline::set_batch(int64_t nf_, const int64_t *shp) {
 }
 
 dms_status Pipeline::init_common(const dms_options *o) {
+    virtual_max = o ? o->virtual_max : 1;
     max_iters = o ? o->max_iters : 0;
     d1_mode = o ? o->d1_mode : 0;
     if (cudaGetDevice(&device) != cudaSuccess) return DMS_ERR_CUDA;
@@ -4848,7 +4904,7 @@ dms_status Pipeline::backward(int dim, uint64_t rid, const double *gbirth, const
                               double *grad, void *stream) {
     if (!has_result || rid != result_id) return DMS_ERR_STATE;   // not the caller's pairing
     if (dim < 0 || dim > 2 || !grad) return DMS_ERR_INVALID_ARG;
-    const int64_t total = n_pairs[dim] + n_ess[dim];
+    const int64_t total = list_rows(dim);
     if (total == 0) return DMS_OK;
     const int64_t *pofs = nullptr, *vofs = nullptr;
     if (batch) {   // per-field pair ranges of this dimension and field offsets
@@ -4866,7 +4922,7 @@ dms_status Pipeline::fetch(int dim, dms_pair *out, int64_t cap, int64_t *written
     *written = 0;
     if (!has_result) return DMS_ERR_STATE;
     if (dim < 0 || dim > 2) return DMS_ERR_INVALID_ARG;
-    const int64_t total = n_pairs[dim] + n_ess[dim];
+    const int64_t total = list_rows(dim);
     if (total > cap) return DMS_ERR_CAPACITY;
     if (total == 0) return DMS_OK;
     if (!out) return DMS_ERR_INVALID_ARG;

@@ -32,6 +32,8 @@ struct Pipeline {
     int64_t nx = 0, ny = 0, nz = 0, n = 0;
     dms_dtype dtype = DMS_F32;
     int64_t max_iters = 0;
+    int virtual_max = 1;    // 1: the outer boundary is one virtual maximum (Sec. 5.2);
+                            // 0: no virtual maximum (App. A)
     int d1_mode = 0;        // 0: by column density, 1: reduce columns (homology),
                             // 2: anti-transpose (cohomology), 3: lazy columns
                             // (propagation interleaved with the reduction)
@@ -96,6 +98,11 @@ struct Pipeline {
     dms_status compute(const void *values, int on_host, void *stream);
     dms_status reshape(int64_t nx, int64_t ny, int64_t nz);
     dms_status fetch(int dim, dms_pair *out, int64_t cap, int64_t *written, int out_is_device);
+    // rows of output list dim: its finite pairs and infinite classes (the D2
+    // list also holds the infinite classes of dimension 3)
+    int64_t list_rows(int dim) const {
+        return n_pairs[dim] + n_ess[dim] + (dim == 2 ? n_ess[3] : 0);
+    }
     dms_status backward(int dim, uint64_t rid, const double *gbirth, const double *gdeath,
                         double *grad, void *stream);
     void destroy();

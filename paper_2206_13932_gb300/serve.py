@@ -13,11 +13,14 @@ of their grids -- on a reusable batch handle.  Each result is the same as the
 request's diagram computed alone (the pipeline is deterministic, handles
 share no state, and a batch's per-field pairs equal the single-grid ones).
 
-Device memory: the requests in flight stay within ``mem_budget``.  A handle's
-buffers only grow, so after a request a slot keeps the handle only while that
-request fit the slot's share of the budget (``keeps_buffers``); a larger one
-is freed at once.  Idle handles therefore hold at most ``mem_budget / slots``
-each.
+Device memory: the requests in flight stay within ``mem_budget``, each
+charged by the estimate ``request_bytes``.  A handle's buffers only grow, so a
+slot keeps at most one handle between requests (the one it used last), and
+only while the device memory that handle really holds (``device_bytes``,
+which includes D1 pools grown on noisy fields) and the request's estimate
+both fit the slot's share of the budget (``keeps_buffers``); otherwise the
+handle is freed at once.  Idle handles therefore hold at most
+``mem_budget / slots`` each, measured, not estimated.
 """
 from __future__ import annotations
 
@@ -38,8 +41,8 @@ def request_bytes(n_vertices: int, itemsize: int) -> int:
 
 
 def keeps_buffers(need: int, budget: int, slots: int) -> bool:
-    """Whether a slot keeps a handle (and its device buffers) after running a
-    request of ``need`` bytes: only within the slot's share of the budget."""
+    """Whether a slot keeps a handle (and its device buffers) that holds
+    ``need`` bytes: only within the slot's share of the budget."""
     return need <= budget // max(1, int(slots))
 
 
@@ -159,7 +162,7 @@ class DiagramServer:
             stream, setup_error = be.stream(), None
         except Exception as e:   # every request this slot takes then reports it
             stream, setup_error = None, e
-        grids, batches = {}, {}
+        held = None          # (kind, dtype, handle): the one handle kept between requests
         while True:
             got = self._take()
             if got is None:
@@ -173,39 +176,49 @@ class DiagramServer:
                     raise setup_error
                 dt = reqs[0].values.dtype
                 shapes = [(r.values.shape[2], r.values.shape[1], r.values.shape[0]) for r in reqs]
+                kind = "grid" if len(reqs) == 1 else "batch"
+                h = None
+                if held is not None and held[0] == kind and held[1] == dt:
+                    h = held[2]
+                elif held is not None:              # another kind or dtype: free it first
+                    held[2].close()
+                held = None
                 with be.current(stream):
-                    if len(reqs) == 1:
-                        g = grids.get(dt)
-                        if g is None:
-                            g = grids[dt] = be.Grid(shapes[0], dt)
-                        elif g.shape_xyz != shapes[0]:
-                            g.reshape(shapes[0])
-                        g.compute(reqs[0].values, stream=be.handle(stream))
-                        reqs[0].result = {d: g.fetch(d) for d in range(3)}
+                    if kind == "grid":
+                        if h is None:
+                            h = be.Grid(shapes[0], dt)
+                        elif h.shape_xyz != shapes[0]:
+                            h.reshape(shapes[0])
+                        held = (kind, dt, h)
+                        h.compute(reqs[0].values, stream=be.handle(stream))
+                        reqs[0].result = {d: h.fetch(d) for d in range(3)}
                     else:
-                        b = batches.get(dt)
-                        if b is None:
-                            b = batches[dt] = be.Batch(shapes, dt)
+                        if h is None:
+                            h = be.Batch(shapes, dt)
                         else:
-                            b.reshape(shapes)
-                        b.compute([r.values for r in reqs], stream=be.handle(stream))
-                        for r, res in zip(reqs, b.results()):
+                            h.reshape(shapes)
+                        held = (kind, dt, h)
+                        h.compute([r.values for r in reqs], stream=be.handle(stream))
+                        for r, res in zip(reqs, h.results()):
                             r.result = res
             except Exception as e:   # reported to the caller
                 for r in reqs:
                     r.error = e
-            if not keeps_buffers(need, self.mem_budget, self.slots):
-                handles = grids if len(reqs) == 1 else batches
-                h = handles.pop(reqs[0].values.dtype, None)
-                if h is not None:
-                    h.close()
+            if held is not None:
+                try:
+                    kept = max(need, held[2].device_bytes())
+                except Exception:
+                    kept = None
+                if kept is None or not keeps_buffers(kept, self.mem_budget, self.slots):
+                    held[2].close()
+                    held = None
             t = time.perf_counter()
             self._release(need)
             for r in reqs:
                 r.finished = t
                 r.done.set()
-        for g in list(grids.values()) + list(batches.values()):
-            g.close()
+        if held is not None:
+            held[2].close()
 
 
 def run_stream(fields, arrivals, slots: int, mem_budget: int = 16 << 30, max_batch: int = 1,
@@ -230,6 +243,14 @@ def run_stream(fields, arrivals, slots: int, mem_budget: int = 16 << 30, max_bat
 
 
 def latency_stats(reqs):
+    """Latency percentiles (arrival to result), split into the wait for a slot
+    (arrival to admission) and the service (admission to result)."""
     lat = np.array([r.finished - r.arrival for r in reqs]) * 1e3
+    wait = np.array([r.admitted - r.arrival for r in reqs]) * 1e3
+    serv = np.array([r.finished - r.admitted for r in reqs]) * 1e3
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean())}
+            "mean_ms": float(lat.mean()),
+            "wait_p50_ms": float(np.percentile(wait, 50)),
+            "wait_p99_ms": float(np.percentile(wait, 99)),
+            "service_p50_ms": float(np.percentile(serv, 50)),
+            "service_p99_ms": float(np.percentile(serv, 99))}

@@ -136,8 +136,10 @@ def test_backward_refuses_a_newer_result(ad):
     with dms.Grid((10, 9, 8), np.float64) as g:
         ta = torch.from_numpy(a).cuda().requires_grad_(True)
         tb = torch.from_numpy(b).cuda().requires_grad_(True)
-        la = sum(ad.persistence_diagram(ta, g)[d].birth.sum() for d in range(3))
-        lb = sum(ad.persistence_diagram(tb, g)[d].birth.sum() for d in range(3))
+        da = ad.persistence_diagram(ta, g)          # one compute per field
+        la = sum(da[d].birth.sum() for d in range(3))
+        db = ad.persistence_diagram(tb, g)
+        lb = sum(db[d].birth.sum() for d in range(3))
         with pytest.raises(dms.DmsError) as e:
             la.backward()
         assert e.value.status == 6

@@ -73,7 +73,7 @@ def test_argument_checks_without_gpu():
     assert create(1 << 16, 1 << 16, 1) == bad            # nx*ny >= 2^31
     assert create(1 << 11, 1 << 10, 1 << 10) == bad      # N >= 2^31
     assert create(4, 4, 4, dtype=3) == bad
-    assert create(4, 4, 4, opts=dms._Options(0, 0, 0)) == bad    # no virtual maximum
+    assert create(4, 4, 4, opts=dms._Options(2, 0, 0)) == bad    # virtual maximum neither 0 nor 1
     assert create(4, 4, 4, opts=dms._Options(1, -1, 0)) == bad    # negative iteration cap
     assert create(4, 4, 4, opts=dms._Options(1, 0, 4)) == bad    # unknown D1 mode
     assert lib.dms_grid_create(4, 4, 4, 1, None, None) == bad     # no output handle

@@ -53,12 +53,17 @@ def _diagram(v):
 
 class _FakeGrid:
     ledger = None
+    extra = 0          # device bytes a handle holds beyond the request's estimate
 
     def __init__(self, shape_xyz, dtype):
         self.shape_xyz = tuple(shape_xyz)
         self.dtype = np.dtype(dtype)
         self.ledger.count("created")
         self.res = None
+        self.nbytes = 0
+
+    def device_bytes(self):
+        return self.nbytes
 
     def reshape(self, shape_xyz):
         self.shape_xyz = tuple(shape_xyz)
@@ -66,6 +71,7 @@ class _FakeGrid:
 
     def compute(self, values, stream=None):
         self.ledger.enter(_bytes(values))
+        self.nbytes = max(self.nbytes, _bytes(values) + self.extra)   # buffers only grow
         try:
             time.sleep(0.002)
             self.res = _diagram(values)
@@ -91,6 +97,7 @@ class _FakeBatch(_FakeGrid):
     def compute(self, fields, stream=None):
         n = sum(_bytes(f) for f in fields)
         self.ledger.enter(n)
+        self.nbytes = max(self.nbytes, n + self.extra)
         try:
             time.sleep(0.002)
             self.per = [_diagram(f) for f in fields]
@@ -102,10 +109,10 @@ class _FakeBatch(_FakeGrid):
 
 
 class _FakeBackend:
-    def __init__(self):
+    def __init__(self, extra=0):
         self.ledger = _Ledger()
-        grid = type("Grid", (_FakeGrid,), {"ledger": self.ledger})
-        batch = type("Batch", (_FakeBatch,), {"ledger": self.ledger})
+        grid = type("Grid", (_FakeGrid,), {"ledger": self.ledger, "extra": extra})
+        batch = type("Batch", (_FakeBatch,), {"ledger": self.ledger, "extra": extra})
         self.Grid, self.Batch = grid, batch
 
     def stream(self):
@@ -153,6 +160,23 @@ def test_handles_kept_within_the_share_and_freed_above_it():
     be = _FakeBackend()
     serve.run_stream([big] * 3, np.arange(3) * 0.05, slots=2, mem_budget=budget, backend=be)
     assert be.ledger.created == 3 and be.ledger.closed == 3   # freed after every request
+
+
+def test_handles_holding_more_than_their_estimate_are_freed():
+    """A handle whose real device memory (device_bytes: pools grown on noisy
+    fields) exceeds the slot's share is freed after the request even though
+    the request's estimate fit; each slot keeps one handle at most."""
+    small = _fields(6, seed=3, lo=4, hi=6)
+    budget = 2 * 10 * max(_bytes(f) for f in small)      # estimates within the share
+    be = _FakeBackend(extra=budget)                      # but every handle holds more
+    serve.run_stream(small, np.zeros(len(small)), slots=2, mem_budget=budget, backend=be)
+    assert be.ledger.created == len(small) and be.ledger.closed == len(small)
+    mixed = _fields(12, seed=6, lo=4, hi=6)
+    mixed = [f if i % 2 else f.astype(np.float64) for i, f in enumerate(mixed)]
+    be = _FakeBackend()
+    serve.run_stream(mixed, np.arange(len(mixed)) * 0.01, slots=1,
+                     mem_budget=10 * budget, backend=be)
+    assert be.ledger.created == be.ledger.closed == len(mixed)   # dtype switch frees the other
 
 
 def test_a_failing_compute_reaches_only_its_request():

@@ -8,9 +8,10 @@ maximum vertices and raw value bits.
 - the batching-and-serving workload: 64 of its 1024 fields (the 32 smallest
   and 32 drawn at random), computed one by one and as one batch;
 - the differentiation workload: field 0 of the 8 x 128^3 batch, the pairing
-  the backward pass uses;
-- 256^3 white noise, the full-size random-field configuration (about five
-  minutes of oracle time on one core).
+  the backward pass uses.
+
+The full-size configurations are checked against stored digests of the
+same oracle's output in tests/test_zz_fullsize_gpu.py.
 
 The oracle runs in a process pool (spawn) on the host's cores while the GPU
 computes."""
@@ -110,14 +111,3 @@ def test_differentiation_pairing_against_the_standard_reduction(dms, pool):
         support |= set(dg[d].birth_vertex.cpu().numpy()[keep].tolist())
         support |= set(dg[d].death_vertex.cpu().numpy()[keep].tolist())
     assert set(np.nonzero(g)[0].tolist()) <= support
-
-
-def test_noise256_full_size_against_the_standard_reduction(dms, pool):
-    """The full-size random-field configuration: 256^3 float32 white noise,
-    seed 2, every pair against the standard reduction."""
-    v = sf.config_field("noise256_f32")
-    job = pool.apply_async(oracle.fastpairs, (v,))
-    diag = _gpu(dms, v)
-    rows = job.get()
-    assert sum(1 for r in rows if r[0] == 1) > 3 * 10 ** 6
-    compare(v, diag, rows)

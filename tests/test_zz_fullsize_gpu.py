@@ -1,10 +1,18 @@
 """Parity at the full benchmark sizes, in the configuration bench.py times.
 
-The oracle's full reduction does not finish at these sizes, so the check uses
-what the oracle computes there: D0 and D2 simplex for simplex from its
-union-find special cases, and D1 through the Euler characteristic of every
-sub-level set (chi(K_i) = #D0 alive - #D1 alive + #D2 alive at each vertex
-level i), which holds at any size."""
+- Against the standard reduction itself: the oracle's fast mode was run on
+  the full-size fields by tests/golden/make_oracle_digest.py, which stored,
+  per dimension, the pair counts and the SHA-256 of the canonical pair list
+  (and the SHA-256 of the field it ran on).  The GPU's pairs, put in the
+  same canonical form, must hash the same: every pair of D0, D1 and D2 by
+  simplex id and maximum vertex.
+- Independently of those digests: D0 and D2 simplex for simplex against the
+  union-find special cases, and D1 through the Euler characteristic of every
+  sub-level set (chi(K_i) = #D0 alive - #D1 alive + #D2 alive at each vertex
+  level i), which holds at any size."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -84,6 +92,35 @@ def gpu():
         pytest.skip("no CUDA device")
     import paper_2206_13932_gb300 as dms
     dms.build()
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _digest_check(name):
+    from tests.golden.make_oracle_digest import canonical
+    with open(os.path.join(GOLDEN, f"{name}_oracle.json")) as f:
+        want = json.load(f)
+    v = sf.config_field(name)               # on the CPU, as the digest was made
+    assert sf.sha256(v) == want["field_sha256"], "the field differs from the oracle's input"
+    diag = _gpu(v)
+    check_bits(v, diag)
+    rows = []
+    for d in range(3):
+        p = diag[d]
+        rows.append(np.stack([p["dim"].astype(np.int64), p["birth_simplex"], p["death_simplex"],
+                              p["birth_vertex"], p["death_vertex"],
+                              p["essential"].astype(np.int64)], axis=1))
+    got = canonical(np.concatenate(rows).astype(np.int64))
+    for d in ("0", "1", "2"):
+        assert got[d]["finite"] == want["dims"][d]["finite"], d
+        assert got[d]["infinite"] == want["dims"][d]["infinite"], d
+        assert got[d]["sha256"] == want["dims"][d]["sha256"], d
+
+
+def test_noise256_f32_against_the_standard_reduction(gpu):
+    """256^3 float32 white noise, seed 2: every pair equals the oracle's."""
+    _digest_check("noise256_f32")
 
 
 def test_noise256_f32_full(gpu):
