@@ -146,26 +146,48 @@ static int lower_star(const fctx_t *c, int64_t v, int dim, int64_t *ids, fkey_t 
     return cnt;
 }
 
-/* Reduced columns kept in one append-only arena (standard reduction: a
- * column is final once processed). */
+/* Reduced columns kept in an append-only arena (standard reduction: a
+ * column is final once processed), made of chunks of fixed size so that it
+ * grows without copying.  A column lies within one chunk; its place is
+ * (chunk << 40) | offset. */
+#define ARENA_CHUNK ((int64_t)1 << 24)
 typedef struct {
-    fkey_t *e;
-    int64_t n, cap;
+    fkey_t **chunk;
+    int64_t nchunk, capchunk, used;    /* used: entries in the last chunk */
+    int64_t lastcap;                   /* entries the last chunk holds */
 } arena_t;
 
 static int arena_push(arena_t *a, const fkey_t *src, int64_t len, int64_t *start)
 {
-    if (a->n + len > a->cap) {
-        int64_t nc = a->cap ? a->cap : 1 << 16;
-        while (nc < a->n + len) nc *= 2;
-        fkey_t *ne = realloc(a->e, sizeof(fkey_t) * (size_t)nc);
-        if (!ne) return OR_ERR_MEM;
-        a->e = ne; a->cap = nc;
+    if (a->nchunk == 0 || a->used + len > a->lastcap) {
+        if (a->nchunk == a->capchunk) {
+            int64_t nc = a->capchunk ? 2 * a->capchunk : 64;
+            fkey_t **nch = realloc(a->chunk, sizeof(fkey_t *) * (size_t)nc);
+            if (!nch) return OR_ERR_MEM;
+            a->chunk = nch; a->capchunk = nc;
+        }
+        int64_t cap = len > ARENA_CHUNK ? len : ARENA_CHUNK;
+        fkey_t *c = malloc(sizeof(fkey_t) * (size_t)cap);
+        if (!c) return OR_ERR_MEM;
+        a->chunk[a->nchunk++] = c;
+        a->used = 0;
+        a->lastcap = cap;
     }
-    memcpy(a->e + a->n, src, sizeof(fkey_t) * (size_t)len);
-    *start = a->n;
-    a->n += len;
+    memcpy(a->chunk[a->nchunk - 1] + a->used, src, sizeof(fkey_t) * (size_t)len);
+    *start = ((a->nchunk - 1) << 40) | a->used;
+    a->used += len;
     return OR_OK;
+}
+
+static const fkey_t *arena_at(const arena_t *a, int64_t start)
+{
+    return a->chunk[start >> 40] + (start & (((int64_t)1 << 40) - 1));
+}
+
+static void arena_free(arena_t *a)
+{
+    for (int64_t i = 0; i < a->nchunk; i++) free(a->chunk[i]);
+    free(a->chunk);
 }
 
 /* dst <- dst + src (mod 2), both sorted increasingly. */
@@ -200,18 +222,21 @@ static int xor_into(fkey_t **dst, int64_t *dn, int64_t *dcap, const fkey_t *src,
  *   owner:   out, per (dim-1)-simplex id: the dim-simplex whose reduced
  *            column has it as pivot, or -1.
  *   zero:    out, per dim-simplex id: 1 when its column reduced to zero (or
- *            was cleared), else 0. */
-static int reduce_dim(const fctx_t *c, int dim, const int64_t *cleared, int64_t *owner,
+ *            was cleared), else 0.
+ * Simplex ids fit in int32 (checked by the caller). */
+static int reduce_dim(const fctx_t *c, int dim, const int32_t *cleared, int32_t *owner,
                       uint8_t *zero, int64_t *additions)
 {
     const int64_t n = c->n, nrow = n * ID_MULT[dim - 1], ncol = n * ID_MULT[dim];
     for (int64_t i = 0; i < nrow; i++) owner[i] = -1;
     for (int64_t i = 0; i < ncol; i++) zero[i] = 1;
-    /* where each stored (non-apparent) column sits in the arena */
-    int64_t *cstart = malloc(sizeof(int64_t) * (size_t)(ncol ? ncol : 1));
-    int32_t *clen = malloc(sizeof(int32_t) * (size_t)(ncol ? ncol : 1));
-    if (!cstart || !clen) { free(cstart); free(clen); return OR_ERR_MEM; }
-    for (int64_t i = 0; i < ncol; i++) clen[i] = -1;      /* -1: not stored (apparent) */
+    /* stored (non-apparent) columns: colidx[tau] indexes cstart/clen, -1 for
+     * a column kept implicit */
+    int32_t *colidx = calloc((size_t)ncol + 1, sizeof(int32_t));
+    int64_t *cstart = NULL, ncols = 0, capcols = 0;
+    int64_t *clen = NULL;
+    if (!colidx) return OR_ERR_MEM;
+    for (int64_t i = 0; i < ncol; i++) colidx[i] = -1;
     arena_t arena = {0};
     fkey_t *col = NULL, *tmp = NULL, bnd[4];
     int64_t cn = 0, ccap = 0, tcap = 0;
@@ -237,8 +262,9 @@ static int reduce_dim(const fctx_t *c, int dim, const int64_t *cleared, int64_t 
                 int64_t low = id_of_key(c, dim - 1, col[cn - 1]);
                 int64_t k = owner[low];
                 if (k < 0) break;
-                if (clen[k] >= 0) {
-                    st = xor_into(&col, &cn, &ccap, arena.e + cstart[k], clen[k], &tmp, &tcap);
+                int32_t ki = colidx[k];
+                if (ki >= 0) {
+                    st = xor_into(&col, &cn, &ccap, arena_at(&arena, cstart[ki]), clen[ki], &tmp, &tcap);
                 } else {
                     fkey_t kb[4];
                     int kn = boundary_keys(c, dim, k, kb);
@@ -250,20 +276,31 @@ static int reduce_dim(const fctx_t *c, int dim, const int64_t *cleared, int64_t 
             }
             if (st || cn == 0) continue;
             int64_t low = id_of_key(c, dim - 1, col[cn - 1]);
-            owner[low] = tau;
+            owner[low] = (int32_t)tau;
             zero[tau] = 0;
             if (added) {
-                if (cn > INT32_MAX) { st = OR_ERR_MEM; break; }
-                st = arena_push(&arena, col, cn, &cstart[tau]);
-                clen[tau] = (int32_t)cn;
+                if (ncols == capcols) {
+                    int64_t nc = capcols ? 2 * capcols : 1 << 16;
+                    int64_t *ns = realloc(cstart, sizeof(int64_t) * (size_t)nc);
+                    if (!ns) { st = OR_ERR_MEM; break; }
+                    cstart = ns;
+                    int64_t *nl = realloc(clen, sizeof(int64_t) * (size_t)nc);
+                    if (!nl) { st = OR_ERR_MEM; break; }
+                    clen = nl;
+                    capcols = nc;
+                }
+                if (ncols >= INT32_MAX) { st = OR_ERR_MEM; break; }
+                st = arena_push(&arena, col, cn, &cstart[ncols]);
+                clen[ncols] = cn;
+                colidx[tau] = (int32_t)ncols++;
             }
         }
     }
-    free(col); free(tmp); free(arena.e); free(cstart); free(clen);
+    free(col); free(tmp); arena_free(&arena); free(cstart); free(clen); free(colidx);
     return st;
 }
 
-static int emit_pairs(const fctx_t *c, int dim, const int64_t *owner, int keep_zero,
+static int emit_pairs(const fctx_t *c, int dim, const int32_t *owner, int keep_zero,
                       result_t *res)
 {
     /* owner indexes (dim-1)-simplices; each pivot gives the pair
@@ -289,6 +326,7 @@ int oracle_fastpairs(int64_t nx, int64_t ny, int64_t nz, int dtype, const void *
                      int keep_zero, int64_t **out_rows, int64_t *out_n, int64_t *additions)
 {
     if (!grid_ok(nx, ny, nz) || !values || !out_rows || !out_n) return OR_ERR_ARG;
+    if (12 * nx * ny * nz >= ((int64_t)1 << 31)) return OR_ERR_ARG;   /* int32 simplex ids */
     fctx_t c = {{nx, ny, nz}, nx * ny * nz, NULL, NULL};
     const int64_t n = c.n;
     int st;
@@ -303,10 +341,10 @@ int oracle_fastpairs(int64_t nx, int64_t ny, int64_t nz, int dtype, const void *
 
     /* owner[d]: per (d-1)-simplex, the d-simplex whose column it is the
      * pivot of; zero[d]: per d-simplex, column reduced to zero */
-    int64_t *owner[4] = {NULL, NULL, NULL, NULL};
+    int32_t *owner[4] = {NULL, NULL, NULL, NULL};
     uint8_t *zero[4] = {NULL, NULL, NULL, NULL};
     for (int d = 1; d <= 3 && !st; d++) {
-        owner[d] = malloc(sizeof(int64_t) * (size_t)(n * ID_MULT[d - 1]));
+        owner[d] = malloc(sizeof(int32_t) * (size_t)(n * ID_MULT[d - 1]));
         zero[d] = malloc((size_t)(n * ID_MULT[d]));
         if (!owner[d] || !zero[d]) st = OR_ERR_MEM;
     }

@@ -123,6 +123,13 @@ def test_noise256_f32_against_the_standard_reduction(gpu):
     _digest_check("noise256_f32")
 
 
+def test_mixture512_u16_against_the_standard_reduction(gpu):
+    """The 512^3 uint16 recipe (64 Gaussians + 5 % noise, quantised: heavy
+    ties), seed 3, at full size, in the configuration bench.py times: every
+    pair equals the oracle's."""
+    _digest_check("mixture512_u16")
+
+
 def test_noise256_f32_full(gpu):
     """256^3 float32 white noise, seed 2 (the benchmark workload)."""
     _check_full(sf.config_field("noise256_f32"))
