@@ -193,13 +193,16 @@ dms_status dms_backward_pairs(dms_grid grid, int dim, uint64_t result_id,
 
 /* Per-stage device milliseconds of the last compute (CUDA events):
  * [0] gradient (classification + ProcessLowerStars + compaction),
- * [1] sorting critical simplices, [2] D0, [3] D2, [4] D1, [5] output,
- * [6] total, [7] host-to-device copy (values_on_host = 1 only). */
+ * [1] sorting critical simplices, [2] D0 (D2's ascending walks run beside
+ * it on a second stream of the handle, as the paper runs D0 and D2 as
+ * parallel tasks), [3] D2 (its elder rule, once those walks are done),
+ * [4] D1, [5] output, [6] total, [7] host-to-device copy (values_on_host =
+ * 1 only). */
 dms_status dms_get_stage_ms(dms_grid grid, float ms[8]);
 
 /* Statistics of the last compute: [0] critical vertices, [1..4] critical
  * simplices of dimension 0..3, [5] kernel launches, [6] D0 halving levels,
- * [7] D2 halving levels, [8] D1 reduction rounds, [9] D1 columns, [10] D1
+ * [7] D2 halving levels (both over the spanning forest's arcs), [8] D1 reduction rounds, [9] D1 columns, [10] D1
  * columns whose boundary outgrew the first scratch pass (lazy mode: column
  * advances that did), [11] D1 column additions, [12] D1 column-pool entries
  * used (4 B each; lazy mode 16 B), [13] D1 pool regrowths, [14] bytes read
@@ -216,9 +219,11 @@ dms_status dms_get_device_bytes(dms_grid grid, int64_t *bytes);
  * pairs recorded on the compute stream around the launches (host round trips
  * between launches of one family are included): [0] classify (the per-vertex
  * stencil), [1] compaction, [2] radix sort, [3] ProcessLowerStars, [4] emit
- * of the critical simplices, [5] D0 arcs, [6] D0 union-find rounds, [7] D2
- * arcs, [8] D2 union-find rounds, [9] D1 boundary tracing, [10] D1
- * reduction (lazy mode: [9] is 0, [10] covers both), [11] output. */
+ * of the critical simplices, [5] D0 arcs, [6] D0 elder rule (spanning
+ * forest and halving levels), [7] D2 arcs (timed on the second stream,
+ * beside [5]-[6]), [8] D2 elder rule, [9] D1 boundary tracing, [10] D1
+ * reduction (lazy mode: [9] is 0, [10] covers both), [11] output.  [6] and
+ * [8] include the host's round trips between Borůvka rounds. */
 dms_status dms_get_kernel_ms(dms_grid grid, float ms[12]);
 
 /* Lower-link classification of every vertex and the id-ordered list of the
@@ -266,7 +271,7 @@ dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, 
  *                             (8..1024; default 48; larger traces retry with
  *                             16x more)
  *   DMS_TUNE_RED_BLOCK_BELOW  active columns below which a whole block
- *                             performs a column's additions (>= 0; 4096)
+ *                             performs a column's additions (>= 0; 16384)
  *   DMS_TUNE_LAZY_HEAP        first-pass heap entries of a lazy advance
  *                             (8..1024; default 48)
  *   DMS_TUNE_LAZY_DENSITY     d1_mode 0 reduces lazily when there are fewer

@@ -28,13 +28,13 @@ from . import _check
 
 TUNABLES = ("pls_block", "trace_block", "trace_per_sm", "trace_heap", "red_block_below",
             "lazy_heap", "lazy_density", "red_async", "pls_sort")
-DEFAULT = (128, 128, 2048, 48, 4096, 48, 32, 1, 1)
+DEFAULT = (128, 128, 2048, 48, 16384, 48, 32, 1, 1)
 CANDIDATES = {
     "pls_block": (64, 128, 256),
     "trace_block": (64, 128, 256),
     "trace_per_sm": (1024, 2048, 4096),
     "trace_heap": (32, 48, 96),
-    "red_block_below": (2048, 4096, 8192),
+    "red_block_below": (4096, 16384, 32768),
     "lazy_heap": (32, 48, 96),
     "lazy_density": (16, 32, 64),
     "red_async": (0, 1),

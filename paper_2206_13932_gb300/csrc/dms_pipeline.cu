@@ -884,7 +884,8 @@ __device__ __forceinline__ int64_t descend(const GridParams &g, const uint8_t *_
 // lowest neighbour) reach (Sec. 5.1 (a)-(b)).
 template <bool Bt>
 __global__ void k_d0_arcs(Geo<Bt> geo, const uint8_t *__restrict__ flags,
-                          const int32_t *__restrict__ vrank, const int32_t *__restrict__ v1,
+                          const int32_t *__restrict__ vrank, const int32_t *__restrict__ base0,
+                          const int32_t *__restrict__ v1,
                           const uint8_t *__restrict__ l1, int64_t n1, int32_t *A, int32_t *B,
                           int32_t *young, int64_t max_steps, DevStatus *st) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -893,10 +894,11 @@ __global__ void k_d0_arcs(Geo<Bt> geo, const uint8_t *__restrict__ flags,
     const GridParams &g = geo.at(x);
     int64_t u = x + g.dlin[l1[j]];
     int64_t ma = descend(g, flags, x, max_steps, st), mb = descend(g, flags, u, max_steps, st);
-    // on failure both ends go to node 0: a self-loop, harmless until the
-    // host reports the error
-    A[j] = ma < 0 || mb < 0 ? 0 : vrank[ma];
-    B[j] = ma < 0 || mb < 0 ? 0 : vrank[mb];
+    // nodes are the minima by their index in C0 (the lexicographic order, so a
+    // smaller index is an older minimum); on failure both ends go to node 0: a
+    // self-loop, harmless until the host reports the error
+    A[j] = ma < 0 || mb < 0 ? 0 : base0[vrank[ma]];
+    B[j] = ma < 0 || mb < 0 ? 0 : base0[vrank[mb]];
     young[j] = -1;
 }
 
@@ -973,18 +975,14 @@ __device__ __forceinline__ int32_t dc_find(DcSlot *tab, int32_t a) {
     }
 }
 
-// The kernels of one level run over the arcs still open (act[0..nact)): an
-// arc whose two ends carry one label has both ends in one component at its
-// segment's start, and components only merge, so it closes a cycle and is
-// dropped from the later levels (its young stays -1).
-//
-// light arcs of each segment: register both endpoint labels.
-__global__ void k_dc_insert(const int32_t *__restrict__ act, int64_t nact, int64_t narcs,
-                            int shift, int descending, const int32_t *A, const int32_t *B,
-                            DcSlot *tab, uint32_t mask, DevStatus *st) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nact) return;
-    const int64_t j = act[k];
+// light arcs of each segment: register both endpoint labels.  An arc whose
+// two ends already carry the same label joins nothing: its label is left out
+// (a heavy arc looking it up keeps it, as its component in the light half
+// is then itself or is registered by another arc).
+__global__ void k_dc_insert(int64_t narcs, int shift, int descending, const int32_t *A,
+                            const int32_t *B, DcSlot *tab, uint32_t mask, DevStatus *st) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= narcs) return;
     int64_t t = dc_time(j, narcs, descending);
     int64_t seg = t >> shift;
     if ((t >> (shift - 1)) & 1) return;                  // heavy half
@@ -1001,12 +999,11 @@ __global__ void k_dc_insert(const int32_t *__restrict__ act, int64_t nact, int64
 
 // light arcs: union their endpoints; a root is hooked under the root holding
 // the older label (smaller for D0, larger for D2)
-__global__ void k_dc_union(const int32_t *__restrict__ act, int64_t nact, int64_t narcs,
-                           int shift, int descending, int older_is_larger, const int32_t *A,
-                           const int32_t *B, DcSlot *tab, uint32_t mask, DevStatus *st) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nact) return;
-    const int64_t j = act[k];
+__global__ void k_dc_union(int64_t narcs, int shift, int descending, int older_is_larger,
+                           const int32_t *A, const int32_t *B, DcSlot *tab, uint32_t mask,
+                           DevStatus *st) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= narcs) return;
     int64_t t = dc_time(j, narcs, descending);
     int64_t seg = t >> shift;
     if ((t >> (shift - 1)) & 1) return;
@@ -1026,39 +1023,108 @@ __global__ void k_dc_union(const int32_t *__restrict__ act, int64_t nact, int64_
     atomicOr(&st->err, kErrIter);
 }
 
-// heavy arcs: relabel endpoints by the light half's components; then every
-// open arc flags whether it is still open
-__global__ void k_dc_relabel(const int32_t *__restrict__ act, int64_t nact, int64_t narcs,
-                             int shift, int descending, int32_t *A, int32_t *B, DcSlot *tab,
-                             uint32_t mask, int32_t *open) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nact) return;
-    const int64_t j = act[k];
+// heavy arcs: relabel endpoints by the light half's components
+__global__ void k_dc_relabel(int64_t narcs, int shift, int descending, int32_t *A, int32_t *B,
+                             DcSlot *tab, uint32_t mask) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= narcs) return;
     int64_t t = dc_time(j, narcs, descending);
     int64_t seg = t >> shift;
-    int32_t a = A[j], b = B[j];
-    if ((t >> (shift - 1)) & 1) {                        // heavy half
-        int32_t s = dc_lookup(tab, mask, ((unsigned long long)seg << 32) | (uint32_t)a);
-        if (s >= 0) a = A[j] = tab[dc_find(tab, s)].lab;
-        s = dc_lookup(tab, mask, ((unsigned long long)seg << 32) | (uint32_t)b);
-        if (s >= 0) b = B[j] = tab[dc_find(tab, s)].lab;
+    if (!((t >> (shift - 1)) & 1)) return;               // light half
+    int32_t *ends[2] = {&A[j], &B[j]};
+    for (int e = 0; e < 2; e++) {
+        int32_t s = dc_lookup(tab, mask, ((unsigned long long)seg << 32) | (uint32_t)*ends[e]);
+        if (s >= 0) *ends[e] = tab[dc_find(tab, s)].lab;
     }
-    open[k] = a != b;
 }
 
-// the arcs open at the start: ends in different minima (maxima)
-__global__ void k_dc_open(const int32_t *A, const int32_t *B, int64_t narcs, int32_t *open) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < narcs) open[j] = A[j] != B[j];
+// ------------------------------- minimum spanning forest of an arc graph
+//
+// Only the arcs of the minimum spanning forest (weight = the arc's turn,
+// distinct for all arcs) can join two components at their turn: Kruskal's
+// order takes exactly those.  The others close cycles and pair nothing, so
+// the elder rule's halving levels run over the forest's arcs only.  The
+// forest is found by Borůvka's rounds: every component takes its lightest
+// arc to another component; a component is named by a root node, and nodes
+// point (comp) to their root after every round.
+__global__ void k_bv_best(const int32_t *__restrict__ act, int64_t nact, int64_t narcs,
+                          int descending, const int32_t *__restrict__ A,
+                          const int32_t *__restrict__ B, const int32_t *__restrict__ comp,
+                          uint32_t *best, int32_t *open) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nact) return;
+    const int64_t j = act ? act[k] : k;
+    const int32_t ca = comp[A[j]], cb = comp[B[j]];
+    open[k] = ca != cb;
+    if (ca == cb) return;
+    const uint32_t w = (uint32_t)dc_time(j, narcs, descending);
+    atomicMin(&best[ca], w);
+    atomicMin(&best[cb], w);
+}
+
+// each root that found an arc: the root at its other end (comp is not
+// written in this kernel), and the arc joins the forest
+__global__ void k_bv_pick(int64_t nnodes, int64_t narcs, int descending,
+                          const int32_t *__restrict__ A, const int32_t *__restrict__ B,
+                          const int32_t *__restrict__ comp, const uint32_t *__restrict__ best,
+                          int32_t *tgt, uint8_t *msf) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nnodes) return;
+    tgt[r] = -1;
+    if (comp[r] != r || best[r] == 0xFFFFFFFFu) return;
+    const int64_t w = best[r];
+    const int64_t j = descending ? narcs - 1 - w : w;
+    const int32_t ca = comp[A[j]], cb = comp[B[j]];
+    tgt[r] = ca == r ? cb : ca;
+    msf[j] = 1;
+}
+
+// hook every such root under the other end's root; when two roots took the
+// same arc, the smaller one stays a root (no other cycle can form: weights
+// are distinct)
+__global__ void k_bv_hook(int64_t nnodes, const int32_t *__restrict__ tgt, int32_t *comp,
+                          unsigned long long *hooks) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nnodes) return;
+    const int32_t t = tgt[r];
+    if (t < 0) return;
+    if (tgt[t] == r && r < t) return;
+    comp[r] = t;
+    atomicAdd(hooks, 1ull);
+}
+
+// every node to its root (concurrent writes only shorten paths to one root)
+__global__ void k_bv_jump(int64_t nnodes, int32_t *comp, DevStatus *st) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nnodes) return;
+    int32_t x = comp[v];
+    for (int64_t it = 0; it <= nnodes; it++) {
+        const int32_t p = comp[x];
+        if (p == x) { comp[v] = x; return; }
+        x = p;
+    }
+    atomicOr(&st->err, kErrIter);
+}
+
+// the forest's arcs in their order: positions (scan of msf) -> packed arrays
+__global__ void k_bv_gather(int64_t narcs, const uint8_t *__restrict__ msf,
+                            const int32_t *__restrict__ pos, const int32_t *__restrict__ A,
+                            const int32_t *__restrict__ B, int32_t *A2, int32_t *B2,
+                            int32_t *idx) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= narcs || !msf[j]) return;
+    const int32_t k = pos[j];
+    A2[k] = A[j]; B2[k] = B[j]; idx[k] = (int32_t)j;
 }
 
 // every arc now sees the components at its turn: the elder rule
-__global__ void k_dc_decide(const int32_t *__restrict__ act, int64_t nact, int older_is_larger,
-                            const int32_t *A, const int32_t *B, int32_t *young, uint8_t *died) {
+__global__ void k_dc_decide(int64_t narcs, int older_is_larger, const int32_t *A,
+                            const int32_t *B, const int32_t *__restrict__ idx, int32_t *young,
+                            uint8_t *died) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nact) return;
-    const int64_t j = act[k];
-    int32_t a = A[j], b = B[j];
+    if (k >= narcs) return;
+    const int64_t j = idx ? idx[k] : k;
+    int32_t a = A[k], b = B[k];
     if (a == b) { young[j] = -1; return; }
     int32_t y = older_is_larger ? (a < b ? a : b) : (a > b ? a : b);
     young[j] = y;
@@ -1137,25 +1203,32 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
             if (kv > kb || (kv == kb && v > best)) { kb = kv; best = v; bl = l; }
         }
         if (bl >= 0) {   // re-express the tet in the star of its maximum vertex
-            uint16_t mask = 0;
             int ox = -S.dx[bl], oy = -S.dy[bl], oz = -S.dz[bl];
             int ly = S.link_of_dc[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
             if (ly < 0) { atomicOr(&st->err, kErrState); return vmax; }
-            mask |= (uint16_t)(1u << ly);
+            int lks[2], nk = 0;
             for (int k = 0; k < 3; k++) {
                 int l = S.tet_v[h][k];
                 if (l == bl) continue;
                 int ex = S.dx[l] + ox, ey = S.dy[l] + oy, ez = S.dz[l] + oz;
-                if (ex < -1 || ex > 1 || ey < -1 || ey > 1 || ez < -1 || ez > 1) {
+                if (ex < -1 || ex > 1 || ey < -1 || ey > 1 || ez < -1 || ez > 1 || nk >= 2) {
                     atomicOr(&st->err, kErrState);
                     return vmax;
                 }
                 int lk = S.link_of_dc[(ex + 1) + 3 * (ey + 1) + 9 * (ez + 1)];
                 if (lk < 0) { atomicOr(&st->err, kErrState); return vmax; }
-                mask |= (uint16_t)(1u << lk);
+                lks[nk++] = lk;
             }
+            if (nk != 2) { atomicOr(&st->err, kErrState); return vmax; }
+            // the star tet on links (ly, lks[0], lks[1]): one of the (at most
+            // two) star tets on the star triangle (lks[0], lks[1])
+            const int sf = S.tri_of_pair[lks[0]][lks[1]];
+            if (sf < 0) { atomicOr(&st->err, kErrState); return vmax; }
             int hn = -1;
-            for (int q = 0; q < kTets; q++) if (S.tet_mask[q] == mask) hn = q;
+            for (uint32_t cm = S.tets_of_tri[sf]; cm; cm &= cm - 1) {
+                const int q = __ffs(cm) - 1;
+                if (S.tet_mask[q] >> ly & 1) hn = q;
+            }
             if (hn < 0) { atomicOr(&st->err, kErrState); return vmax; }
             y = best;
             h = hn;
@@ -1283,12 +1356,12 @@ __device__ HeapEnt heap_pop(TraceCtx &c) {
 template <typename T>
 __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams &g,
                              const T *__restrict__ values, uint8_t *flags, GradRec *grad,
-                             const int32_t *__restrict__ vrank, const CritRec *__restrict__ recs,
-                             const int32_t *__restrict__ base1, const uint8_t *__restrict__ is_row,
-                             int64_t y, int m, DevStatus *st) {
+                             const unsigned long long *__restrict__ vcrit, int64_t y, int m,
+                             DevStatus *st) {
     if (m < 0 || m >= kLinks) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
     const uint8_t fy = ((volatile const uint8_t *)flags)[y];
     const T vy = values[y];
+    const unsigned long long cw = vcrit[y];   // read beside the others; used if y is critical
     GradRec G;
     {
         const ulonglong2 *src = (const ulonglong2 *)&grad[y];
@@ -1309,12 +1382,15 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
     }
     if (!slot || c.used * 4 >= (c.hashmask + 1) * 3) { c.overflow = true; return; }
     uint32_t info;
-    if (fy & kFlagCritical) {
-        int32_t i = vrank[y];
-        CritRec rec = recs[i];
-        if (rec.crit_e >> m & 1) {
-            int32_t j1 = base1[i] + local_index(S, rec, 1, m);
-            if (!is_row[j1]) return;            // paired in D0: dropped
+    if ((fy & kFlagCritical) && (cw >> (32 + m) & 1)) {   // a critical edge
+        {
+            if (!(cw >> (48 + m) & 1)) return;  // paired in D0: dropped
+            // its C1 index: the vertex's first, plus its critical edges of lower
+            // rank (the G order of edges of one lower star)
+            const int rm = grad_rank(G, m);
+            int32_t j1 = (int32_t)(uint32_t)cw;
+            for (uint32_t q = (uint32_t)(cw >> 32) & kAllLinks; q; q &= q - 1)
+                j1 += grad_rank(G, __ffs(q) - 1) < rm;
             if (c.rn >= c.rcap) { c.overflow = true; return; }
             c.rows[c.rn] = j1;
             c.rslot[c.rn] = (int32_t)(slot - c.hash);
@@ -1369,20 +1445,17 @@ __device__ __forceinline__ HashEnt *trace_find(TraceCtx &c, int64_t y, int m) {
 template <typename T>
 __device__ __forceinline__ void trace_expand(TraceCtx &c, const StarTables &S, const GridParams &g,
                                              const T *__restrict__ values, uint8_t *flags,
-                                             GradRec *grad, const int32_t *__restrict__ vrank,
-                                             const CritRec *__restrict__ recs,
-                                             const int32_t *__restrict__ base1,
-                                             const uint8_t *__restrict__ is_row, int64_t y, int s,
-                                             int m, const GradRec &G, DevStatus *st) {
+                                             GradRec *grad,
+                                             const unsigned long long *__restrict__ vcrit,
+                                             int64_t y, int s, int m, const GradRec &G,
+                                             DevStatus *st) {
     int ta = S.tri_v[s][0], tb = S.tri_v[s][1];
-    if (m >= 0) trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, y,
-                                ta == m ? tb : ta, st);
+    if (m >= 0) trace_toggle<T>(c, S, g, values, flags, grad, vcrit, y, ta == m ? tb : ta, st);
     bool aup = grad_rank(G, ta) > grad_rank(G, tb);
     int hi = aup ? ta : tb, lo = aup ? tb : ta;
     int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
                          9 * (S.dz[lo] - S.dz[hi] + 1)];
-    trace_toggle<T>(c, S, g, values, flags, grad, vrank, recs, base1, is_row, y + g.dlin[hi], l,
-                    st);
+    trace_toggle<T>(c, S, g, values, flags, grad, vcrit, y + g.dlin[hi], l, st);
 }
 
 // One thread per column: the Morse boundary of a critical triangle restricted
@@ -1395,9 +1468,7 @@ __device__ __forceinline__ void trace_expand(TraceCtx &c, const StarTables &S, c
 template <typename T, bool B>
 __global__ void __launch_bounds__(256, 4)
     k_d1_trace(const T *__restrict__ values, Geo<B> geo, uint8_t *flags, GradRec *grad,
-               const int32_t *__restrict__ vrank, const CritRec *__restrict__ recs,
-               const int32_t *__restrict__ base1, const uint8_t *__restrict__ is_row,
-               const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
+               const unsigned long long *__restrict__ vcrit, const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
                const int32_t *__restrict__ colmap, const int32_t *__restrict__ todo,
                int64_t ntodo, HeapEnt *heap_all, HashEnt *hash_all, int32_t *rows_all, int hcap,
                int hashcap, int rcap, int32_t gen_base, int32_t *pool, int64_t pool_cap,
@@ -1450,10 +1521,8 @@ __global__ void __launch_bounds__(256, 4)
             c.gen = gen_base + cj;
             // boundary: (x,a), (x,b) and the edge between x+a and x+b
             const GradRec Gx = grad_get(S, *gp, values, flags, grad, x);
-            trace_toggle<T>(c, S, *gp, values, flags, grad, vrank, recs, base1, is_row, x,
-                            S.tri_v[s][0], st);
-            trace_expand<T>(c, S, *gp, values, flags, grad, vrank, recs, base1, is_row, x, s,
-                            S.tri_v[s][0], Gx, st);
+            trace_toggle<T>(c, S, *gp, values, flags, grad, vcrit, x, S.tri_v[s][0], st);
+            trace_expand<T>(c, S, *gp, values, flags, grad, vcrit, x, s, S.tri_v[s][0], Gx, st);
             continue;
         }
         if (c.hn > 0 && !c.overflow) {
@@ -1465,10 +1534,9 @@ __global__ void __launch_bounds__(256, 4)
             if (!e || !hinfo_parity(e->info)) continue;
             e->info &= ~(1u << 31);
             const uint32_t spec = hinfo_aux(e->info);
-            trace_toggle<T>(c, S, *gp, values, flags, grad, vrank, recs, base1, is_row, y,
-                            (int)(spec & 15), st);
-            trace_toggle<T>(c, S, *gp, values, flags, grad, vrank, recs, base1, is_row,
-                            y + gp->dlin[(spec >> 4) & 15], (int)((spec >> 8) & 15), st);
+            trace_toggle<T>(c, S, *gp, values, flags, grad, vcrit, y, (int)(spec & 15), st);
+            trace_toggle<T>(c, S, *gp, values, flags, grad, vcrit, y + gp->dlin[(spec >> 4) & 15],
+                            (int)((spec >> 8) & 15), st);
             continue;
         }
         // the column is complete (or outgrew the scratch): write it out
@@ -3202,11 +3270,10 @@ __global__ void k_flag(int kind, OutArgs a, int64_t n, int32_t *flag) {
     flag[i] = f;
 }
 
-// D0 infinite: minima never killed.  node ids of minima are their critical ranks.
-__global__ void k_flag_min(const int32_t *v0, int64_t n0, const int32_t *vrank,
-                           const uint8_t *died0, int32_t *flag) {
+// D0 infinite: minima never killed (D0 nodes are the minima's indices in C0).
+__global__ void k_flag_min(int64_t n0, const uint8_t *died0, int32_t *flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n0) flag[i] = !died0[vrank[v0[i]]];
+    if (i < n0) flag[i] = !died0[i];
 }
 
 // In a batch the ids are written relative to the pair's field (a simplex id
@@ -3229,7 +3296,7 @@ __global__ void k_write(int kind, OutArgs a, const T *__restrict__ values, Geo<B
     int dim = 0, ess = 0;
     switch (kind) {
         case 0: {   // D0: (minimum, critical edge)
-            bv = a.vc[a.young0[i]]; bs = bv;
+            bv = a.v0[a.young0[i]]; bs = bv;
             dv = a.v1[i]; ds = edge_id(S, geo.at(dv), dv, a.l1[i]);
             dim = 0; break;
         }
@@ -3305,6 +3372,28 @@ __global__ void k_compact_list(const int32_t *list, const int32_t *flag32, const
                                int64_t m, int32_t *out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < m && flag32[k]) out[pos[k]] = list ? list[k] : (int32_t)k;
+}
+
+// The word of each critical vertex that the D1 trace reads beside its flags
+// and record: bits 0-31 the C1 index of its first critical edge, bits 32-45
+// its critical edges (star links), bits 48-61 those that are rows (1-saddles
+// not paired in D0).  One load in place of the chain vrank -> record ->
+// base -> row flag.
+__global__ void k_row_words(const int32_t *__restrict__ vc, int64_t nc,
+                            const CritRec *__restrict__ recs, const int32_t *__restrict__ base1,
+                            const uint8_t *__restrict__ is_row, unsigned long long *vcrit) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const StarTables &S = g_star;
+    const CritRec rec = recs[i];
+    const int32_t b1 = base1[i];
+    uint32_t rows = 0;
+    for (uint16_t m = rec.crit_e; m; m &= m - 1) {
+        const int n = __ffs(m) - 1;
+        if (is_row[b1 + local_index(S, rec, 1, n)]) rows |= 1u << n;
+    }
+    vcrit[vc[i]] = (unsigned long long)(uint32_t)b1 | ((unsigned long long)rec.crit_e << 32) |
+                   ((unsigned long long)rows << 48);
 }
 
 // ------------------------------------------------ backward (differentiation)
@@ -3421,6 +3510,7 @@ struct Ctx {
     cudaEvent_t *kev;   // kernel family start/end pairs
     int64_t launches = 0;
     StageRanges nv;     // NVTX range of the current stage
+    DevBuf *scan_buf = nullptr;   // scan partials of this stream (null: P.scan_tmp)
 };
 #define KEV(i) cudaEventRecord(c.kev[i], c.s)
 
@@ -3505,8 +3595,9 @@ dms_status scan(Ctx &c, const int32_t *in, int32_t *out, int64_t n, long long *t
     for (int64_t m = ntiles; m > 1; m = (m + kScanTile - 1) / kScanTile) sizes.push_back(m);
     size_t need = 0;
     for (int64_t m : sizes) need += 2 * (size_t)m;
-    if (!c.P.scan_tmp.ensure(4 * need + 1024)) return DMS_ERR_OOM;
-    int32_t *base = c.P.scan_tmp.as<int32_t>();
+    DevBuf &tmp = c.scan_buf ? *c.scan_buf : c.P.scan_tmp;
+    if (!tmp.ensure(4 * need + 1024)) return DMS_ERR_OOM;
+    int32_t *base = tmp.as<int32_t>();
     std::vector<const int32_t *> lin;
     std::vector<int32_t *> loff;
     const int32_t *cur = in;
@@ -3544,52 +3635,76 @@ dms_status sync_status(Ctx &c) {
     return DMS_OK;
 }
 
-// Elder-rule pairing of one arc graph (D0: increasing order, older = smaller
-// node id; D2: decreasing order, older = larger node id).  Returns the number
-// of halving levels.
-dms_status elder_rule(Ctx &c, int64_t narcs, int descending, int older_is_larger, int32_t *young,
-                      uint8_t *died, int64_t *levels_out) {
+// Elder-rule pairing of one arc graph over nodes 0..nnodes-1 (D0: the
+// minima, increasing order, older = smaller node; D2: the maxima and the
+// outside node, decreasing order, older = larger node).  The minimum
+// spanning forest's arcs are found first (Borůvka); the halving levels then
+// run over them alone.  Returns the number of halving levels.
+dms_status elder_rule(Ctx &c, int32_t *A, int32_t *B, int64_t narcs, int64_t nnodes,
+                      int descending, int older_is_larger, int32_t *young, uint8_t *died,
+                      int64_t *levels_out) {
     Pipeline &P = c.P;
-    int32_t *A = P.arc_a.as<int32_t>(), *B = P.arc_b.as<int32_t>();
     *levels_out = 0;
-    if (narcs == 0) return DMS_OK;
-    int L = 0;
-    while (((int64_t)1 << L) < narcs) L++;
-    // the open arcs (two lists, this level's and the next's), their flags and scan
+    if (narcs == 0 || nnodes == 0) return DMS_OK;
+    // ---- Borůvka: comp (nodes), best (nodes), tgt (nodes); the open arcs
+    // (two lists), their flags and scan; the forest flag per arc
+    DMS_ALLOC(P.bv_node, 12 * nnodes + 16);
+    int32_t *comp = P.bv_node.as<int32_t>(), *tgt = comp + nnodes;
+    uint32_t *best = (uint32_t *)(tgt + nnodes);
     DMS_ALLOC(P.dc_par, 8 * narcs + 8);
     DMS_ALLOC(P.dc_lab, 8 * narcs + 8);
+    DMS_ALLOC(P.bv_msf, narcs + 8);
     int32_t *act = P.dc_par.as<int32_t>(), *act2 = act + narcs;
     int32_t *open = P.dc_lab.as<int32_t>(), *pos = open + narcs;
-    DMS_LAUNCH(narcs, 256, k_dc_open, A, B, narcs, open);
+    uint8_t *msf = P.bv_msf.as<uint8_t>();
+    DMS_LAUNCH(nnodes, 256, k_iota32, comp, nnodes);
+    DMS_CUDA(cudaMemsetAsync(msf, 0, narcs, c.s));
+    const int32_t *list = nullptr;      // all arcs in the first round
+    int64_t nact = narcs;
+    for (int round = 0; nact > 0; round++) {
+        if (round > 64) return DMS_ERR_ITER_LIMIT;   // each round at least halves the roots
+        DMS_CUDA(cudaMemsetAsync(best, 0xFF, 4 * nnodes, c.s));
+        DMS_CUDA(cudaMemsetAsync(&c.st->misc[0], 0, sizeof(long long), c.s));
+        DMS_LAUNCH(nact, 256, k_bv_best, list, nact, narcs, descending, A, B, comp, best, open);
+        DMS_LAUNCH(nnodes, 256, k_bv_pick, nnodes, narcs, descending, A, B, comp, best, tgt, msf);
+        DMS_LAUNCH(nnodes, 256, k_bv_hook, nnodes, tgt, comp,
+                   (unsigned long long *)&c.st->misc[0]);
+        DMS_LAUNCH(nnodes, 256, k_bv_jump, nnodes, comp, c.st);
+        // the arcs still open at the round's start that may join components
+        DMS_TRY(scan(c, open, pos, nact, &c.st->total[3]));
+        DMS_TRY(sync_status(c));
+        const int64_t nnext = c.hst->total[3];
+        if (c.hst->misc[0] == 0) break;              // no component took an arc: done
+        DMS_LAUNCH(nact, 256, k_compact_list, list, open, pos, nact, act2);
+        std::swap(act, act2);
+        list = act;
+        nact = nnext;
+    }
+    // ---- the forest's arcs, in their order
+    DMS_LAUNCH(narcs, 256, k_u8_to_i32, msf, narcs, open);
     DMS_TRY(scan(c, open, pos, narcs, &c.st->total[3]));
     DMS_TRY(sync_status(c));
-    int64_t nact = c.hst->total[3];
-    DMS_LAUNCH(narcs, 256, k_compact_list, (const int32_t *)nullptr, open, pos, narcs, act);
-    // at most two keys per open arc: a table at most 2/3 full
+    const int64_t m = c.hst->total[3];
+    if (m == 0) return DMS_OK;
+    DMS_ALLOC(P.bv_arcs, 12 * m + 16);
+    int32_t *A2 = P.bv_arcs.as<int32_t>(), *B2 = A2 + m, *idx = B2 + m;
+    DMS_LAUNCH(narcs, 256, k_bv_gather, narcs, msf, pos, A, B, A2, B2, idx);
+    // ---- halving levels over the forest's arcs
+    int L = 0;
+    while (((int64_t)1 << L) < m) L++;
+    // at most one key per light-arc endpoint per level: a table at most 2/3 full
     uint32_t cap = 1024;
-    while ((int64_t)cap < 3 * nact + 2) cap <<= 1;
+    while ((int64_t)cap * 2 < 3 * m + 2) cap <<= 1;
     DMS_ALLOC(P.dc_keys, sizeof(DcSlot) * (size_t)cap);
     DcSlot *tab = P.dc_keys.as<DcSlot>();
-    for (int shift = L; shift >= 1 && nact > 0; shift--) {
-        uint32_t lcap = 1024;
-        while ((int64_t)lcap < 3 * nact + 2) lcap <<= 1;
-        DMS_CUDA(cudaMemsetAsync(tab, 0xFF, sizeof(DcSlot) * (size_t)lcap, c.s));
-        DMS_LAUNCH(nact, 256, k_dc_insert, act, nact, narcs, shift, descending, A, B, tab,
-                   lcap - 1, c.st);
-        DMS_LAUNCH(nact, 256, k_dc_union, act, nact, narcs, shift, descending, older_is_larger, A,
-                   B, tab, lcap - 1, c.st);
-        DMS_LAUNCH(nact, 256, k_dc_relabel, act, nact, narcs, shift, descending, A, B, tab,
-                   lcap - 1, open);
-        if (shift > 1) {   // keep the arcs still open
-            DMS_TRY(scan(c, open, pos, nact, &c.st->total[3]));
-            DMS_TRY(sync_status(c));
-            const int64_t nnext = c.hst->total[3];
-            DMS_LAUNCH(nact, 256, k_compact_list, act, open, pos, nact, act2);
-            std::swap(act, act2);
-            nact = nnext;
-        }
+    for (int shift = L; shift >= 1; shift--) {
+        DMS_CUDA(cudaMemsetAsync(tab, 0xFF, sizeof(DcSlot) * (size_t)cap, c.s));
+        DMS_LAUNCH(m, 256, k_dc_insert, m, shift, descending, A2, B2, tab, cap - 1, c.st);
+        DMS_LAUNCH(m, 256, k_dc_union, m, shift, descending, older_is_larger, A2, B2, tab,
+                   cap - 1, c.st);
+        DMS_LAUNCH(m, 256, k_dc_relabel, m, shift, descending, A2, B2, tab, cap - 1);
     }
-    DMS_LAUNCH(nact, 256, k_dc_decide, act, nact, older_is_larger, A, B, young, died);
+    DMS_LAUNCH(m, 256, k_dc_decide, m, older_is_larger, A2, B2, idx, young, died);
     *levels_out = L;
     return DMS_OK;
 }
@@ -4225,6 +4340,26 @@ dms_status launch_pls(Ctx &c, const T *values, const Geo<B> &geo, const int32_t 
     return DMS_OK;
 }
 
+// D2's ascending walks (Sec. 5.2) on the stream of c: every critical triangle
+// ascends on both sides to the maxima (or the outside node) it links; the
+// arcs go to P.arc2_a / P.arc2_b.  The walks of a warp start at nearby
+// vertices (vertex-id order), so they share the records they read.
+template <typename T, bool B>
+dms_status d2_walks(Ctx &c, const T *values, const Geo<B> &geo, int64_t n2, int32_t vmax,
+                    int64_t max_steps, int32_t *young2) {
+    Pipeline &P = c.P;
+    KEV(14);
+    const int32_t *order2 = nullptr;
+    DMS_TRY(order_by_vertex(c, P.c_vert[2].as<int32_t>(), nullptr, n2, 0, &order2));
+    DMS_LAUNCH(n2, 128, (k_d2_arcs<T, B>), values, geo, P.flags.as<uint8_t>(),
+               P.grad.as<GradRec>(), P.vrank.as<int32_t>(), P.recs.as<CritRec>(),
+               P.base[3].as<int32_t>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(), n2,
+               order2, vmax, P.virtual_max, P.arc2_a.as<int32_t>(), P.arc2_b.as<int32_t>(),
+               young2, max_steps, c.st);
+    KEV(15);
+    return DMS_OK;
+}
+
 template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     using K = typename Key<T>::K;
     Pipeline &P = c.P;
@@ -4351,40 +4486,53 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     c.nv.next("dms/d0");
 
     // union-find state shared by D0 and D2; results kept for the output
-    const int64_t narc_max = std::max(n1, n2);
-    DMS_ALLOC(P.arc_a, 4 * narc_max + 4);
-    DMS_ALLOC(P.arc_b, 4 * narc_max + 4);
+    DMS_ALLOC(P.arc_a, 4 * n1 + 4);
+    DMS_ALLOC(P.arc_b, 4 * n1 + 4);
+    DMS_ALLOC(P.arc2_a, 4 * n2 + 4);
+    DMS_ALLOC(P.arc2_b, 4 * n2 + 4);
     DMS_ALLOC(P.young, 4 * (n1 + n2) + 8);
     DMS_ALLOC(P.died, nc + n3 + 16);
     int32_t *young0 = P.young.as<int32_t>(), *young2 = young0 + n1;
     uint8_t *died0 = P.died.as<uint8_t>(), *died3 = died0 + nc;
     DMS_CUDA(cudaMemsetAsync(died0, 0, nc + n3 + 1, c.s));
 
+    // ---- D2's ascending walks on the second stream, beside D0 (the paper runs
+    // D0 and D2 as parallel tasks, Sec. 7.2); they read only the gradient and
+    // the critical lists, and write their own arcs
+    const int32_t vmax = (int32_t)n3;
+    DMS_CUDA(cudaEventRecord((cudaEvent_t)P.ev_fork, c.s));
+    DMS_CUDA(cudaStreamWaitEvent((cudaStream_t)P.s2, (cudaEvent_t)P.ev_fork, 0));
+    {
+        Ctx c2 = c;
+        c2.s = (cudaStream_t)P.s2;
+        c2.scan_buf = &P.scan_tmp2;
+        c2.launches = 0;
+        c2.nv.open = false;
+        DMS_TRY((d2_walks<T, B>(c2, values, geo, n2, vmax, max_steps, young2)));
+        c.launches += c2.launches;
+        DMS_CUDA(cudaEventRecord((cudaEvent_t)P.ev_join, c2.s));
+    }
+
     // ---- D0: arcs between minima, elder rule in increasing order
     KEV(10);
     DMS_LAUNCH(n1, 256, k_d0_arcs<B>, geo, P.flags.as<uint8_t>(), P.vrank.as<int32_t>(),
+               P.base[0].as<int32_t>(),
                P.c_vert[1].as<int32_t>(), P.c_loc[1].as<uint8_t>(), n1, P.arc_a.as<int32_t>(),
                P.arc_b.as<int32_t>(), young0, max_steps, c.st);
     KEV(11);
     KEV(12);
-    DMS_TRY(elder_rule(c, n1, 0, 0, young0, died0, &P.rounds_d0));
+    DMS_TRY(elder_rule(c, P.arc_a.as<int32_t>(), P.arc_b.as<int32_t>(), n1, n0, 0, 0, young0,
+                       died0, &P.rounds_d0));
     KEV(13);
     cudaEventRecord(ev[4], c.s);
     c.nv.next("dms/d2");
 
-    // ---- D2: arcs between maxima (node n3 = the virtual maximum), decreasing
-    const int32_t vmax = (int32_t)n3;
-    KEV(14);
-    const int32_t *order2 = nullptr;
-    DMS_TRY(order_by_vertex(c, P.c_vert[2].as<int32_t>(), nullptr, n2, 0, &order2));
-    DMS_LAUNCH(n2, 128, (k_d2_arcs<T, B>), values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
-               P.vrank.as<int32_t>(),
-               P.recs.as<CritRec>(), P.base[3].as<int32_t>(), P.c_vert[2].as<int32_t>(),
-               P.c_loc[2].as<uint8_t>(), n2, order2, vmax, P.virtual_max, P.arc_a.as<int32_t>(),
-               P.arc_b.as<int32_t>(), young2, max_steps, c.st);
-    KEV(15);
+    // ---- D2: arcs between maxima (node n3 = the virtual maximum), decreasing,
+    // once the walks on the second stream are done
+    DMS_CUDA(cudaStreamWaitEvent(c.s, (cudaEvent_t)P.ev_join, 0));
     KEV(16);
-    DMS_TRY(elder_rule(c, n2, 1, 1, young2, died3, &P.rounds_d2));
+    DMS_TRY(elder_rule(c, P.arc2_a.as<int32_t>(), P.arc2_b.as<int32_t>(), n2, n3 + 1, 1, 1,
+                       young2, died3, &P.rounds_d2));
     KEV(17);
     DMS_TRY(sync_status(c));
     cudaEventRecord(ev[5], c.s);
@@ -4422,6 +4570,9 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     if (ncols > 0 && mode == 3) {
         DMS_TRY((reduce_lazy<T, B>(c, values, ncols, n1, is_row)));
     } else if (ncols > 0) {
+        DMS_ALLOC(P.vcrit, 8 * n + 8);
+        DMS_LAUNCH(nc, 256, k_row_words, P.vc.as<int32_t>(), nc, P.recs.as<CritRec>(),
+                   P.base[1].as<int32_t>(), is_row, P.vcrit.as<unsigned long long>());
         int64_t pool_cap = std::max<int64_t>(1 << 24, 128 * ncols + 1024);
         DMS_ALLOC(P.d1_pool, 4 * pool_cap);
         uint8_t *ovf = P.d1_ovf.as<uint8_t>();
@@ -4447,8 +4598,8 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
                                 &corder));
         DMS_CUDA(cudaMemsetAsync(&c.st->trace_next, 0, sizeof(unsigned long long), c.s));
         k_d1_trace<T, B><<<(unsigned)(nthreads / tb), tb, 0, c.s>>>(
-            values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
-            P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
+            values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
+            P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
             P.d1_colmap.as<int32_t>(), corder, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,
             P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
             ovf, &c.st->trace_next, c.st);
@@ -4490,9 +4641,8 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
             DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nt * sizeof(HashEnt), c.s));
             DMS_CUDA(cudaMemsetAsync(&c.st->trace_next, 0, sizeof(unsigned long long), c.s));
             k_d1_trace<T, B><<<(unsigned)(nt / 32), 32, 0, c.s>>>(
-                values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(), P.vrank.as<int32_t>(),
-                P.recs.as<CritRec>(), P.base[1].as<int32_t>(), is_row, P.c_vert[2].as<int32_t>(),
-                P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), todo, ntodo, heap, hash,
+                values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
+                P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), todo, ntodo, heap, hash,
                 rows, hcap, hashcap, rcap, gen, P.d1_pool.as<int32_t>(), pool_cap,
                 P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), ovf, &c.st->trace_next, c.st);
             c.launches++;
@@ -4542,8 +4692,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     int32_t *fl = P.flag_a.as<int32_t>(), *ps = P.flag_b.as<int32_t>();
     for (int q = 0; q < 7; q++) {
         if (q == 1)
-            DMS_LAUNCH(part_n[q], 256, k_flag_min, a.v0, part_n[q], P.vrank.as<int32_t>(), died0,
-                       fl + foff[q]);
+            DMS_LAUNCH(part_n[q], 256, k_flag_min, part_n[q], died0, fl + foff[q]);
         else
             DMS_LAUNCH(part_n[q], 256, k_flag, q, a, part_n[q], fl + foff[q]);
         DMS_TRY(scan(c, fl + foff[q], ps + foff[q], part_n[q], &c.st->parts[q]));
@@ -4781,6 +4930,10 @@ dms_status Pipeline::init_common(const dms_options *o) {
         if (cudaEventCreate((cudaEvent_t *)&kev[i]) != cudaSuccess) return DMS_ERR_CUDA;
     for (int i = 0; i < 8; i++)
         if (cudaEventCreate((cudaEvent_t *)&sev[i]) != cudaSuccess) return DMS_ERR_CUDA;
+    if (cudaStreamCreateWithFlags((cudaStream_t *)&s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags((cudaEvent_t *)&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags((cudaEvent_t *)&ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return DMS_ERR_CUDA;
     return DMS_OK;
 }
 
@@ -4803,9 +4956,10 @@ std::vector<DevBuf *> Pipeline::buffers() {
     std::vector<DevBuf *> all = {&d1_row, &d1_rowpaired, &d1_rowpos, &d1_rowmap, &d1_cocnt, &d1_costart,
                      &d1_cofill, &d1_act, &d1_next, &d1_re, &d1_stamp, &grad, &values_dev, &flags,    &vrank,     &tile_cnt,  &tile_off,   &vc,
                      &vc_tmp,     &keys,     &keys_tmp,  &recs,      &arc_a,      &arc_b,
-                     &dc_keys,    &dc_par,   &dc_lab,    &young,     &died,       &rowcol,
+                     &dc_keys,    &dc_par,   &dc_lab,    &bv_node,   &bv_msf,    &bv_arcs,
+                     &young,     &died,       &rowcol,
                      &flag_a,     &flag_b,   &d1_colmap, &d1_start,  &d1_len,     &d1_owner,
-                     &d1_ovf,     &d1_pool,  &d1_scratch, &d1_todo,  &scan_tmp,   &dstat,
+                     &d1_ovf,     &d1_pool,  &d1_scratch, &d1_todo,  &scan_tmp,   &scan_tmp2, &arc2_a, &arc2_b, &vcrit, &dstat,
                      &d1_astamp, &lz_small.buf, &lz_big.buf, &d1_rowcol,
                      &fields_dev, &field_of, &field_off_dev, &fmax_field, &bt_k[0], &bt_k[1],
                      &bt_v[0], &bt_v[1], &bt_h[0], &bt_h[1], &bt_cnt, &out_tmp, &bx_buf[0],
@@ -4832,6 +4986,10 @@ void Pipeline::destroy() {
     for (int i = 0; i < 8; i++) if (sev[i]) cudaEventDestroy((cudaEvent_t)sev[i]);
     for (int i = 0; i < 24; i++) kev[i] = nullptr;
     for (int i = 0; i < 8; i++) sev[i] = nullptr;
+    if (ev_fork) cudaEventDestroy((cudaEvent_t)ev_fork);
+    if (ev_join) cudaEventDestroy((cudaEvent_t)ev_join);
+    if (s2) cudaStreamDestroy((cudaStream_t)s2);
+    ev_fork = ev_join = s2 = nullptr;
 }
 
 dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
@@ -4895,6 +5053,7 @@ dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
         result_id++;
     } else {
         cudaStreamSynchronize(c.s);
+        if (s2) cudaStreamSynchronize((cudaStream_t)s2);
         cudaGetLastError();
     }
     return s;

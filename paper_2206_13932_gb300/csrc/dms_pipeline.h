@@ -52,6 +52,7 @@ struct Pipeline {
     DevBuf c_vert[4], c_loc[4];
     DevBuf arc_a, arc_b, young, died, rowcol, flag_a, flag_b;
     DevBuf dc_keys, dc_par, dc_lab;   // elder-rule halving levels
+    DevBuf bv_node, bv_msf, bv_arcs;  // elder rule: spanning-forest nodes, flags, arcs
     DevBuf d1_act, d1_next, d1_re, d1_stamp;   // D1 reduction work lists
     DevBuf d1_row, d1_rowpaired;               // D1 result per column / row
     DevBuf d1_rowpos, d1_rowmap, d1_cocnt, d1_costart, d1_cofill;   // transpose
@@ -72,12 +73,16 @@ struct Pipeline {
     DevBuf fields_dev, field_of, field_off_dev, fmax_field;
     DevBuf out_field[3], bt_k[2], bt_v[2], bt_h[2], bt_cnt, out_tmp, batch_pofs[3];
     std::vector<int64_t> batch_off[3];   // per dimension: nf + 1 pair offsets
-    DevBuf scan_tmp;
+    DevBuf scan_tmp, scan_tmp2;   // scan partials: compute stream, second stream
+    DevBuf arc2_a, arc2_b;        // D2 arcs (computed beside D0 on the second stream)
+    DevBuf vcrit;                 // D1 trace: a word per critical vertex (rows among its edges)
+    void *s2 = nullptr;           // cudaStream_t: D2's ascending walks run there beside D0
+    void *ev_fork = nullptr, *ev_join = nullptr;   // cudaEvent_t between the two streams
     DevBuf dstat;           // device status words
     void *hstat = nullptr;  // pinned host mirror
 
     // launch shapes and capacities (dms_set_tuning; order of DMS_TUNE_*)
-    int32_t tune[DMS_TUNING_COUNT] = {128, 128, 2048, 48, 4096, 48, 32, 1, 1};
+    int32_t tune[DMS_TUNING_COUNT] = {128, 128, 2048, 48, 16384, 48, 32, 1, 1};
 
     int64_t n_crit = 0, n_c[4] = {0, 0, 0, 0};
     int64_t n_pairs[3] = {0, 0, 0}, n_ess[4] = {0, 0, 0, 0};

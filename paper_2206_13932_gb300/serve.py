@@ -46,21 +46,27 @@ def keeps_buffers(need: int, budget: int, slots: int) -> bool:
     return need <= budget // max(1, int(slots))
 
 
-def select_batch(pending, in_flight: int, budget: int, max_batch: int):
+def select_batch(pending, in_flight: int, budget: int, max_batch: int,
+                 max_vertices: int | None = None):
     """Admission: how many of the pending requests (a list of (vertices,
     dtype) in arrival order) start now, and their bytes.  The oldest ones that
-    fit the free budget, up to max_batch, all of the head's dtype; nothing
-    overtakes a head request that does not fit, so it is never starved."""
-    k, need = 0, 0
+    fit the free budget, up to max_batch and (after the first) up to
+    max_vertices in all, all of the head's dtype; nothing overtakes a head
+    request that does not fit, so it is never starved.  The vertex bound keeps
+    one batched pass short, so requests behind it wait less."""
+    k, need, verts = 0, 0, 0
     for size, dtype in pending:
         dt = np.dtype(dtype)
         if k and dt != np.dtype(pending[0][1]):
+            break
+        if k and max_vertices is not None and verts + size > max_vertices:
             break
         r = request_bytes(size, dt.itemsize)
         if in_flight + need + r > budget:
             break
         k += 1
         need += r
+        verts += size
         if k == max_batch:
             break
     return k, need
@@ -101,15 +107,17 @@ class Request:
 class DiagramServer:
     """``slots`` concurrent passes at most, within ``mem_budget`` bytes.  With
     ``max_batch`` > 1 a free slot takes up to that many waiting requests (in
-    arrival order, one dtype, within the budget) and computes them as one
-    batch (``dms_batch_create``): one pass of the pipeline for all of them."""
+    arrival order, one dtype, within the budget, and after the first at most
+    ``max_batch_vertices`` vertices in all) and computes them as one batch
+    (``dms_batch_create``): one pass of the pipeline for all of them."""
 
     def __init__(self, slots: int = 4, mem_budget: int = 16 << 30, max_batch: int = 1,
-                 backend=None):
+                 backend=None, max_batch_vertices: int | None = 1 << 21):
         self._be = backend if backend is not None else CudaBackend()
         self.slots = slots
         self.mem_budget = mem_budget
         self.max_batch = max(1, int(max_batch))
+        self.max_batch_vertices = max_batch_vertices
         self._pending = []                 # FIFO of admitted-later requests
         self._cv = threading.Condition()
         self._in_flight_bytes = 0
@@ -143,7 +151,8 @@ class DiagramServer:
                 if self._stop and not self._pending:
                     return None
                 k, need = select_batch([(r.values.size, r.values.dtype) for r in self._pending],
-                                       self._in_flight_bytes, self.mem_budget, self.max_batch)
+                                       self._in_flight_bytes, self.mem_budget, self.max_batch,
+                                       self.max_batch_vertices)
                 if k:
                     take = self._pending[:k]
                     del self._pending[:k]

@@ -43,3 +43,12 @@ def test_idle_handles_stay_within_a_share_of_the_budget():
     assert not keeps_buffers(101, 400, 4)
     assert keeps_buffers(400, 400, 1) and not keeps_buffers(401, 400, 1)
     assert keeps_buffers(0, 0, 0)
+
+
+def test_batch_bounded_by_vertices_after_the_first():
+    pend = [_req(3000), _req(3000), _req(3000), _req(100)]
+    # the first request is always taken, even above the bound
+    assert select_batch(pend, 0, 10 ** 12, 8, max_vertices=1000)[0] == 1
+    assert select_batch(pend, 0, 10 ** 12, 8, max_vertices=6000)[0] == 2
+    assert select_batch(pend, 0, 10 ** 12, 8, max_vertices=9100)[0] == 4
+    assert select_batch(pend, 0, 10 ** 12, 8, max_vertices=None)[0] == 4
