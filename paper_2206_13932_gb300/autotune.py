@@ -6,8 +6,9 @@ ProcessLowerStars and of the first D1 trace pass, the number of trace
 threads per SM and their heap size, the number of active columns below which
 a whole block performs a column's additions (and the asynchronous tail
 starts), the heap size of a lazy advance, the column density below which D1
-mode 0 reduces lazily, and whether the tail of the traced reduction runs as
-one asynchronous pass, and when ProcessLowerStars sorts its stars by shape.
+mode 0 reduces lazily, whether the tail of the traced reduction runs as
+one asynchronous pass, when ProcessLowerStars sorts its stars by shape, and
+whether D2's ascending walks run on a second stream beside D0.
 
 ``tune`` runs a coordinate descent: starting from the handle's current
 values, it tries each candidate of one tunable with the others fixed, keeps
@@ -27,8 +28,8 @@ import numpy as np
 from . import _check
 
 TUNABLES = ("pls_block", "trace_block", "trace_per_sm", "trace_heap", "red_block_below",
-            "lazy_heap", "lazy_density", "red_async", "pls_sort")
-DEFAULT = (128, 128, 2048, 48, 16384, 48, 32, 1, 1)
+            "lazy_heap", "lazy_density", "red_async", "pls_sort", "d2_beside_d0")
+DEFAULT = (128, 128, 2048, 48, 16384, 48, 32, 1, 1, 1)
 CANDIDATES = {
     "pls_block": (64, 128, 256),
     "trace_block": (64, 128, 256),
@@ -39,6 +40,7 @@ CANDIDATES = {
     "lazy_density": (16, 32, 64),
     "red_async": (0, 1),
     "pls_sort": (0, 1, 2),
+    "d2_beside_d0": (0, 1),
 }
 
 
@@ -66,7 +68,8 @@ def valid(values) -> bool:
             d["trace_per_sm"] % d["trace_block"] == 0 and
             8 <= d["trace_heap"] <= 1024 and d["red_block_below"] >= 0 and
             8 <= d["lazy_heap"] <= 1024 and 1 <= d["lazy_density"] <= 4096 and
-            d["red_async"] in (0, 1) and d["pls_sort"] in (0, 1, 2))
+            d["red_async"] in (0, 1) and d["pls_sort"] in (0, 1, 2) and
+            d["d2_beside_d0"] in (0, 1))
 
 
 def measure(grid, field, repeats: int = 3) -> float:

@@ -1143,10 +1143,22 @@ __device__ __noinline__ GradRec grad_fill(const StarTables &S, const GridParams 
                                           const T *__restrict__ values, uint8_t *flags,
                                           GradRec *grad, int64_t y);
 
+// dense: every record was computed before the walks (nothing writes flags or
+// records meanwhile), so the record is read through L1 without its flag.
 template <typename T>
 __device__ __forceinline__ GradRec grad_get(const StarTables &S, const GridParams &g,
                                             const T *__restrict__ values, uint8_t *flags,
-                                            GradRec *grad, int64_t y) {
+                                            GradRec *grad, int64_t y, bool dense = false) {
+    if (dense) {
+        GradRec G;
+        const ulonglong2 *src = (const ulonglong2 *)&grad[y];
+        for (int k = 0; k < 3; k++) {
+            const ulonglong2 v = __ldg(src + k);
+            G.w[2 * k] = v.x;
+            G.w[2 * k + 1] = v.y;
+        }
+        return G;
+    }
     if (((volatile const uint8_t *)flags)[y] & kFlagGradient) {
         GradRec G;
         const ulonglong2 *src = (const ulonglong2 *)&grad[y];
@@ -1189,8 +1201,11 @@ template <typename T>
 __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__restrict__ values,
                           uint8_t *flags, GradRec *grad, const int32_t *__restrict__ vrank,
                           const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
-                          int64_t y, int h, int32_t vmax, int64_t max_steps, DevStatus *st) {
+                          int64_t y, int h, int32_t vmax, int64_t max_steps, bool dense,
+                          DevStatus *st) {
     using K = typename Key<T>::K;
+    int cx, cy, cz;     // coordinates of y, followed as the walk moves
+    coords(g, y, cx, cy, cz);
     for (int64_t step = 0; step < max_steps; step++) {
         // the maximum vertex of the tet
         K kb = Key<T>::of(values[y]);
@@ -1231,6 +1246,7 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
             }
             if (hn < 0) { atomicOr(&st->err, kErrState); return vmax; }
             y = best;
+            cx += S.dx[bl]; cy += S.dy[bl]; cz += S.dz[bl];
             h = hn;
         }
         if (flags[y] & kFlagCritical) {
@@ -1238,15 +1254,13 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
             CritRec rec = recs[i];
             if (rec.crit_h >> h & 1) return base3[i] + local_index(S, rec, 3, h);
         }
-        GradRec G = grad_get(S, g, values, flags, grad, y);
+        GradRec G = grad_get(S, g, values, flags, grad, y, dense);
         int s2 = grad_tet_pair(G, h);
         if (s2 >= kTris) { atomicOr(&st->err, kErrState); return vmax; }
         uint32_t other = S.tets_of_tri[s2] & ~(1u << h);
         if (!other) { atomicOr(&st->err, kErrState); return vmax; }
         int h2 = __ffs(other) - 1;
         int w = __ffs(S.tet_mask[h2] & ~S.tri_mask[s2]) - 1;
-        int cx, cy, cz;
-        coords(g, y, cx, cy, cz);
         if (!(present_links(S, g, cx, cy, cz) >> w & 1)) return vmax;   // the outer boundary
         h = h2;
     }
@@ -1261,7 +1275,7 @@ __global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *fl
                           const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
                           int64_t n2, const int32_t *__restrict__ order, int32_t vmax,
                           int vmax_on, int32_t *A, int32_t *B, int32_t *young, int64_t max_steps,
-                          DevStatus *st) {
+                          int dense, DevStatus *st) {
     // arcs in vertex-id order (`order`), so that the walks of a warp start
     // close together and share the records they read.  Without the virtual
     // maximum (App. A) a 2-saddle whose ascent leaves the domain on either
@@ -1283,7 +1297,7 @@ __global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *fl
         m &= m - 1;
         int w = __ffs(S.tet_mask[h] & ~S.tri_mask[s]) - 1;
         ends[e] = (pres >> w & 1) ? ascend(S, g, values, flags, grad, vrank, recs, base3, x, h,
-                                           vmax, max_steps, st)
+                                           vmax, max_steps, dense != 0, st)
                                   : vmax;
     }
     if (!vmax_on && (ends[0] == vmax || ends[1] == vmax)) ends[0] = ends[1] = vmax;
@@ -1303,6 +1317,9 @@ struct TraceCtx {
     int hn, rn, used;
     int32_t gen;
     bool overflow;
+    bool dense;        // every record was computed before the walks: nothing
+                       // writes flags or records meanwhile, so they may be
+                       // cached in L1
 };
 
 __device__ __forceinline__ uint32_t hash64(unsigned long long k) {
@@ -1359,14 +1376,14 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
                              const unsigned long long *__restrict__ vcrit, int64_t y, int m,
                              DevStatus *st) {
     if (m < 0 || m >= kLinks) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
-    const uint8_t fy = ((volatile const uint8_t *)flags)[y];
+    const uint8_t fy = c.dense ? __ldg(flags + y) : ((volatile const uint8_t *)flags)[y];
     const T vy = values[y];
     const unsigned long long cw = vcrit[y];   // read beside the others; used if y is critical
     GradRec G;
     {
         const ulonglong2 *src = (const ulonglong2 *)&grad[y];
         for (int k = 0; k < 3; k++) {
-            const ulonglong2 v = __ldcg(src + k);
+            const ulonglong2 v = c.dense ? __ldg(src + k) : __ldcg(src + k);
             G.w[2 * k] = v.x;
             G.w[2 * k + 1] = v.y;
         }
@@ -1473,11 +1490,12 @@ __global__ void __launch_bounds__(256, 4)
                int64_t ntodo, HeapEnt *heap_all, HashEnt *hash_all, int32_t *rows_all, int hcap,
                int hashcap, int rcap, int32_t gen_base, int32_t *pool, int64_t pool_cap,
                int64_t *col_start, int32_t *col_len, uint8_t *overflow,
-               unsigned long long *next_col, DevStatus *st) {
+               unsigned long long *next_col, int dense, DevStatus *st) {
     const StarTables &S = g_star;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     TraceCtx c;
+    c.dense = dense != 0;
     c.heap = heap_all + tid * hcap;
     c.hash = hash_all + tid * hashcap;
     c.rows = rows_all + tid * 2 * rcap;
@@ -1520,7 +1538,7 @@ __global__ void __launch_bounds__(256, 4)
             c.hn = 0; c.rn = 0; c.used = 0; c.overflow = false;
             c.gen = gen_base + cj;
             // boundary: (x,a), (x,b) and the edge between x+a and x+b
-            const GradRec Gx = grad_get(S, *gp, values, flags, grad, x);
+            const GradRec Gx = grad_get(S, *gp, values, flags, grad, x, c.dense);
             trace_toggle<T>(c, S, *gp, values, flags, grad, vcrit, x, S.tri_v[s][0], st);
             trace_expand<T>(c, S, *gp, values, flags, grad, vcrit, x, s, S.tri_v[s][0], Gx, st);
             continue;
@@ -2427,6 +2445,9 @@ struct LazyCtx {
     int hcap, hashmask, hn, used;
     int32_t gen;
     bool overflow;
+    bool dense;        // every record was computed before the walks: nothing
+                       // writes flags or records meanwhile, so they may be
+                       // cached in L1
 };
 
 __device__ __forceinline__ HashEnt *lz_find(LazyCtx &c, unsigned long long key) {
@@ -4355,7 +4376,7 @@ dms_status d2_walks(Ctx &c, const T *values, const Geo<B> &geo, int64_t n2, int3
                P.grad.as<GradRec>(), P.vrank.as<int32_t>(), P.recs.as<CritRec>(),
                P.base[3].as<int32_t>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(), n2,
                order2, vmax, P.virtual_max, P.arc2_a.as<int32_t>(), P.arc2_b.as<int32_t>(),
-               young2, max_steps, c.st);
+               young2, max_steps, P.dense_grad ? 1 : 0, c.st);
     KEV(15);
     return DMS_OK;
 }
@@ -4367,6 +4388,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     cudaEvent_t *ev = c.ev;
     const int64_t n = P.n;
     const int64_t max_steps = P.max_iters > 0 ? P.max_iters : n + 1;
+    P.dense_grad = false;
     DMS_CUDA(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s));
 
     // ---- gradient: classification, compaction, sort, ProcessLowerStars
@@ -4427,7 +4449,8 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
         KEV(6);
         const int ps = P.tune[DMS_TUNE_PLS_SORT];
         const bool sort_stars = ps == 2 || (ps == 1 && nc * 4 > n);
-        if (nc * 4 > n || n <= kDenseGradientBelow)
+        P.dense_grad = nc * 4 > n || n <= kDenseGradientBelow;
+        if (P.dense_grad)
             DMS_TRY((launch_pls<T, B>(c, values, geo, nullptr, n, sort_stars)));
         else
             DMS_TRY((launch_pls<T, B>(c, values, geo, P.vc.as<int32_t>(), nc, sort_stars)));
@@ -4500,9 +4523,10 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     // D0 and D2 as parallel tasks, Sec. 7.2); they read only the gradient and
     // the critical lists, and write their own arcs
     const int32_t vmax = (int32_t)n3;
-    DMS_CUDA(cudaEventRecord((cudaEvent_t)P.ev_fork, c.s));
-    DMS_CUDA(cudaStreamWaitEvent((cudaStream_t)P.s2, (cudaEvent_t)P.ev_fork, 0));
-    {
+    const bool beside = P.tune[DMS_TUNE_D2_BESIDE_D0] != 0;
+    if (beside) {
+        DMS_CUDA(cudaEventRecord((cudaEvent_t)P.ev_fork, c.s));
+        DMS_CUDA(cudaStreamWaitEvent((cudaStream_t)P.s2, (cudaEvent_t)P.ev_fork, 0));
         Ctx c2 = c;
         c2.s = (cudaStream_t)P.s2;
         c2.scan_buf = &P.scan_tmp2;
@@ -4529,7 +4553,8 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
 
     // ---- D2: arcs between maxima (node n3 = the virtual maximum), decreasing,
     // once the walks on the second stream are done
-    DMS_CUDA(cudaStreamWaitEvent(c.s, (cudaEvent_t)P.ev_join, 0));
+    if (beside) DMS_CUDA(cudaStreamWaitEvent(c.s, (cudaEvent_t)P.ev_join, 0));
+    else DMS_TRY((d2_walks<T, B>(c, values, geo, n2, vmax, max_steps, young2)));
     KEV(16);
     DMS_TRY(elder_rule(c, P.arc2_a.as<int32_t>(), P.arc2_b.as<int32_t>(), n2, n3 + 1, 1, 1,
                        young2, died3, &P.rounds_d2));
@@ -4602,7 +4627,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
             P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
             P.d1_colmap.as<int32_t>(), corder, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,
             P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
-            ovf, &c.st->trace_next, c.st);
+            ovf, &c.st->trace_next, P.dense_grad ? 1 : 0, c.st);
         c.launches++;
         DMS_CUDA(cudaGetLastError());
         // columns whose trace outgrew the scratch run again with 16x more; the
@@ -4644,7 +4669,8 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
                 values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
                 P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), todo, ntodo, heap, hash,
                 rows, hcap, hashcap, rcap, gen, P.d1_pool.as<int32_t>(), pool_cap,
-                P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), ovf, &c.st->trace_next, c.st);
+                P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), ovf, &c.st->trace_next,
+                P.dense_grad ? 1 : 0, c.st);
             c.launches++;
             DMS_CUDA(cudaGetLastError());
             gen += (int32_t)ncols;

@@ -76,13 +76,14 @@ struct Pipeline {
     DevBuf scan_tmp, scan_tmp2;   // scan partials: compute stream, second stream
     DevBuf arc2_a, arc2_b;        // D2 arcs (computed beside D0 on the second stream)
     DevBuf vcrit;                 // D1 trace: a word per critical vertex (rows among its edges)
+    bool dense_grad = false;      // every gradient record was computed before the walks
     void *s2 = nullptr;           // cudaStream_t: D2's ascending walks run there beside D0
     void *ev_fork = nullptr, *ev_join = nullptr;   // cudaEvent_t between the two streams
     DevBuf dstat;           // device status words
     void *hstat = nullptr;  // pinned host mirror
 
     // launch shapes and capacities (dms_set_tuning; order of DMS_TUNE_*)
-    int32_t tune[DMS_TUNING_COUNT] = {128, 128, 2048, 48, 16384, 48, 32, 1, 1};
+    int32_t tune[DMS_TUNING_COUNT] = {128, 128, 2048, 48, 16384, 48, 32, 1, 1, 1};
 
     int64_t n_crit = 0, n_c[4] = {0, 0, 0, 0};
     int64_t n_pairs[3] = {0, 0, 0}, n_ess[4] = {0, 0, 0, 0};

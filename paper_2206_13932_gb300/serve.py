@@ -112,7 +112,7 @@ class DiagramServer:
     (``dms_batch_create``): one pass of the pipeline for all of them."""
 
     def __init__(self, slots: int = 4, mem_budget: int = 16 << 30, max_batch: int = 1,
-                 backend=None, max_batch_vertices: int | None = 1 << 21):
+                 backend=None, max_batch_vertices: int | None = None):
         self._be = backend if backend is not None else CudaBackend()
         self.slots = slots
         self.mem_budget = mem_budget
