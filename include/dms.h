@@ -271,7 +271,9 @@ dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, 
  *                             (8..1024; default 48; larger traces retry with
  *                             16x more)
  *   DMS_TUNE_RED_BLOCK_BELOW  active columns below which a whole block
- *                             performs a column's additions (>= 0; 16384)
+ *                             performs a column's additions (>= 0; -1, the
+ *                             default: the larger of 4096 and one column
+ *                             in 1600)
  *   DMS_TUNE_LAZY_HEAP        first-pass heap entries of a lazy advance
  *                             (8..1024; default 48)
  *   DMS_TUNE_LAZY_DENSITY     d1_mode 0 reduces lazily when there are fewer

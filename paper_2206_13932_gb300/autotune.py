@@ -29,13 +29,13 @@ from . import _check
 
 TUNABLES = ("pls_block", "trace_block", "trace_per_sm", "trace_heap", "red_block_below",
             "lazy_heap", "lazy_density", "red_async", "pls_sort", "d2_beside_d0")
-DEFAULT = (128, 128, 2048, 48, 16384, 48, 32, 1, 1, 1)
+DEFAULT = (128, 128, 2048, 48, -1, 48, 32, 1, 1, 1)
 CANDIDATES = {
     "pls_block": (64, 128, 256),
     "trace_block": (64, 128, 256),
     "trace_per_sm": (1024, 2048, 4096),
     "trace_heap": (32, 48, 96),
-    "red_block_below": (4096, 16384, 32768),
+    "red_block_below": (-1, 4096, 16384),
     "lazy_heap": (32, 48, 96),
     "lazy_density": (16, 32, 64),
     "red_async": (0, 1),
@@ -66,7 +66,7 @@ def valid(values) -> bool:
     return (block(d["pls_block"], 512) and block(d["trace_block"], 256) and
             d["trace_block"] <= d["trace_per_sm"] <= 8192 and
             d["trace_per_sm"] % d["trace_block"] == 0 and
-            8 <= d["trace_heap"] <= 1024 and d["red_block_below"] >= 0 and
+            8 <= d["trace_heap"] <= 1024 and d["red_block_below"] >= -1 and
             8 <= d["lazy_heap"] <= 1024 and 1 <= d["lazy_density"] <= 4096 and
             d["red_async"] in (0, 1) and d["pls_sort"] in (0, 1, 2) and
             d["d2_beside_d0"] in (0, 1))

@@ -144,7 +144,7 @@ dms_status dms_set_tuning(dms_grid grid, const int32_t *v, int count) {
     if (per_sm < v[DMS_TUNE_TRACE_BLOCK] || per_sm > 8192 || per_sm % v[DMS_TUNE_TRACE_BLOCK])
         return DMS_ERR_INVALID_ARG;
     if (v[DMS_TUNE_TRACE_HEAP] < 8 || v[DMS_TUNE_TRACE_HEAP] > 1024) return DMS_ERR_INVALID_ARG;
-    if (v[DMS_TUNE_RED_BLOCK_BELOW] < 0) return DMS_ERR_INVALID_ARG;
+    if (v[DMS_TUNE_RED_BLOCK_BELOW] < -1) return DMS_ERR_INVALID_ARG;
     if (v[DMS_TUNE_LAZY_HEAP] < 8 || v[DMS_TUNE_LAZY_HEAP] > 1024) return DMS_ERR_INVALID_ARG;
     if (v[DMS_TUNE_LAZY_DENSITY] < 1 || v[DMS_TUNE_LAZY_DENSITY] > 4096) return DMS_ERR_INVALID_ARG;
     if (v[DMS_TUNE_RED_ASYNC] != 0 && v[DMS_TUNE_RED_ASYNC] != 1) return DMS_ERR_INVALID_ARG;

@@ -38,7 +38,7 @@ def test_valid_mirrors_the_ranges_the_library_accepts():
     """The refusals of dms_set_tuning (checked on a GPU in
     test_autotune_gpu.py) are refused here already."""
     for k, bad in ((0, 48), (0, 1024), (1, 16), (1, 512), (2, 100), (3, 4), (5, 2000), (6, 0),
-                   (7, 2), (8, 3), (2, 16384), (4, -1)):
+                   (7, 2), (8, 3), (2, 16384), (4, -2), (9, 2)):
         vals = tuple(bad if i == k else x for i, x in enumerate(at.DEFAULT))
         assert not at.valid(vals), (at.TUNABLES[k], bad)
     assert not at.valid(at.DEFAULT[:-1])

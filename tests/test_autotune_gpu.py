@@ -40,7 +40,8 @@ def test_every_candidate_gives_the_same_pairs(dms):
 def test_out_of_range_values_are_refused(dms):
     from paper_2206_13932_gb300 import autotune as at
     with dms.Grid((8, 8, 8), np.float32) as g:
-        for k, bad in ((0, 48), (0, 1024), (1, 16), (1, 512), (2, 100), (3, 4), (5, 2000), (6, 0), (7, 2), (8, 3)):
+        for k, bad in ((0, 48), (0, 1024), (1, 16), (1, 512), (2, 100), (3, 4), (5, 2000), (6, 0), (7, 2),
+                       (8, 3), (4, -2), (9, 2)):
             vals = tuple(bad if i == k else x for i, x in enumerate(at.DEFAULT))
             with pytest.raises(dms.DmsError):
                 at.set_tuning(g, vals)
