@@ -15,8 +15,9 @@ bounded sub-volumes of the same field, on this machine's host cores.
 Rooflines in the line: ``roofline`` for the kernel family that takes the most
 device time, ``roofline_gradient`` for the gradient stage (classification,
 compaction and ProcessLowerStars) against its algorithmic bytes N*s_in +
-8*|C| (every value read once, every critical simplex written once), and
-``roofline_classify`` for the per-vertex stencil alone.
+8*|C| (every value read once, every critical simplex written once),
+``roofline_classify`` for the per-vertex stencil alone, and
+``roofline_pls`` for ProcessLowerStars against the issue rate.
 """
 from __future__ import annotations
 
@@ -53,6 +54,12 @@ SERVE_BATCH = 16            # most requests one batched pass takes
 # _CLASSIFY_SPANS); otherwise reported as null.
 CLASSIFY_TRAFFIC = {"sources_sha256": "eb26737328563b5ce987eccc9b9472e26eb7afd8df787c6404174cb78de85218",
                     "bytes_per_launch": 268718336 + 117972992}
+# Warp instructions issued per star by the shape-sorted ProcessLowerStars
+# kernel, from one ncu capture (profiles/pls_sorted_noise192.md: 4 876 004 637
+# instructions for 7 077 888 stars of 192^3 noise, 57 % of them PL-critical,
+# like this workload), valid only for the code it was taken on (_PLS_SPANS).
+PLS_ISSUE = {"sources_sha256": "0e1541eb610add831382a7de687b3c1a8905858cc27a6209d40fc0429736d1db",
+             "warp_inst_per_star": 4876004637 / 7077888, "simt_lanes": 12.96}
 
 
 def _code_only(src: str) -> str:
@@ -88,11 +95,20 @@ _CLASSIFY_SPANS = (("", "stage 2: stable LSD radix sort"), ("struct ClsTiling", 
                    ("k_classify2<T><<<", ");"))
 
 
-def _classify_code_of(pipeline_src: str, common_src: str):
-    """Comment-free text of the code behind the classification kernel, or None
-    when a marker is missing."""
+# The code behind the ProcessLowerStars kernel of the bench (shape-sorted
+# blocks): the shape-sorted kernel and its launch; dms_common.cuh (star view,
+# ProcessLowerStars) counts whole.
+_PLS_SPANS = (("template <typename T, bool B, int NT>\n__global__ void __launch_bounds__(NT)\n"
+               "    k_pls_sorted(", "// The critical cells of the lower star of each sorted"),
+              ("dms_status launch_pls(Ctx &c", "return DMS_OK;\n}"))
+
+
+def _code_of(pipeline_src: str, common_src: str, spans):
+    """Comment-free text of the code behind a kernel (dms_common.cuh and the
+    spans of dms_pipeline.cu between each pair of markers), or None when a
+    marker is missing."""
     parts = [common_src]
-    for a, b in _CLASSIFY_SPANS:
+    for a, b in spans:
         i = pipeline_src.find(a) if a else 0
         j = pipeline_src.find(b, i + len(a)) if i >= 0 else -1
         if i < 0 or j < 0:
@@ -101,16 +117,22 @@ def _classify_code_of(pipeline_src: str, common_src: str):
     return "\0".join(_code_only(p) for p in parts)
 
 
-def _kernel_sources_sha256():
-    """Hash of the code (comments excluded) behind the classification kernel:
-    the stored DRAM traffic is reported only while it matches."""
+def _classify_code_of(pipeline_src: str, common_src: str):
+    """Comment-free text of the code behind the classification kernel, or None
+    when a marker is missing."""
+    return _code_of(pipeline_src, common_src, _CLASSIFY_SPANS)
+
+
+def _kernel_sources_sha256(spans=_CLASSIFY_SPANS):
+    """Hash of the code (comments excluded) behind a kernel (by default the
+    classification's): a stored ncu figure is reported only while it matches."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2206_13932_gb300", "csrc")
     with open(os.path.join(csrc, "dms_pipeline.cu")) as f:
         pipeline_src = f.read()
     with open(os.path.join(csrc, "dms_common.cuh")) as f:
         common_src = f.read()
-    code = _classify_code_of(pipeline_src, common_src)
+    code = _code_of(pipeline_src, common_src, spans)
     return None if code is None else hashlib.sha256(code.encode()).hexdigest()
 
 
@@ -322,13 +344,37 @@ def roofline_classify(n, s_in, kavg, hbm, src):
             "algorithmic_bytes_per_launch": nbytes, "peak_source": src}
 
 
-def roofline_dominant(dom, kavg, rgrad, rcls, hbm, src):
-    """The family with the most device time.  The stencil and the gradient
-    stage are measured against HBM; the walks, union-find levels and the D1
-    reduction have no algorithmic byte count that bounds them (dependent
-    gathers, atomics and addition chains) and are reported with their time."""
+def roofline_pls(n, stats, kavg):
+    """ProcessLowerStars is bound by instruction issue (its integer work per
+    star), so its roofline is the issue rate: 152 SMs x 4 schedulers x one
+    warp instruction per cycle at the 2070 MHz maximum clock.  Achieved = the
+    warp instructions it issues (ncu count per star x the stars of this
+    launch) over its CUDA-event time; null when the kernel's code differs
+    from the capture's."""
+    ok = PLS_ISSUE["sources_sha256"] == _kernel_sources_sha256(_PLS_SPANS)
+    crit = stats.get("critical_vertices", n)
+    stars = n if (crit * 4 > n or n <= (1 << 25)) else crit     # dense or critical only
+    ms = kavg["process_lower_stars"]
+    peak = SMS * SMSPS * SM_MAX_MHZ * 1e6 / 1e9
+    ach = PLS_ISSUE["warp_inst_per_star"] * stars / (ms * 1e-3) / 1e9 if ok and ms > 0 else None
+    return {"bound": "alu", "kernel": "k_pls_sorted (ProcessLowerStars, shape-sorted blocks)",
+            "achieved": ach, "peak": peak, "unit": "G warp instructions/s",
+            "frac": ach / peak if ach is not None else None, "traffic": None, "ms": ms,
+            "stars": stars, "peak_source": "152 SMs x 4 schedulers x 2070 MHz",
+            "note": "issue-bound; about 40 % of the lanes of an issued instruction do work "
+                    f"({PLS_ISSUE['simt_lanes']} of 32, divergent star shapes)"}
+
+
+def roofline_dominant(dom, kavg, rgrad, rcls, hbm, src, rpls=None):
+    """The family with the most device time.  The stencil is measured against
+    HBM, ProcessLowerStars against the issue rate; the walks, union-find
+    levels and the D1 reduction have no algorithmic byte count that bounds
+    them (dependent gathers, atomics and addition chains) and are reported
+    with their time."""
     if dom == "classify":
         return dict(rcls)
+    if dom == "process_lower_stars" and rpls is not None:
+        return dict(rpls)
     if dom in ("process_lower_stars", "compact"):
         return dict(rgrad)
     return {"bound": "hbm", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s",
@@ -423,7 +469,8 @@ def run_ours(args):
     src = "measured" if peaks else "fallback"
     rgrad = roofline_gradient(n, s_in, stats, kavg, hbm, src)
     rcls = roofline_classify(n, s_in, kavg, hbm, src)
-    roofline = roofline_dominant(dom, kavg, rgrad, rcls, hbm, src)
+    rpls = roofline_pls(n, stats, kavg)
+    roofline = roofline_dominant(dom, kavg, rgrad, rcls, hbm, src, rpls)
     serving = None
     if not args.no_serve:
         try:
@@ -445,6 +492,7 @@ def run_ours(args):
         "roofline": roofline,
         "roofline_gradient": rgrad,
         "roofline_classify": rcls,
+        "roofline_pls": rpls,
         "dominant_kernel": {"name": dom, "ms": kavg[dom]},
         "kernel_ms": kavg,
         "stage_ms": stage,

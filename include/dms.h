@@ -72,6 +72,11 @@ typedef struct {
                              expanded only as far as its current pivot,
                              between rounds of the reduction (Alg. 3's
                              interleaving); all modes give the same pairs    */
+    int generators;       /* 1: also compute a persistent 1-cycle generator
+                             of every D1 pair (Sec. 8; dms_fetch_generators).
+                             Single grids of fewer than 2^31 / 7 vertices,
+                             with d1_mode 0 or 1 (the traced reduction runs
+                             in rounds); 0: not computed (the default)       */
 } dms_options;
 
 /* One persistence pair (or infinite class) of the result.
@@ -167,6 +172,20 @@ dms_status dms_get_counts(dms_grid grid, int64_t pairs[3], int64_t essential[4])
  * copy; the result is already complete when dms_compute_diagram returns). */
 dms_status dms_fetch_pairs(dms_grid grid, int dim, dms_pair *out, int64_t cap,
                            int64_t *written, int out_is_device);
+
+/* Persistent 1-cycle generators of the D1 pairs of the last compute (Sec. 8),
+ * for a handle created with dms_options.generators = 1 (DMS_ERR_STATE
+ * otherwise, or without a result).  out[0..cap) receives int64 records, one
+ * per D1 pair in the order of dms_fetch_pairs(1): the birth edge id, the
+ * death triangle id, k, then the ids of the k edges of the cycle.  The cycle
+ * has the birth edge as its highest edge and differs from the boundary of
+ * the death triangle by a sum of boundaries of triangles before it: it is
+ * the Boundary of Alg. 3 for that pair up to the order of propagation (the
+ * reduction here expands every regular edge of a column, Alg. 3 only those
+ * that become its highest), so a valid generator, not necessarily the same
+ * edges.  *written = the number of int64 words of all records; if cap is
+ * smaller, DMS_ERR_CAPACITY is returned and nothing is copied. */
+dms_status dms_fetch_generators(dms_grid grid, int64_t *out, int64_t cap, int64_t *written);
 
 /* Identifier of the last successful compute of the handle: every
  * successful dms_compute_diagram gives a new value (a counter of the

@@ -49,7 +49,7 @@ class DmsError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("virtual_max", ctypes.c_int), ("max_iters", ctypes.c_int64),
-                ("d1_mode", ctypes.c_int)]
+                ("d1_mode", ctypes.c_int), ("generators", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -84,6 +84,8 @@ def load(build_if_missing: bool = False):
             lib.dms_backward_pairs.restype = ctypes.c_int
             lib.dms_get_result_id.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
             lib.dms_get_result_id.restype = ctypes.c_int
+            lib.dms_fetch_generators.argtypes = [vp, vp, i64, p64]
+            lib.dms_fetch_generators.restype = ctypes.c_int
             lib.dms_grid_reshape.argtypes = [vp, i64, i64, i64]
             lib.dms_grid_reshape.restype = ctypes.c_int
             lib.dms_batch_create.argtypes = [i64, p64, ctypes.c_int, ctypes.POINTER(_Options),
@@ -118,16 +120,18 @@ class Grid:
     """A handle of ``dms_grid``: one grid shape and dtype, reusable across fields.
     ``virtual_max=False`` drops the virtual maximum on the outer boundary
     (App. A): unpaired maxima are then infinite classes of dimension 3,
-    listed at the end of ``fetch(2)``."""
+    listed at the end of ``fetch(2)``.  ``generators=True`` also computes a
+    persistent 1-cycle generator of every D1 pair (``generators()``)."""
 
     def __init__(self, shape_xyz, dtype, max_iters: int = 0, d1_mode: int = 0,
-                 virtual_max: bool = True):
+                 virtual_max: bool = True, generators: bool = False):
         self._lib = load()
         self.shape_xyz = tuple(int(s) for s in shape_xyz)
         self.dtype = np.dtype(dtype)
         if self.dtype not in _DTYPE_CODE:
             raise TypeError(f"unsupported dtype {self.dtype}")
-        opts = _Options(int(bool(virtual_max)), int(max_iters), int(d1_mode))
+        opts = _Options(int(bool(virtual_max)), int(max_iters), int(d1_mode),
+                        int(bool(generators)))
         h = ctypes.c_void_p()
         nx, ny, nz = self.shape_xyz
         _check(self._lib.dms_grid_create(nx, ny, nz, _DTYPE_CODE[self.dtype],
@@ -245,6 +249,24 @@ class Grid:
         b = ctypes.c_int64(0)
         _check(self._lib.dms_get_device_bytes(self._h, ctypes.byref(b)), "dms_get_device_bytes")
         return int(b.value)
+
+    def generators(self) -> dict:
+        """{(birth edge id, death triangle id): array of the cycle's edge ids}
+        for the D1 pairs of the last compute (a grid made with
+        ``generators=True``; Sec. 8)."""
+        w = ctypes.c_int64(0)
+        st = self._lib.dms_fetch_generators(self._h, None, 0, ctypes.byref(w))
+        if st not in (0, 7):
+            _check(st, "dms_fetch_generators")
+        buf = np.zeros(max(w.value, 1), np.int64)
+        _check(self._lib.dms_fetch_generators(self._h, buf.ctypes.data, len(buf),
+                                              ctypes.byref(w)), "dms_fetch_generators")
+        out, i, flat = {}, 0, buf[: w.value]
+        while i < len(flat):
+            k = int(flat[i + 2])
+            out[(int(flat[i]), int(flat[i + 1]))] = flat[i + 3:i + 3 + k].copy()
+            i += 3 + k
+        return out
 
     def result_id(self) -> int:
         """Identifier of the last successful compute (new for every compute)."""

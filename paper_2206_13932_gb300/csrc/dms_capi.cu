@@ -79,6 +79,11 @@ dms_status dms_fetch_pairs(dms_grid grid, int dim, dms_pair *out, int64_t cap, i
     return grid->p.fetch(dim, out, cap, written, out_is_device);
 }
 
+dms_status dms_fetch_generators(dms_grid grid, int64_t *out, int64_t cap, int64_t *written) {
+    if (!grid) return DMS_ERR_INVALID_ARG;
+    return grid->p.fetch_generators(out, cap, written);
+}
+
 dms_status dms_get_result_id(dms_grid grid, uint64_t *result_id) {
     if (!grid || !result_id) return DMS_ERR_INVALID_ARG;
     if (!grid->p.has_result) return DMS_ERR_STATE;

@@ -1320,6 +1320,7 @@ struct TraceCtx {
     bool dense;        // every record was computed before the walks: nothing
                        // writes flags or records meanwhile, so they may be
                        // cached in L1
+    bool gens;         // generator mode: compressed edges kept as passive entries
 };
 
 __device__ __forceinline__ uint32_t hash64(unsigned long long k) {
@@ -1388,7 +1389,10 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
             G.w[2 * k + 1] = v.y;
         }
     }
-    if ((fy & 0xF) == m) return;
+    // the head of y's vertex->edge vector: compressed away (Sec. 1.1 / 5), or
+    // a passive entry in the generator mode
+    const bool head = (fy & 0xF) == m;
+    if (head && !c.gens) return;
     unsigned long long key = (((unsigned long long)y << 4) | (unsigned)m) + 1;
     uint32_t hpos = hash64(key) & c.hashmask;
     HashEnt *slot = nullptr;
@@ -1399,9 +1403,23 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
     }
     if (!slot || c.used * 4 >= (c.hashmask + 1) * 3) { c.overflow = true; return; }
     uint32_t info;
-    if ((fy & kFlagCritical) && (cw >> (32 + m) & 1)) {   // a critical edge
+    const bool crit = (fy & kFlagCritical) && (cw >> (32 + m) & 1);
+    if (head || (crit && !(cw >> (48 + m) & 1))) {
+        // a head, or a critical edge paired in D0 (dropped unless generator mode
+        // -- heads returned above then): a passive entry -(edge id + 1)
+        if (!c.gens) return;
+        if (c.rn >= c.rcap) { c.overflow = true; return; }
+        c.rows[c.rn] = (int32_t)(-1 - edge_id(S, g, y, m));
+        c.rslot[c.rn] = (int32_t)(slot - c.hash);
+        c.rn++;
+        slot->key = key;
+        slot->gen = c.gen;
+        slot->info = hinfo((uint32_t)(c.rn - 1), 0, kKindRow, 1);
+        c.used++;
+        return;
+    }
+    if (crit) {                                            // a row
         {
-            if (!(cw >> (48 + m) & 1)) return;  // paired in D0: dropped
             // its C1 index: the vertex's first, plus its critical edges of lower
             // rank (the G order of edges of one lower star)
             const int rm = grad_rank(G, m);
@@ -1490,12 +1508,13 @@ __global__ void __launch_bounds__(256, 4)
                int64_t ntodo, HeapEnt *heap_all, HashEnt *hash_all, int32_t *rows_all, int hcap,
                int hashcap, int rcap, int32_t gen_base, int32_t *pool, int64_t pool_cap,
                int64_t *col_start, int32_t *col_len, uint8_t *overflow,
-               unsigned long long *next_col, int dense, DevStatus *st) {
+               unsigned long long *next_col, int dense, int gens, DevStatus *st) {
     const StarTables &S = g_star;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     TraceCtx c;
     c.dense = dense != 0;
+    c.gens = gens != 0;
     c.heap = heap_all + tid * hcap;
     c.hash = hash_all + tid * hashcap;
     c.rows = rows_all + tid * 2 * rcap;
@@ -1600,6 +1619,14 @@ __global__ void __launch_bounds__(256, 4)
 // owner of a row is always a column whose pivot is that row (the CAS
 // "temporary pairs" of Sec. 7.2, made round-synchronous).
 
+// Column lists are decreasing int32.  Rows (C1 indices) are >= 0; in the
+// generator mode a column also carries passive entries, -(edge id + 1), for
+// the edges the Morse boundary compresses away (heads of vertex->edge vectors
+// and critical edges paired in D0): they sort after every row, are added mod
+// 2 like rows and are never a pivot.  A column has a pivot iff its first
+// entry is a row.  kListEnd is below every entry.
+constexpr int32_t kListEnd = INT32_MIN;
+
 // Appends v to list[*count] with one atomic per warp (all active lanes call).
 __device__ __forceinline__ void warp_append(bool take, int32_t v, int32_t *list,
                                             unsigned long long *count) {
@@ -1624,8 +1651,9 @@ __global__ void k_red_claim(const int32_t *__restrict__ active, int64_t nactive,
     int32_t old = 0;
     if (q < nactive) {
         int32_t cj = active[q];
-        if (len[cj] > 0) {
-            old = atomicMin(&owner[pool[start[cj]]], cj);
+        const int32_t piv = len[cj] > 0 ? pool[start[cj]] : -1;
+        if (piv >= 0) {
+            old = atomicMin(&owner[piv], cj);
             take = old != kNoOwner && old > cj;
         }
     }
@@ -1653,7 +1681,7 @@ __global__ void k_red_publish(const int32_t *__restrict__ active, int64_t nactiv
     if (l <= 0) return;
     const long long s0 = start[cj];
     const int32_t r = pool[s0];
-    if (owner[r] == cj) rowcol[r] = RowCol{s0, l, cj};
+    if (r >= 0 && owner[r] == cj) rowcol[r] = RowCol{s0, l, cj};
 }
 
 // Every non-zero column that owns its pivot publishes it (after the pool moved).
@@ -1665,7 +1693,7 @@ __global__ void k_red_publish_all(int64_t ncol, const int64_t *__restrict__ star
     if (c >= ncol || len[c] <= 0) return;
     const long long s0 = start[c];
     const int32_t r = pool[s0];
-    if (owner[r] == (int32_t)c) rowcol[r] = RowCol{s0, len[c], (int32_t)c};
+    if (r >= 0 && owner[r] == (int32_t)c) rowcol[r] = RowCol{s0, len[c], (int32_t)c};
 }
 
 // Merge path split of two decreasing lists: how many of the first d
@@ -1696,7 +1724,7 @@ __device__ int warp_symdiff(const int32_t *A, int la, const int32_t *B, int lb, 
     {
         int i = i0, j = j0;
         while (i < i1 || j < j1) {
-            int32_t x = i < i1 ? A[i] : -1, y = j < j1 ? B[j] : -1;
+            int32_t x = i < i1 ? A[i] : kListEnd, y = j < j1 ? B[j] : kListEnd;
             if (x > y) { cnt++; i++; }
             else if (y > x) { cnt++; j++; }
             else { i++; j++; }
@@ -1711,7 +1739,7 @@ __device__ int warp_symdiff(const int32_t *A, int la, const int32_t *B, int lb, 
     int o = inc - cnt;
     int i = i0, j = j0;
     while (i < i1 || j < j1) {
-        int32_t x = i < i1 ? A[i] : -1, y = j < j1 ? B[j] : -1;
+        int32_t x = i < i1 ? A[i] : kListEnd, y = j < j1 ? B[j] : kListEnd;
         if (x > y) { out[o++] = x; i++; }
         else if (y > x) { out[o++] = y; j++; }
         else { i++; j++; }                      // 1 + 1 = 0 (mod 2)
@@ -1759,7 +1787,9 @@ __global__ void __launch_bounds__(256)
         bool changed = false;
         unsigned chain = 0;
         for (int it = 0; la > 0 && it < (1 << 24); it++) {
-            const RowCol rc = rowcol[resident ? acc[cur][0] : pool[sa]];
+            const int32_t head = resident ? acc[cur][0] : pool[sa];
+            if (head < 0) break;                 // no row left: no pivot
+            const RowCol rc = rowcol[head];
             const int32_t k = rc.col;
             if (k == cj || k == kNoOwner || k > cj) break;
             const int lb = rc.len;
@@ -1805,10 +1835,11 @@ __global__ void __launch_bounds__(256)
         }
         adds += chain;
         longest = max(longest, chain);
+        __syncwarp();
         if (changed && lane == 0) {
             start[cj] = sa;
             len[cj] = la;
-            if (la > 0) next[atomicAdd((unsigned long long *)&st->misc[1], 1ull)] = cj;
+            if (la > 0 && pool[sa] >= 0) next[atomicAdd((unsigned long long *)&st->misc[1], 1ull)] = cj;
         }
         __syncwarp();
     }
@@ -1841,7 +1872,7 @@ __device__ int block_symdiff(const int32_t *A, int la, const int32_t *B, int lb,
     {
         int i = i0, j = j0;
         while (i < i1 || j < j1) {
-            int32_t x = i < i1 ? A[i] : -1, y = j < j1 ? B[j] : -1;
+            int32_t x = i < i1 ? A[i] : kListEnd, y = j < j1 ? B[j] : kListEnd;
             if (x > y) { cnt++; i++; }
             else if (y > x) { cnt++; j++; }
             else { i++; j++; }
@@ -1861,7 +1892,7 @@ __device__ int block_symdiff(const int32_t *A, int la, const int32_t *B, int lb,
     int o = pre + inc - cnt;
     int i = i0, j = j0;
     while (i < i1 || j < j1) {
-        int32_t x = i < i1 ? A[i] : -1, y = j < j1 ? B[j] : -1;
+        int32_t x = i < i1 ? A[i] : kListEnd, y = j < j1 ? B[j] : kListEnd;
         if (x > y) { out[o++] = x; i++; }
         else if (y > x) { out[o++] = y; j++; }
         else { i++; j++; }
@@ -1917,7 +1948,10 @@ __global__ void __launch_bounds__(kRedBlock)
     // thread 0 keeps the owner record of the next pivot; it is loaded for the
     // predicted pivot before each merge, so its latency overlaps the merge
     RowCol pre{0, 0, kNoOwner};
-    if (threadIdx.x == 0 && la > 0) pre = rowcol[resident ? acc[0][0] : pool[sa]];
+    if (threadIdx.x == 0 && la > 0) {
+        const int32_t head = resident ? acc[0][0] : pool[sa];
+        if (head >= 0) pre = rowcol[head];
+    }
     for (int it = 0; la > 0 && it < (1 << 24); it++) {
         if (threadIdx.x == 0) s_rc = pre;
         __syncthreads();
@@ -1936,9 +1970,9 @@ __global__ void __launch_bounds__(kRedBlock)
             // cancelling tops that the lists do not share
             const int32_t *A = resident ? acc[cur] : pool + sa;
             int i = 1, j = 1;
-            int32_t nt = -1;
+            int32_t nt = kListEnd;
             while (i < la || j < lb) {
-                const int32_t x = i < la ? A[i] : -1, y = j < lb ? B[j] : -1;
+                const int32_t x = i < la ? A[i] : kListEnd, y = j < lb ? B[j] : kListEnd;
                 if (x != y) { nt = x > y ? x : y; break; }
                 i++; j++;
             }
@@ -1981,11 +2015,12 @@ __global__ void __launch_bounds__(kRedBlock)
             sa = (int64_t)pos;
         }
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         if (changed) {
             start[cj] = sa;
             len[cj] = la;
-            if (la > 0) next[atomicAdd((unsigned long long *)&st->misc[1], 1ull)] = cj;
+            if (la > 0 && pool[sa] >= 0) next[atomicAdd((unsigned long long *)&st->misc[1], 1ull)] = cj;
         }
         if (chain) {
             atomicAdd((unsigned long long *)&st->misc[2], (unsigned long long)chain);
@@ -2052,7 +2087,7 @@ __device__ int block_symdiff_g(const int32_t *A, int la, const int32_t *B, int l
     {
         int i = i0, j = j0;
         while (i < i1 || j < j1) {
-            int32_t x = i < i1 ? ld_list<AG>(A + i) : -1, y = j < j1 ? ld_list<BG>(B + j) : -1;
+            int32_t x = i < i1 ? ld_list<AG>(A + i) : kListEnd, y = j < j1 ? ld_list<BG>(B + j) : kListEnd;
             if (x > y) { cnt++; i++; }
             else if (y > x) { cnt++; j++; }
             else { i++; j++; }
@@ -2071,7 +2106,7 @@ __device__ int block_symdiff_g(const int32_t *A, int la, const int32_t *B, int l
     int o = pre + inc - cnt;
     int i = i0, j = j0;
     while (i < i1 || j < j1) {
-        int32_t x = i < i1 ? ld_list<AG>(A + i) : -1, y = j < j1 ? ld_list<BG>(B + j) : -1;
+        int32_t x = i < i1 ? ld_list<AG>(A + i) : kListEnd, y = j < j1 ? ld_list<BG>(B + j) : kListEnd;
         if (x > y) { out[o++] = x; i++; }
         else if (y > x) { out[o++] = y; j++; }
         else { i++; j++; }
@@ -2356,6 +2391,7 @@ __global__ void k_d1_result_homology(int64_t ncols, const int64_t *__restrict__ 
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
     int32_t r = len[c] > 0 ? pool[start[c]] : -1;
+    if (r < 0) r = -1;                  // no row: no pivot (passive entries only)
     d1_row[c] = r;
     if (r >= 0) row_paired[r] = 1;
 }
@@ -2448,6 +2484,7 @@ struct LazyCtx {
     bool dense;        // every record was computed before the walks: nothing
                        // writes flags or records meanwhile, so they may be
                        // cached in L1
+    bool gens;         // generator mode: compressed edges kept as passive entries
 };
 
 __device__ __forceinline__ HashEnt *lz_find(LazyCtx &c, unsigned long long key) {
@@ -3842,7 +3879,7 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
                               ? (int64_t)P.tune[DMS_TUNE_RED_BLOCK_BELOW]
                               : std::max<int64_t>(4096, ncol / 1600);
     for (int64_t r = 0; r < limit; r++, stamp++) {
-        if (nactive <= below && P.tune[DMS_TUNE_RED_ASYNC]) {
+        if (nactive <= below && P.tune[DMS_TUNE_RED_ASYNC] && !P.generators) {
             // the tail: one asynchronous pass instead of rounds
             dms_status s = reduce_tail_async(c, ncol, &nactive, pool_cap);
             P.rounds_d1 = r + 1;
@@ -4367,6 +4404,69 @@ dms_status launch_pls(Ctx &c, const T *values, const Geo<B> &geo, const int32_t 
     return DMS_OK;
 }
 
+// ------------------------------------------ generators of the D1 pairs
+//
+// In the generator mode each traced column also carries, as passive entries,
+// the edges the Morse boundary compresses away, so its list is the full
+// simplicial boundary of the 2-chain it swept: the 2-saddle and the
+// triangles of its descending paths.  Additions keep that (a sum of such
+// boundaries), so when the reduction ends the list of a paired column is a
+// 1-cycle homologous to the boundary of its 2-saddle among the simplices
+// before it (every swept triangle and every column added is earlier), with
+// no triangle-paired edge left, and its highest edge is its pivot: the
+// highest edge of a 1-cycle is a positive edge, and the rows are the
+// positive edges left (Sec. 8's generator, Boundary(sigma_j)).
+//
+// Records per D1 pair, in column order (the order of the D1 pairs): birth
+// edge id, death triangle id, k, then the k edge ids of the cycle.
+__global__ void k_gen_count(int64_t ncols, const int32_t *__restrict__ d1_row,
+                            const int32_t *__restrict__ len, int32_t *cnt) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncols) cnt[c] = d1_row[c] >= 0 ? 3 + len[c] : 0;
+}
+
+__global__ void k_gen_write(int64_t ncols, const int32_t *__restrict__ d1_row,
+                            const int64_t *__restrict__ start, const int32_t *__restrict__ len,
+                            const int32_t *__restrict__ pool, const int32_t *__restrict__ pos,
+                            const int32_t *__restrict__ colmap, const int32_t *__restrict__ v1,
+                            const uint8_t *__restrict__ l1, const int32_t *__restrict__ v2,
+                            const uint8_t *__restrict__ l2, GridParams g, int64_t *out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols || d1_row[c] < 0) return;
+    const StarTables &S = g_star;
+    int64_t o = pos[c];
+    const int32_t r = d1_row[c], j2 = colmap[c];
+    out[o++] = edge_id(S, g, v1[r], l1[r]);
+    out[o++] = tri_id(S, g, v2[j2], l2[j2]);
+    const int L = len[c];
+    out[o++] = L;
+    const int32_t *e = pool + start[c];
+    for (int k = 0; k < L; k++) {
+        const int32_t x = e[k];
+        out[o++] = x >= 0 ? edge_id(S, g, v1[x], l1[x]) : -1 - (int64_t)x;
+    }
+}
+
+dms_status generator_records(Ctx &c, int64_t ncols) {
+    Pipeline &P = c.P;
+    DMS_ALLOC(P.flag_a, 4 * ncols + 4);
+    DMS_ALLOC(P.flag_b, 4 * ncols + 4);
+    int32_t *cnt = P.flag_a.as<int32_t>(), *pos = P.flag_b.as<int32_t>();
+    DMS_LAUNCH(ncols, 256, k_gen_count, ncols, P.d1_row.as<int32_t>(), P.d1_len.as<int32_t>(),
+               cnt);
+    DMS_TRY(scan(c, cnt, pos, ncols, &c.st->total[3]));
+    DMS_TRY(sync_status(c));
+    const int64_t words = c.hst->total[3];
+    if (words >= ((int64_t)1 << 31)) return DMS_ERR_CAPACITY;
+    DMS_ALLOC(P.gen_out, 8 * words + 8);
+    DMS_LAUNCH(ncols, 128, k_gen_write, ncols, P.d1_row.as<int32_t>(), P.d1_start.as<int64_t>(),
+               P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(), pos, P.d1_colmap.as<int32_t>(),
+               P.c_vert[1].as<int32_t>(), P.c_loc[1].as<uint8_t>(), P.c_vert[2].as<int32_t>(),
+               P.c_loc[2].as<uint8_t>(), c.g, P.gen_out.as<int64_t>());
+    P.gen_words = words;
+    return DMS_OK;
+}
+
 // D2's ascending walks (Sec. 5.2) on the stream of c: every critical triangle
 // ascends on both sides to the maxima (or the outside node) it links; the
 // arcs go to P.arc2_a / P.arc2_b.  The walks of a warp start at nearby
@@ -4595,8 +4695,9 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
     // fields) have long descending walls that the lazy columns expand only
     // as far as their pivots; dense ones (noisy fields) have short traces and
     // long chains of additions that the traced 4-byte columns serve better
-    const int mode = P.d1_mode != 0 ? P.d1_mode
-                                    : (ncols * P.tune[DMS_TUNE_LAZY_DENSITY] < n ? 3 : 1);
+    const int mode = P.generators ? 1
+                     : P.d1_mode != 0 ? P.d1_mode
+                                      : (ncols * P.tune[DMS_TUNE_LAZY_DENSITY] < n ? 3 : 1);
     P.d1_mode_used = mode;
     if (ncols > 0 && mode == 3) {
         DMS_TRY((reduce_lazy<T, B>(c, values, ncols, n1, is_row)));
@@ -4633,7 +4734,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
             P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
             P.d1_colmap.as<int32_t>(), corder, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,
             P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
-            ovf, &c.st->trace_next, P.dense_grad ? 1 : 0, c.st);
+            ovf, &c.st->trace_next, P.dense_grad ? 1 : 0, P.generators, c.st);
         c.launches++;
         DMS_CUDA(cudaGetLastError());
         // columns whose trace outgrew the scratch run again with 16x more; the
@@ -4676,7 +4777,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
                 P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), todo, ntodo, heap, hash,
                 rows, hcap, hashcap, rcap, gen, P.d1_pool.as<int32_t>(), pool_cap,
                 P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), ovf, &c.st->trace_next,
-                P.dense_grad ? 1 : 0, c.st);
+                P.dense_grad ? 1 : 0, P.generators, c.st);
             c.launches++;
             DMS_CUDA(cudaGetLastError());
             gen += (int32_t)ncols;
@@ -4695,6 +4796,9 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
         KEV(19);
         KEV(20);
         DMS_TRY(reduce_d1(c, ncols, n1, is_row));
+        if constexpr (!B) {
+            if (P.generators) DMS_TRY(generator_records(c, ncols));
+        }
         KEV(21);
     }
     cudaEventRecord(ev[6], c.s);
@@ -4856,6 +4960,12 @@ dms_status Pipeline::init(int64_t nx_, int64_t ny_, int64_t nz_, dms_dtype dt,
     if (dt != DMS_U16 && dt != DMS_F32 && dt != DMS_F64) return DMS_ERR_INVALID_ARG;
     if (o && o->virtual_max != 0 && o->virtual_max != 1) return DMS_ERR_INVALID_ARG;
     if (o && o->max_iters < 0) return DMS_ERR_INVALID_ARG;
+    if (o && (o->generators != 0 && o->generators != 1)) return DMS_ERR_INVALID_ARG;
+    // generators: the traced reduction (mode 0 or 1); passive entries hold
+    // edge ids in int32
+    if (o && o->generators &&
+        (o->d1_mode > 1 || 7 * nx_ * ny_ * nz_ >= ((int64_t)1 << 31)))
+        return DMS_ERR_INVALID_ARG;
     if (o && (o->d1_mode < 0 || o->d1_mode > 3)) return DMS_ERR_INVALID_ARG;
     nx = nx_; ny = ny_; nz = nz_; n = nx * ny * nz; dtype = dt;
     return init_common(o);
@@ -4893,8 +5003,8 @@ dms_status Pipeline::init_batch(int64_t nf_, const int64_t *shp, dms_dtype dt,
     if (dt != DMS_U16 && dt != DMS_F32 && dt != DMS_F64) return DMS_ERR_INVALID_ARG;
     if (!batch_shapes_ok(nf_, shp)) return DMS_ERR_INVALID_ARG;   // before any CUDA call
     if (o && ((o->virtual_max != 0 && o->virtual_max != 1) || o->max_iters < 0 ||
-              o->d1_mode < 0 || o->d1_mode > 3))
-        return DMS_ERR_INVALID_ARG;
+              o->d1_mode < 0 || o->d1_mode > 3 || o->generators != 0))
+        return DMS_ERR_INVALID_ARG;   // generators: single grids only
     batch = true;
     dtype = dt;
     dms_status s = init_common(o);
@@ -4945,6 +5055,7 @@ dms_status Pipeline::set_batch(int64_t nf_, const int64_t *shp) {
 
 dms_status Pipeline::init_common(const dms_options *o) {
     virtual_max = o ? o->virtual_max : 1;
+    generators = o ? o->generators : 0;
     max_iters = o ? o->max_iters : 0;
     d1_mode = o ? o->d1_mode : 0;
     if (cudaGetDevice(&device) != cudaSuccess) return DMS_ERR_CUDA;
@@ -4976,6 +5087,7 @@ dms_status Pipeline::reshape(int64_t nx_, int64_t ny_, int64_t nz_) {
     if (nx_ * ny_ >= ((int64_t)1 << 31) || nx_ * ny_ * nz_ >= ((int64_t)1 << 31))
         return DMS_ERR_INVALID_ARG;
     const int64_t n2 = nx_ * ny_ * nz_;
+    if (generators && 7 * n2 >= ((int64_t)1 << 31)) return DMS_ERR_INVALID_ARG;
     if (!flags.ensure(n2) || !vrank.ensure(4 * n2) || !grad.ensure(sizeof(GradRec) * n2))
         return DMS_ERR_OOM;
     nx = nx_; ny = ny_; nz = nz_; n = n2;
@@ -4991,7 +5103,7 @@ std::vector<DevBuf *> Pipeline::buffers() {
                      &dc_keys,    &dc_par,   &dc_lab,    &bv_node,   &bv_msf,    &bv_arcs,
                      &young,     &died,       &rowcol,
                      &flag_a,     &flag_b,   &d1_colmap, &d1_start,  &d1_len,     &d1_owner,
-                     &d1_ovf,     &d1_pool,  &d1_scratch, &d1_todo,  &scan_tmp,   &scan_tmp2, &arc2_a, &arc2_b, &vcrit, &dstat,
+                     &d1_ovf,     &d1_pool,  &d1_scratch, &d1_todo,  &scan_tmp,   &scan_tmp2, &arc2_a, &arc2_b, &vcrit, &gen_out, &dstat,
                      &d1_astamp, &lz_small.buf, &lz_big.buf, &d1_rowcol,
                      &fields_dev, &field_of, &field_off_dev, &fmax_field, &bt_k[0], &bt_k[1],
                      &bt_v[0], &bt_v[1], &bt_h[0], &bt_h[1], &bt_cnt, &out_tmp, &bx_buf[0],
@@ -5026,6 +5138,7 @@ void Pipeline::destroy() {
 
 dms_status Pipeline::compute(const void *values, int on_host, void *stream) {
     has_result = false;
+    gen_words = 0;
     if (!values || (on_host != 0 && on_host != 1)) return DMS_ERR_INVALID_ARG;
     int cur = 0;
     if (cudaGetDevice(&cur) != cudaSuccess) return DMS_ERR_CUDA;
@@ -5105,6 +5218,19 @@ dms_status Pipeline::backward(int dim, uint64_t rid, const double *gbirth, const
     k_scatter_pair_grads<<<blocks_for(total, 256), 256, 0, (cudaStream_t)stream>>>(
         out_pairs[dim].as<dms_pair>(), total, gbirth, gdeath, grad, pofs, vofs, (int)nf);
     return cudaGetLastError() == cudaSuccess ? DMS_OK : DMS_ERR_CUDA;
+}
+
+dms_status Pipeline::fetch_generators(int64_t *out, int64_t cap, int64_t *written) {
+    if (!written) return DMS_ERR_INVALID_ARG;
+    *written = 0;
+    if (!has_result || !generators) return DMS_ERR_STATE;
+    *written = gen_words;
+    if (gen_words > cap) return DMS_ERR_CAPACITY;
+    if (gen_words == 0) return DMS_OK;
+    if (!out) return DMS_ERR_INVALID_ARG;
+    if (cudaMemcpy(out, gen_out.p, 8 * gen_words, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return DMS_ERR_CUDA;
+    return DMS_OK;
 }
 
 dms_status Pipeline::fetch(int dim, dms_pair *out, int64_t cap, int64_t *written,

@@ -34,6 +34,9 @@ struct Pipeline {
     int64_t max_iters = 0;
     int virtual_max = 1;    // 1: the outer boundary is one virtual maximum (Sec. 5.2);
                             // 0: no virtual maximum (App. A)
+    int generators = 0;     // 1: a 1-cycle generator per D1 pair (Sec. 8)
+    DevBuf gen_out;         // the generator records of the last compute (int64)
+    int64_t gen_words = 0;
     int d1_mode = 0;        // 0: by column density, 1: reduce columns (homology),
                             // 2: anti-transpose (cohomology), 3: lazy columns
                             // (propagation interleaved with the reduction)
@@ -104,6 +107,7 @@ struct Pipeline {
     dms_status compute(const void *values, int on_host, void *stream);
     dms_status reshape(int64_t nx, int64_t ny, int64_t nz);
     dms_status fetch(int dim, dms_pair *out, int64_t cap, int64_t *written, int out_is_device);
+    dms_status fetch_generators(int64_t *out, int64_t cap, int64_t *written);
     // rows of output list dim: its finite pairs and infinite classes (the D2
     // list also holds the infinite classes of dimension 3)
     int64_t list_rows(int dim) const {

@@ -155,13 +155,23 @@ def test_no_serve_skips_the_section(fake_device):
     assert _run(fake_device, {"no_serve": True})["serving"] is None
 
 
-def test_dominant_gradient_reports_the_stage(fake_device, monkeypatch):
+def test_dominant_pls_reports_the_issue_rate(fake_device, monkeypatch):
     """When ProcessLowerStars takes the most time, the headline roofline is
-    the gradient stage's."""
+    its issue rate (an ALU-bound kernel), with the gradient stage's HBM figure
+    beside it; a stale instruction count is reported as null."""
     def kms(self):
         return {k: (9.0 if k == "process_lower_stars" else 1.0) for k in self.KERNELS}
     import paper_2206_13932_gb300 as dms
     monkeypatch.setattr(dms.Grid, "kernel_ms", kms)
     d = _run(fake_device, {"no_serve": True})
-    assert d["roofline"]["kernel"].startswith("gradient stage")
-    assert d["roofline"] == d["roofline_gradient"]
+    r = d["roofline"]
+    assert r == d["roofline_pls"] and r["bound"] == "alu"
+    assert r["peak"] == pytest.approx(152 * 4 * 2.07)
+    stars = 16 ** 3          # 100 critical vertices of 4096, but a small grid: dense
+    assert r["achieved"] == pytest.approx(
+        fake_device.PLS_ISSUE["warp_inst_per_star"] * stars / 9e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert d["roofline_gradient"]["kernel"].startswith("gradient stage")
+    monkeypatch.setitem(fake_device.PLS_ISSUE, "sources_sha256", "stale")
+    d = _run(fake_device, {"no_serve": True})
+    assert d["roofline"]["achieved"] is None and d["roofline"]["frac"] is None

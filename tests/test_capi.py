@@ -76,6 +76,12 @@ def test_argument_checks_without_gpu():
     assert create(4, 4, 4, opts=dms._Options(2, 0, 0)) == bad    # virtual maximum neither 0 nor 1
     assert create(4, 4, 4, opts=dms._Options(1, -1, 0)) == bad    # negative iteration cap
     assert create(4, 4, 4, opts=dms._Options(1, 0, 4)) == bad    # unknown D1 mode
+    assert create(4, 4, 4, opts=dms._Options(1, 0, 0, 2)) == bad  # generators neither 0 nor 1
+    assert create(4, 4, 4, opts=dms._Options(1, 0, 3, 1)) == bad  # generators need the traced mode
+    assert create(1 << 10, 1 << 10, 300, opts=dms._Options(1, 0, 0, 1)) == bad  # 7N >= 2^31
+    shapes = (ctypes.c_int64 * 3)(4, 4, 4)
+    assert lib.dms_batch_create(1, shapes, 1, ctypes.byref(dms._Options(1, 0, 0, 1)),
+                                ctypes.byref(h)) == bad          # generators: single grids
     assert lib.dms_grid_create(4, 4, 4, 1, None, None) == bad     # no output handle
     assert not h.value
     null = ctypes.c_void_p(0)
@@ -90,6 +96,7 @@ def test_argument_checks_without_gpu():
     assert lib.dms_backward_pairs(null, 0, 0, null, null, null, null) == bad
     r = ctypes.c_uint64(0)
     assert lib.dms_get_result_id(null, ctypes.byref(r)) == bad
+    assert lib.dms_fetch_generators(null, null, 0, ctypes.byref(w)) == bad
     assert lib.dms_get_stage_ms(null, (ctypes.c_float * 8)()) == bad
     assert lib.dms_get_kernel_ms(null, (ctypes.c_float * 12)()) == bad
     assert lib.dms_get_stats(null, (ctypes.c_int64 * 16)()) == bad
