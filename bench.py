@@ -54,12 +54,15 @@ SERVE_BATCH = 16            # most requests one batched pass takes
 # _CLASSIFY_SPANS); otherwise reported as null.
 CLASSIFY_TRAFFIC = {"sources_sha256": "eb26737328563b5ce987eccc9b9472e26eb7afd8df787c6404174cb78de85218",
                     "bytes_per_launch": 268718336 + 117972992}
-# Warp instructions issued per star by the shape-sorted ProcessLowerStars
-# kernel, from one ncu capture (profiles/pls_sorted_noise192.md: 4 876 004 637
-# instructions for 7 077 888 stars of 192^3 noise, 57 % of them PL-critical,
-# like this workload), valid only for the code it was taken on (_PLS_SPANS).
-PLS_ISSUE = {"sources_sha256": "0e1541eb610add831382a7de687b3c1a8905858cc27a6209d40fc0429736d1db",
-             "warp_inst_per_star": 4876004637 / 7077888, "simt_lanes": 12.96}
+# Warp instructions issued per star by ProcessLowerStars' two kernels
+# (k_pls_keys + k_pls_run), from one ncu capture (profiles/pls_two_pass_noise192.md:
+# 636 403 702 + 2 582 852 077 instructions for 7 077 888 stars of 192^3 noise,
+# 57 % of them PL-critical, like this workload), valid only for the code it
+# was taken on (_PLS_SPANS).  The radix sort between the two passes is not
+# counted, so the achieved rate is a slight underestimate.
+PLS_ISSUE = {"sources_sha256": "7f19cdca98c3ab36bf1ab919a8cc52583bf891635271fb5dff14897ce0d2009e",
+             "warp_inst_per_star": (636403702 + 2582852077) / 7077888, "simt_lanes": 17.67,
+             "alu_pipe_pct_run": 86.1}
 
 
 def _code_only(src: str) -> str:
@@ -95,11 +98,12 @@ _CLASSIFY_SPANS = (("", "stage 2: stable LSD radix sort"), ("struct ClsTiling", 
                    ("k_classify2<T><<<", ");"))
 
 
-# The code behind the ProcessLowerStars kernel of the bench (shape-sorted
-# blocks): the shape-sorted kernel and its launch; dms_common.cuh (star view,
-# ProcessLowerStars) counts whole.
-_PLS_SPANS = (("template <typename T, bool B, int NT>\n__global__ void __launch_bounds__(NT)\n"
-               "    k_pls_sorted(", "// The critical cells of the lower star of each sorted"),
+# The code behind ProcessLowerStars in the bench (two passes around a sort
+# of the stars by shape): both kernels, the radix sort between them, and the
+# launch; dms_common.cuh (star view, ProcessLowerStars) counts whole.
+_PLS_SPANS = (("__global__ void __launch_bounds__(256)\n    k_pls_keys(",
+               "// The critical cells of the lower star of each sorted"),
+              ("dms_status radix_u32(Ctx &c", "return DMS_OK;\n}"),
               ("dms_status launch_pls(Ctx &c", "return DMS_OK;\n}"))
 
 
@@ -324,7 +328,7 @@ def roofline_gradient(n, s_in, stats, kavg, hbm, src):
     nbytes = n * s_in + 8 * ncrit
     ms = kavg["classify"] + kavg["compact"] + kavg["process_lower_stars"]
     gbs = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else None
-    return {"bound": "hbm", "kernel": "gradient stage (k_classify2, k_compact2, k_pls_sorted)",
+    return {"bound": "hbm", "kernel": "gradient stage (k_classify2, k_compact2, k_pls_keys, k_pls_run)",
             "achieved": gbs, "peak": hbm, "unit": "GB/s",
             "frac": gbs / hbm if gbs is not None else None, "traffic": None,
             "algorithmic_bytes_per_launch": nbytes, "ms": ms, "peak_source": src,
@@ -357,12 +361,14 @@ def roofline_pls(n, stats, kavg):
     ms = kavg["process_lower_stars"]
     peak = SMS * SMSPS * SM_MAX_MHZ * 1e6 / 1e9
     ach = PLS_ISSUE["warp_inst_per_star"] * stars / (ms * 1e-3) / 1e9 if ok and ms > 0 else None
-    return {"bound": "alu", "kernel": "k_pls_sorted (ProcessLowerStars, shape-sorted blocks)",
+    return {"bound": "alu", "kernel": "k_pls_keys + k_pls_run (ProcessLowerStars, stars sorted by shape)",
             "achieved": ach, "peak": peak, "unit": "G warp instructions/s",
             "frac": ach / peak if ach is not None else None, "traffic": None, "ms": ms,
             "stars": stars, "peak_source": "152 SMs x 4 schedulers x 2070 MHz",
-            "note": "issue-bound; about 40 % of the lanes of an issued instruction do work "
-                    f"({PLS_ISSUE['simt_lanes']} of 32, divergent star shapes)"}
+            "note": "issue-bound: the second pass keeps its ALU pipe "
+                    f"{PLS_ISSUE['alu_pipe_pct_run']} % busy (ncu); about "
+                    f"{PLS_ISSUE['simt_lanes']} of the 32 lanes of an issued instruction do work "
+                    "(the order of the lower links differs within a warp)"}
 
 
 def roofline_dominant(dom, kavg, rgrad, rcls, hbm, src, rpls=None):

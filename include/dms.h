@@ -303,10 +303,10 @@ dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, 
  *                             asynchronous pass (compare-and-swap ownership
  *                             and a device work queue); 0: in rounds
  *                             (default 1)
- *   DMS_TUNE_PLS_SORT         ProcessLowerStars on blocks of 1024 stars sorted
- *                             by shape: 0 never, 1 when more than a quarter
- *                             of the vertices are critical (default), 2
- *                             always
+ *   DMS_TUNE_PLS_SORT         ProcessLowerStars in two passes with the stars
+ *                             sorted by shape (lower-link mask) in between:
+ *                             0 never, 1 when more than a quarter of the
+ *                             vertices are critical (default), 2 always
  *   DMS_TUNE_D2_BESIDE_D0     1: D2's ascending walks run on a second stream of
  *                             the handle beside D0 (the paper's D0 || D2
  *                             tasks); 0: after D0 on the compute stream

@@ -709,62 +709,49 @@ __global__ void k_pls(const T *__restrict__ values, Geo<B> geo, const int32_t *_
     flags[x] = (uint8_t)(flags[x] | kFlagGradient);
 }
 
-// The same, for fields whose stars vary widely (noise): the work of a lower
-// star grows with its size and shape, so a block first loads the stars of its
-// NT vertices (coalesced), sorts them in shared memory by (number of lower
-// links, lower mask), and each thread then runs ProcessLowerStars on the star
-// at its sorted position, so that the threads of a warp follow similar paths.
-template <typename T, bool B, int NT>
-__global__ void __launch_bounds__(NT)
-    k_pls_sorted(const T *__restrict__ values, Geo<B> geo, const int32_t *__restrict__ list,
-                 int64_t count, uint8_t *flags, GradRec *grad) {
-    __shared__ uint32_t skey[NT];
-    __shared__ uint16_t sidx[NT];
-    __shared__ unsigned long long srank[NT];
-    const int t = threadIdx.x;
-    const StarTables &S = g_star;
-    const int64_t i = (int64_t)blockIdx.x * NT + t;
-    uint32_t key = 0xFFFFFFFFu;
-    if (i < count) {
-        const int64_t x = list ? list[i] : i;
-        const GridParams &g = geo.at(x);
-        StarView sv;
-        load_star(S, g, values, x, sv);
-        unsigned long long rk = 0;
-        for (int n = 0; n < kLinks; n++) rk |= (unsigned long long)(sv.rank[n] & 15) << (4 * n);
-        srank[t] = rk;
-        key = ((uint32_t)__popc(sv.lower) << 14) | sv.lower;
-    }
-    skey[t] = key;
-    sidx[t] = (uint16_t)t;
-    __syncthreads();
-    // bitonic sort of (key, index), ascending
-    for (int k = 2; k <= NT; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const int l = t ^ j;
-            if (l > t) {
-                const bool up = (t & k) == 0;
-                const uint32_t a = skey[t], b = skey[l];
-                if (up ? a > b : a < b) {
-                    skey[t] = b; skey[l] = a;
-                    const uint16_t u = sidx[t]; sidx[t] = sidx[l]; sidx[l] = u;
-                }
-            }
-            __syncthreads();
-        }
-    const uint32_t mykey = skey[t];
-    if (mykey == 0xFFFFFFFFu) return;
-    const int src = sidx[t];
-    const int64_t si = (int64_t)blockIdx.x * NT + src;
-    const int64_t x = list ? list[si] : si;
+// The same in two passes, for fields whose stars vary widely (noise): the
+// work of a lower star depends on its shape (which links are lower) and
+// grows with its size.  The first pass loads each star in id order
+// (coalesced stencils) and keeps its lower mask as a sort key, its position
+// and its link ranks (4 bits a link); the stars are then sorted by mask over
+// the whole grid, and the second pass runs ProcessLowerStars in that order,
+// so the 32 threads of a warp share one shape and only the order of the
+// lower links differs between them.  Each warp and block finishes on its
+// own: no barrier ties a fast star to a slow one.
+template <typename T, bool B>
+__global__ void __launch_bounds__(256)
+    k_pls_keys(const T *__restrict__ values, Geo<B> geo, const int32_t *__restrict__ list,
+               int64_t count, uint32_t *__restrict__ key, int32_t *__restrict__ pos,
+               unsigned long long *__restrict__ ranks, uint8_t *flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t x = list ? list[i] : i;
+    StarView sv;
+    load_star(g_star, geo.at(x), values, x, sv);
+    unsigned long long rk = 0;
+    for (int n = 0; n < kLinks; n++) rk |= (unsigned long long)(sv.rank[n] & 15) << (4 * n);
+    ranks[i] = rk;
+    key[i] = sv.lower;
+    pos[i] = (int32_t)i;
+    // the second pass fills the record before any later kernel reads it
+    flags[x] = (uint8_t)(flags[x] | kFlagGradient);
+}
+
+__global__ void k_pls_run(const int32_t *__restrict__ list, const uint32_t *__restrict__ key,
+                          const int32_t *__restrict__ pos,
+                          const unsigned long long *__restrict__ ranks, int64_t count,
+                          GradRec *grad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int32_t j = pos[i];
+    const int64_t x = list ? list[j] : j;
+    const unsigned long long rk = ranks[j];
     uint8_t rank[kLinks];
-    const unsigned long long rk = srank[src];
     for (int n = 0; n < kLinks; n++) rank[n] = (uint8_t)((rk >> (4 * n)) & 15);
     PLSResult R;
     GradRec G;
-    pls(S, (uint16_t)(mykey & kAllLinks), rank, R, &G);
+    pls(g_star, (uint16_t)(key[i] & kAllLinks), rank, R, &G);
     grad[x] = G;
-    flags[x] = (uint8_t)(flags[x] | kFlagGradient);
 }
 
 // The critical cells of the lower star of each sorted critical vertex, read
@@ -4345,6 +4332,28 @@ dms_status group_by_field(Ctx &c, int d, int64_t rows) {
     return DMS_OK;
 }
 
+// Stable LSD radix sort of n (32-bit key, int32 value) pairs on the low
+// `bits` bits of the keys, 8 bits a pass, with P.ord_h as histograms; the
+// sorted pairs end in (kin, vin) (the pointers swap with each pass).
+dms_status radix_u32(Ctx &c, uint32_t *&kin, int32_t *&vin, uint32_t *&kout, int32_t *&vout,
+                     int64_t n, int bits, int rtiles) {
+    Pipeline &P = c.P;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_rs_hist<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(kin, n, shift, P.ord_h[0].as<int32_t>(),
+                                                           rtiles);
+        c.launches++;
+        DMS_TRY(scan(c, P.ord_h[0].as<int32_t>(), P.ord_h[1].as<int32_t>(), (int64_t)256 * rtiles,
+                     &c.st->total[1]));
+        k_rs_scatter<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(kin, vin, kout, vout, n, shift,
+                                                              P.ord_h[1].as<int32_t>(), rtiles);
+        c.launches++;
+        DMS_CUDA(cudaGetLastError());
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    return DMS_OK;
+}
+
 // A permutation of n items (item i at vertex vert[idx[i]], or vert[i]) into
 // vertex-id order, by a stable LSD radix sort; *perm points into scratch
 // buffer `slot` (0 or 1) and stays valid until the next call with that slot.
@@ -4366,25 +4375,13 @@ dms_status order_by_vertex(Ctx &c, const int32_t *vert, const int32_t *idx, int6
     DMS_LAUNCH(n, 256, k_gather_vid, vert, idx, n, kin, vin);
     int bits = 0;
     while (bits < 32 && (((int64_t)1 << bits) < P.n)) bits++;
-    for (int shift = 0; shift < bits; shift += 8) {
-        k_rs_hist<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(kin, n, shift, P.ord_h[0].as<int32_t>(),
-                                                           rtiles);
-        c.launches++;
-        DMS_TRY(scan(c, P.ord_h[0].as<int32_t>(), P.ord_h[1].as<int32_t>(), (int64_t)256 * rtiles,
-                     &c.st->total[1]));
-        k_rs_scatter<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(kin, vin, kout, vout, n, shift,
-                                                              P.ord_h[1].as<int32_t>(), rtiles);
-        c.launches++;
-        DMS_CUDA(cudaGetLastError());
-        std::swap(kin, kout);
-        std::swap(vin, vout);
-    }
+    DMS_TRY(radix_u32(c, kin, vin, kout, vout, n, bits, rtiles));
     *perm = vin;
     return DMS_OK;
 }
 
-// ProcessLowerStars: sorted by star shape in blocks of 1024 when `sorted`,
-// else plain with the tuned block size.
+// ProcessLowerStars with the tuned block size: in id order, or, when
+// `sorted`, in two passes with the stars sorted by shape in between.
 template <typename T, bool B>
 dms_status launch_pls(Ctx &c, const T *values, const Geo<B> &geo, const int32_t *list,
                       int64_t count, bool sorted) {
@@ -4392,13 +4389,31 @@ dms_status launch_pls(Ctx &c, const T *values, const Geo<B> &geo, const int32_t 
     if (count <= 0) return DMS_OK;
     uint8_t *fl = P.flags.as<uint8_t>();
     GradRec *gr = P.grad.as<GradRec>();
-    if (sorted) {
-        k_pls_sorted<T, B, 1024><<<blocks_for(count, 1024), 1024, 0, c.s>>>(values, geo, list, count,
-                                                                        fl, gr);
-    } else {
-        const int nt = P.tune[DMS_TUNE_PLS_BLOCK];
+    const int nt = P.tune[DMS_TUNE_PLS_BLOCK];
+    if (!sorted) {
         k_pls<T, B><<<blocks_for(count, nt), nt, 0, c.s>>>(values, geo, list, count, fl, gr);
+        c.launches++;
+        DMS_CUDA(cudaGetLastError());
+        return DMS_OK;
     }
+    // the vertex-order scratch is free here: the walks that use it come later
+    for (int k = 0; k < 2; k++) {
+        DMS_ALLOC(P.ord_k[k], 4 * count + 4);
+        DMS_ALLOC(P.ord_v[k], 4 * count + 4);
+    }
+    DMS_ALLOC(P.pls_ranks, 8 * count + 8);
+    const int rtiles = (int)((count + kRsTile - 1) / kRsTile);
+    DMS_ALLOC(P.ord_h[0], 4 * (size_t)256 * rtiles);
+    DMS_ALLOC(P.ord_h[1], 4 * (size_t)256 * rtiles);
+    uint32_t *kin = P.ord_k[0].as<uint32_t>(), *kout = P.ord_k[1].as<uint32_t>();
+    int32_t *vin = P.ord_v[0].as<int32_t>(), *vout = P.ord_v[1].as<int32_t>();
+    unsigned long long *rk = P.pls_ranks.as<unsigned long long>();
+    k_pls_keys<T, B><<<blocks_for(count, 256), 256, 0, c.s>>>(values, geo, list, count, kin, vin,
+                                                              rk, fl);
+    c.launches++;
+    DMS_CUDA(cudaGetLastError());
+    DMS_TRY(radix_u32(c, kin, vin, kout, vout, count, kLinks, rtiles));
+    k_pls_run<<<blocks_for(count, nt), nt, 0, c.s>>>(list, kin, vin, rk, count, gr);
     c.launches++;
     DMS_CUDA(cudaGetLastError());
     return DMS_OK;
@@ -5108,7 +5123,8 @@ std::vector<DevBuf *> Pipeline::buffers() {
                      &fields_dev, &field_of, &field_off_dev, &fmax_field, &bt_k[0], &bt_k[1],
                      &bt_v[0], &bt_v[1], &bt_h[0], &bt_h[1], &bt_cnt, &out_tmp, &bx_buf[0],
                      &bx_buf[1], &d1_info, &d1_queue, &d1_aq, &ord_k[0], &ord_k[1], &ord_k[2],
-                     &ord_k[3], &ord_v[0], &ord_v[1], &ord_v[2], &ord_v[3], &ord_h[0], &ord_h[1]};
+                     &ord_k[3], &ord_v[0], &ord_v[1], &ord_v[2], &ord_v[3], &ord_h[0], &ord_h[1],
+                     &pls_ranks};
     for (int d = 0; d < 4; d++)
         for (DevBuf *b : {&cnt[d], &base[d], &c_vert[d], &c_loc[d]}) all.push_back(b);
     for (int d = 0; d < 3; d++)

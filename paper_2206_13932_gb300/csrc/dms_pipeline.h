@@ -62,7 +62,9 @@ struct Pipeline {
     DevBuf d1_colmap, d1_start, d1_len, d1_owner, d1_ovf, d1_pool, d1_scratch, d1_todo;
     DevBuf d1_rowcol;                          // D1: owner of each row with its list
     DevBuf d1_info, d1_queue, d1_aq;           // D1: asynchronous tail (lists, queue)
-    DevBuf ord_k[4], ord_v[4], ord_h[2];       // vertex-id orders of walks (two slots)
+    DevBuf ord_k[4], ord_v[4], ord_h[2];       // vertex-id orders of walks (two slots); slot 0
+                                               // also sorts stars for ProcessLowerStars
+    DevBuf pls_ranks;                          // u64 per sorted star: its link ranks
     DevBuf d1_astamp;                          // lazy D1: last advance per column
     LazyScratch lz_small, lz_big;              // lazy D1: advance scratch
     DevBuf bx_buf[2];                          // lazy D1: block expansion scratch
