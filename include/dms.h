@@ -260,8 +260,7 @@ dms_status dms_get_kernel_ms(dms_grid grid, float ms[12]);
  * DMS_ERR_INVALID_ARG.  All calls share that array: calls that overlap on
  * the GPU (from several streams or threads) race and must be serialised by
  * the caller.  The first call on a device (with that device current) looks
- * up the array's address and uploads the star tables; make that first call
- * before any stream capture.
+ * up the array's address and uploads the star tables.
  *
  * values:       device pointer, nx*ny*nz elements of dtype, x fastest.
  * flags_out:    device pointer, nx*ny*nz bytes: low nibble = link index of

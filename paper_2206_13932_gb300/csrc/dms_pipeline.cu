@@ -4908,7 +4908,7 @@ std::mutex g_static_mutex;
 StaticScratch *g_static_ptr[64] = {nullptr};   // per device, from cudaGetSymbolAddress
 
 // Set-up on first use on a device (that device current): the star tables and
-// the address of the scratch array.  Must run before any stream capture.
+// the address of the scratch array.
 dms_status static_setup(int device, StaticScratch **out) {
     if (device < 0 || device >= 64) return DMS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_static_mutex);
