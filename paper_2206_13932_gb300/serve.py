@@ -185,7 +185,10 @@ class DiagramServer:
                     raise setup_error
                 dt = reqs[0].values.dtype
                 shapes = [(r.values.shape[2], r.values.shape[1], r.values.shape[0]) for r in reqs]
-                kind = "grid" if len(reqs) == 1 else "batch"
+                # with batching on, a slot runs even a lone request as a batch
+                # of one, so it keeps one handle of one kind and never frees
+                # it to switch kinds (a free synchronises the whole device)
+                kind = "batch" if self.max_batch > 1 else "grid"
                 h = None
                 if held is not None and held[0] == kind and held[1] == dt:
                     h = held[2]
