@@ -310,19 +310,12 @@ dms_status dms_classify_static(const void *values, dms_dtype dtype, int64_t nx, 
  *                             the handle beside D0 (the paper's D0 || D2
  *                             tasks); 0: after D0 on the compute stream
  *                             (default 1)
- *   DMS_TUNE_TRACE_SMEM       1: the D1 trace's first pass keeps each
- *                             column's hash and heap in shared memory (64 and
- *                             32 entries a lane); the columns that outgrow it
- *                             are traced again with the global-memory scratch
- *                             (uint16 and float32 values; float64 and the
- *                             generator mode always use the global scratch);
- *                             0: the global-memory scratch only (default 1)
  * dms_set_tuning checks every value and changes nothing when one is out of
  * range (DMS_ERR_INVALID_ARG); count must be DMS_TUNING_COUNT. */
 enum {
     DMS_TUNE_PLS_BLOCK = 0, DMS_TUNE_TRACE_BLOCK, DMS_TUNE_TRACE_PER_SM, DMS_TUNE_TRACE_HEAP,
     DMS_TUNE_RED_BLOCK_BELOW, DMS_TUNE_LAZY_HEAP, DMS_TUNE_LAZY_DENSITY, DMS_TUNE_RED_ASYNC,
-    DMS_TUNE_PLS_SORT, DMS_TUNE_D2_BESIDE_D0, DMS_TUNE_TRACE_SMEM, DMS_TUNING_COUNT
+    DMS_TUNE_PLS_SORT, DMS_TUNE_D2_BESIDE_D0, DMS_TUNING_COUNT
 };
 dms_status dms_set_tuning(dms_grid grid, const int32_t *values, int count);
 dms_status dms_get_tuning(dms_grid grid, int32_t *values, int count);

@@ -28,9 +28,8 @@ import numpy as np
 from . import _check
 
 TUNABLES = ("pls_block", "trace_block", "trace_per_sm", "trace_heap", "red_block_below",
-            "lazy_heap", "lazy_density", "red_async", "pls_sort", "d2_beside_d0",
-            "trace_smem")
-DEFAULT = (128, 128, 2048, 48, -1, 48, 32, 1, 1, 1, 1)
+            "lazy_heap", "lazy_density", "red_async", "pls_sort", "d2_beside_d0")
+DEFAULT = (128, 128, 2048, 48, -1, 48, 32, 1, 1, 1)
 CANDIDATES = {
     "pls_block": (64, 128, 256),
     "trace_block": (64, 128, 256),
@@ -42,7 +41,6 @@ CANDIDATES = {
     "red_async": (0, 1),
     "pls_sort": (0, 1, 2),
     "d2_beside_d0": (0, 1),
-    "trace_smem": (0, 1),
 }
 
 
@@ -71,7 +69,7 @@ def valid(values) -> bool:
             8 <= d["trace_heap"] <= 1024 and d["red_block_below"] >= -1 and
             8 <= d["lazy_heap"] <= 1024 and 1 <= d["lazy_density"] <= 4096 and
             d["red_async"] in (0, 1) and d["pls_sort"] in (0, 1, 2) and
-            d["d2_beside_d0"] in (0, 1) and d["trace_smem"] in (0, 1))
+            d["d2_beside_d0"] in (0, 1))
 
 
 def measure(grid, field, repeats: int = 3) -> float:

@@ -154,7 +154,6 @@ dms_status dms_set_tuning(dms_grid grid, const int32_t *v, int count) {
     if (v[DMS_TUNE_LAZY_DENSITY] < 1 || v[DMS_TUNE_LAZY_DENSITY] > 4096) return DMS_ERR_INVALID_ARG;
     if (v[DMS_TUNE_RED_ASYNC] != 0 && v[DMS_TUNE_RED_ASYNC] != 1) return DMS_ERR_INVALID_ARG;
     if (v[DMS_TUNE_D2_BESIDE_D0] != 0 && v[DMS_TUNE_D2_BESIDE_D0] != 1) return DMS_ERR_INVALID_ARG;
-    if (v[DMS_TUNE_TRACE_SMEM] != 0 && v[DMS_TUNE_TRACE_SMEM] != 1) return DMS_ERR_INVALID_ARG;
     for (int k = 0; k < DMS_TUNING_COUNT; k++) grid->p.tune[k] = v[k];
     return DMS_OK;
 }

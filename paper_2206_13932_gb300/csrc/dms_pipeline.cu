@@ -1611,261 +1611,6 @@ __global__ void __launch_bounds__(256, 4)
     }
 }
 
-// The same trace with each lane's scratch in shared memory, for the columns
-// that fit in it (almost all of them on dense fields): a hash of kSmHash
-// entries and a heap of kSmHeap, entry k of lane l at [k][l], so a lane's
-// random probe hits its own bank.  An edge (y, m) is keyed by its offset
-// from the column's vertex x and its classification order in the lower star
-// of y (unique among the lower edges of y); the heap holds (order key of y,
-// that key), the same topological order as the global-memory trace.  The
-// rows are kept in the hash (C1 index in the info), and the odd ones are
-// gathered when the column is written out, which also clears the lane's
-// table for its next column.  A column that outgrows the scratch (or walks
-// more than 2^27 ids from x) is marked and traced again by k_d1_trace.
-constexpr int kSmHash = 64, kSmHeap = 32;
-constexpr uint32_t kSmEmpty = 0xFFFFFFFFu;
-constexpr uint32_t kSmParity = 1u << 31, kSmRow = 1u << 30;
-constexpr int kSmBytesPerWarp = 32 * (kSmHash * 8 + kSmHeap * 8);
-// blocks of one warp: 24 KB each, nine resident per SM (plus 1 KB reserved each)
-constexpr int kSmWarpsPerSM = 9;
-
-__device__ __forceinline__ uint32_t mix32(uint32_t k) {   // MurmurHash3's finaliser
-    k ^= k >> 16; k *= 0x85ebca6bu; k ^= k >> 13; k *= 0xc2b2ae35u; k ^= k >> 16;
-    return k;
-}
-
-struct SmCtx {
-    uint32_t *key, *inf;          // this lane's column of the warp's tables (stride 32)
-    unsigned long long *heap;
-    int64_t x;                    // the column's vertex
-    int hn, used;
-    bool overflow, dense;
-};
-
-__device__ __forceinline__ void sm_push(SmCtx &c, unsigned long long e) {
-    int i = c.hn++;
-    while (i > 0) {
-        const int p = (i - 1) >> 1;
-        const unsigned long long pe = c.heap[p * 32];
-        if (pe >= e) break;
-        c.heap[i * 32] = pe;
-        i = p;
-    }
-    c.heap[i * 32] = e;
-}
-
-__device__ __forceinline__ unsigned long long sm_pop(SmCtx &c) {
-    const unsigned long long top = c.heap[0];
-    const unsigned long long last = c.heap[--c.hn * 32];
-    int i = 0;
-    while (true) {
-        const int l = 2 * i + 1;
-        if (l >= c.hn) break;
-        const int r = l + 1;
-        unsigned long long cm = c.heap[l * 32];
-        int m = l;
-        if (r < c.hn) {
-            const unsigned long long cr = c.heap[r * 32];
-            if (cr > cm) { cm = cr; m = r; }
-        }
-        if (last >= cm) break;
-        c.heap[i * 32] = cm;
-        i = m;
-    }
-    if (c.hn > 0) c.heap[i * 32] = last;
-    return top;
-}
-
-// Toggles (mod 2) edge (y, link m) of the expanding boundary (as
-// trace_toggle, without the generator mode's passive entries).
-template <typename T>
-__device__ void sm_toggle(SmCtx &c, const StarTables &S, const GridParams &g,
-                          const T *__restrict__ values, uint8_t *flags, GradRec *grad,
-                          const unsigned long long *__restrict__ vcrit, int64_t y, int m,
-                          DevStatus *st) {
-    if (m < 0 || m >= kLinks) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
-    const uint8_t fy = c.dense ? __ldg(flags + y) : ((volatile const uint8_t *)flags)[y];
-    const T vy = values[y];
-    const unsigned long long cw = vcrit[y];
-    GradRec G;
-    {
-        const ulonglong2 *src = (const ulonglong2 *)&grad[y];
-        for (int k = 0; k < 3; k++) {
-            const ulonglong2 v = c.dense ? __ldg(src + k) : __ldcg(src + k);
-            G.w[2 * k] = v.x;
-            G.w[2 * k + 1] = v.y;
-        }
-    }
-    if ((fy & 0xF) == m) return;                          // the head of y's vector
-    const bool crit = (fy & kFlagCritical) && (cw >> (32 + m) & 1);
-    if (crit && !(cw >> (48 + m) & 1)) return;            // critical, paired in D0
-    if (!(fy & kFlagGradient)) G = grad_fill(S, g, values, flags, grad, y);
-    const int64_t off = y - c.x;
-    if (off >= ((int64_t)1 << 27) || off < -((int64_t)1 << 27)) { c.overflow = true; return; }
-    const uint32_t key = ((uint32_t)(off + ((int64_t)1 << 27)) << 4) |
-                         (uint32_t)grad_edge_order(G, m);
-    const uint32_t h0 = mix32(key);
-    int slot = -1;
-    for (int p = 0; p < kSmHash; p++) {
-        const int i = (int)((h0 + p) & (kSmHash - 1));
-        const uint32_t k = c.key[i * 32];
-        if (k == kSmEmpty) { slot = i; break; }
-        if (k == key) { c.inf[i * 32] ^= kSmParity; return; }
-    }
-    if (slot < 0 || (c.used + 1) * 4 > kSmHash * 3) { c.overflow = true; return; }
-    uint32_t info;
-    if (crit) {                                           // a row: its C1 index
-        const int rm = grad_rank(G, m);
-        int32_t j1 = (int32_t)(uint32_t)cw;
-        for (uint32_t q = (uint32_t)(cw >> 32) & kAllLinks; q; q &= q - 1)
-            j1 += grad_rank(G, __ffs(q) - 1) < rm;
-        info = kSmParity | kSmRow | (uint32_t)j1;
-    } else {                                              // regular: expanded later
-        const int sp = grad_edge_pair(G, m);
-        if (sp >= kTris) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
-        const int ta = S.tri_v[sp][0], tb = S.tri_v[sp][1];
-        const bool aup = grad_rank(G, ta) > grad_rank(G, tb);
-        const int hi = aup ? ta : tb, lo = aup ? tb : ta;
-        const int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
-                                   9 * (S.dz[lo] - S.dz[hi] + 1)];
-        if (l < 0) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
-        if (c.hn >= kSmHeap) { c.overflow = true; return; }
-        sm_push(c, ((unsigned long long)Key<T>::of(vy) << 32) | key);
-        info = kSmParity | (uint32_t)(ta == m ? tb : ta) | ((uint32_t)hi << 4) |
-               ((uint32_t)l << 8);
-    }
-    c.key[slot * 32] = key;
-    c.inf[slot * 32] = info;
-    c.used++;
-}
-
-template <typename T, bool B>
-__global__ void __launch_bounds__(32)
-    k_d1_trace_sm(const T *__restrict__ values, Geo<B> geo, uint8_t *flags, GradRec *grad,
-                  const unsigned long long *__restrict__ vcrit, const int32_t *__restrict__ v2,
-                  const uint8_t *__restrict__ l2, const int32_t *__restrict__ colmap,
-                  const int32_t *__restrict__ todo, int64_t ntodo, int32_t *pool,
-                  int64_t pool_cap, int64_t *col_start, int32_t *col_len, uint8_t *overflow,
-                  unsigned long long *next_col, int dense, DevStatus *st) {
-    static_assert(sizeof(typename Key<T>::K) <= 4, "order keys of at most 32 bits");
-    extern __shared__ unsigned long long sm_trace[];
-    const StarTables &S = g_star;
-    const int lane = threadIdx.x & 31;
-    SmCtx c;
-    c.heap = sm_trace + lane;
-    c.key = (uint32_t *)(sm_trace + 32 * kSmHeap) + lane;
-    c.inf = c.key + 32 * kSmHash;
-    c.dense = dense != 0;
-    for (int k = 0; k < kSmHash; k++) c.key[k * 32] = kSmEmpty;
-    int32_t cj = -1;
-    bool done = false;
-    const GridParams *gp = nullptr;
-    // the same two warp collectives in every iteration on all lanes; a column
-    // takes at most kSmHash + 2 steps, which bounds the loop
-    const int64_t max_iter = ntodo * (int64_t)(kSmHash + 8) + 64;
-    for (int64_t iter = 0;; iter++) {
-        const bool need = cj < 0 && !done;
-        const unsigned want = __ballot_sync(0xffffffffu, need);
-        unsigned long long base = 0;
-        if (want) {
-            const int leader = __ffs(want) - 1;
-            if (lane == leader) base = atomicAdd(next_col, (unsigned long long)__popc(want));
-            base = __shfl_sync(0xffffffffu, base, leader);
-        }
-        bool started = false;
-        if (need) {
-            const int64_t q = (int64_t)base + __popc(want & lanemask_lt());
-            if (q >= ntodo) done = true;
-            else { cj = todo ? todo[q] : (int32_t)q; started = true; }
-        }
-        if (__all_sync(0xffffffffu, done)) break;
-        if (iter >= max_iter) {
-            atomicOr(&st->err, kErrIter);
-            break;
-        }
-        if (cj < 0) continue;
-        if (started) {
-            const int32_t j2 = colmap[cj];
-            const int64_t x = v2[j2];
-            gp = &geo.at(x);
-            const int s = l2[j2];
-            c.x = x; c.hn = 0; c.used = 0; c.overflow = false;
-            // boundary of triangle s: (x,a), (x,b) and the edge between x+a and x+b
-            const GradRec Gx = grad_get(S, *gp, values, flags, grad, x, c.dense);
-            const int ta = S.tri_v[s][0], tb = S.tri_v[s][1];
-            sm_toggle<T>(c, S, *gp, values, flags, grad, vcrit, x, ta, st);
-            sm_toggle<T>(c, S, *gp, values, flags, grad, vcrit, x, tb, st);
-            const bool aup = grad_rank(Gx, ta) > grad_rank(Gx, tb);
-            const int hi = aup ? ta : tb, lo = aup ? tb : ta;
-            const int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
-                                       9 * (S.dz[lo] - S.dz[hi] + 1)];
-            sm_toggle<T>(c, S, *gp, values, flags, grad, vcrit, x + gp->dlin[hi], l, st);
-            continue;
-        }
-        if (c.hn > 0 && !c.overflow) {
-            // one expansion: the latest regular edge, if its parity is odd
-            const uint32_t key = (uint32_t)sm_pop(c);
-            const uint32_t h0 = mix32(key);
-            int slot = -1;
-            for (int p = 0; p < kSmHash; p++) {
-                const int i = (int)((h0 + p) & (kSmHash - 1));
-                const uint32_t k = c.key[i * 32];
-                if (k == key) { slot = i; break; }
-                if (k == kSmEmpty) break;
-            }
-            if (slot < 0) { atomicOr(&st->err, kErrState); c.overflow = true; continue; }
-            const uint32_t info = c.inf[slot * 32];
-            if (!(info & kSmParity)) continue;
-            c.inf[slot * 32] = info & ~kSmParity;
-            const int64_t y = c.x + (int64_t)(key >> 4) - ((int64_t)1 << 27);
-            sm_toggle<T>(c, S, *gp, values, flags, grad, vcrit, y, (int)(info & 15), st);
-            sm_toggle<T>(c, S, *gp, values, flags, grad, vcrit, y + gp->dlin[(info >> 4) & 15],
-                         (int)((info >> 8) & 15), st);
-            continue;
-        }
-        // the column is complete (or outgrew the scratch): gather its odd rows
-        // into the front of the key array while clearing the table
-        const int32_t col = cj;
-        cj = -1;
-        int len = 0;
-        for (int i = 0; i < kSmHash; i++) {
-            const uint32_t k = c.key[i * 32];
-            if (k == kSmEmpty) continue;
-            const uint32_t info = c.inf[i * 32];
-            c.key[i * 32] = kSmEmpty;
-            if ((info & (kSmParity | kSmRow)) == (kSmParity | kSmRow))
-                c.key[len++ * 32] = info & (kSmRow - 1);
-        }
-        if (c.overflow) {
-            for (int k = 0; k < len; k++) c.key[k * 32] = kSmEmpty;
-            overflow[col] = 1;
-            col_len[col] = 0;
-            continue;
-        }
-        for (int k = 1; k < len; k++) {                  // decreasing
-            const uint32_t v = c.key[k * 32];
-            int p = k;
-            while (p > 0 && c.key[(p - 1) * 32] < v) { c.key[p * 32] = c.key[(p - 1) * 32]; p--; }
-            c.key[p * 32] = v;
-        }
-        overflow[col] = 0;
-        if (len == 0) { col_len[col] = 0; col_start[col] = 0; continue; }
-        const unsigned long long pos = atomicAdd(&st->pool_top, (unsigned long long)len);
-        if ((int64_t)(pos + len) > pool_cap) {
-            atomicOr(&st->err, kErrCap);
-            for (int k = 0; k < len; k++) c.key[k * 32] = kSmEmpty;
-            col_len[col] = 0;
-            continue;
-        }
-        for (int k = 0; k < len; k++) {
-            pool[pos + k] = (int32_t)c.key[k * 32];
-            c.key[k * 32] = kSmEmpty;
-        }
-        col_start[col] = (int64_t)pos;
-        col_len[col] = len;
-    }
-}
-
 // --------------------------------------------- stage 7: D1 column reduction
 //
 // Standard reduction of the columns (increasing lexicographic order) with the
@@ -4997,116 +4742,84 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
         uint8_t *ovf = P.d1_ovf.as<uint8_t>();
         DMS_CUDA(cudaMemsetAsync(ovf, 0, ncols, c.s));
         DMS_CUDA(cudaMemsetAsync(&c.st->pool_top, 0, sizeof(unsigned long long), c.s));
-        // the columns in vertex-id order: the walks of a warp share the records they read
+        // first pass: small per-thread scratch that stays in L2
+        int hcap = P.tune[DMS_TUNE_TRACE_HEAP], hashcap = hash_cap_for(hcap), rcap = hcap;
+        const int tb = P.tune[DMS_TUNE_TRACE_BLOCK];
+        int64_t nthreads = (int64_t)152 * P.tune[DMS_TUNE_TRACE_PER_SM];
+        if (ncols < nthreads) nthreads = (ncols + tb - 1) / tb * tb;
+        size_t per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
+                     (size_t)rcap * 8;
+        DMS_ALLOC(P.d1_scratch, per * nthreads);
+        HeapEnt *heap = P.d1_scratch.as<HeapEnt>();
+        HashEnt *hash = (HashEnt *)(heap + (size_t)hcap * nthreads);
+        int32_t *rows = (int32_t *)(hash + (size_t)hashcap * nthreads);
+        DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nthreads * sizeof(HashEnt), c.s));
         KEV(18);
         auto dbg_p1 = std::chrono::steady_clock::now();
+        // columns in vertex-id order: the walks of a warp share the records they read
         const int32_t *corder = nullptr;
         DMS_TRY(order_by_vertex(c, P.c_vert[2].as<int32_t>(), P.d1_colmap.as<int32_t>(), ncols, 1,
                                 &corder));
+        DMS_CUDA(cudaMemsetAsync(&c.st->trace_next, 0, sizeof(unsigned long long), c.s));
+        k_d1_trace<T, B><<<(unsigned)(nthreads / tb), tb, 0, c.s>>>(
+            values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
+            P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
+            P.d1_colmap.as<int32_t>(), corder, ncols, heap, hash, rows, hcap, hashcap, rcap, 0,
+            P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+            ovf, &c.st->trace_next, P.dense_grad ? 1 : 0, P.generators, c.st);
+        c.launches++;
+        DMS_CUDA(cudaGetLastError());
+        // columns whose trace outgrew the scratch run again with 16x more; the
+        // list of them is compacted on the device (flag, scan, scatter), the
+        // host reads only its length
         DMS_ALLOC(P.flag_a, 4 * ncols + 4);
         DMS_ALLOC(P.flag_b, 4 * ncols + 4);
         int32_t *f32 = P.flag_a.as<int32_t>(), *fpos = P.flag_b.as<int32_t>();
-        // The columns whose trace outgrew the last pass's scratch (listed in
-        // id order on the device: flag, scan, scatter; the host reads only
-        // the count) -> todo.
-        DMS_ALLOC(P.d1_todo, 8 * ncols + 8);   // two lists: this pass's and the next's
-        int32_t *todo = P.d1_todo.as<int32_t>(), *todo_next = todo + ncols;
-        int64_t ntodo = ncols;
-        const int32_t *pass_list = corder;      // the columns of the pass
-        auto collect_overflow = [&]() -> dms_status {
-            const int32_t *prev = pass_list == corder ? nullptr : pass_list;
-            const int64_t nprev = ntodo;
-            DMS_LAUNCH(nprev, 256, k_flags_of, prev, nprev, ovf, f32);
-            DMS_TRY(scan(c, f32, fpos, nprev, &c.st->total[3]));
-            DMS_TRY(sync_status(c));
-            const int64_t nnext = c.hst->total[3];
-            int32_t *dst = prev == todo ? todo_next : todo;
-            DMS_LAUNCH(nprev, 256, k_compact_list, prev, f32, fpos, nprev, dst);
-            if (prev == todo) std::swap(todo, todo_next);
-            if (pass_list == corder) P.d1_overflow = nnext;   // after the first pass
-            pass_list = todo;
-            ntodo = nnext;
-            return DMS_OK;
-        };
-        if constexpr (sizeof(typename Key<T>::K) <= 4) {
-            if (P.tune[DMS_TUNE_TRACE_SMEM] != 0 && !P.generators) {
-                // first pass: each lane's scratch in shared memory (nine warps per SM)
-                DMS_CUDA(cudaFuncSetAttribute(k_d1_trace_sm<T, B>,
-                                              cudaFuncAttributePreferredSharedMemoryCarveout,
-                                              (int)cudaSharedmemCarveoutMaxShared));
-                DMS_CUDA(cudaMemsetAsync(&c.st->trace_next, 0, sizeof(unsigned long long), c.s));
-                int64_t nw = (int64_t)152 * kSmWarpsPerSM;
-                if (ncols < 32 * nw) nw = (ncols + 31) / 32;
-                k_d1_trace_sm<T, B><<<(unsigned)nw, 32, kSmBytesPerWarp, c.s>>>(
-                    values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
-                    P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(),
-                    P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), corder, ncols,
-                    P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(),
-                    P.d1_len.as<int32_t>(), ovf, &c.st->trace_next, P.dense_grad ? 1 : 0, c.st);
-                c.launches++;
-                DMS_CUDA(cudaGetLastError());
-                DMS_TRY(collect_overflow());
-            }
-        }
-        // then (or first) a small per-thread scratch in global memory
-        int hcap = P.tune[DMS_TUNE_TRACE_HEAP], hashcap = hash_cap_for(hcap), rcap = hcap;
-        int32_t gen = 0;
-        if (ntodo > 0) {
-            const int tb = P.tune[DMS_TUNE_TRACE_BLOCK];
-            int64_t nthreads = (int64_t)152 * P.tune[DMS_TUNE_TRACE_PER_SM];
-            if (ntodo < nthreads) nthreads = (ntodo + tb - 1) / tb * tb;
-            const size_t per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
-                               (size_t)rcap * 8;
-            DMS_ALLOC(P.d1_scratch, per * nthreads);
-            HeapEnt *heap = P.d1_scratch.as<HeapEnt>();
-            HashEnt *hash = (HashEnt *)(heap + (size_t)hcap * nthreads);
-            int32_t *rows = (int32_t *)(hash + (size_t)hashcap * nthreads);
-            DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nthreads * sizeof(HashEnt), c.s));
-            DMS_CUDA(cudaMemsetAsync(&c.st->trace_next, 0, sizeof(unsigned long long), c.s));
-            k_d1_trace<T, B><<<(unsigned)(nthreads / tb), tb, 0, c.s>>>(
-                values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
-                P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(),
-                P.d1_colmap.as<int32_t>(), pass_list, ntodo, heap, hash, rows, hcap, hashcap, rcap,
-                0, P.d1_pool.as<int32_t>(), pool_cap, P.d1_start.as<int64_t>(),
-                P.d1_len.as<int32_t>(), ovf, &c.st->trace_next, P.dense_grad ? 1 : 0,
-                P.generators, c.st);
-            c.launches++;
-            DMS_CUDA(cudaGetLastError());
-            DMS_TRY(collect_overflow());
-            gen = (int32_t)ncols;
-        }
+        DMS_LAUNCH(ncols, 256, k_flags_of, (const int32_t *)nullptr, ncols, ovf, f32);
+        DMS_TRY(scan(c, f32, fpos, ncols, &c.st->total[3]));
+        DMS_TRY(sync_status(c));
+        int64_t ntodo = c.hst->total[3];
+        P.d1_overflow = ntodo;
+        DMS_ALLOC(P.d1_todo, 8 * ntodo + 8);   // two lists: this pass's and the next's
+        int32_t *todo = P.d1_todo.as<int32_t>(), *todo_next = todo + ntodo;
+        DMS_LAUNCH(ncols, 256, k_compact_list, (const int32_t *)nullptr, f32, fpos, ncols, todo);
         auto dbg_t0 = std::chrono::steady_clock::now();
         if (getenv("DMS_DEBUG")) {
-            fprintf(stderr, "d1 trace first passes: %lld columns, %lld overflow, pool %llu, %.3f ms\n",
+            fprintf(stderr, "d1 trace pass 1: %lld columns, %lld overflow, pool %llu, %.3f ms\n",
                     (long long)ncols, (long long)ntodo, c.hst->pool_top,
                     std::chrono::duration<double, std::milli>(dbg_t0 - dbg_p1).count());
         }
-        // columns still outgrowing it run again with 16x more
+        int32_t gen = (int32_t)ncols;
         while (ntodo > 0) {
             hcap *= 16; hashcap *= 16; rcap *= 16;
             if (hashcap > (1 << 24)) return DMS_ERR_CAPACITY;
-            const size_t per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
-                               (size_t)rcap * 8;
+            per = (size_t)hcap * sizeof(HeapEnt) + (size_t)hashcap * sizeof(HashEnt) +
+                  (size_t)rcap * 8;
             int64_t nt = std::min<int64_t>(ntodo,
                                            std::max<int64_t>(32, ((int64_t)4 << 30) / (int64_t)per));
             nt = (nt + 31) / 32 * 32;
             DMS_ALLOC(P.d1_scratch, per * nt);
-            HeapEnt *heap = P.d1_scratch.as<HeapEnt>();
-            HashEnt *hash = (HashEnt *)(heap + (size_t)hcap * nt);
-            int32_t *rows = (int32_t *)(hash + (size_t)hashcap * nt);
+            heap = P.d1_scratch.as<HeapEnt>();
+            hash = (HashEnt *)(heap + (size_t)hcap * nt);
+            rows = (int32_t *)(hash + (size_t)hashcap * nt);
             DMS_CUDA(cudaMemsetAsync(hash, 0xFF, (size_t)hashcap * nt * sizeof(HashEnt), c.s));
             DMS_CUDA(cudaMemsetAsync(&c.st->trace_next, 0, sizeof(unsigned long long), c.s));
             k_d1_trace<T, B><<<(unsigned)(nt / 32), 32, 0, c.s>>>(
                 values, geo, P.flags.as<uint8_t>(), P.grad.as<GradRec>(),
-                P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(),
-                P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), pass_list, ntodo, heap, hash,
+                P.vcrit.as<unsigned long long>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(), P.d1_colmap.as<int32_t>(), todo, ntodo, heap, hash,
                 rows, hcap, hashcap, rcap, gen, P.d1_pool.as<int32_t>(), pool_cap,
                 P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), ovf, &c.st->trace_next,
                 P.dense_grad ? 1 : 0, P.generators, c.st);
             c.launches++;
             DMS_CUDA(cudaGetLastError());
             gen += (int32_t)ncols;
-            DMS_TRY(collect_overflow());
+            DMS_LAUNCH(ntodo, 256, k_flags_of, todo, ntodo, ovf, f32);
+            DMS_TRY(scan(c, f32, fpos, ntodo, &c.st->total[3]));
+            DMS_TRY(sync_status(c));
+            const int64_t nnext = c.hst->total[3];
+            DMS_LAUNCH(ntodo, 256, k_compact_list, todo, f32, fpos, ntodo, todo_next);
+            std::swap(todo, todo_next);
+            ntodo = nnext;
         }
         if (getenv("DMS_DEBUG"))
             fprintf(stderr, "d1 trace retries: %.3f ms\n",

@@ -88,7 +88,7 @@ struct Pipeline {
     void *hstat = nullptr;  // pinned host mirror
 
     // launch shapes and capacities (dms_set_tuning; order of DMS_TUNE_*)
-    int32_t tune[DMS_TUNING_COUNT] = {128, 128, 2048, 48, -1, 48, 32, 1, 1, 1, 1};
+    int32_t tune[DMS_TUNING_COUNT] = {128, 128, 2048, 48, -1, 48, 32, 1, 1, 1};
 
     int64_t n_crit = 0, n_c[4] = {0, 0, 0, 0};
     int64_t n_pairs[3] = {0, 0, 0}, n_ess[4] = {0, 0, 0, 0};

@@ -6,21 +6,25 @@ while others are on the GPU starts right away in a free slot, so the work of
 several requests overlaps on the device.  Each slot is a host thread that
 owns a CUDA stream and one reusable ``dms_grid`` per dtype (reshaped per
 request, so its device buffers are kept across requests); the C ABI calls
-release the GIL, so slots drive the GPU concurrently.  With max_batch > 1 a
-slot takes every waiting request it can (up to max_batch, within the budget)
-and runs them as one batch -- one pass of the pipeline over the disjoint union
-of their grids -- on a reusable batch handle.  Each result is the same as the
+release the GIL, so slots drive the GPU concurrently.  With max_batch > 1 and
+a backlog (more requests waiting than ``batch_above``, by default the number
+of slots) a slot takes every waiting request it can (up to max_batch, within
+the budget) and runs them as one batch -- one pass of the pipeline over the
+disjoint union of their grids -- on a reusable batch handle.  Without a
+backlog requests run one by one: a batch raises the throughput of a saturated
+server, but a request in it waits for the whole batch.  Each result is the same as the
 request's diagram computed alone (the pipeline is deterministic, handles
 share no state, and a batch's per-field pairs equal the single-grid ones).
 
 Device memory: the requests in flight stay within ``mem_budget``, each
 charged by the estimate ``request_bytes``.  A handle's buffers only grow, so a
-slot keeps at most one handle between requests (the one it used last), and
-only while the device memory that handle really holds (``device_bytes``,
-which includes D1 pools grown on noisy fields) and the request's estimate
-both fit the slot's share of the budget (``keeps_buffers``); otherwise the
-handle is freed at once.  Idle handles therefore hold at most
-``mem_budget / slots`` each, measured, not estimated.
+slot keeps at most one handle of each kind (grid, batch) between requests,
+and only while the device memory they really hold (``device_bytes``, which
+includes D1 pools grown on noisy fields; the request's estimate for the one
+just used) fits the slot's share of the budget (``keeps_buffers``); above it
+the other kind's handle is freed first, then the one just used.  A slot's idle
+handles therefore hold at most ``mem_budget / slots``, measured, not
+estimated.
 """
 from __future__ import annotations
 
@@ -47,13 +51,17 @@ def keeps_buffers(need: int, budget: int, slots: int) -> bool:
 
 
 def select_batch(pending, in_flight: int, budget: int, max_batch: int,
-                 max_vertices: int | None = None):
+                 max_vertices: int | None = None, batch_above: int | None = None):
     """Admission: how many of the pending requests (a list of (vertices,
     dtype) in arrival order) start now, and their bytes.  The oldest ones that
     fit the free budget, up to max_batch and (after the first) up to
     max_vertices in all, all of the head's dtype; nothing overtakes a head
     request that does not fit, so it is never starved.  The vertex bound keeps
-    one batched pass short, so requests behind it wait less."""
+    one batched pass short, so requests behind it wait less.  With
+    ``batch_above`` set, only a backlog of more than that many pending
+    requests is batched; a shorter queue is served one request at a time."""
+    if batch_above is not None and len(pending) <= batch_above:
+        max_batch = 1
     k, need, verts = 0, 0, 0
     for size, dtype in pending:
         dt = np.dtype(dtype)
@@ -106,18 +114,21 @@ class Request:
 
 class DiagramServer:
     """``slots`` concurrent passes at most, within ``mem_budget`` bytes.  With
-    ``max_batch`` > 1 a free slot takes up to that many waiting requests (in
+    ``max_batch`` > 1, while more than ``batch_above`` requests wait (default:
+    the number of slots), a free slot takes up to max_batch of them (in
     arrival order, one dtype, within the budget, and after the first at most
     ``max_batch_vertices`` vertices in all) and computes them as one batch
     (``dms_batch_create``): one pass of the pipeline for all of them."""
 
     def __init__(self, slots: int = 4, mem_budget: int = 16 << 30, max_batch: int = 1,
-                 backend=None, max_batch_vertices: int | None = None):
+                 backend=None, max_batch_vertices: int | None = None,
+                 batch_above: int | None = None):
         self._be = backend if backend is not None else CudaBackend()
         self.slots = slots
         self.mem_budget = mem_budget
         self.max_batch = max(1, int(max_batch))
         self.max_batch_vertices = max_batch_vertices
+        self.batch_above = slots if batch_above is None else int(batch_above)
         self._pending = []                 # FIFO of admitted-later requests
         self._cv = threading.Condition()
         self._in_flight_bytes = 0
@@ -152,7 +163,7 @@ class DiagramServer:
                     return None
                 k, need = select_batch([(r.values.size, r.values.dtype) for r in self._pending],
                                        self._in_flight_bytes, self.mem_budget, self.max_batch,
-                                       self.max_batch_vertices)
+                                       self.max_batch_vertices, self.batch_above)
                 if k:
                     take = self._pending[:k]
                     del self._pending[:k]
@@ -171,7 +182,7 @@ class DiagramServer:
             stream, setup_error = be.stream(), None
         except Exception as e:   # every request this slot takes then reports it
             stream, setup_error = None, e
-        held = None          # (kind, dtype, handle): the one handle kept between requests
+        held = {}            # kind -> (dtype, handle): at most one of each kind between requests
         while True:
             got = self._take()
             if got is None:
@@ -180,28 +191,24 @@ class DiagramServer:
             t = time.perf_counter()
             for r in reqs:
                 r.admitted = t
+            kind = "grid" if len(reqs) == 1 else "batch"
             try:
                 if setup_error is not None:
                     raise setup_error
                 dt = reqs[0].values.dtype
                 shapes = [(r.values.shape[2], r.values.shape[1], r.values.shape[0]) for r in reqs]
-                # with batching on, a slot runs even a lone request as a batch
-                # of one, so it keeps one handle of one kind and never frees
-                # it to switch kinds (a free synchronises the whole device)
-                kind = "batch" if self.max_batch > 1 else "grid"
                 h = None
-                if held is not None and held[0] == kind and held[1] == dt:
-                    h = held[2]
-                elif held is not None:              # another kind or dtype: free it first
-                    held[2].close()
-                held = None
+                if kind in held and held[kind][0] == dt:
+                    h = held[kind][1]
+                elif kind in held:                  # another dtype: free it first
+                    held.pop(kind)[1].close()
                 with be.current(stream):
                     if kind == "grid":
                         if h is None:
                             h = be.Grid(shapes[0], dt)
                         elif h.shape_xyz != shapes[0]:
                             h.reshape(shapes[0])
-                        held = (kind, dt, h)
+                        held[kind] = (dt, h)
                         h.compute(reqs[0].values, stream=be.handle(stream))
                         reqs[0].result = {d: h.fetch(d) for d in range(3)}
                     else:
@@ -209,37 +216,46 @@ class DiagramServer:
                             h = be.Batch(shapes, dt)
                         else:
                             h.reshape(shapes)
-                        held = (kind, dt, h)
+                        held[kind] = (dt, h)
                         h.compute([r.values for r in reqs], stream=be.handle(stream))
                         for r, res in zip(reqs, h.results()):
                             r.result = res
             except Exception as e:   # reported to the caller
                 for r in reqs:
                     r.error = e
-            if held is not None:
-                try:
-                    kept = max(need, held[2].device_bytes())
-                except Exception:
-                    kept = None
-                if kept is None or not keeps_buffers(kept, self.mem_budget, self.slots):
-                    held[2].close()
-                    held = None
+            self._trim(held, kind, need)
             t = time.perf_counter()
             self._release(need)
             for r in reqs:
                 r.finished = t
                 r.done.set()
-        if held is not None:
-            held[2].close()
+        for _, h in held.values():
+            h.close()
+
+    def _trim(self, held, used, need):
+        """Frees held handles until what they hold fits the slot's share:
+        the kind not just used first."""
+        def size(kind):
+            try:
+                b = held[kind][1].device_bytes()
+            except Exception:
+                return None
+            return max(need, b) if kind == used else b
+        for kind in sorted(held, key=lambda k: k == used):
+            sizes = [size(k) for k in held]
+            if None not in sizes and keeps_buffers(sum(sizes), self.mem_budget, self.slots):
+                return
+            held.pop(kind)[1].close()
 
 
 def run_stream(fields, arrivals, slots: int, mem_budget: int = 16 << 30, max_batch: int = 1,
-               backend=None):
+               backend=None, **server_options):
     """Replays requests arriving at ``arrivals`` (seconds from start) through
     a server; returns the requests (with timings and results) and the wall
-    time."""
+    time.  ``server_options`` go to DiagramServer (max_batch_vertices,
+    batch_above)."""
     srv = DiagramServer(slots=slots, mem_budget=mem_budget, max_batch=max_batch,
-                        backend=backend)
+                        backend=backend, **server_options)
     reqs = []
     t0 = time.perf_counter()
     for i, (f, a) in enumerate(zip(fields, arrivals)):

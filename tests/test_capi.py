@@ -101,8 +101,8 @@ def test_argument_checks_without_gpu():
     assert lib.dms_get_kernel_ms(null, (ctypes.c_float * 12)()) == bad
     assert lib.dms_get_stats(null, (ctypes.c_int64 * 16)()) == bad
     assert lib.dms_get_device_bytes(null, ctypes.byref(w)) == bad
-    assert lib.dms_set_tuning(null, (ctypes.c_int32 * 11)(), 11) == bad
-    assert lib.dms_get_tuning(null, (ctypes.c_int32 * 11)(), 11) == bad
+    assert lib.dms_set_tuning(null, (ctypes.c_int32 * 10)(), 10) == bad
+    assert lib.dms_get_tuning(null, (ctypes.c_int32 * 10)(), 10) == bad
     assert lib.dms_grid_destroy(null) == bad
     assert lib.dms_batch_create(1, None, 1, None, ctypes.byref(h)) == bad
     # the allocation-free classification checks its arguments first too

@@ -52,3 +52,11 @@ def test_batch_bounded_by_vertices_after_the_first():
     assert select_batch(pend, 0, 10 ** 12, 8, max_vertices=6000)[0] == 2
     assert select_batch(pend, 0, 10 ** 12, 8, max_vertices=9100)[0] == 4
     assert select_batch(pend, 0, 10 ** 12, 8, max_vertices=None)[0] == 4
+
+
+def test_only_a_backlog_is_batched():
+    pend = [_req(100)] * 6
+    assert select_batch(pend, 0, 10 ** 12, 8, batch_above=4)[0] == 6
+    assert select_batch(pend[:4], 0, 10 ** 12, 8, batch_above=4)[0] == 1
+    assert select_batch(pend[:4], 0, 10 ** 12, 8)[0] == 4
+    assert select_batch(pend[:5], 0, 10 ** 12, 8, batch_above=4)[0] == 5

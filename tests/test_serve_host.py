@@ -179,6 +179,18 @@ def test_handles_holding_more_than_their_estimate_are_freed():
     assert be.ledger.created == be.ledger.closed == len(mixed)   # dtype switch frees the other
 
 
+def test_a_slot_keeps_one_handle_of_each_kind():
+    """With batching on, a backlog runs as batches and the requests after it
+    one by one; a slot keeps its batch handle and its grid handle (both
+    within its share) instead of freeing one to make the other."""
+    fields = _fields(40, seed=7, lo=4, hi=6)
+    be = _FakeBackend()
+    reqs, _ = serve.run_stream(fields, np.r_[np.zeros(30), 0.05 + 0.02 * np.arange(10)],
+                               slots=2, mem_budget=10 ** 9, max_batch=8, backend=be)
+    assert all(r.error is None for r in reqs)
+    assert be.ledger.created <= 4 and be.ledger.created == be.ledger.closed
+
+
 def test_a_failing_compute_reaches_only_its_request():
     fields = _fields(20, seed=4)
     fields[7] = fields[7].copy()
