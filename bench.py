@@ -371,7 +371,47 @@ def roofline_pls(n, stats, kavg):
                     "(the order of the lower links differs within a warp)"}
 
 
-def roofline_dominant(dom, kavg, rgrad, rcls, hbm, src, rpls=None):
+def roofline_trace(s_in, work, stats, kavg, hbm, src):
+    """The D1 boundary trace against HBM.  Its algorithmic bytes are what the
+    walks must read: per edge toggled, the gradient record (48 B), flag byte,
+    value and row word (8 B) of the edge's vertex; per column, its entry
+    (column map, vertex, local triangle: 9 B), the record of its vertex and
+    its output slot (12 B + 1 overflow byte).  Toggles are counted on the
+    device (dms_get_work)."""
+    tog, cols = work["trace_toggles"], stats["d1_columns"]
+    nbytes = tog * (48 + 1 + s_in + 8) + cols * (9 + 48 + 13)
+    ms = kavg["d1_trace"]
+    gbs = nbytes / (ms * 1e-3) / 1e9 if ms > 0 and tog > 0 else None
+    return {"bound": "hbm", "kernel": "k_d1_trace (D1 boundary trace)", "achieved": gbs,
+            "peak": hbm, "unit": "GB/s", "frac": gbs / hbm if gbs is not None else None,
+            "traffic": None, "algorithmic_bytes_per_launch": nbytes, "ms": ms,
+            "toggles": tog, "expansions": work["trace_expansions"], "columns": cols,
+            "peak_source": src,
+            "note": "latency-bound: each toggle's loads wait on the hash probe and heap "
+                    "push of the step before it (per-thread scratch); the record gathers are "
+                    "random"}
+
+
+def roofline_reduce(work, stats, kavg, hbm, src):
+    """The D1 reduction: the bytes its column additions read and write
+    against HBM, beside the latency view -- its time over the longest chain
+    of dependent additions one kernel made is the time per link of the
+    critical path."""
+    nbytes = stats["d1_bytes_read"] + stats["d1_bytes_written"]
+    ms = kavg["d1_reduce"]
+    gbs = nbytes / (ms * 1e-3) / 1e9 if ms > 0 and nbytes > 0 else None
+    chain = work["d1_longest_chain"]
+    return {"bound": "hbm", "kernel": "k_red_* (D1 reduction: rounds and asynchronous tail)",
+            "achieved": gbs, "peak": hbm, "unit": "GB/s",
+            "frac": gbs / hbm if gbs is not None else None, "traffic": None,
+            "algorithmic_bytes_per_launch": nbytes, "ms": ms, "peak_source": src,
+            "additions": stats["d1_additions"], "longest_chain": chain,
+            "us_per_chain_addition": 1e3 * ms / chain if chain else None,
+            "note": "bound by chains of dependent additions (each waits on the list its "
+                    "predecessor wrote), not by bytes"}
+
+
+def roofline_dominant(dom, kavg, rgrad, rcls, hbm, src, rpls=None, rtrace=None, rred=None):
     """The family with the most device time.  The stencil is measured against
     HBM, ProcessLowerStars against the issue rate; the walks, union-find
     levels and the D1 reduction have no algorithmic byte count that bounds
@@ -383,6 +423,10 @@ def roofline_dominant(dom, kavg, rgrad, rcls, hbm, src, rpls=None):
         return dict(rpls)
     if dom in ("process_lower_stars", "compact"):
         return dict(rgrad)
+    if dom == "d1_trace" and rtrace is not None:
+        return dict(rtrace)
+    if dom == "d1_reduce" and rred is not None:
+        return dict(rred)
     return {"bound": "hbm", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s",
             "frac": None, "traffic": None, "ms": kavg[dom], "peak_source": src,
             "note": "latency-bound (dependent loads, atomics); no algorithmic byte count"}
@@ -476,7 +520,10 @@ def run_ours(args):
     rgrad = roofline_gradient(n, s_in, stats, kavg, hbm, src)
     rcls = roofline_classify(n, s_in, kavg, hbm, src)
     rpls = roofline_pls(n, stats, kavg)
-    roofline = roofline_dominant(dom, kavg, rgrad, rcls, hbm, src, rpls)
+    work = g.work()
+    rtrace = roofline_trace(s_in, work, stats, kavg, hbm, src)
+    rred = roofline_reduce(work, stats, kavg, hbm, src)
+    roofline = roofline_dominant(dom, kavg, rgrad, rcls, hbm, src, rpls, rtrace, rred)
     serving = None
     if not args.no_serve:
         try:
@@ -499,6 +546,8 @@ def run_ours(args):
         "roofline_gradient": rgrad,
         "roofline_classify": rcls,
         "roofline_pls": rpls,
+        "roofline_d1_trace": rtrace,
+        "roofline_d1_reduce": rred,
         "dominant_kernel": {"name": dom, "ms": kavg[dom]},
         "kernel_ms": kavg,
         "stage_ms": stage,

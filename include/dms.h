@@ -228,6 +228,16 @@ dms_status dms_get_stage_ms(dms_grid grid, float ms[8]);
  * by D1 column additions, [15] bytes written by D1 column additions. */
 dms_status dms_get_stats(dms_grid grid, int64_t stats[16]);
 
+/* Work counts of the last compute that rooflines are computed from: [0]
+ * edges toggled by the D1 boundary trace (each reads the gradient record,
+ * flag byte, value and row word of the edge's vertex: the walks of the
+ * descending paths of Sec. 5.3), [1] regular edges it expanded, [2] the
+ * longest chain of dependent column additions one reduction kernel made
+ * (a column adding the owners of its pivots one after another; the rounds'
+ * and the asynchronous tail's chains), [3] 0 (reserved).  The lazy D1 mode
+ * (d1_mode 3) reports 0 in [0] and [1]. */
+dms_status dms_get_work(dms_grid grid, int64_t work[4]);
+
 /* Device memory the handle holds now, in bytes: the sum of its device
  * arenas (grid-sized state, critical lists, union-find tables, D1 pools and
  * output), which only grow and are kept across computes and reshapes.  Host

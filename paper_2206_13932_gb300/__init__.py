@@ -74,6 +74,8 @@ def load(build_if_missing: bool = False):
             lib.dms_fetch_pairs.argtypes = [vp, ctypes.c_int, vp, i64, p64, ctypes.c_int]
             lib.dms_get_stage_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
             lib.dms_get_stats.argtypes = [vp, p64]
+            lib.dms_get_work.argtypes = [vp, p64]
+            lib.dms_get_work.restype = ctypes.c_int
             lib.dms_get_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
             lib.dms_get_device_bytes.argtypes = [vp, p64]
             lib.dms_get_device_bytes.restype = ctypes.c_int
@@ -243,6 +245,14 @@ class Grid:
         ms = (ctypes.c_float * 12)()
         _check(self._lib.dms_get_kernel_ms(self._h, ms), "dms_get_kernel_ms")
         return dict(zip(self.KERNELS, [float(x) for x in ms]))
+
+    def work(self):
+        """Work counts of the last compute (``dms_get_work``): edges the D1
+        trace toggled and expanded, the longest chain of column additions."""
+        w = (ctypes.c_int64 * 4)()
+        _check(self._lib.dms_get_work(self._h, w), "dms_get_work")
+        return {"trace_toggles": int(w[0]), "trace_expansions": int(w[1]),
+                "d1_longest_chain": int(w[2])}
 
     def device_bytes(self) -> int:
         """Device memory this handle holds now (its arenas only grow)."""

@@ -125,6 +125,16 @@ dms_status dms_get_stats(dms_grid grid, int64_t stats[16]) {
     return DMS_OK;
 }
 
+dms_status dms_get_work(dms_grid grid, int64_t work[4]) {
+    if (!grid || !work) return DMS_ERR_INVALID_ARG;
+    if (!grid->p.has_result) return DMS_ERR_STATE;
+    work[0] = grid->p.trace_toggles;
+    work[1] = grid->p.trace_expansions;
+    work[2] = grid->p.d1_longest_chain;
+    work[3] = 0;
+    return DMS_OK;
+}
+
 dms_status dms_get_device_bytes(dms_grid grid, int64_t *bytes) {
     if (!grid || !bytes) return DMS_ERR_INVALID_ARG;
     *bytes = grid->p.device_bytes();

@@ -46,6 +46,7 @@ struct DevStatus {
     long long misc[4];
     long long bx[4];               // block expansions: nodes, levels (discovery, order), columns
     unsigned long long trace_next; // D1 trace: next column to take
+    unsigned long long trace_work[2];   // D1 trace: edges toggled, edges expanded
 };
 
 // Record of a critical vertex after ProcessLowerStars.
@@ -1476,26 +1477,6 @@ __device__ __forceinline__ HashEnt *trace_find(TraceCtx &c, int64_t y, int m) {
     return nullptr;
 }
 
-// The two further edges of star triangle s of y when edge (y, m) is expanded
-// through it: (y, other) and the edge between the triangle's two link
-// vertices, expressed in the star of the higher of them (by the ranks of the
-// lower star of y).
-template <typename T>
-__device__ __forceinline__ void trace_expand(TraceCtx &c, const StarTables &S, const GridParams &g,
-                                             const T *__restrict__ values, uint8_t *flags,
-                                             GradRec *grad,
-                                             const unsigned long long *__restrict__ vcrit,
-                                             int64_t y, int s, int m, const GradRec &G,
-                                             DevStatus *st) {
-    int ta = S.tri_v[s][0], tb = S.tri_v[s][1];
-    if (m >= 0) trace_toggle<T>(c, S, g, values, flags, grad, vcrit, y, ta == m ? tb : ta, st);
-    bool aup = grad_rank(G, ta) > grad_rank(G, tb);
-    int hi = aup ? ta : tb, lo = aup ? tb : ta;
-    int l = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
-                         9 * (S.dz[lo] - S.dz[hi] + 1)];
-    trace_toggle<T>(c, S, g, values, flags, grad, vcrit, y + g.dlin[hi], l, st);
-}
-
 // One thread per column: the Morse boundary of a critical triangle restricted
 // to the rows (1-saddles not paired in D0), as a descending list of C1
 // indices appended to the column pool.  The walks differ widely in length,
@@ -1528,8 +1509,17 @@ __global__ void __launch_bounds__(256, 4)
     const GridParams *gp = nullptr;
     // every iteration runs the same two warp collectives on all lanes (the
     // ballot and the vote); the per-lane work after them has none.  A column
-    // takes at most hashcap + 8 steps, which bounds the loop.
-    const int64_t max_iter = ntodo * (int64_t)(hashcap + 8) + 64;
+    // takes at most 2 * hashcap + 4 iterations (its start, a pop and two
+    // toggles per pushed edge, its write-out), which bounds the loop.
+    const int64_t max_iter = ntodo * (int64_t)(2 * hashcap + 8) + 64;
+    // Pending toggles of this lane: the three edges of a column's start or the
+    // two of an expansion.  One is done per iteration, so the lanes of a warp
+    // run the toggle -- its loads, hash probe and heap push -- together,
+    // whatever step their columns are at.
+    int np = 0;
+    int64_t y0 = 0, y1 = 0, y2 = 0;
+    int m0 = 0, m1 = 0, m2 = 0;
+    unsigned long long ntog = 0, nexp = 0;
     for (int64_t iter = 0;; iter++) {
         // lanes without a column take the next ones
         const bool need = cj < 0 && !done;
@@ -1552,33 +1542,52 @@ __global__ void __launch_bounds__(256, 4)
             break;
         }
         if (cj < 0) continue;
-        if (started) {
-            const int32_t j2 = colmap[cj];
-            const int64_t x = v2[j2];
-            gp = &geo.at(x);
-            const int s = l2[j2];
-            c.hn = 0; c.rn = 0; c.used = 0; c.overflow = false;
-            c.gen = gen_base + cj;
-            // boundary: (x,a), (x,b) and the edge between x+a and x+b
-            const GradRec Gx = grad_get(S, *gp, values, flags, grad, x, c.dense);
-            trace_toggle<T>(c, S, *gp, values, flags, grad, vcrit, x, S.tri_v[s][0], st);
-            trace_expand<T>(c, S, *gp, values, flags, grad, vcrit, x, s, S.tri_v[s][0], Gx, st);
+        if (np == 0) {
+            if (started) {
+                const int32_t j2 = colmap[cj];
+                const int64_t x = v2[j2];
+                gp = &geo.at(x);
+                const int s = l2[j2];
+                c.hn = 0; c.rn = 0; c.used = 0; c.overflow = false;
+                c.gen = gen_base + cj;
+                // boundary: (x,a), (x,b) and the edge between x+a and x+b, in the
+                // star of the higher of the two
+                const GradRec Gx = grad_get(S, *gp, values, flags, grad, x, c.dense);
+                const int ta = S.tri_v[s][0], tb = S.tri_v[s][1];
+                const bool aup = grad_rank(Gx, ta) > grad_rank(Gx, tb);
+                const int hi = aup ? ta : tb, lo = aup ? tb : ta;
+                y0 = x; m0 = ta;
+                y1 = x; m1 = tb;
+                y2 = x + gp->dlin[hi];
+                m2 = S.link_of_dc[(S.dx[lo] - S.dx[hi] + 1) + 3 * (S.dy[lo] - S.dy[hi] + 1) +
+                                  9 * (S.dz[lo] - S.dz[hi] + 1)];
+                np = 3;
+            } else if (c.hn > 0 && !c.overflow) {
+                // one expansion, if the popped edge's parity is odd
+                const HeapEnt top = heap_pop(c);
+                const int64_t y = (int64_t)(top.lo >> 12);
+                const int m = (int)(top.lo & 0xF);
+                HashEnt *e = trace_find(c, y, m);
+                if (e && hinfo_parity(e->info)) {
+                    e->info &= ~(1u << 31);
+                    const uint32_t spec = hinfo_aux(e->info);
+                    y0 = y; m0 = (int)(spec & 15);
+                    y1 = y + gp->dlin[(spec >> 4) & 15]; m1 = (int)((spec >> 8) & 15);
+                    np = 2;
+                    nexp++;
+                }
+            }
+        }
+        if (c.overflow) np = 0;                  // the column is dropped: no more toggles
+        if (np > 0) {
+            const int64_t ty = np == 3 ? y2 : np == 2 ? y1 : y0;
+            const int tm = np == 3 ? m2 : np == 2 ? m1 : m0;
+            np--;
+            ntog++;
+            trace_toggle<T>(c, S, *gp, values, flags, grad, vcrit, ty, tm, st);
             continue;
         }
-        if (c.hn > 0 && !c.overflow) {
-            // one expansion
-            const HeapEnt top = heap_pop(c);
-            const int64_t y = (int64_t)(top.lo >> 12);
-            const int m = (int)(top.lo & 0xF);
-            HashEnt *e = trace_find(c, y, m);
-            if (!e || !hinfo_parity(e->info)) continue;
-            e->info &= ~(1u << 31);
-            const uint32_t spec = hinfo_aux(e->info);
-            trace_toggle<T>(c, S, *gp, values, flags, grad, vcrit, y, (int)(spec & 15), st);
-            trace_toggle<T>(c, S, *gp, values, flags, grad, vcrit, y + gp->dlin[(spec >> 4) & 15],
-                            (int)((spec >> 8) & 15), st);
-            continue;
-        }
+        if (c.hn > 0 && !c.overflow) continue;
         // the column is complete (or outgrew the scratch): write it out
         const int32_t col = cj;
         cj = -1;
@@ -1608,6 +1617,15 @@ __global__ void __launch_bounds__(256, 4)
         for (int k = 0; k < len; k++) pool[pos + k] = c.rows[k];
         col_start[col] = (int64_t)pos;
         col_len[col] = len;
+    }
+    // the loop ends on warp-uniform conditions: all lanes are here
+    for (int o = 16; o > 0; o >>= 1) {
+        ntog += __shfl_down_sync(0xffffffffu, ntog, o);
+        nexp += __shfl_down_sync(0xffffffffu, nexp, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&st->trace_work[0], ntog);
+        atomicAdd(&st->trace_work[1], nexp);
     }
 }
 
@@ -3891,6 +3909,7 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
                 P.d1_io_read = c.hst->red_io[0];
                 P.d1_io_written = c.hst->red_io[1];
                 P.d1_additions = c.hst->misc[2];
+                P.d1_longest_chain = c.hst->misc[3];
                 P.d1_pool_used = (int64_t)c.hst->pool_top;
                 return DMS_OK;
             }
@@ -3959,6 +3978,7 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
             P.d1_io_read = c.hst->red_io[0];
             P.d1_io_written = c.hst->red_io[1];
             P.d1_additions = c.hst->misc[2];
+            P.d1_longest_chain = c.hst->misc[3];
             P.d1_pool_used = (int64_t)c.hst->pool_top;
             return DMS_OK;
         }
@@ -4731,6 +4751,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
                      : P.d1_mode != 0 ? P.d1_mode
                                       : (ncols * P.tune[DMS_TUNE_LAZY_DENSITY] < n ? 3 : 1);
     P.d1_mode_used = mode;
+    P.trace_toggles = P.trace_expansions = P.d1_longest_chain = 0;
     if (ncols > 0 && mode == 3) {
         DMS_TRY((reduce_lazy<T, B>(c, values, ncols, n1, is_row)));
     } else if (ncols > 0) {
@@ -4825,6 +4846,8 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
             fprintf(stderr, "d1 trace retries: %.3f ms\n",
                     std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
                                                               dbg_t0).count());
+        P.trace_toggles = (int64_t)c.hst->trace_work[0];   // read by the last status sync
+        P.trace_expansions = (int64_t)c.hst->trace_work[1];
         KEV(19);
         KEV(20);
         DMS_TRY(reduce_d1(c, ncols, n1, is_row));

@@ -95,6 +95,7 @@ struct Pipeline {
     int64_t launches = 0, rounds_d0 = 0, rounds_d2 = 0, rounds_d1 = 0  /* D0/D2: halving levels */, d1_cols = 0;
     int64_t d1_overflow = 0, d1_additions = 0, d1_pool_used = 0, d1_pool_grows = 0;
     int64_t d1_io_read = 0, d1_io_written = 0;
+    int64_t trace_toggles = 0, trace_expansions = 0, d1_longest_chain = 0;
     float stage_ms[8] = {0};
     float kernel_ms[12] = {0};
     void *kev[24] = {nullptr};   // cudaEvent_t pairs per kernel family

@@ -47,7 +47,10 @@ class _FakeGrid:
 
     def stats(self):
         return {"launches": 50, "d1_bytes_read": 10 ** 8, "d1_bytes_written": 5 * 10 ** 7,
-                "c0": 10, "c1": 20, "c2": 30, "c3": 40}
+                "c0": 10, "c1": 20, "c2": 30, "c3": 40, "d1_columns": 25, "d1_additions": 60}
+
+    def work(self):
+        return {"trace_toggles": 1000, "trace_expansions": 400, "d1_longest_chain": 8}
 
     def counts(self):
         return (3, 2, 1), (1, 0, 0, 0)
@@ -127,7 +130,10 @@ def test_one_line_with_every_contract_key(fake_device):
     assert d["e2e"]["d2h_bytes_per_step"] == (4 + 2 + 1) * 56
     assert "512^3 uint16" in d["config"]["workload"]
     r = d["roofline"]                      # d1_reduce dominates the fake timings
-    assert r["kernel"] == "d1_reduce" and r["achieved"] is None and r["frac"] is None
+    assert r == d["roofline_d1_reduce"] and r["bound"] == "hbm"
+    assert r["achieved"] == pytest.approx(1.5e8 / 4e-3 / 1e9)      # merge bytes / time
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["longest_chain"] == 8 and r["us_per_chain_addition"] == pytest.approx(500.0)
     rg = d["roofline_gradient"]            # N*s_in + 8*|C| over classify+compact+PLS
     assert rg["algorithmic_bytes_per_launch"] == 16 ** 3 * 2 + 8 * 100
     assert rg["achieved"] == pytest.approx((16 ** 3 * 2 + 800) / 3e-3 / 1e9)
@@ -175,3 +181,20 @@ def test_dominant_pls_reports_the_issue_rate(fake_device, monkeypatch):
     monkeypatch.setitem(fake_device.PLS_ISSUE, "sources_sha256", "stale")
     d = _run(fake_device, {"no_serve": True})
     assert d["roofline"]["achieved"] is None and d["roofline"]["frac"] is None
+
+
+def test_dominant_trace_reports_its_record_bytes(fake_device, monkeypatch):
+    """When the D1 trace takes the most time, the headline roofline is its
+    record reads (per toggle: record, flag, value, row word; per column: its
+    entry, record and output slot) over its time, against HBM."""
+    def kms(self):
+        return {k: (9.0 if k == "d1_trace" else 1.0) for k in self.KERNELS}
+    import paper_2206_13932_gb300 as dms
+    monkeypatch.setattr(dms.Grid, "kernel_ms", kms)
+    d = _run(fake_device, {"no_serve": True})
+    r = d["roofline"]
+    assert r == d["roofline_d1_trace"] and r["bound"] == "hbm"
+    nbytes = 1000 * (48 + 1 + 2 + 8) + 25 * (9 + 48 + 13)
+    assert r["algorithmic_bytes_per_launch"] == nbytes
+    assert r["achieved"] == pytest.approx(nbytes / 9e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])

@@ -100,6 +100,7 @@ def test_argument_checks_without_gpu():
     assert lib.dms_get_stage_ms(null, (ctypes.c_float * 8)()) == bad
     assert lib.dms_get_kernel_ms(null, (ctypes.c_float * 12)()) == bad
     assert lib.dms_get_stats(null, (ctypes.c_int64 * 16)()) == bad
+    assert lib.dms_get_work(null, (ctypes.c_int64 * 4)()) == bad
     assert lib.dms_get_device_bytes(null, ctypes.byref(w)) == bad
     assert lib.dms_set_tuning(null, (ctypes.c_int32 * 10)(), 10) == bad
     assert lib.dms_get_tuning(null, (ctypes.c_int32 * 10)(), 10) == bad
