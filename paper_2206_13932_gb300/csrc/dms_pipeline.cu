@@ -1197,129 +1197,76 @@ __device__ __noinline__ GradRec grad_fill(const StarTables &S, const GridParams 
 
 // ------------------------------------------------------ stage 5: D2 arcs
 
-// Tet h of the star of y, whose highest vertex is y + dlin[bl], as a tet of
-// the star of that vertex (false: not a tet of the stencil, an error).
-__device__ __forceinline__ bool tet_in_star_of(const StarTables &S, int h, int bl, int &hn) {
-    const int ox = -S.dx[bl], oy = -S.dy[bl], oz = -S.dz[bl];
-    const int ly = S.link_of_dc[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
-    if (ly < 0) return false;
-    int lks[2], nk = 0;
-    for (int k = 0; k < 3; k++) {
-        const int l = S.tet_v[h][k];
-        if (l == bl) continue;
-        const int ex = S.dx[l] + ox, ey = S.dy[l] + oy, ez = S.dz[l] + oz;
-        if (ex < -1 || ex > 1 || ey < -1 || ey > 1 || ez < -1 || ez > 1 || nk >= 2) return false;
-        const int lk = S.link_of_dc[(ex + 1) + 3 * (ey + 1) + 9 * (ez + 1)];
-        if (lk < 0) return false;
-        lks[nk++] = lk;
-    }
-    if (nk != 2) return false;
-    // the star tet on links (ly, lks[0], lks[1]): one of the (at most two)
-    // star tets on the star triangle (lks[0], lks[1])
-    const int sf = S.tri_of_pair[lks[0]][lks[1]];
-    if (sf < 0) return false;
-    hn = -1;
-    for (uint32_t cm = S.tets_of_tri[sf]; cm; cm &= cm - 1) {
-        const int q = __ffs(cm) - 1;
-        if (S.tet_mask[q] >> ly & 1) hn = q;
-    }
-    return hn >= 0;
-}
-
-// Per critical vertex: its critical star tets (bits 32-55) and the C3 index
-// of the first (bits 0-31), so that the ascending walks test a tet with the
-// loads of a step instead of two more dependent ones.
-__global__ void k_tet_words(const int32_t *__restrict__ vc, int64_t nc,
-                            const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
-                            unsigned long long *tw) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nc) return;
-    tw[vc[i]] = ((unsigned long long)recs[i].crit_h << 32) | (uint32_t)base3[i];
-}
-
 // The critical tet (node index) or the virtual maximum reached from tet h of
 // the star of y by the ascending walk of the dual gradient (Sec. 5.2): a
 // regular tet is the head of a triangle->tet vector; cross that triangle to
-// its other tet; the outer boundary is the virtual maximum.  The walk keeps
-// the highest vertex y of its tet with y's record: crossing a face of the
-// lower star of y reaches a tet with one new vertex, and only when that
-// vertex is higher does the walk move there.  Its value, flag, tet word and
-// record are loaded together (the record speculatively, when every record is
-// precomputed), so a step waits on one round trip.
+// its other tet; the outer boundary is the virtual maximum.
 template <typename T>
 __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__restrict__ values,
-                          uint8_t *flags, GradRec *grad, const unsigned long long *__restrict__ tw,
+                          uint8_t *flags, GradRec *grad, const int32_t *__restrict__ vrank,
+                          const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
                           int64_t y, int h, int32_t vmax, int64_t max_steps, bool dense,
                           DevStatus *st) {
     using K = typename Key<T>::K;
     int cx, cy, cz;     // coordinates of y, followed as the walk moves
     coords(g, y, cx, cy, cz);
-    // the highest vertex of the first tet
-    K ky = Key<T>::of(values[y]);
-    {
+    for (int64_t step = 0; step < max_steps; step++) {
+        // the maximum vertex of the tet
+        K kb = Key<T>::of(values[y]);
         int64_t best = y;
         int bl = -1;
         for (int k = 0; k < 3; k++) {
-            const int l = S.tet_v[h][k];
-            const int64_t v = y + g.dlin[l];
-            const K kv = Key<T>::of(values[v]);
-            if (kv > ky || (kv == ky && v > best)) { ky = kv; best = v; bl = l; }
+            int l = S.tet_v[h][k];
+            int64_t v = y + g.dlin[l];
+            K kv = Key<T>::of(values[v]);
+            if (kv > kb || (kv == kb && v > best)) { kb = kv; best = v; bl = l; }
         }
-        if (bl >= 0) {
-            int hn;
-            if (!tet_in_star_of(S, h, bl, hn)) { atomicOr(&st->err, kErrState); return vmax; }
+        if (bl >= 0) {   // re-express the tet in the star of its maximum vertex
+            int ox = -S.dx[bl], oy = -S.dy[bl], oz = -S.dz[bl];
+            int ly = S.link_of_dc[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
+            if (ly < 0) { atomicOr(&st->err, kErrState); return vmax; }
+            int lks[2], nk = 0;
+            for (int k = 0; k < 3; k++) {
+                int l = S.tet_v[h][k];
+                if (l == bl) continue;
+                int ex = S.dx[l] + ox, ey = S.dy[l] + oy, ez = S.dz[l] + oz;
+                if (ex < -1 || ex > 1 || ey < -1 || ey > 1 || ez < -1 || ez > 1 || nk >= 2) {
+                    atomicOr(&st->err, kErrState);
+                    return vmax;
+                }
+                int lk = S.link_of_dc[(ex + 1) + 3 * (ey + 1) + 9 * (ez + 1)];
+                if (lk < 0) { atomicOr(&st->err, kErrState); return vmax; }
+                lks[nk++] = lk;
+            }
+            if (nk != 2) { atomicOr(&st->err, kErrState); return vmax; }
+            // the star tet on links (ly, lks[0], lks[1]): one of the (at most
+            // two) star tets on the star triangle (lks[0], lks[1])
+            const int sf = S.tri_of_pair[lks[0]][lks[1]];
+            if (sf < 0) { atomicOr(&st->err, kErrState); return vmax; }
+            int hn = -1;
+            for (uint32_t cm = S.tets_of_tri[sf]; cm; cm &= cm - 1) {
+                const int q = __ffs(cm) - 1;
+                if (S.tet_mask[q] >> ly & 1) hn = q;
+            }
+            if (hn < 0) { atomicOr(&st->err, kErrState); return vmax; }
             y = best;
             cx += S.dx[bl]; cy += S.dy[bl]; cz += S.dz[bl];
             h = hn;
         }
-    }
-    uint8_t fy = dense ? __ldg(flags + y) : ((volatile const uint8_t *)flags)[y];
-    unsigned long long twy = tw[y];
-    GradRec G = grad_get(S, g, values, flags, grad, y, dense);
-    for (int64_t step = 0; step < max_steps; step++) {
-        if ((fy & kFlagCritical) && (twy >> (32 + h) & 1)) {
-            // its index: the vertex's first, plus its critical tets of lower G
-            uint8_t r[kLinks];
-            unpack_ranks(G.w[5], r);
-            const uint16_t ch = code_tet(S, r, h);
-            int k = 0;
-            for (uint32_t m = (uint32_t)(twy >> 32); m; m &= m - 1)
-                k += code_tet(S, r, __ffs(m) - 1) < ch;
-            return (int32_t)(uint32_t)twy + k;
+        if (flags[y] & kFlagCritical) {
+            int32_t i = vrank[y];
+            CritRec rec = recs[i];
+            if (rec.crit_h >> h & 1) return base3[i] + local_index(S, rec, 3, h);
         }
-        const int s2 = grad_tet_pair(G, h);
+        GradRec G = grad_get(S, g, values, flags, grad, y, dense);
+        int s2 = grad_tet_pair(G, h);
         if (s2 >= kTris) { atomicOr(&st->err, kErrState); return vmax; }
-        const uint32_t other = S.tets_of_tri[s2] & ~(1u << h);
+        uint32_t other = S.tets_of_tri[s2] & ~(1u << h);
         if (!other) { atomicOr(&st->err, kErrState); return vmax; }
-        const int h2 = __ffs(other) - 1;
-        const int w = __ffs(S.tet_mask[h2] & ~S.tri_mask[s2]) - 1;
+        int h2 = __ffs(other) - 1;
+        int w = __ffs(S.tet_mask[h2] & ~S.tri_mask[s2]) - 1;
         if (!(present_links(S, g, cx, cy, cz) >> w & 1)) return vmax;   // the outer boundary
-        const int64_t v = y + g.dlin[w];
-        const K kv = Key<T>::of(values[v]);
-        const uint8_t fv = dense ? __ldg(flags + v) : ((volatile const uint8_t *)flags)[v];
-        const unsigned long long twv = tw[v];
-        GradRec Gv;
-        if (dense) {
-            const ulonglong2 *src = (const ulonglong2 *)&grad[v];
-            for (int k = 0; k < 3; k++) {
-                const ulonglong2 q = __ldg(src + k);
-                Gv.w[2 * k] = q.x;
-                Gv.w[2 * k + 1] = q.y;
-            }
-        }
-        if (kv < ky || (kv == ky && v < y)) {   // h2 lies in the lower star of y
-            h = h2;
-            continue;
-        }
-        int hn;
-        if (!tet_in_star_of(S, h2, w, hn)) { atomicOr(&st->err, kErrState); return vmax; }
-        y = v;
-        ky = kv;
-        fy = fv;
-        twy = twv;
-        G = dense ? Gv : grad_get(S, g, values, flags, grad, y, false);
-        cx += S.dx[w]; cy += S.dy[w]; cz += S.dz[w];
-        h = hn;
+        h = h2;
     }
     atomicOr(&st->err, kErrIter);
     return vmax;
@@ -1327,7 +1274,8 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
 
 template <typename T, bool Bt>
 __global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *flags,
-                          GradRec *grad, const unsigned long long *__restrict__ tw,
+                          GradRec *grad, const int32_t *__restrict__ vrank,
+                          const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
                           const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
                           int64_t n2, const int32_t *__restrict__ order, int32_t vmax,
                           int vmax_on, int32_t *A, int32_t *B, int32_t *young, int64_t max_steps,
@@ -1352,7 +1300,7 @@ __global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *fl
         int h = __ffs(m) - 1;
         m &= m - 1;
         int w = __ffs(S.tet_mask[h] & ~S.tri_mask[s]) - 1;
-        ends[e] = (pres >> w & 1) ? ascend(S, g, values, flags, grad, tw, x, h,
+        ends[e] = (pres >> w & 1) ? ascend(S, g, values, flags, grad, vrank, recs, base3, x, h,
                                            vmax, max_steps, dense != 0, st)
                                   : vmax;
     }
@@ -1433,10 +1381,6 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
                              const unsigned long long *__restrict__ vcrit, int64_t y, int m,
                              DevStatus *st) {
     if (m < 0 || m >= kLinks) { atomicOr(&st->err, kErrState); c.overflow = true; return; }
-    // the edge's first hash slot is read beside the vertex's words
-    const unsigned long long key = (((unsigned long long)y << 4) | (unsigned)m) + 1;
-    const uint32_t hpos = hash64(key) & c.hashmask;
-    const HashEnt e0 = c.hash[hpos];
     const uint8_t fy = c.dense ? __ldg(flags + y) : ((volatile const uint8_t *)flags)[y];
     const T vy = values[y];
     const unsigned long long cw = vcrit[y];   // read beside the others; used if y is critical
@@ -1453,19 +1397,17 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
     // a passive entry in the generator mode
     const bool head = (fy & 0xF) == m;
     if (head && !c.gens) return;
-    const bool crit = (fy & kFlagCritical) && (cw >> (32 + m) & 1);
-    // a critical edge paired in D0 is dropped as well (never hashed) unless
-    // the generator mode keeps it as a passive entry
-    if (crit && !(cw >> (48 + m) & 1) && !c.gens) return;
+    unsigned long long key = (((unsigned long long)y << 4) | (unsigned)m) + 1;
+    uint32_t hpos = hash64(key) & c.hashmask;
     HashEnt *slot = nullptr;
     for (int p = 0; p <= c.hashmask; p++) {
         HashEnt *e = &c.hash[(hpos + p) & c.hashmask];
-        const int32_t eg = p ? e->gen : e0.gen;
-        if (eg != c.gen) { slot = e; break; }
-        if ((p ? e->key : e0.key) == key) { e->info ^= 1u << 31; return; }
+        if (e->gen != c.gen) { slot = e; break; }
+        if (e->key == key) { e->info ^= 1u << 31; return; }
     }
     if (!slot || c.used * 4 >= (c.hashmask + 1) * 3) { c.overflow = true; return; }
     uint32_t info;
+    const bool crit = (fy & kFlagCritical) && (cw >> (32 + m) & 1);
     if (head || (crit && !(cw >> (48 + m) & 1))) {
         // a head, or a critical edge paired in D0 (dropped unless generator mode
         // -- heads returned above then): a passive entry -(edge id + 1)
@@ -4588,13 +4530,9 @@ dms_status d2_walks(Ctx &c, const T *values, const Geo<B> &geo, int64_t n2, int3
     KEV(14);
     const int32_t *order2 = nullptr;
     DMS_TRY(order_by_vertex(c, P.c_vert[2].as<int32_t>(), nullptr, n2, 0, &order2));
-    // the tet words share the buffer of the D1 trace's row words (written later)
-    DMS_ALLOC(P.vcrit, 8 * P.n + 8);
-    DMS_LAUNCH(P.n_crit, 256, k_tet_words, P.vc.as<int32_t>(), P.n_crit, P.recs.as<CritRec>(),
-               P.base[3].as<int32_t>(), P.vcrit.as<unsigned long long>());
     DMS_LAUNCH(n2, 128, (k_d2_arcs<T, B>), values, geo, P.flags.as<uint8_t>(),
-               P.grad.as<GradRec>(), P.vcrit.as<unsigned long long>(),
-               P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(), n2,
+               P.grad.as<GradRec>(), P.vrank.as<int32_t>(), P.recs.as<CritRec>(),
+               P.base[3].as<int32_t>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(), n2,
                order2, vmax, P.virtual_max, P.arc2_a.as<int32_t>(), P.arc2_b.as<int32_t>(),
                young2, max_steps, P.dense_grad ? 1 : 0, c.st);
     KEV(15);
