@@ -1312,10 +1312,6 @@ __global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *fl
 
 // ------------------------------------------ stage 6: D1 boundary tracing
 
-// The trace's per-thread scratch is interleaved by warp: entry k of lane l
-// at [k][l], so the lanes' entries of one index share sectors.
-constexpr int kTs = 32;
-
 struct TraceCtx {
     HeapEnt *heap;
     HashEnt *hash;
@@ -1346,27 +1342,27 @@ __device__ void heap_push(TraceCtx &c, HeapEnt e) {
     int i = c.hn++;
     while (i > 0) {
         int p = (i - 1) >> 1;
-        if (!heap_less(c.heap[p * kTs], e)) break;
-        c.heap[i * kTs] = c.heap[p * kTs];
+        if (!heap_less(c.heap[p], e)) break;
+        c.heap[i] = c.heap[p];
         i = p;
     }
-    c.heap[i * kTs] = e;
+    c.heap[i] = e;
 }
 
 __device__ HeapEnt heap_pop(TraceCtx &c) {
     HeapEnt top = c.heap[0];
-    HeapEnt last = c.heap[(--c.hn) * kTs];
+    HeapEnt last = c.heap[--c.hn];
     int i = 0;
     while (true) {
         int l = 2 * i + 1;
         if (l >= c.hn) break;
         int r = l + 1;
-        int m = (r < c.hn && heap_less(c.heap[l * kTs], c.heap[r * kTs])) ? r : l;
-        if (!heap_less(last, c.heap[m * kTs])) break;
-        c.heap[i * kTs] = c.heap[m * kTs];
+        int m = (r < c.hn && heap_less(c.heap[l], c.heap[r])) ? r : l;
+        if (!heap_less(last, c.heap[m])) break;
+        c.heap[i] = c.heap[m];
         i = m;
     }
-    if (c.hn > 0) c.heap[i * kTs] = last;
+    if (c.hn > 0) c.heap[i] = last;
     return top;
 }
 
@@ -1405,7 +1401,7 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
     uint32_t hpos = hash64(key) & c.hashmask;
     HashEnt *slot = nullptr;
     for (int p = 0; p <= c.hashmask; p++) {
-        HashEnt *e = &c.hash[((hpos + p) & c.hashmask) * kTs];
+        HashEnt *e = &c.hash[(hpos + p) & c.hashmask];
         if (e->gen != c.gen) { slot = e; break; }
         if (e->key == key) { e->info ^= 1u << 31; return; }
     }
@@ -1417,8 +1413,8 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
         // -- heads returned above then): a passive entry -(edge id + 1)
         if (!c.gens) return;
         if (c.rn >= c.rcap) { c.overflow = true; return; }
-        c.rows[c.rn * kTs] = (int32_t)(-1 - edge_id(S, g, y, m));
-        c.rslot[c.rn * kTs] = (int32_t)((slot - c.hash) / kTs);
+        c.rows[c.rn] = (int32_t)(-1 - edge_id(S, g, y, m));
+        c.rslot[c.rn] = (int32_t)(slot - c.hash);
         c.rn++;
         slot->key = key;
         slot->gen = c.gen;
@@ -1435,8 +1431,8 @@ __device__ void trace_toggle(TraceCtx &c, const StarTables &S, const GridParams 
             for (uint32_t q = (uint32_t)(cw >> 32) & kAllLinks; q; q &= q - 1)
                 j1 += grad_rank(G, __ffs(q) - 1) < rm;
             if (c.rn >= c.rcap) { c.overflow = true; return; }
-            c.rows[c.rn * kTs] = j1;
-            c.rslot[c.rn * kTs] = (int32_t)((slot - c.hash) / kTs);
+            c.rows[c.rn] = j1;
+            c.rslot[c.rn] = (int32_t)(slot - c.hash);
             info = hinfo((uint32_t)c.rn, 0, kKindRow, 1);
             c.rn++;
             slot->key = key;
@@ -1474,7 +1470,7 @@ __device__ __forceinline__ HashEnt *trace_find(TraceCtx &c, int64_t y, int m) {
     unsigned long long key = (((unsigned long long)y << 4) | (unsigned)m) + 1;
     uint32_t hpos = hash64(key) & c.hashmask;
     for (int p = 0; p <= c.hashmask; p++) {
-        HashEnt *e = &c.hash[((hpos + p) & c.hashmask) * kTs];
+        HashEnt *e = &c.hash[(hpos + p) & c.hashmask];
         if (e->gen != c.gen) return nullptr;
         if (e->key == key) return e;
     }
@@ -1503,11 +1499,10 @@ __global__ void __launch_bounds__(256, 4)
     TraceCtx c;
     c.dense = dense != 0;
     c.gens = gens != 0;
-    const int64_t wbase = tid - lane;                 // the warp's first thread
-    c.heap = heap_all + wbase * hcap + lane;
-    c.hash = hash_all + wbase * hashcap + lane;
-    c.rows = rows_all + wbase * 2 * rcap + lane;
-    c.rslot = c.rows + kTs * rcap;
+    c.heap = heap_all + tid * hcap;
+    c.hash = hash_all + tid * hashcap;
+    c.rows = rows_all + tid * 2 * rcap;
+    c.rslot = c.rows + rcap;
     c.hcap = hcap; c.hashmask = hashcap - 1; c.rcap = rcap;
     int32_t cj = -1;
     bool done = false;
@@ -1604,16 +1599,12 @@ __global__ void __launch_bounds__(256, 4)
         // the rows with odd multiplicity, sorted decreasingly
         int len = 0;
         for (int k = 0; k < c.rn; k++)
-            if (hinfo_parity(c.hash[c.rslot[k * kTs] * kTs].info))
-                c.rows[(len++) * kTs] = c.rows[k * kTs];
+            if (hinfo_parity(c.hash[c.rslot[k]].info)) c.rows[len++] = c.rows[k];
         for (int k = 1; k < len; k++) {
-            const int32_t v = c.rows[k * kTs];
+            const int32_t v = c.rows[k];
             int p = k;
-            while (p > 0 && c.rows[(p - 1) * kTs] < v) {
-                c.rows[p * kTs] = c.rows[(p - 1) * kTs];
-                p--;
-            }
-            c.rows[p * kTs] = v;
+            while (p > 0 && c.rows[p - 1] < v) { c.rows[p] = c.rows[p - 1]; p--; }
+            c.rows[p] = v;
         }
         overflow[col] = 0;
         if (len == 0) { col_len[col] = 0; col_start[col] = 0; continue; }
@@ -1623,7 +1614,7 @@ __global__ void __launch_bounds__(256, 4)
             col_len[col] = 0;
             continue;
         }
-        for (int k = 0; k < len; k++) pool[pos + k] = c.rows[k * kTs];
+        for (int k = 0; k < len; k++) pool[pos + k] = c.rows[k];
         col_start[col] = (int64_t)pos;
         col_len[col] = len;
     }
