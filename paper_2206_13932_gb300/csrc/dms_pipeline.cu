@@ -46,6 +46,7 @@ struct DevStatus {
     long long misc[4];
     long long bx[4];               // block expansions: nodes, levels (discovery, order), columns
     unsigned long long trace_next; // D1 trace: next column to take
+    unsigned long long red_work;   // D1 reduction round: columns that add this round
     unsigned long long trace_work[2];   // D1 trace: edges toggled, edges expanded
 };
 
@@ -1774,35 +1775,60 @@ __device__ int warp_symdiff(const int32_t *A, int la, const int32_t *B, int lb, 
     return total;
 }
 
-// One warp per listed column (active or displaced): while its pivot is owned
-// by an earlier column, add that column (mod 2).  Owners never change inside
-// this kernel (a column owns a row only while the row is its pivot, and
-// claims happen in k_red_claim), so every column added is stable.  Stops at
-// its own pivot, an unclaimed pivot or one claimed by a later column (those
-// claim it in the next round).  A column listed twice is processed once.
+// The listed columns (active, then displaced owners) that add something in
+// this round: their pivot is owned by an earlier column.  One thread per
+// entry, so the common case -- a column that owns its pivot, or whose pivot
+// is free or owned by a later column -- costs one thread's loads instead of
+// a warp's turn; each column is taken once per round (stamp).  Owners do not
+// change until the next claims, so the list is exactly the columns that
+// k_red_add changes.
+__global__ void k_red_need(const int32_t *__restrict__ active, int64_t nactive,
+                           const int32_t *__restrict__ recheck,
+                           const int64_t *__restrict__ start, const int32_t *__restrict__ len,
+                           const int32_t *__restrict__ pool, const RowCol *__restrict__ rowcol,
+                           int32_t *stamp, int32_t round, int32_t *work, DevStatus *st) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nre = *(volatile long long *)&st->misc[0];
+    bool take = false;
+    int32_t cj = 0;
+    if (q < nactive + nre) {
+        cj = q < nactive ? active[q] : recheck[q - nactive];
+        if (atomicExch(&stamp[cj], round) != round && len[cj] > 0) {
+            const int32_t head = pool[start[cj]];
+            if (head >= 0) {
+                const int32_t k = rowcol[head].col;
+                take = k != kNoOwner && k < cj;
+            }
+        }
+    }
+    warp_append(take, cj, work, &st->red_work);
+}
+
+// One warp per column of the round's work list (k_red_need): while its pivot
+// is owned by an earlier column, add that column (mod 2).  Owners never
+// change inside this kernel (a column owns a row only while the row is its
+// pivot, and claims happen in k_red_claim), so every column added is stable.
+// Stops at its own pivot, an unclaimed pivot or one claimed by a later
+// column (those claim it in the next round).
 // Short columns stay in the warp's shared memory through their chain (the
 // merge-path searches then probe shared memory, not the pool), and the
 // added column is staged there too; the result is written to the pool once.
 constexpr int kWarpAcc = 256;
 __global__ void __launch_bounds__(256)
-    k_red_add(const int32_t *__restrict__ active, int64_t nactive,
-              const int32_t *__restrict__ recheck, int64_t *start, int32_t *len, int32_t *pool,
-              const RowCol *__restrict__ rowcol, int32_t *stamp, int32_t round, int32_t *next,
-              int64_t pool_cap, DevStatus *st) {
+    k_red_add(const int32_t *__restrict__ work, int64_t *start, int32_t *len, int32_t *pool,
+              const RowCol *__restrict__ rowcol, int32_t *next, int64_t pool_cap,
+              DevStatus *st) {
     __shared__ int32_t wsm[8][3 * kWarpAcc];
     const int lane = threadIdx.x & 31;
     int32_t *acc[2] = {wsm[threadIdx.x >> 5], wsm[threadIdx.x >> 5] + kWarpAcc};
     int32_t *stg = wsm[threadIdx.x >> 5] + 2 * kWarpAcc;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nre = *(volatile long long *)&st->misc[0];
+    const int64_t nwork = (int64_t)*(volatile unsigned long long *)&st->red_work;
     unsigned adds = 0, longest = 0;
     unsigned long long io_r = 0, io_w = 0;
-    for (int64_t q = warp; q < nactive + nre; q += nwarps) {
-        int32_t cj = q < nactive ? active[q] : recheck[q - nactive];
-        int fresh = 0;
-        if (lane == 0) fresh = atomicExch(&stamp[cj], round) != round;
-        if (!__shfl_sync(0xffffffffu, fresh, 0)) continue;
+    for (int64_t q = warp; q < nwork; q += nwarps) {
+        const int32_t cj = work[q];
         int la = len[cj];
         int64_t sa = start[cj];
         bool resident = la <= kWarpAcc;
@@ -3889,6 +3915,7 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
     DMS_ALLOC(P.d1_next, 4 * 3 * ncol + 4);
     DMS_ALLOC(P.d1_re, 4 * ncol + 4);
     DMS_ALLOC(P.d1_stamp, 4 * ncol + 4);
+    DMS_ALLOC(P.d1_work, 4 * 2 * ncol + 4);
     DMS_CUDA(cudaMemsetAsync(P.d1_owner.p, 0x7F, 4 * nent + 4, c.s));
     DMS_CUDA(cudaMemsetAsync(rowcol, 0x7F, sizeof(RowCol) * (nent + 1), c.s));
     DMS_CUDA(cudaMemsetAsync(P.d1_stamp.p, 0xFF, 4 * ncol + 4, c.s));
@@ -3935,11 +3962,16 @@ dms_status reduce_columns(Ctx &c, int64_t ncol, int64_t nent, int64_t pool_used)
                    P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
                    P.d1_owner.as<int32_t>(), rowcol);
         if (nactive > below) {
+            // the columns that add something (displaced owners included: at
+            // most one per claim), then a warp for each of them
+            DMS_CUDA(cudaMemsetAsync(&c.st->red_work, 0, sizeof(unsigned long long), c.s));
+            DMS_LAUNCH(2 * nactive, 256, k_red_need, P.d1_act.as<int32_t>(), nactive,
+                       P.d1_re.as<int32_t>(), P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+                       P.d1_pool.as<int32_t>(), rowcol, P.d1_stamp.as<int32_t>(), (int32_t)stamp,
+                       P.d1_work.as<int32_t>(), c.st);
             DMS_LAUNCH(std::min<int64_t>(64 * nactive, (int64_t)152 * 64 * 256), 256, k_red_add,
-                       P.d1_act.as<int32_t>(), nactive, P.d1_re.as<int32_t>(),
-                       P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(), P.d1_pool.as<int32_t>(),
-                       rowcol, P.d1_stamp.as<int32_t>(), (int32_t)stamp,
-                       P.d1_next.as<int32_t>(), pool_cap, c.st);
+                       P.d1_work.as<int32_t>(), P.d1_start.as<int64_t>(), P.d1_len.as<int32_t>(),
+                       P.d1_pool.as<int32_t>(), rowcol, P.d1_next.as<int32_t>(), pool_cap, c.st);
         } else {
             // one block per column (grid covers active + displaced, <= 2x active)
             k_red_add_block<<<(unsigned)(2 * nactive), kRedBlock, kRedSmem, c.s>>>(
@@ -5159,7 +5191,7 @@ dms_status Pipeline::reshape(int64_t nx_, int64_t ny_, int64_t nz_) {
 // Every device buffer of the handle.
 std::vector<DevBuf *> Pipeline::buffers() {
     std::vector<DevBuf *> all = {&d1_row, &d1_rowpaired, &d1_rowpos, &d1_rowmap, &d1_cocnt, &d1_costart,
-                     &d1_cofill, &d1_act, &d1_next, &d1_re, &d1_stamp, &grad, &values_dev, &flags,    &vrank,     &tile_cnt,  &tile_off,   &vc,
+                     &d1_cofill, &d1_act, &d1_next, &d1_re, &d1_stamp, &d1_work, &grad, &values_dev, &flags,    &vrank,     &tile_cnt,  &tile_off,   &vc,
                      &vc_tmp,     &keys,     &keys_tmp,  &recs,      &arc_a,      &arc_b,
                      &dc_keys,    &dc_par,   &dc_lab,    &bv_node,   &bv_msf,    &bv_arcs,
                      &young,     &died,       &rowcol,

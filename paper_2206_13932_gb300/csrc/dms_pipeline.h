@@ -56,7 +56,7 @@ struct Pipeline {
     DevBuf arc_a, arc_b, young, died, rowcol, flag_a, flag_b;
     DevBuf dc_keys, dc_par, dc_lab;   // elder-rule halving levels
     DevBuf bv_node, bv_msf, bv_arcs;  // elder rule: spanning-forest nodes, flags, arcs
-    DevBuf d1_act, d1_next, d1_re, d1_stamp;   // D1 reduction work lists
+    DevBuf d1_act, d1_next, d1_re, d1_stamp, d1_work;   // D1 reduction work lists
     DevBuf d1_row, d1_rowpaired;               // D1 result per column / row
     DevBuf d1_rowpos, d1_rowmap, d1_cocnt, d1_costart, d1_cofill;   // transpose
     DevBuf d1_colmap, d1_start, d1_len, d1_owner, d1_ovf, d1_pool, d1_scratch, d1_todo;
