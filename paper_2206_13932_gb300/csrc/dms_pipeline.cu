@@ -714,14 +714,12 @@ __global__ void k_pls(const T *__restrict__ values, Geo<B> geo, const int32_t *_
 // The same in two passes, for fields whose stars vary widely (noise): the
 // work of a lower star depends on its shape (which links are lower) and
 // grows with its size.  The first pass loads each star in id order
-// (coalesced stencils) and keeps its sort key -- the lower mask, then the
-// links of the three lowest lower neighbours -- its position and its link
-// ranks (4 bits a link); the stars are then sorted by that key over the
-// whole grid, and the second pass runs ProcessLowerStars in that order, so
-// the 32 threads of a warp share one shape and mostly the same first steps.
-// Each warp and block finishes on its own: no barrier ties a fast star to a
-// slow one.
-constexpr int kPlsKeyBits = kLinks + 12;
+// (coalesced stencils) and keeps its lower mask as a sort key, its position
+// and its link ranks (4 bits a link); the stars are then sorted by mask over
+// the whole grid, and the second pass runs ProcessLowerStars in that order,
+// so the 32 threads of a warp share one shape and only the order of the
+// lower links differs between them.  Each warp and block finishes on its
+// own: no barrier ties a fast star to a slow one.
 template <typename T, bool B>
 __global__ void __launch_bounds__(256)
     k_pls_keys(const T *__restrict__ values, Geo<B> geo, const int32_t *__restrict__ list,
@@ -735,11 +733,7 @@ __global__ void __launch_bounds__(256)
     unsigned long long rk = 0;
     for (int n = 0; n < kLinks; n++) rk |= (unsigned long long)(sv.rank[n] & 15) << (4 * n);
     ranks[i] = rk;
-    uint32_t low3 = 0xFFFu;                    // links of rank 0, 1, 2 (15: none)
-    for (int n = 0; n < kLinks; n++)
-        if ((sv.lower >> n & 1) && sv.rank[n] < 3)
-            low3 = (low3 & ~(0xFu << (8 - 4 * sv.rank[n]))) | ((uint32_t)n << (8 - 4 * sv.rank[n]));
-    key[i] = ((uint32_t)sv.lower << 12) | low3;
+    key[i] = sv.lower;
     pos[i] = (int32_t)i;
     // the second pass fills the record before any later kernel reads it
     flags[x] = (uint8_t)(flags[x] | kFlagGradient);
@@ -758,7 +752,7 @@ __global__ void k_pls_run(const int32_t *__restrict__ list, const uint32_t *__re
     for (int n = 0; n < kLinks; n++) rank[n] = (uint8_t)((rk >> (4 * n)) & 15);
     PLSResult R;
     GradRec G;
-    pls(g_star, (uint16_t)((key[i] >> 12) & kAllLinks), rank, R, &G);
+    pls(g_star, (uint16_t)(key[i] & kAllLinks), rank, R, &G);
     grad[x] = G;
 }
 
@@ -4487,7 +4481,7 @@ dms_status launch_pls(Ctx &c, const T *values, const Geo<B> &geo, const int32_t 
                                                               rk, fl);
     c.launches++;
     DMS_CUDA(cudaGetLastError());
-    DMS_TRY(radix_u32(c, kin, vin, kout, vout, count, kPlsKeyBits, rtiles));
+    DMS_TRY(radix_u32(c, kin, vin, kout, vout, count, kLinks, rtiles));
     k_pls_run<<<blocks_for(count, nt), nt, 0, c.s>>>(list, kin, vin, rk, count, gr);
     c.launches++;
     DMS_CUDA(cudaGetLastError());
