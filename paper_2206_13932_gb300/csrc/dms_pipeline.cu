@@ -1043,6 +1043,58 @@ __global__ void k_dc_relabel(int64_t narcs, int shift, int descending, int32_t *
     }
 }
 
+// The last levels at once: segments of 2^kDcSegBits consecutive turns, each
+// taken through its arcs in turn order by one warp, with a union-find over
+// the segment's labels in shared memory (the lanes register the labels, then
+// lane 0 walks the arcs).  Within a segment this is what the remaining
+// halving levels compute: every arc gets the components at its own turn,
+// each named by its oldest label.
+constexpr int kDcSegBits = 8, kDcSeg = 1 << kDcSegBits, kDcSegSlots = 4 * kDcSeg;
+__global__ void __launch_bounds__(32)
+    k_dc_segment(int64_t narcs, int descending, int older_is_larger, int32_t *A, int32_t *B,
+                 DevStatus *st) {
+    __shared__ int32_t lab[kDcSegSlots];    // label of each slot (-1: free)
+    __shared__ int16_t par[kDcSegSlots];    // union-find parent (a slot)
+    __shared__ int16_t ends[2 * kDcSeg];    // each arc's two slots, in turn order
+    const int lane = threadIdx.x;
+    const int64_t t0 = (int64_t)blockIdx.x * kDcSeg;
+    const int cnt = (int)(narcs - t0 < kDcSeg ? narcs - t0 : kDcSeg);
+    for (int i = lane; i < kDcSegSlots; i += 32) lab[i] = -1;
+    __syncwarp();
+    for (int k = lane; k < cnt; k += 32) {
+        const int64_t j = dc_time(t0 + k, narcs, descending);   // the arc of turn t0 + k
+        for (int e = 0; e < 2; e++) {
+            const int32_t v = e ? B[j] : A[j];
+            const uint32_t h = hash_key((unsigned long long)(uint32_t)v) & (kDcSegSlots - 1);
+            int sl = -1;
+            for (int p = 0; p < kDcSegSlots; p++) {   // at most 2 * kDcSeg labels: never full
+                const int q = (int)((h + p) & (kDcSegSlots - 1));
+                const int32_t old = atomicCAS(&lab[q], -1, v);
+                if (old == -1 || old == v) { sl = q; break; }
+            }
+            if (sl < 0) { atomicOr(&st->err, kErrCap); sl = 0; }
+            par[sl] = (int16_t)sl;
+            ends[2 * k + e] = (int16_t)sl;
+        }
+    }
+    __syncwarp();
+    if (lane != 0) return;
+    for (int k = 0; k < cnt; k++) {
+        int ra = ends[2 * k], rb = ends[2 * k + 1];
+        while (par[ra] != ra) { par[ra] = par[par[ra]]; ra = par[ra]; }
+        while (par[rb] != rb) { par[rb] = par[par[rb]]; rb = par[rb]; }
+        const int64_t j = dc_time(t0 + k, narcs, descending);
+        const int32_t la = lab[ra], lb = lab[rb];
+        A[j] = la;
+        B[j] = lb;
+        if (ra != rb) {
+            const bool a_older = older_is_larger ? la > lb : la < lb;
+            if (a_older) par[rb] = (int16_t)ra;
+            else par[ra] = (int16_t)rb;
+        }
+    }
+}
+
 // ------------------------------- minimum spanning forest of an arc graph
 //
 // Only the arcs of the minimum spanning forest (weight = the arc's turn,
@@ -3804,12 +3856,17 @@ dms_status elder_rule(Ctx &c, int32_t *A, int32_t *B, int64_t narcs, int64_t nno
     DcSlot *tab = P.dc_keys.as<DcSlot>();
     // cleared once: the keys of each level tell its slots from earlier levels
     DMS_CUDA(cudaMemsetAsync(tab, 0xFF, sizeof(DcSlot) * (size_t)cap, c.s));
-    for (int shift = L; shift >= 1; shift--) {
+    for (int shift = L; shift > kDcSegBits; shift--) {
         DMS_LAUNCH(m, 256, k_dc_insert, m, shift, descending, A2, B2, tab, cap - 1, c.st);
         DMS_LAUNCH(m, 256, k_dc_union, m, shift, descending, older_is_larger, A2, B2, tab,
                    cap - 1, c.st);
         DMS_LAUNCH(m, 256, k_dc_relabel, m, shift, descending, A2, B2, tab, cap - 1);
     }
+    // levels kDcSegBits .. 1: each segment of 2^kDcSegBits turns in one warp
+    k_dc_segment<<<(unsigned)((m + kDcSeg - 1) / kDcSeg), 32, 0, c.s>>>(
+        m, descending, older_is_larger, A2, B2, c.st);
+    c.launches++;
+    DMS_CUDA(cudaGetLastError());
     DMS_LAUNCH(m, 256, k_dc_decide, m, older_is_larger, A2, B2, idx, young, died);
     *levels_out = L;
     return DMS_OK;
