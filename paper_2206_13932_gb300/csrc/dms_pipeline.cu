@@ -1263,17 +1263,22 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
     using K = typename Key<T>::K;
     int cx, cy, cz;     // coordinates of y, followed as the walk moves
     coords(g, y, cx, cy, cz);
+    K ky = Key<T>::of(values[y]);
+    int wn = -1;        // after a crossing: the link of the tet's one new vertex
     for (int64_t step = 0; step < max_steps; step++) {
-        // the maximum vertex of the tet
-        K kb = Key<T>::of(values[y]);
+        // the maximum vertex of the tet: any of its vertices for the first
+        // tet; after crossing a face of the lower star of y, y or the new one
+        K kb = ky;
         int64_t best = y;
         int bl = -1;
         for (int k = 0; k < 3; k++) {
-            int l = S.tet_v[h][k];
-            int64_t v = y + g.dlin[l];
-            K kv = Key<T>::of(values[v]);
+            const int l = wn >= 0 ? wn : S.tet_v[h][k];
+            const int64_t v = y + g.dlin[l];
+            const K kv = Key<T>::of(values[v]);
             if (kv > kb || (kv == kb && v > best)) { kb = kv; best = v; bl = l; }
+            if (wn >= 0) break;
         }
+        ky = kb;
         if (bl >= 0) {   // re-express the tet in the star of its maximum vertex
             int ox = -S.dx[bl], oy = -S.dy[bl], oz = -S.dz[bl];
             int ly = S.link_of_dc[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
@@ -1320,6 +1325,7 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
         int w = __ffs(S.tet_mask[h2] & ~S.tri_mask[s2]) - 1;
         if (!(present_links(S, g, cx, cy, cz) >> w & 1)) return vmax;   // the outer boundary
         h = h2;
+        wn = w;
     }
     atomicOr(&st->err, kErrIter);
     return vmax;
