@@ -91,11 +91,14 @@ def _code_only(src: str) -> str:
 
 
 # The code that decides the classification kernel's DRAM traffic, as
-# (start, end) markers in dms_pipeline.cu: everything up to the end of the
-# classification stage (tables, scan, the kernels), the tiling of its launch,
-# and the launch itself.  dms_common.cuh counts whole.
-_CLASSIFY_SPANS = (("", "stage 2: stable LSD radix sort"), ("struct ClsTiling", "struct Ctx"),
-                   ("k_classify2<T><<<", ");"))
+# (start, end) markers in dms_pipeline.cu: the star tables and utilities, the
+# classification stage (its kernels), the tiling of its launch, and the launch
+# itself.  dms_common.cuh counts whole.
+_CLASSIFY_SPANS = (("// ------------------------------------------------------------ host tables",
+                    "// ------------------------------------------------------------------ scan"),
+                   ("// --------------------------------------------------- stage 1: classification",
+                    "stage 2: stable LSD radix sort"),
+                   ("struct ClsTiling", "struct Ctx"), ("k_classify2<T><<<", ");"))
 
 
 # The code behind ProcessLowerStars in the bench (two passes around a sort

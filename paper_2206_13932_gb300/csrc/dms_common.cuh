@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace dms {
@@ -161,18 +162,48 @@ __device__ __forceinline__ void load_star(const StarTables &S, const GridParams 
     }
     sv.lower = lower;
     sv.descent = kNoDescent;
+    if constexpr (sizeof(K) <= 4) {
+        // Ties are broken by vertex id, and among the links that are present
+        // the id order is fixed: the negative offsets -7..-1 (links 13..7),
+        // then +1..+7 (links 0..6).  So (key, position in that order) packs
+        // into one integer, and one comparison per pair of links fills the
+        // masks below[n] of the links ordered before link n.
+        using P = typename std::conditional<sizeof(T) <= 2, uint32_t, unsigned long long>::type;
+        P pk[kLinks];
 #pragma unroll
-    for (int n = 0; n < kLinks; n++) {
-        uint8_t r = 0;
-        if (lower >> n & 1) {
+        for (int n = 0; n < kLinks; n++)
+            pk[n] = ((P)kn[n] << 4) | (P)(n < 7 ? 7 + n : 13 - n);
+        uint16_t below[kLinks];
 #pragma unroll
-            for (int m = 0; m < kLinks; m++)
-                if ((lower >> m & 1) && m != n &&
-                    (kn[m] < kn[n] || (kn[m] == kn[n] && g.dlin[m] < g.dlin[n])))
-                    r++;
-            if (r == 0) sv.descent = (uint8_t)n;
+        for (int n = 0; n < kLinks; n++) below[n] = 0;
+#pragma unroll
+        for (int n = 1; n < kLinks; n++)
+#pragma unroll
+            for (int m = 0; m < n; m++) {
+                const bool mb = pk[m] < pk[n];
+                below[n] |= (uint16_t)mb << m;
+                below[m] |= (uint16_t)!mb << n;
+            }
+#pragma unroll
+        for (int n = 0; n < kLinks; n++) {
+            const uint8_t r = (uint8_t)__popc(below[n] & lower);
+            if ((lower >> n & 1) && r == 0) sv.descent = (uint8_t)n;
+            sv.rank[n] = (lower >> n & 1) ? r : 0;
         }
-        sv.rank[n] = r;
+    } else {
+#pragma unroll
+        for (int n = 0; n < kLinks; n++) {
+            uint8_t r = 0;
+            if (lower >> n & 1) {
+#pragma unroll
+                for (int m = 0; m < kLinks; m++)
+                    if ((lower >> m & 1) && m != n &&
+                        (kn[m] < kn[n] || (kn[m] == kn[n] && g.dlin[m] < g.dlin[n])))
+                        r++;
+                if (r == 0) sv.descent = (uint8_t)n;
+            }
+            sv.rank[n] = r;
+        }
     }
 }
 

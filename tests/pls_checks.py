@@ -190,6 +190,8 @@ def random_field(rng, shape, kind):
         return rng.random((nz, ny, nx)) - 0.5
     if kind == "ties":
         return rng.integers(0, 3, (nz, ny, nx)).astype(np.uint16)
+    if kind == "ties64":
+        return rng.integers(0, 3, (nz, ny, nx)).astype(np.float64)
     if kind == "signed":
         pool = np.array([-0.0, 0.0, -1.5, 1.5, np.inf, -np.inf, 2.0], dtype=np.float32)
         return pool[rng.integers(0, len(pool), (nz, ny, nx))]
@@ -204,7 +206,7 @@ def main(include_dir):
         failed = []
         try:
             for shape in [(3, 3, 3), (4, 3, 3), (3, 4, 2), (4, 4, 3), (5, 3, 1)]:
-                for kind in ("float", "ties", "perm", "signed"):
+                for kind in ("float", "ties", "ties64", "perm", "signed"):
                     for rep in range(6):
                         v = random_field(rng, shape, kind)
                         if rep == 0:

@@ -85,11 +85,9 @@ def test_star_view_follows_the_vertex_order(hv, dtype):
     rng = np.random.default_rng(11)
     for shape in [(3, 3, 3), (5, 4, 3), (4, 1, 6), (1, 1, 5)]:
         for _ in range(4):
-            if dtype == np.uint16:
-                v = pc.random_field(rng, shape, "ties")
-            else:
-                v = pc.random_field(rng, shape, "signed").astype(dtype)
-            pc.check_star_view(hv, v)
+            pc.check_star_view(hv, pc.random_field(rng, shape, "ties").astype(dtype))
+            if dtype != np.uint16:
+                pc.check_star_view(hv, pc.random_field(rng, shape, "signed").astype(dtype))
 
 
 def test_order_keys_and_nan(hv):
@@ -133,6 +131,9 @@ MUTANTS = [
      "bool lo = kn[n] < kv || (kn[n] == kv && n >= 7);",
      "bool lo = kn[n] < kv || (kn[n] == kv && n < 7);"),
     ("ranks of tied neighbours reversed",
+     "pk[n] = ((P)kn[n] << 4) | (P)(n < 7 ? 7 + n : 13 - n);",
+     "pk[n] = ((P)kn[n] << 4) | (P)(n < 7 ? 6 - n : n);"),
+    ("ranks of tied neighbours reversed (float64)",
      "(kn[m] < kn[n] || (kn[m] == kn[n] && g.dlin[m] < g.dlin[n]))",
      "(kn[m] < kn[n] || (kn[m] == kn[n] && g.dlin[m] > g.dlin[n]))"),
     ("negative floats not flipped",
