@@ -52,16 +52,16 @@ SERVE_BATCH = 16            # most requests one batched pass takes
 # one ncu capture (profiles/classify_u16_512.md), valid only for the code it
 # was taken on (sha256 of the code behind that kernel, comments excluded:
 # _CLASSIFY_SPANS); otherwise reported as null.
-CLASSIFY_TRAFFIC = {"sources_sha256": "eb26737328563b5ce987eccc9b9472e26eb7afd8df787c6404174cb78de85218",
-                    "bytes_per_launch": 268718336 + 117972992}
+CLASSIFY_TRAFFIC = {"sources_sha256": "549b412bd718737b55508d3b5f790f81571780dce33b77c61faf823f22740f0f",
+                    "bytes_per_launch": 268509184 + 118023680}
 # Warp instructions issued per star by ProcessLowerStars' two kernels
 # (k_pls_keys + k_pls_run), from one ncu capture (profiles/pls_two_pass_noise192.md:
-# 636 403 702 + 2 582 852 077 instructions for 7 077 888 stars of 192^3 noise,
+# 201 719 808 + 2 582 852 077 instructions for 7 077 888 stars of 192^3 noise,
 # 57 % of them PL-critical, like this workload), valid only for the code it
 # was taken on (_PLS_SPANS).  The radix sort between the two passes is not
 # counted, so the achieved rate is a slight underestimate.
-PLS_ISSUE = {"sources_sha256": "7f19cdca98c3ab36bf1ab919a8cc52583bf891635271fb5dff14897ce0d2009e",
-             "warp_inst_per_star": (636403702 + 2582852077) / 7077888, "simt_lanes": 17.67,
+PLS_ISSUE = {"sources_sha256": "f9df60d7d9a730c7ec559d1687d15bf03bf1981066434b7e84e65a651be413f7",
+             "warp_inst_per_star": (201719808 + 2582852077) / 7077888, "simt_lanes": 19.3,
              "alu_pipe_pct_run": 86.1}
 
 
