@@ -495,15 +495,20 @@ def run_ours(args):
     counts = g.counts()
     stage = g.stage_ms()
     # ---- end to end through the C ABI: pinned host field in, host pairs out
-    e2e_ms = []
+    e2e_ms, comp_ms, fetch_ms, h2d_ms = [], [], [], []
     d2h = 0
     for k in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.compute(host)
+        t1 = time.perf_counter()
         pairs = [g.fetch(d, out=outs[d]) for d in range(3)]
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        t2 = time.perf_counter()
+        e2e_ms.append(1e3 * (t2 - t0))
+        comp_ms.append(1e3 * (t1 - t0))
+        fetch_ms.append(1e3 * (t2 - t1))
+        h2d_ms.append(g.stage_ms()["h2d"])
         d2h = sum(p.nbytes for p in pairs)
     e2e_val = replicas.job_throughput(
         n, replicas.max_over_ranks(statistics.mean(e2e_ms), device="cuda")) / 1e6
@@ -544,6 +549,12 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": n * s_in,
                 "d2h_bytes_per_step": d2h},
+        # where an end-to-end step goes (wall clock, mean): the compute call
+        # with its host-to-device copy (and that copy alone, CUDA events), then
+        # the three fetches of the pairs into pinned host memory
+        "e2e_split_ms": {"compute_call": statistics.mean(comp_ms),
+                         "h2d_copy": statistics.mean(h2d_ms),
+                         "fetch_calls": statistics.mean(fetch_ms)},
         "gpu_launches": launches,
         "roofline": roofline,
         "roofline_gradient": rgrad,
