@@ -1250,14 +1250,24 @@ __device__ __noinline__ GradRec grad_fill(const StarTables &S, const GridParams 
 
 // ------------------------------------------------------ stage 5: D2 arcs
 
+// Per critical vertex: its critical star tets (bits 32-55) and the C3 index
+// of the first (bits 0-31), so that an ascending walk tests a tet with the
+// loads of its step instead of two more dependent ones.
+__global__ void k_tet_words(const int32_t *__restrict__ vc, int64_t nc,
+                            const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
+                            unsigned long long *tw) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    tw[vc[i]] = ((unsigned long long)recs[i].crit_h << 32) | (uint32_t)base3[i];
+}
+
 // The critical tet (node index) or the virtual maximum reached from tet h of
 // the star of y by the ascending walk of the dual gradient (Sec. 5.2): a
 // regular tet is the head of a triangle->tet vector; cross that triangle to
 // its other tet; the outer boundary is the virtual maximum.
 template <typename T>
 __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__restrict__ values,
-                          uint8_t *flags, GradRec *grad, const int32_t *__restrict__ vrank,
-                          const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
+                          uint8_t *flags, GradRec *grad, const unsigned long long *__restrict__ tw,
                           int64_t y, int h, int32_t vmax, int64_t max_steps, bool dense,
                           DevStatus *st) {
     using K = typename Key<T>::K;
@@ -1311,12 +1321,21 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
             cx += S.dx[bl]; cy += S.dy[bl]; cz += S.dz[bl];
             h = hn;
         }
-        if (flags[y] & kFlagCritical) {
-            int32_t i = vrank[y];
-            CritRec rec = recs[i];
-            if (rec.crit_h >> h & 1) return base3[i] + local_index(S, rec, 3, h);
-        }
+        // the vertex's flag, tet word and record, read together
+        const uint8_t fy = dense ? __ldg(flags + y) : ((volatile const uint8_t *)flags)[y];
+        const unsigned long long twy = tw[y];
         GradRec G = grad_get(S, g, values, flags, grad, y, dense);
+        if ((fy & kFlagCritical) && (twy >> (32 + h) & 1)) {
+            // a critical tet: the vertex's first C3 index plus its critical
+            // tets of lower G (the ranks are the record's)
+            uint8_t r[kLinks];
+            unpack_ranks(G.w[5], r);
+            const uint16_t ch = code_tet(S, r, h);
+            int k = 0;
+            for (uint32_t m = (uint32_t)(twy >> 32); m; m &= m - 1)
+                k += code_tet(S, r, __ffs(m) - 1) < ch;
+            return (int32_t)(uint32_t)twy + k;
+        }
         int s2 = grad_tet_pair(G, h);
         if (s2 >= kTris) { atomicOr(&st->err, kErrState); return vmax; }
         uint32_t other = S.tets_of_tri[s2] & ~(1u << h);
@@ -1333,8 +1352,7 @@ __device__ int32_t ascend(const StarTables &S, const GridParams &g, const T *__r
 
 template <typename T, bool Bt>
 __global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *flags,
-                          GradRec *grad, const int32_t *__restrict__ vrank,
-                          const CritRec *__restrict__ recs, const int32_t *__restrict__ base3,
+                          GradRec *grad, const unsigned long long *__restrict__ tw,
                           const int32_t *__restrict__ v2, const uint8_t *__restrict__ l2,
                           int64_t n2, const int32_t *__restrict__ order, int32_t vmax,
                           int vmax_on, int32_t *A, int32_t *B, int32_t *young, int64_t max_steps,
@@ -1359,7 +1377,7 @@ __global__ void k_d2_arcs(const T *__restrict__ values, Geo<Bt> geo, uint8_t *fl
         int h = __ffs(m) - 1;
         m &= m - 1;
         int w = __ffs(S.tet_mask[h] & ~S.tri_mask[s]) - 1;
-        ends[e] = (pres >> w & 1) ? ascend(S, g, values, flags, grad, vrank, recs, base3, x, h,
+        ends[e] = (pres >> w & 1) ? ascend(S, g, values, flags, grad, tw, x, h,
                                            vmax, max_steps, dense != 0, st)
                                   : vmax;
     }
@@ -4625,9 +4643,13 @@ dms_status d2_walks(Ctx &c, const T *values, const Geo<B> &geo, int64_t n2, int3
     KEV(14);
     const int32_t *order2 = nullptr;
     DMS_TRY(order_by_vertex(c, P.c_vert[2].as<int32_t>(), nullptr, n2, 0, &order2));
+    // the tet words share the buffer of the D1 trace's row words (written later)
+    DMS_ALLOC(P.vcrit, 8 * P.n + 8);
+    DMS_LAUNCH(P.n_crit, 256, k_tet_words, P.vc.as<int32_t>(), P.n_crit, P.recs.as<CritRec>(),
+               P.base[3].as<int32_t>(), P.vcrit.as<unsigned long long>());
     DMS_LAUNCH(n2, 128, (k_d2_arcs<T, B>), values, geo, P.flags.as<uint8_t>(),
-               P.grad.as<GradRec>(), P.vrank.as<int32_t>(), P.recs.as<CritRec>(),
-               P.base[3].as<int32_t>(), P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(), n2,
+               P.grad.as<GradRec>(), P.vcrit.as<unsigned long long>(),
+               P.c_vert[2].as<int32_t>(), P.c_loc[2].as<uint8_t>(), n2,
                order2, vmax, P.virtual_max, P.arc2_a.as<int32_t>(), P.arc2_b.as<int32_t>(),
                young2, max_steps, P.dense_grad ? 1 : 0, c.st);
     KEV(15);
