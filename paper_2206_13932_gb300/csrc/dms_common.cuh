@@ -316,14 +316,46 @@ __device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank,
         LT &= ~S.tris_of_link[n];
         LH &= ~S.tets_of_link[n];
     }
-    uint16_t codeT[kTris];
-    uint16_t codeH[kTets];
-    for (uint64_t m = LT; m; m &= m - 1) { int s = __ffsll(m) - 1; codeT[s] = code_tri(S, rank, s); }
-    for (uint32_t m = LH; m; m &= m - 1) { int h = __ffs(m) - 1; codeH[h] = code_tet(S, rank, h); }
+    // the link of each rank (nibble r of lrw) and the rank of each lower link
+    unsigned long long lrw = 0, rkw = 0;
+    int p = 0;
+    for (uint16_t m = L; m; m &= m - 1) {
+        const int n = __ffs(m) - 1;
+        lrw |= (unsigned long long)n << (4 * rank[n]);
+        rkw |= (unsigned long long)rank[n] << (4 * n);
+        p++;
+    }
+    // The lower triangles and tets in G order, each given its position in it:
+    // a cell's G is its link ranks in decreasing order, so for each highest
+    // rank hi, each triangle (hi, lo) for lo increasing, followed by its tets
+    // (hi, lo, t) for t increasing.  The priority queues are then bit sets
+    // over positions, and a pop is a find-first-set.
+    int8_t posT[kTris], posH[kTets];
+    uint8_t cell_at[kTris + kTets], hi_at[kTris + kTets];   // tet h: 0x40 | h
+    int np = 0;
+    for (int hi = 1; hi < p; hi++) {
+        const int a = (int)((lrw >> (4 * hi)) & 15);
+        for (int lo = 0; lo < hi; lo++) {
+            const int b = (int)((lrw >> (4 * lo)) & 15);
+            const int s = S.tri_of_pair[a][b];
+            if (s < 0) continue;
+            posT[s] = (int8_t)np; cell_at[np] = (uint8_t)s; hi_at[np] = (uint8_t)hi; np++;
+            for (int t = 0; t < lo; t++) {
+                const int c = (int)((lrw >> (4 * t)) & 15);
+                for (uint32_t m = S.tets_of_tri[s]; m; m &= m - 1) {
+                    const int q = __ffs(m) - 1;
+                    if (S.tet_mask[q] >> c & 1) {
+                        posH[q] = (int8_t)np; cell_at[np] = (uint8_t)(0x40 | q);
+                        hi_at[np] = (uint8_t)hi; np++;
+                    }
+                }
+            }
+        }
+    }
 
     uint16_t cE = 0;  uint64_t cT = 0;  uint32_t cH = 0;   // classified
-    uint64_t pT = 0;  uint32_t pH = 0;                     // PQone
-    uint16_t zE = 0;  uint64_t zT = 0;  uint32_t zH = 0;   // PQzero
+    uint64_t pq = 0;                                       // PQone, by position
+    uint32_t zr = 0;  uint64_t pz = 0;                     // PQzero: edges by rank, cells by position
     int eorder = 0;
 
     auto unpaired_tri = [&](int s) -> uint16_t {   // unclassified edges of s
@@ -335,87 +367,73 @@ __device__ inline void pls(const StarTables &S, uint16_t L, const uint8_t *rank,
     auto push_cof_edge = [&](int n) {
         for (uint64_t m = S.tris_of_link[n] & LT & ~cT; m; m &= m - 1) {
             int s = __ffsll(m) - 1;
-            if (__popc(unpaired_tri(s)) == 1) pT |= 1ull << s;
+            if (__popc(unpaired_tri(s)) == 1) pq |= 1ull << posT[s];
         }
     };
     auto push_cof_tri = [&](int s) {
         for (uint32_t m = S.tets_of_tri[s] & LH & ~cH; m; m &= m - 1) {
             int h = __ffs(m) - 1;
-            if (__popcll(unpaired_tet(h)) == 1) pH |= 1u << h;
+            if (__popcll(unpaired_tet(h)) == 1) pq |= 1ull << posH[h];
         }
     };
 
     // the vertex is paired with its lowest edge
-    int n0 = -1;
-    for (uint16_t m = L; m; m &= m - 1) { int n = __ffs(m) - 1; if (rank[n] == 0) n0 = n; }
+    const int n0 = (int)(lrw & 15);
     cE = (uint16_t)(1u << n0);
     if (G) { epair[n0] = kHead; eord[n0] = (uint8_t)eorder; }
     eorder++;
-    zE = (uint16_t)(L & ~cE);
+    zr = ((1u << p) - 1) & ~1u;
     push_cof_edge(n0);
 
     for (int guard = 0; guard < 4 * (kLinks + kTris + kTets); guard++) {
-        while (pT | pH) {
+        while (pq) {
             // pop the smallest G among PQone
-            uint16_t best = 0xFFFF; int bi = -1; bool btet = false;
-            for (uint64_t m = pT; m; m &= m - 1) {
-                int s = __ffsll(m) - 1;
-                if (codeT[s] < best) { best = codeT[s]; bi = s; btet = false; }
-            }
-            for (uint32_t m = pH; m; m &= m - 1) {
-                int h = __ffs(m) - 1;
-                if (codeH[h] < best) { best = codeH[h]; bi = h; btet = true; }
-            }
-            if (!btet) {
-                int s = bi;
-                pT &= ~(1ull << s);
+            const int ps = __ffsll(pq) - 1;
+            pq &= pq - 1;
+            const int cell = cell_at[ps];
+            if (!(cell & 0x40)) {
+                int s = cell;
                 if (cT >> s & 1) continue;
                 uint16_t u = unpaired_tri(s);
-                if (u == 0) { zT |= 1ull << s; continue; }
+                if (u == 0) { pz |= 1ull << ps; continue; }
                 int n = __ffs(u) - 1;                  // the unique unclassified edge
-                cE |= (uint16_t)(1u << n); cT |= 1ull << s; zE &= (uint16_t)~(1u << n);
+                cE |= (uint16_t)(1u << n); cT |= 1ull << s;
+                zr &= ~(1u << ((rkw >> (4 * n)) & 15));
                 if (G) { epair[n] = (uint8_t)s; eord[n] = (uint8_t)eorder; }
                 eorder++;
                 push_cof_tri(s);
                 push_cof_edge(n);
             } else {
-                int h = bi;
-                pH &= ~(1u << h);
+                int h = cell & 63;
                 if (cH >> h & 1) continue;
                 uint64_t u = unpaired_tet(h);
-                if (u == 0) { zH |= 1u << h; continue; }
+                if (u == 0) { pz |= 1ull << ps; continue; }
                 int s = __ffsll(u) - 1;                // the unique unclassified face
-                cT |= 1ull << s; cH |= 1u << h; zT &= ~(1ull << s);
+                cT |= 1ull << s; cH |= 1u << h; pz &= ~(1ull << posT[s]);
                 if (G) tpair[h] = (uint8_t)s;
                 push_cof_tri(s);
             }
         }
-        if (!(zE | zT | zH)) break;
-        // the smallest G among PQzero is critical
-        uint16_t best = 0xFFFF; int bi = -1, bd = -1;
-        for (uint16_t m = zE; m; m &= m - 1) {
-            int n = __ffs(m) - 1;
-            uint16_t c = code_edge(rank, n);
-            if (c < best) { best = c; bi = n; bd = 1; }
-        }
-        for (uint64_t m = zT; m; m &= m - 1) {
-            int s = __ffsll(m) - 1;
-            if (codeT[s] < best) { best = codeT[s]; bi = s; bd = 2; }
-        }
-        for (uint32_t m = zH; m; m &= m - 1) {
-            int h = __ffs(m) - 1;
-            if (codeH[h] < best) { best = codeH[h]; bi = h; bd = 3; }
-        }
-        if (bd == 1) {
-            zE &= (uint16_t)~(1u << bi); cE |= (uint16_t)(1u << bi); R.crit_e |= (uint16_t)(1u << bi);
+        if (!(zr | pz)) break;
+        // the smallest G among PQzero is critical: an edge of rank r comes
+        // before every cell whose highest rank is r or more
+        const int re = zr ? __ffs(zr) - 1 : kLinks;
+        const int pc = pz ? __ffsll(pz) - 1 : -1;
+        if (pc < 0 || re <= hi_at[pc]) {
+            const int bi = (int)((lrw >> (4 * re)) & 15);
+            zr &= ~(1u << re); cE |= (uint16_t)(1u << bi); R.crit_e |= (uint16_t)(1u << bi);
             if (G) eord[bi] = (uint8_t)eorder;
             eorder++;
             push_cof_edge(bi);
-        } else if (bd == 2) {
-            zT &= ~(1ull << bi); cT |= 1ull << bi; R.crit_t |= 1ull << bi;
-            push_cof_tri(bi);
         } else {
-            zH &= ~(1u << bi); cH |= 1u << bi; R.crit_h |= 1u << bi;
+            pz &= ~(1ull << pc);
+            const int cell = cell_at[pc];
+            if (!(cell & 0x40)) {
+                cT |= 1ull << cell; R.crit_t |= 1ull << cell;
+                push_cof_tri(cell);
+            } else {
+                cH |= 1u << (cell & 63); R.crit_h |= 1u << (cell & 63);
+            }
         }
     }
     pack();

@@ -118,15 +118,15 @@ def test_order_keys_and_nan(hv):
 # (name, exact text of dms_common.cuh, replacement); the text occurs once
 MUTANTS = [
     ("the vertex paired with its highest edge",
-     "if (rank[n] == 0) n0 = n;", "if (rank[n] == __popc(L) - 1) n0 = n;"),
-    ("triangle keys in the wrong order",
-     "int hi = a > b ? a : b, lo = a > b ? b : a;", "int hi = a > b ? b : a, lo = a > b ? a : b;"),
-    ("tet keys sorted wrongly",
-     "    if (b < c) { t = b; b = c; c = t; }", "    if (b > c) { t = b; b = c; c = t; }"),
+     "const int n0 = (int)(lrw & 15);", "const int n0 = (int)((lrw >> (4 * (p - 1))) & 15);"),
+    ("triangles of one highest rank in the wrong order",
+     "for (int lo = 0; lo < hi; lo++) {", "for (int lo = hi - 1; lo >= 0; lo--) {"),
+    ("tets of one triangle in the wrong order",
+     "for (int t = 0; t < lo; t++) {", "for (int t = lo - 1; t >= 0; t--) {"),
     ("PQzero edges taken out of order",
-     "            if (c < best) { best = c; bi = n; bd = 1; }",
-     "            if (c < best && bd < 0) { best = c; bi = n; bd = 1; }"),
-    ("no edge waits in PQzero", "    zE = (uint16_t)(L & ~cE);", "    zE = 0;"),
+     "const int re = zr ? __ffs(zr) - 1 : kLinks;",
+     "const int re = zr ? __ffs((zr & (zr - 1)) ? (zr & (zr - 1)) : zr) - 1 : kLinks;"),
+    ("no edge waits in PQzero", "    zr = ((1u << p) - 1) & ~1u;", "    zr = 0;"),
     ("ties decided against the vertex id",
      "bool lo = kn[n] < kv || (kn[n] == kv && n >= 7);",
      "bool lo = kn[n] < kv || (kn[n] == kv && n < 7);"),
