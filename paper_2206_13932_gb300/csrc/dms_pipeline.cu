@@ -648,17 +648,27 @@ __global__ void __launch_bounds__(kRsThreads)
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// One stable LSD pass: the items of a tile of kRsTile go to their digit's
+// run, after the runs of the earlier tiles (hoff: the scanned histograms).
+// For 32-bit keys the tile is first ordered by digit in shared memory, so
+// that the writes of a warp go to a few consecutive runs instead of 32
+// scattered positions; 64-bit keys are written from registers.
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads)
     k_rs_scatter(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *kout,
                  int32_t *vout, int64_t n, int shift, const int32_t *__restrict__ hoff,
                  int ntiles) {
+    constexpr bool kStaged = sizeof(K) == 4;
     __shared__ int wc[kRsWarps][256];
-    __shared__ int wb[kRsWarps][256];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ int wb[kStaged ? 1 : kRsWarps][256];
+    __shared__ int dstart[256], gbase[256], wsum[kRsWarps];
+    __shared__ K skey[kStaged ? kRsTile : 1];
+    __shared__ int32_t sval[kStaged ? kRsTile : 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&wc[0][0])[i] = 0;
     __syncthreads();
-    int64_t wbase = (int64_t)blockIdx.x * kRsTile + (int64_t)w * kRsPerWarp;
+    const int64_t tbase = (int64_t)blockIdx.x * kRsTile;
+    const int64_t wbase = tbase + (int64_t)w * kRsPerWarp;
     for (int it = 0; it < kRsPerWarp / 32; it++) {
         int64_t i = wbase + it * 32 + lane;
         bool ok = i < n;
@@ -667,26 +677,73 @@ __global__ void __launch_bounds__(kRsThreads)
         if (ok && lane == __ffs(peers) - 1) wc[w][d] += __popc(peers);
     }
     __syncthreads();
-    {
-        int d = threadIdx.x;
-        int run = hoff[(int64_t)d * ntiles + blockIdx.x];
-        for (int q = 0; q < kRsWarps; q++) { wb[q][d] = run; run += wc[q][d]; }
-    }
-    __syncthreads();
-    for (int it = 0; it < kRsPerWarp / 32; it++) {
-        int64_t i = wbase + it * 32 + lane;
-        bool ok = i < n;
-        K kv = ok ? kin[i] : 0;
-        int d = ok ? (int)((kv >> shift) & 255) : 256 + lane;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (ok) {
-            int pos = wb[w][d] + __popc(peers & lanemask_lt());
-            kout[pos] = kv;
-            vout[pos] = vin[i];
+    if constexpr (kStaged) {
+        // thread t: digit t's run in the tile (a block scan of the digit
+        // totals), each warp's place in it, and the run's global start
+        const int t = threadIdx.x;
+        int tot = 0;
+        for (int q = 0; q < kRsWarps; q++) tot += wc[q][t];
+        int x = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        __syncwarp();
-        if (ok && lane == __ffs(peers) - 1) wb[w][d] += __popc(peers);
-        __syncwarp();
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        int pre = 0;
+        for (int q = 0; q < w; q++) pre += wsum[q];
+        const int excl = pre + x - tot;
+        dstart[t] = excl;
+        int run = excl;
+        for (int q = 0; q < kRsWarps; q++) { const int c = wc[q][t]; wc[q][t] = run; run += c; }
+        gbase[t] = hoff[(int64_t)t * ntiles + blockIdx.x];
+        __syncthreads();
+        for (int it = 0; it < kRsPerWarp / 32; it++) {
+            int64_t i = wbase + it * 32 + lane;
+            bool ok = i < n;
+            K kv = ok ? kin[i] : 0;
+            int d = ok ? (int)((kv >> shift) & 255) : 256 + lane;
+            unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (ok) {
+                const int li = wc[w][d] + __popc(peers & lanemask_lt());
+                skey[li] = kv;
+                sval[li] = vin[i];
+            }
+            __syncwarp();
+            if (ok && lane == __ffs(peers) - 1) wc[w][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        const int cnt = (int)(n - tbase < kRsTile ? n - tbase : kRsTile);
+        for (int li = threadIdx.x; li < cnt; li += kRsThreads) {
+            const K kv = skey[li];
+            const int d = (int)((kv >> shift) & 255);
+            const int pos = gbase[d] + (li - dstart[d]);
+            kout[pos] = kv;
+            vout[pos] = sval[li];
+        }
+    } else {
+        {
+            int d = threadIdx.x;
+            int run = hoff[(int64_t)d * ntiles + blockIdx.x];
+            for (int q = 0; q < kRsWarps; q++) { wb[q][d] = run; run += wc[q][d]; }
+        }
+        __syncthreads();
+        for (int it = 0; it < kRsPerWarp / 32; it++) {
+            int64_t i = wbase + it * 32 + lane;
+            bool ok = i < n;
+            K kv = ok ? kin[i] : 0;
+            int d = ok ? (int)((kv >> shift) & 255) : 256 + lane;
+            unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (ok) {
+                int pos = wb[w][d] + __popc(peers & lanemask_lt());
+                kout[pos] = kv;
+                vout[pos] = vin[i];
+            }
+            __syncwarp();
+            if (ok && lane == __ffs(peers) - 1) wb[w][d] += __popc(peers);
+            __syncwarp();
+        }
     }
 }
 
