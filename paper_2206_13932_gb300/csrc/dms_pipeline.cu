@@ -650,15 +650,17 @@ __global__ void __launch_bounds__(kRsThreads)
 
 // One stable LSD pass: the items of a tile of kRsTile go to their digit's
 // run, after the runs of the earlier tiles (hoff: the scanned histograms).
-// For 32-bit keys the tile is first ordered by digit in shared memory, so
-// that the writes of a warp go to a few consecutive runs instead of 32
-// scattered positions; 64-bit keys are written from registers.
-template <typename K>
+// Staged (32-bit keys only): the tile is first ordered by digit in shared
+// memory, so that the writes of a warp go to a few consecutive runs instead
+// of 32 scattered positions.  It takes 43 KB of shared memory a block, which
+// is why the sorts that run beside latency-bound walks on another stream
+// use the unstaged form (their L1 would shrink).
+template <typename K, bool kStaged = false>
 __global__ void __launch_bounds__(kRsThreads)
     k_rs_scatter(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *kout,
                  int32_t *vout, int64_t n, int shift, const int32_t *__restrict__ hoff,
                  int ntiles) {
-    constexpr bool kStaged = sizeof(K) == 4;
+    static_assert(!kStaged || sizeof(K) == 4, "staged scatter: 32-bit keys");
     __shared__ int wc[kRsWarps][256];
     __shared__ int wb[kStaged ? 1 : kRsWarps][256];
     __shared__ int dstart[256], gbase[256], wsum[kRsWarps];
@@ -4543,7 +4545,7 @@ dms_status group_by_field(Ctx &c, int d, int64_t rows) {
 // `bits` bits of the keys, 8 bits a pass, with P.ord_h as histograms; the
 // sorted pairs end in (kin, vin) (the pointers swap with each pass).
 dms_status radix_u32(Ctx &c, uint32_t *&kin, int32_t *&vin, uint32_t *&kout, int32_t *&vout,
-                     int64_t n, int bits, int rtiles) {
+                     int64_t n, int bits, int rtiles, bool staged = false) {
     Pipeline &P = c.P;
     for (int shift = 0; shift < bits; shift += 8) {
         k_rs_hist<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(kin, n, shift, P.ord_h[0].as<int32_t>(),
@@ -4551,8 +4553,12 @@ dms_status radix_u32(Ctx &c, uint32_t *&kin, int32_t *&vin, uint32_t *&kout, int
         c.launches++;
         DMS_TRY(scan(c, P.ord_h[0].as<int32_t>(), P.ord_h[1].as<int32_t>(), (int64_t)256 * rtiles,
                      &c.st->total[1]));
-        k_rs_scatter<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(kin, vin, kout, vout, n, shift,
-                                                              P.ord_h[1].as<int32_t>(), rtiles);
+        if (staged)
+            k_rs_scatter<uint32_t, true><<<rtiles, kRsThreads, 0, c.s>>>(
+                kin, vin, kout, vout, n, shift, P.ord_h[1].as<int32_t>(), rtiles);
+        else
+            k_rs_scatter<uint32_t><<<rtiles, kRsThreads, 0, c.s>>>(
+                kin, vin, kout, vout, n, shift, P.ord_h[1].as<int32_t>(), rtiles);
         c.launches++;
         DMS_CUDA(cudaGetLastError());
         std::swap(kin, kout);
@@ -4619,7 +4625,7 @@ dms_status launch_pls(Ctx &c, const T *values, const Geo<B> &geo, const int32_t 
                                                               rk, fl);
     c.launches++;
     DMS_CUDA(cudaGetLastError());
-    DMS_TRY(radix_u32(c, kin, vin, kout, vout, count, kLinks, rtiles));
+    DMS_TRY(radix_u32(c, kin, vin, kout, vout, count, kLinks, rtiles, true));
     k_pls_run<<<blocks_for(count, nt), nt, 0, c.s>>>(list, kin, vin, rk, count, gr);
     c.launches++;
     DMS_CUDA(cudaGetLastError());
@@ -4801,7 +4807,7 @@ template <typename T, bool B> dms_status run(Ctx &c, const T *values) {
             c.launches++;
             DMS_TRY(scan(c, P.flag_a.as<int32_t>(), P.flag_b.as<int32_t>(), (int64_t)256 * rtiles,
                          &c.st->total[1]));
-            k_rs_scatter<K><<<rtiles, kRsThreads, 0, c.s>>>(kin, vin, kout, vout, nc, shift,
+            k_rs_scatter<K, sizeof(K) == 4><<<rtiles, kRsThreads, 0, c.s>>>(kin, vin, kout, vout, nc, shift,
                                                            P.flag_b.as<int32_t>(), rtiles);
             c.launches++;
             DMS_CUDA(cudaGetLastError());
