@@ -1617,9 +1617,10 @@ __device__ __forceinline__ HashEnt *trace_find(TraceCtx &c, int64_t y, int m) {
 // to the rows (1-saddles not paired in D0), as a descending list of C1
 // indices appended to the column pool.  The walks differ widely in length,
 // so the loop is flat: in every iteration each lane takes one step of its
-// current column -- start it, expand one edge, or write it out -- and lanes
-// that finish fetch the next column at once (one atomic per warp), instead of
-// the warp waiting for its longest walk before the next batch of columns.
+// current column -- one toggle of an edge its start or an expansion queued,
+// or the column's write-out -- and lanes that finish fetch the next column at
+// once (one atomic per warp), instead of the warp waiting for its longest
+// walk before the next batch of columns.
 template <typename T, bool B>
 __global__ void __launch_bounds__(256, 4)
     k_d1_trace(const T *__restrict__ values, Geo<B> geo, uint8_t *flags, GradRec *grad,
