@@ -13,11 +13,15 @@ that field.
 bounded sub-volumes of the same field, on this machine's host cores.
 
 Rooflines in the line: ``roofline`` for the kernel family that takes the most
-device time, ``roofline_gradient`` for the gradient stage (classification,
-compaction and ProcessLowerStars) against its algorithmic bytes N*s_in +
-8*|C| (every value read once, every critical simplex written once),
-``roofline_classify`` for the per-vertex stencil alone, and
-``roofline_pls`` for ProcessLowerStars against the issue rate.
+device time, ``roofline_d1_trace`` for the D1 boundary trace against the
+record bytes its walks read, ``roofline_d1_reduce`` for the D1 reduction
+(its merge bytes, and its longest chain of additions with the time per
+link), ``roofline_pls`` for ProcessLowerStars against the issue rate,
+``roofline_gradient`` for the gradient stage (classification, compaction and
+ProcessLowerStars) against its algorithmic bytes N*s_in + 8*|C| (every value
+read once, every critical simplex written once), and ``roofline_classify``
+for the per-vertex stencil alone.  ``e2e_split_ms`` splits the end-to-end
+step into the compute call, its host-to-device copy and the fetches.
 """
 from __future__ import annotations
 
