@@ -35,6 +35,11 @@
  *     simplex lies in the lower star of its maximum vertex, and the key of a
  *     simplex starts with the rank of that vertex, so this is exactly the
  *     filtration order restricted to dimension d.
+ *  5. The column under reduction is kept as a max-heap of keys in which a
+ *     key may occur several times (its value: the keys of odd
+ *     multiplicity).  Adding a column pushes its keys, and the lowest row is
+ *     read off the top after equal keys there cancel in pairs; this is the
+ *     same sum mod 2 without merging whole columns at every addition.
  *
  * Result rows as pairsimplices.c (8 int64: dim, birth_id, death_id,
  * birth_vertex, death_vertex, essential, birth_pos, death_pos), except that
@@ -190,31 +195,73 @@ static void arena_free(arena_t *a)
     free(a->chunk);
 }
 
-/* dst <- dst + src (mod 2), both sorted increasingly. */
-static int xor_into(fkey_t **dst, int64_t *dn, int64_t *dcap, const fkey_t *src, int64_t sn,
-                    fkey_t **tmp, int64_t *tcap)
+/* The column under reduction as a max-heap of keys in which a key may occur
+ * several times: its value is the set of keys of odd multiplicity (a sum
+ * mod 2).  Adding a column pushes its keys; equal keys cancel in pairs when
+ * they reach the top, so the lowest row (the largest key of odd
+ * multiplicity) is found without merging whole columns. */
+typedef struct { fkey_t *h; int64_t n, cap; } kheap_t;
+
+static int kheap_push(kheap_t *q, fkey_t k)
 {
-    int64_t need = *dn + sn;
-    if (need > *tcap) {
-        fkey_t *nt = realloc(*tmp, sizeof(fkey_t) * (size_t)need);
-        if (!nt) return OR_ERR_MEM;
-        *tmp = nt; *tcap = need;
+    if (q->n == q->cap) {
+        int64_t nc = q->cap ? 2 * q->cap : 64;
+        fkey_t *nh = realloc(q->h, sizeof(fkey_t) * (size_t)nc);
+        if (!nh) return OR_ERR_MEM;
+        q->h = nh; q->cap = nc;
     }
-    int64_t i = 0, j = 0, k = 0;
-    fkey_t *d = *dst, *t = *tmp;
-    while (i < *dn || j < sn) {
-        if (j >= sn || (i < *dn && key_lt(d[i], src[j]))) t[k++] = d[i++];
-        else if (i >= *dn || key_lt(src[j], d[i])) t[k++] = src[j++];
-        else { i++; j++; }      /* 1 + 1 = 0 (mod 2) */
+    int64_t i = q->n++;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!key_lt(q->h[p], k)) break;
+        q->h[i] = q->h[p];
+        i = p;
     }
-    if (k > *dcap) {
-        fkey_t *nd = realloc(*dst, sizeof(fkey_t) * (size_t)k);
-        if (!nd) return OR_ERR_MEM;
-        *dst = nd; *dcap = k;
-    }
-    memcpy(*dst, t, sizeof(fkey_t) * (size_t)k);
-    *dn = k;
+    q->h[i] = k;
     return OR_OK;
+}
+
+static fkey_t kheap_pop(kheap_t *q)
+{
+    fkey_t top = q->h[0], last = q->h[--q->n];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, m = l;
+        if (l >= q->n) break;
+        if (l + 1 < q->n && key_lt(q->h[l], q->h[l + 1])) m = l + 1;
+        if (!key_lt(last, q->h[m])) break;
+        q->h[i] = q->h[m];
+        i = m;
+    }
+    if (q->n > 0) q->h[i] = last;
+    return top;
+}
+
+/* The keys of odd multiplicity, in decreasing order, into out (which holds
+ * q->n entries); the heap is emptied.  Returns their number. */
+static int64_t kheap_drain(kheap_t *q, fkey_t *out)
+{
+    int64_t m = 0;
+    while (q->n > 0) {
+        fkey_t t = kheap_pop(q);
+        int odd = 1;
+        while (q->n > 0 && key_eq(q->h[0], t)) { kheap_pop(q); odd ^= 1; }
+        if (odd) out[m++] = t;
+    }
+    return m;
+}
+
+/* The lowest row of the column: equal keys at the top cancel in pairs; 0
+ * when the column is zero. */
+static int kheap_pivot(kheap_t *q, fkey_t *top)
+{
+    while (q->n > 0) {
+        fkey_t t = kheap_pop(q);
+        if (q->n > 0 && key_eq(q->h[0], t)) { kheap_pop(q); continue; }
+        *top = t;
+        return kheap_push(q, t) == OR_OK ? 1 : -1;
+    }
+    return 0;
 }
 
 /* Reduction of the columns of dimension dim (1..3).
@@ -238,8 +285,9 @@ static int reduce_dim(const fctx_t *c, int dim, const int32_t *cleared, int32_t 
     if (!colidx) return OR_ERR_MEM;
     for (int64_t i = 0; i < ncol; i++) colidx[i] = -1;
     arena_t arena = {0};
-    fkey_t *col = NULL, *tmp = NULL, bnd[4];
-    int64_t cn = 0, ccap = 0, tcap = 0;
+    kheap_t q = {0};
+    fkey_t *col = NULL, bnd[4];
+    int64_t ccap = 0, live = 0;
     int64_t ids[36];
     fkey_t keys[36];
     int st = OR_OK;
@@ -250,35 +298,57 @@ static int reduce_dim(const fctx_t *c, int dim, const int32_t *cleared, int32_t 
             int64_t tau = ids[s];
             if (cleared && cleared[tau] >= 0) continue;    /* a birth: its column is zero */
             int nb = boundary_keys(c, dim, tau, bnd);
-            if (nb > ccap) {
-                fkey_t *ncol2 = realloc(col, sizeof(fkey_t) * (size_t)nb);
-                if (!ncol2) { st = OR_ERR_MEM; break; }
-                col = ncol2; ccap = nb;
-            }
-            memcpy(col, bnd, sizeof(fkey_t) * (size_t)nb);
-            cn = nb;
+            q.n = 0;
+            for (int e = 0; e < nb && !st; e++) st = kheap_push(&q, bnd[e]);
+            live = nb;
             int added = 0;
-            while (cn > 0) {
-                int64_t low = id_of_key(c, dim - 1, col[cn - 1]);
+            fkey_t top;
+            int has = 0;
+            while (!st && (has = kheap_pivot(&q, &top)) == 1) {
+                int64_t low = id_of_key(c, dim - 1, top);
                 int64_t k = owner[low];
                 if (k < 0) break;
                 int32_t ki = colidx[k];
                 if (ki >= 0) {
-                    st = xor_into(&col, &cn, &ccap, arena_at(&arena, cstart[ki]), clen[ki], &tmp, &tcap);
+                    const fkey_t *src = arena_at(&arena, cstart[ki]);
+                    for (int64_t e = 0; e < clen[ki] && !st; e++) st = kheap_push(&q, src[e]);
                 } else {
                     fkey_t kb[4];
                     int kn = boundary_keys(c, dim, k, kb);
-                    st = xor_into(&col, &cn, &ccap, kb, kn, &tmp, &tcap);
+                    for (int e = 0; e < kn && !st; e++) st = kheap_push(&q, kb[e]);
                 }
-                if (st) break;
                 added = 1;
                 (*additions)++;
+                if (!st && q.n > 2 * live + 64) {
+                    /* cancel the pairs below the top too: a decreasing list
+                     * is itself a valid max-heap */
+                    if (q.n > ccap) {
+                        fkey_t *nc2 = realloc(col, sizeof(fkey_t) * (size_t)q.n);
+                        if (!nc2) { st = OR_ERR_MEM; break; }
+                        col = nc2; ccap = q.n;
+                    }
+                    int64_t m = kheap_drain(&q, col);
+                    memcpy(q.h, col, sizeof(fkey_t) * (size_t)m);
+                    q.n = m;
+                    live = m;
+                }
             }
-            if (st || cn == 0) continue;
-            int64_t low = id_of_key(c, dim - 1, col[cn - 1]);
+            if (has < 0) st = OR_ERR_MEM;
+            if (st || has == 0) continue;                   /* a zero column */
+            int64_t low = id_of_key(c, dim - 1, top);
             owner[low] = (int32_t)tau;
             zero[tau] = 0;
             if (added) {
+                /* the reduced column, stored increasingly */
+                if (q.n > ccap) {
+                    fkey_t *nc2 = realloc(col, sizeof(fkey_t) * (size_t)q.n);
+                    if (!nc2) { st = OR_ERR_MEM; break; }
+                    col = nc2; ccap = q.n;
+                }
+                int64_t cn = kheap_drain(&q, col);
+                for (int64_t i = 0, j = cn - 1; i < j; i++, j--) {
+                    fkey_t t = col[i]; col[i] = col[j]; col[j] = t;
+                }
                 if (ncols == capcols) {
                     int64_t nc = capcols ? 2 * capcols : 1 << 16;
                     int64_t *ns = realloc(cstart, sizeof(int64_t) * (size_t)nc);
@@ -296,7 +366,8 @@ static int reduce_dim(const fctx_t *c, int dim, const int32_t *cleared, int32_t 
             }
         }
     }
-    free(col); free(tmp); arena_free(&arena); free(cstart); free(clen); free(colidx);
+    free(q.h);
+    free(col); arena_free(&arena); free(cstart); free(clen); free(colidx);
     return st;
 }
 
