@@ -123,9 +123,12 @@ def test_noise256_f32_against_the_standard_reduction(gpu):
     _digest_check("noise256_f32")
 
 
-def test_bench_field_is_the_512_recipe(gpu):
-    """bench.py generates the 512^3 uint16 recipe with torch on the GPU: it
-    is the field the CPU recipe gives, byte for byte."""
+def test_mixture512_u16_against_the_standard_reduction(gpu):
+    """The 512^3 uint16 recipe (64 Gaussians + 5 % noise, quantised: heavy
+    ties), seed 3, at full size, in the configuration bench.py times: every
+    pair equals the oracle's.  bench.py generates the field with torch on the
+    GPU: it must be the same field, byte for byte."""
+    _digest_check("mixture512_u16")
     import bench
     assert sf.sha256(bench.workload_field()) == sf.sha256(sf.config_field("mixture512_u16"))
 
